@@ -1,0 +1,374 @@
+"""Benchmark: FE action DoFs/s and roofline fraction on one GB300 (or N replicas).
+
+Workload (one step = one full matrix-free action, every hot-path step):
+linear elasticity, vector P2 Lagrange on tetrahedra, unit cube cut into 32^3
+cubes x 6 Kuhn tets (196,608 cells, 3 x 274,625 DoFs), interior vertices
+jittered by U[-0.15h, 0.15h], lambda = 1.25, mu = 1, quadrature exact to degree
+2 (8-point conical-product rule), u ~ U[-1, 1], FP64 throughout.
+
+Timing: W untimed warm-up steps, then K steps; each step's kernels are bracketed
+by CUDA events on the launch stream and a 256 MB buffer is written between steps
+to flush the 129 MB L2 (outside the events).  The K steps are bracketed by a
+barrier and a device synchronise; the max over ranks is reported.
+
+``--impl reference`` times the CPU oracle (the FP64 reference implementation of
+the method) on the host cores instead, on a bounded sample of the same
+workload.  With ``--gpus N > 1`` (under torchrun) every rank runs an
+independent replica of the workload (the action shards by problem with no data
+exchange); ``value`` sums all ranks' DoFs.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "FE action DoFs/s & % roofline, FP64 vs mixed precision, fwd + adjoint"
+UNIT = "DoFs/s"
+N_CELLS_PER_DIR = 32
+SEED = 20250618
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP64 FMA peak from the part's unit counts and clocks: 1.25 TFLOP/s nominal for a
+# GB300 (152 SMs at up to 2070 MHz, about 4 FP64 flops per SM per clock).
+FP64_NOMINAL_GFLOPS = 1250.0
+WORKLOAD = ("linear elasticity, vector P2 tets, unit cube 32^3 x 6 Kuhn tets (196,608 cells, "
+            "823,875 DoFs), jitter 0.15h, lambda=1.25 mu=1, quadrature degree 2 (8-point "
+            "conical-product rule), FP64")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-extra", action="store_true", help="skip the secondary workloads")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_inputs():
+    from feinputs import structured_mesh, uniform_field
+    m = structured_mesh(3, N_CELLS_PER_DIR, 2, jitter=0.15, seed=SEED)
+    u = uniform_field(m.n_nodes * 3, SEED + 1)
+    return m, u
+
+
+# ---------------------------------------------------------------- CPU oracle
+def cpu_oracle_rate(m, u, budget_cpu_s=12.0, threads=None):
+    """Oracle DoFs/s on the host cores: repeat the full-mesh oracle action until
+    about ``budget_cpu_s`` CPU-seconds were spent (bounded sample)."""
+    import oracle
+    threads = threads or os.cpu_count() or 1
+    o = oracle.Oracle.from_mesh(m, 2)
+    o.elasticity(u, 1.25, 1.0, threads=threads, cells=(0, min(m.n_cells, 2048)))  # warm
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        o.elasticity(u, 1.25, 1.0, threads=threads)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el * threads >= budget_cpu_s or el > budget_cpu_s:
+            break
+    dofs = m.n_nodes * 3
+    return {"value": dofs * reps / el, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{reps} full-mesh oracle actions ({m.n_cells} cells) in {el:.2f} s wall "
+                      f"on {threads} threads"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    m, u = make_inputs()
+    threads = os.cpu_count() or 1
+    import oracle
+    o = oracle.Oracle.from_mesh(m, 2)
+    # each step: the oracle action on a fixed sample of 1/4 of the cells
+    c1 = m.n_cells // 4
+    for _ in range(args.warmup):
+        o.elasticity(u, 1.25, 1.0, threads=threads, cells=(0, c1))
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        o.elasticity(u, 1.25, 1.0, threads=threads, cells=(0, c1))
+        times.append(time.perf_counter() - t0)
+    t = statistics.mean(times) * (m.n_cells / c1)   # full-mesh time equivalent
+    value = m.n_nodes * 3 / t
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "parallelism": "host threads"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"each step: oracle action over cells [0, {c1}) of "
+                                       f"{m.n_cells}, scaled to the full mesh"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- GPU arm
+def time_secondary(fe, torch, flush):
+    """Mass P2 2D (N=64) and Neo-Hookean P4 2D (N=256) forward + adjoint, FP64."""
+    from feinputs import lame_fields, structured_mesh, uniform_field
+    from feinputs.fields import sinusoid_displacement
+    out = {}
+
+    def timed(fn, reps=10):
+        s = torch.cuda.current_stream()
+        for _ in range(3):
+            fn()
+        ts = []
+        for _ in range(reps):
+            flush()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            fn()
+            e1.record(s)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.mean(ts) * 1e-3
+
+    m = structured_mesh(2, 64, 2, jitter=0.2, seed=20250617)
+    M = fe.Mesh(2, 2, m.coords, m.cell2vertex, m.cell2node, m.n_nodes)
+    plan = fe.Plan(M, fe.MASS, 4)
+    u = torch.from_numpy(uniform_field(m.n_nodes, 1)).cuda()
+    y = torch.empty_like(u)
+    t = timed(lambda: plan.apply(u, y))
+    out["mass_p2_2d_n64"] = {"dofs": m.n_nodes, "ms": t * 1e3, "dofs_per_s": m.n_nodes / t,
+                             "gflops": plan.flops() / t / 1e9, "nq": plan.info.nq}
+
+    m = structured_mesh(2, 256, 4, jitter=0.2, seed=20250619)
+    M = fe.Mesh(2, 4, m.coords, m.cell2vertex, m.cell2node, m.n_nodes)
+    mu, lam = lame_fields(m.n_cells, 3)
+    plan = fe.Plan(M, fe.NH_RESIDUAL, 8, mu_cell=mu, lam_cell=lam)
+    u = torch.from_numpy(sinusoid_displacement(m, 4)).cuda()
+    w = torch.from_numpy(uniform_field(m.n_nodes * 2, 5)).cuda()
+    y = torch.empty_like(u)
+    tf = timed(lambda: plan.apply(u, y))
+    ta = timed(lambda: plan.adjoint(u, w))
+    n = m.n_nodes * 2
+    out["nh_p4_2d_n256"] = {"dofs": n, "fwd_ms": tf * 1e3, "adj_ms": ta * 1e3,
+                            "fwd_dofs_per_s": n / tf, "adj_dofs_per_s": n / ta,
+                            "adj_over_fwd": ta / tf, "fwd_gflops": plan.flops() / tf / 1e9,
+                            "nq": plan.info.nq}
+    return out
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build_library()
+    if world > 1:
+        dist.barrier()
+    import paper_2506_17471_gb300 as fe
+
+    m, u_np = make_inputs()
+    M = fe.Mesh(3, 2, m.coords, m.cell2vertex, m.cell2node, m.n_nodes, device=dev)
+    plan = fe.Plan(M, fe.ELASTICITY, 2, lam=1.25, mu=1.0)
+    n_dofs = plan.n_dofs
+    u = torch.from_numpy(u_np).to(dev)
+    y = torch.empty_like(u)
+    flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def flush():
+        flush_buf.fill_(1.0)
+
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 3)):
+        plan.apply(u, y)
+    torch.cuda.synchronize()
+    if plan.status() != 0:
+        raise RuntimeError("device status after warm-up")
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush()
+        ev[i][0].record(stream)
+        plan.apply(u, y)          # zero kernel + action kernel
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    wall = time.perf_counter() - wall0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+
+    # the action kernel alone (accumulate plan: no zero kernel) for the roofline
+    plan_acc = fe.Plan(M, fe.ELASTICITY, 2, lam=1.25, mu=1.0, accumulate=True)
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush()
+        kev[i][0].record(stream)
+        plan_acc.apply(u, y)
+        kev[i][1].record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    kern_ms = [a.elapsed_time(b) for a, b in kev]
+
+    # end to end through the C-ABI with host buffers (pinned)
+    u_host = torch.from_numpy(u_np).pin_memory()
+    y_host = torch.empty_like(u_host).pin_memory()
+    u_dev, y_dev = torch.empty_like(u), torch.empty_like(u)
+    for _ in range(2):
+        plan.apply_host(u_host, y_host, u_dev, y_dev)
+    e2e_t = []
+    for _ in range(args.steps):
+        flush()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan.apply_host(u_host, y_host, u_dev, y_dev)   # H2D + action + D2H + sync
+        e2e_t.append(time.perf_counter() - t0)
+
+    t_step = statistics.mean(step_ms) * 1e-3
+    t_kern = statistics.mean(kern_ms) * 1e-3
+    t_e2e = statistics.mean(e2e_t)
+    if world > 1:
+        tt = torch.tensor([t_step, t_kern, t_e2e], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step, t_kern, t_e2e = [float(x) for x in tt.cpu()]
+
+    flops = plan.flops()
+    peaks = {}
+    if os.path.exists(PEAKS_FILE):
+        with open(PEAKS_FILE) as f:
+            peaks = json.load(f)
+    extra = {}
+    if rank == 0:
+        dfma = fe.measure_fp64_peak()
+        extra["fp64_dfma_measured_gflops"] = dfma
+        if not args.no_extra:
+            extra.update(time_secondary(fe, torch, flush))
+        hbm_bound = flops / plan.info.bytes_min * peaks.get("hbm_gbs", 6800.0)
+        extra["roofline_min_gflops"] = min(FP64_NOMINAL_GFLOPS, hbm_bound)
+        extra["arithmetic_intensity_flop_per_byte"] = flops / plan.info.bytes_min
+        extra["wall_ms_k_steps_incl_flush"] = wall * 1e3
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    achieved = flops / t_kern / 1e9
+    line = {
+        "metric": METRIC, "value": world * n_dofs / t_step, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_cells": m.n_cells, "n_dofs": n_dofs,
+                   "quad_points": plan.info.nq, "parallelism": f"replicas{world}",
+                   "l2": "flushed between steps (256 MB write, outside the timed events)"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_GFLOPS,
+                     "unit": "GFLOP/s", "frac": achieved / FP64_NOMINAL_GFLOPS,
+                     "traffic": None, "kernel": "k_action_tpc<ELASTICITY,3,2>",
+                     "flops_per_launch": flops,
+                     "peak_note": "FP64 FMA peak from unit counts and clocks (1.25 TFLOP/s "
+                                  "nominal); measured DFMA loop in extra"},
+        "e2e": {"value": world * n_dofs / t_e2e, "unit": UNIT, "h2d_bytes_per_step": n_dofs * 8,
+                "d2h_bytes_per_step": n_dofs * 8},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clocks,
+        "extra": extra,
+    }
+    if not args.no_cpu and world == 1:
+        line["cpu_baseline"] = cpu_oracle_rate(m, u_np)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,199 @@
+/*
+ * feaction.h: C-ABI of the GB300 matrix-free finite element action library.
+ *
+ * The library computes the action y = A(u) of a variational form on an affine
+ * simplex mesh without assembling A: per cell it gathers vertex coordinates and
+ * DoFs through the local-to-global maps, contracts the DoFs with the tabulated
+ * reference basis (values or derivatives) at the quadrature points, applies the
+ * affine geometry (Jacobian, determinant, inverse) and the pointwise form,
+ * contracts with the test-function tabulation and scatter-adds into y.  This is
+ * the paper's Algorithm 2 (the action of the bilinear form of Eq.
+ * "generalized_bilinear_form", with the quadrature sum of Eq.
+ * "poisson_action_w_quadrature" and the tabulations of Eq.
+ * "poisson_tabulated_values"); the forms are those of Appendix A (Mass,
+ * Elasticity) plus a compressible Neo-Hookean law (residual and its Jacobian
+ * action) in place of the appendix's St. Venant-Kirchhoff hyperelasticity.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Reference simplex: vertices 0, e_1, ..., e_d (d = 2 or 3).  A cell with
+ *   vertices (v_0..v_d) maps xhat -> x_{v_0} + sum_k xhat_k (x_{v_k} - x_{v_0});
+ *   the Jacobian J[i][k] = x_{v_k}[i] - x_{v_0}[i]; integrals use |det J|.
+ * - Local P_p nodes are multi-indices alpha (alpha_k >= 0, sum <= p) at the
+ *   reference points alpha/p, enumerated by nested ascending loops with alpha_1
+ *   outermost and alpha_d innermost.  cell2node must list a cell's nodes in that
+ *   order.
+ * - Vector-valued fields (elasticity, Neo-Hookean) interleave components:
+ *   DoF index = node * d + component.  Scalar fields: DoF index = node.
+ * - All index arrays are int32, row-major; all real arrays are IEEE double.
+ * - Device pointers are CUDA device (or managed) memory on the current device.
+ *   The caller owns every array; a plan owns only its device tabulation and its
+ *   device status word.  No entry point allocates on the action path.
+ * - Calls that take a stream enqueue work on that stream (a cudaStream_t passed
+ *   as void*; NULL means the legacy default stream) and return without
+ *   synchronising.  Host-detectable errors are returned immediately and nothing
+ *   is enqueued; errors found by the kernels (degenerate cell, index out of
+ *   range, det F <= 0) are recorded in the plan's device status word and read
+ *   with fe_plan_status().  No kernel traps or asserts.
+ */
+#ifndef FEACTION_H
+#define FEACTION_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+enum fe_status {
+    FE_OK = 0,
+    FE_ERR_INVALID_ARG = 1,  /* null pointer, bad size, bad enum value            */
+    FE_ERR_UNSUPPORTED = 2,  /* (form, dim, degree, precision) not compiled in    */
+    FE_ERR_CUDA = 3,         /* a CUDA runtime call failed                        */
+    FE_ERR_BAD_MESH = 4,     /* device: det J == 0 or non-finite in some cell     */
+    FE_ERR_INDEX = 5,        /* device: a cell2node / cell2vertex entry out of range */
+    FE_ERR_TIMEOUT = 6,      /* device: a bounded wait gave up                    */
+    FE_ERR_NO_MEMORY = 7,    /* plan creation could not allocate its tables       */
+    FE_ERR_NONFINITE = 8     /* device: det F <= 0 or non-finite (Neo-Hookean)    */
+};
+
+/* Human-readable name of a status code (static storage; never NULL). */
+const char *fe_status_string(int status);
+
+/* ------------------------------------------------------------------ forms */
+enum fe_form_kind {
+    FE_FORM_MASS = 0,        /* a(u,v) = int u v                       (App. A, Mass)       */
+    FE_FORM_ELASTICITY = 1,  /* a(u,v) = int sigma(u):eps(v), sigma = lambda tr(eps) I + 2 mu eps
+                                                                         (App. A, Elasticity) */
+    FE_FORM_NH_RESIDUAL = 2, /* r(u;v) = int P(F):grad v, F = I + grad u,
+                                P = mu (F - F^{-T}) + lambda ln(det F) F^{-T}; nonlinear in u */
+    FE_FORM_NH_JACOBIAN = 3  /* a(du,v) = d/de r(u_lin + e du; v) at e = 0: the linearisation
+                                of the residual (App. A, Hyperelasticity's bilinear form)    */
+};
+
+enum fe_precision {
+    FE_PREC_FP64 = 0         /* every operation in IEEE double */
+};
+
+/* Flags for fe_form.flags */
+#define FE_FLAG_ACCUMULATE 1u  /* y += A(u) instead of y = A(u) */
+
+/* Mesh: affine simplices with P_degree Lagrange DoFs (Sec. "Background",
+ * Ciarlet triple and local-to-global maps iota_T).  All pointers are device
+ * pointers and must stay valid for the lifetime of every plan built on it. */
+typedef struct fe_mesh {
+    int32_t dim;                 /* 2 or 3                                         */
+    int32_t degree;              /* Lagrange degree p >= 1                         */
+    int32_t n_vertices;          /* rows of coords                                 */
+    int32_t n_cells;             /* rows of cell2vertex / cell2node (may be 0)     */
+    int32_t n_nodes;             /* global P_p node count (DoFs per component)     */
+    const double *coords;        /* [n_vertices][dim]                              */
+    const int32_t *cell2vertex;  /* [n_cells][dim+1]                               */
+    const int32_t *cell2node;    /* [n_cells][C(degree+dim, dim)]                  */
+} fe_mesh;
+
+/* Form descriptor.  Coefficients: ELASTICITY uses the constants (lambda, mu);
+ * the Neo-Hookean kinds use per-cell P0 arrays mu_cell / lambda_cell (device,
+ * [n_cells]) when non-NULL, else the constants.  NH_JACOBIAN linearises at
+ * u_lin (device, [n_nodes*dim]); the plan keeps the pointer, so the caller may
+ * update its contents between calls. */
+typedef struct fe_form {
+    int32_t kind;                /* enum fe_form_kind                              */
+    int32_t quad_degree;         /* quadrature exactness degree q >= 0             */
+    int32_t precision;           /* enum fe_precision                              */
+    uint32_t flags;              /* FE_FLAG_*                                      */
+    double lambda, mu;           /* constant Lame parameters                       */
+    const double *lambda_cell;   /* [n_cells] or NULL                              */
+    const double *mu_cell;       /* [n_cells] or NULL                              */
+    const double *u_lin;         /* [n_nodes*dim] for NH_JACOBIAN, else NULL       */
+} fe_form;
+
+/* ------------------------------------------------------------------ tabulation */
+/* Host function.  Quadrature rule and reference tabulation (Eq.
+ * "poisson_tabulated_values"): the collapsed conical-product Gauss-Jacobi rule
+ * exact to degree quad_degree with n = ceil((quad_degree+1)/2) points per
+ * direction (nq = n^dim; collapsed coordinates xhat_1 = t_1,
+ * xhat_2 = t_2 (1 - t_1), xhat_3 = t_3 (1 - t_1)(1 - t_2); t_1 outermost, each
+ * direction ascending), and the P_degree Lagrange basis values and reference
+ * derivatives at the points.
+ * Outputs (host memory, caller-owned): *nq; pts [nq][dim]; wts [nq];
+ * tab [(1+dim)][nq][n_loc] with row 0 the values and row k the derivative
+ * d/dxhat_k.  cap is the number of doubles available in tab; pts and wts must
+ * hold nq*dim and nq doubles (query with tab == NULL to get *nq only).
+ * Errors: FE_ERR_INVALID_ARG (dim not 1..3, degree < 1 or > 10, quad_degree < 0
+ * or > 40, cap too small). */
+int fe_tabulate(int dim, int degree, int quad_degree, int *nq, double *pts, double *wts,
+                double *tab, size_t cap);
+
+/* ------------------------------------------------------------------ plans */
+typedef struct fe_plan fe_plan;
+
+/* Validates the form/mesh pair, tabulates on the host, uploads the tables to
+ * the current device and selects the kernel.  Synchronous.  The plan stores
+ * copies of *form and *mesh (pointers inside them are borrowed).
+ * Errors: FE_ERR_INVALID_ARG, FE_ERR_UNSUPPORTED, FE_ERR_NO_MEMORY, FE_ERR_CUDA. */
+int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan **out);
+
+/* Frees the plan's device tables and status word.  Synchronises the device.
+ * NULL is accepted. */
+int fe_plan_destroy(fe_plan *plan);
+
+/* y = A(u) (or y += A(u) with FE_FLAG_ACCUMULATE), enqueued on stream.
+ * u, y: device arrays of n_nodes * ncomp doubles (ncomp = 1 for MASS, dim
+ * otherwise); u and y must not alias.  For NH_JACOBIAN u is the direction du.
+ * Errors: FE_ERR_INVALID_ARG before launch, FE_ERR_CUDA on a failed launch. */
+int fe_action(fe_plan *plan, const double *u, double *y, void *stream);
+
+/* Adjoint of the Neo-Hookean residual r(u; mu, lambda) (plan built with
+ * kind = FE_FORM_NH_RESIDUAL and per-cell or constant Lame parameters):
+ *   jtw      = J(u)^T w          (device, n_nodes*dim; overwritten unless
+ *                                 FE_FLAG_ACCUMULATE)
+ *   dmu[c]     = w . dr/dmu_c     = int_c (F - F^{-T}) : grad w      (device, n_cells)
+ *   dlambda[c] = w . dr/dlambda_c = int_c ln(det F) F^{-T} : grad w  (device, n_cells)
+ * The deformation gradient is recomputed at every quadrature point, nothing is
+ * stored between the forward and the adjoint call.  J^T w is formed with the
+ * fourth-order tangent dP/dF, which for a hyperelastic law has major symmetry,
+ * applied to grad w.  dmu and dlambda are overwritten (one value per cell).
+ * Errors: FE_ERR_UNSUPPORTED for other forms, FE_ERR_INVALID_ARG, FE_ERR_CUDA. */
+int fe_action_adjoint(fe_plan *plan, const double *u, const double *w, double *jtw, double *dmu,
+                      double *dlambda, void *stream);
+
+/* End-to-end convenience: copies u_host (n_dofs doubles, ideally pinned) to the
+ * caller's device buffer u_dev, runs fe_action into y_dev, copies y_dev back to
+ * y_host and synchronises the stream.  Allocates nothing. */
+int fe_action_host(fe_plan *plan, const double *u_host, double *y_host, double *u_dev,
+                   double *y_dev, void *stream);
+
+/* Reads and clears the plan's device status word (synchronises the device).
+ * *device_status receives FE_OK or the first device-detected error. */
+int fe_plan_status(fe_plan *plan, int *device_status);
+
+/* Plan facts for callers and benchmarks. */
+typedef struct fe_plan_info {
+    int32_t nq;               /* quadrature points per cell                        */
+    int32_t n_loc;            /* local nodes per cell                              */
+    int32_t ncomp;            /* components per node                               */
+    int32_t kernel;           /* variant id: 0 thread-per-cell                     */
+    int32_t threads_per_block;
+    int32_t grid_blocks;      /* blocks launched per action                        */
+    int64_t n_dofs;           /* n_nodes * ncomp                                   */
+    double flops_per_cell;    /* algorithmic FP64 flops of Algorithm 2 per cell     */
+    double bytes_min;         /* roofline footprint: each DoF, coordinate and map
+                                 entry counted once (Sec. "Roofline Model")         */
+} fe_plan_info;
+
+int fe_plan_get_info(const fe_plan *plan, fe_plan_info *info);
+
+/* ------------------------------------------------------------------ diagnostics */
+/* Measures the device's FP64 FMA throughput with an unrolled independent-chain
+ * kernel: writes the achieved FP64 GFLOP/s (an FMA counts 2) to *gflops.
+ * scratch: device buffer of at least 152*8*256 doubles (results are written
+ * there so the work cannot be elided).  Synchronous. */
+int fe_measure_fp64_peak(double *scratch, size_t scratch_doubles, double *gflops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FEACTION_H */

@@ -1,0 +1,91 @@
+"""ctypes declarations of the C-ABI in include/feaction.h (argument marshalling only).
+
+The shared library is built in-tree by ``paper_2506_17471_gb300.build`` into
+``_build/libfeaction.so``.  Importing this module without that file raises
+ImportError: there is no fallback implementation.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libfeaction.so")
+
+FE_OK = 0
+STATUS_NAMES = {0: "FE_OK", 1: "FE_ERR_INVALID_ARG", 2: "FE_ERR_UNSUPPORTED", 3: "FE_ERR_CUDA",
+                4: "FE_ERR_BAD_MESH", 5: "FE_ERR_INDEX", 6: "FE_ERR_TIMEOUT", 7: "FE_ERR_NO_MEMORY",
+                8: "FE_ERR_NONFINITE"}
+
+FE_FORM_MASS = 0
+FE_FORM_ELASTICITY = 1
+FE_FORM_NH_RESIDUAL = 2
+FE_FORM_NH_JACOBIAN = 3
+FE_PREC_FP64 = 0
+FE_FLAG_ACCUMULATE = 1
+
+# every symbol declared in include/feaction.h
+EXPORTS = ("fe_status_string", "fe_tabulate", "fe_plan_create", "fe_plan_destroy", "fe_action",
+           "fe_action_adjoint", "fe_action_host", "fe_plan_status", "fe_plan_get_info",
+           "fe_measure_fp64_peak")
+
+
+class FeMesh(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("degree", ctypes.c_int32), ("n_vertices", ctypes.c_int32),
+                ("n_cells", ctypes.c_int32), ("n_nodes", ctypes.c_int32),
+                ("coords", ctypes.c_void_p), ("cell2vertex", ctypes.c_void_p),
+                ("cell2node", ctypes.c_void_p)]
+
+
+class FeForm(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("quad_degree", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("flags", ctypes.c_uint32),
+                ("lambda_", ctypes.c_double), ("mu", ctypes.c_double),
+                ("lambda_cell", ctypes.c_void_p), ("mu_cell", ctypes.c_void_p),
+                ("u_lin", ctypes.c_void_p)]
+
+
+class FePlanInfo(ctypes.Structure):
+    _fields_ = [("nq", ctypes.c_int32), ("n_loc", ctypes.c_int32), ("ncomp", ctypes.c_int32),
+                ("kernel", ctypes.c_int32), ("threads_per_block", ctypes.c_int32),
+                ("grid_blocks", ctypes.c_int32), ("n_dofs", ctypes.c_int64),
+                ("flops_per_cell", ctypes.c_double), ("bytes_min", ctypes.c_double)]
+
+
+class FeError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = int(code)
+        super().__init__(f"{STATUS_NAMES.get(self.code, self.code)}{': ' + what if what else ''}")
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"{LIB_PATH} is missing: build the CUDA library first "
+            "(python -c 'import __graft_entry__ as g; g.build()'); there is no CPU fallback")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, Z, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t, ctypes.c_double
+    lib.fe_status_string.argtypes = [I]
+    lib.fe_status_string.restype = ctypes.c_char_p
+    lib.fe_tabulate.argtypes = [I, I, I, ctypes.POINTER(I), P, P, P, Z]
+    lib.fe_plan_create.argtypes = [ctypes.POINTER(FeForm), ctypes.POINTER(FeMesh), ctypes.POINTER(P)]
+    lib.fe_plan_destroy.argtypes = [P]
+    lib.fe_action.argtypes = [P, P, P, P]
+    lib.fe_action_adjoint.argtypes = [P, P, P, P, P, P, P]
+    lib.fe_action_host.argtypes = [P, P, P, P, P, P]
+    lib.fe_plan_status.argtypes = [P, ctypes.POINTER(I)]
+    lib.fe_plan_get_info.argtypes = [P, ctypes.POINTER(FePlanInfo)]
+    lib.fe_measure_fp64_peak.argtypes = [P, Z, ctypes.POINTER(D)]
+    for name in EXPORTS:
+        if name != "fe_status_string":
+            getattr(lib, name).restype = I
+    return lib
+
+
+lib = _load()
+
+
+def check(code: int, what: str = "") -> None:
+    if code != FE_OK:
+        raise FeError(code, what)

@@ -1,0 +1,387 @@
+// C-ABI of the action library: plans, launches, status, diagnostics.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "fe_internal.h"
+
+namespace fe {
+namespace {
+
+constexpr int kMaxVariants = 128;
+Variant g_variants[kMaxVariants];
+int g_nvariants = 0;
+std::once_flag g_once;
+
+void init_registry()
+{
+    int n = 0;
+    n += register_variants_2d_linear(g_variants + n, kMaxVariants - n);
+    n += register_variants_2d_nh(g_variants + n, kMaxVariants - n);
+    n += register_variants_3d(g_variants + n, kMaxVariants - n);
+    g_nvariants = n;
+}
+
+const Variant *find_variant(int form, int dim, int degree, int op)
+{
+    std::call_once(g_once, init_registry);
+    for (int i = 0; i < g_nvariants; ++i) {
+        const Variant &v = g_variants[i];
+        if (v.form == form && v.dim == dim && v.degree == degree && v.op == op) return &v;
+    }
+    return nullptr;
+}
+
+// Algorithmic FP64 flops of Algorithm 2 for one cell (multiply and add count 1
+// each, an FMA 2; a division or a logarithm 1).  Geometry is counted once per
+// cell as in the untransformed kernel.  Eval/quad terms follow the paper's
+// Ops_usable (Eq. "ops_usable"): 2 N_deriv Q n + 2 N_eval Q n.
+double algorithmic_flops(int op, int d, int n, int nq)
+{
+    const double geo = d == 2 ? 11.0 : 50.0;
+    const double d2 = double(d) * d;
+    double eval = 0, pw = 0, quad = 0;
+    switch (op) {
+    case 0:  // mass
+        eval = 2.0 * n;
+        pw = 2.0;
+        quad = 2.0 * n;
+        break;
+    case 1:  // elasticity
+        eval = 2.0 * d2 * n;
+        pw = d == 2 ? 37.0 : 115.0;
+        quad = 2.0 * d2 * n;
+        break;
+    case 2:  // Neo-Hookean residual
+        eval = 2.0 * d2 * n;
+        pw = d == 2 ? 56.0 : 182.0;
+        quad = 2.0 * d2 * n;
+        break;
+    case 3:  // Neo-Hookean Jacobian action
+        eval = 4.0 * d2 * n;
+        pw = d == 2 ? 105.0 : 345.0;
+        quad = 2.0 * d2 * n;
+        break;
+    case 4:  // Neo-Hookean adjoint (J^T w, dmu, dlambda)
+        eval = 4.0 * d2 * n;
+        pw = d == 2 ? 131.0 : 401.0;
+        quad = 2.0 * d2 * n;
+        break;
+    }
+    return geo + nq * (eval + pw + quad);
+}
+
+__global__ void k_zero(double *__restrict__ y, long long n)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long n2 = n / 2;
+    double2 *y2 = reinterpret_cast<double2 *>(y);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += stride)
+        y2[i] = make_double2(0.0, 0.0);
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) y[n - 1] = 0.0;
+}
+
+int g_num_sms = 0;
+
+int num_sms()
+{
+    if (g_num_sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_num_sms <= 0) g_num_sms = 1;
+    }
+    return g_num_sms;
+}
+
+cudaError_t launch_zero(double *y, long long n, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    const int block = 256;
+    long long want = (n / 2 + block - 1) / block;
+    const long long cap = (long long)num_sms() * 8;
+    const int grid = (int)(want < 1 ? 1 : (want > cap ? cap : want));
+    if (reinterpret_cast<uintptr_t>(y) % 16 != 0) {
+        // unaligned output: plain element-wise zeroing
+        return cudaMemsetAsync(y, 0, (size_t)n * sizeof(double), s);
+    }
+    k_zero<<<grid, block, 0, s>>>(y, n);
+    return cudaGetLastError();
+}
+
+int ncomp_of(int kind, int dim) { return kind == FE_FORM_MASS ? 1 : dim; }
+
+int grid_for(const Variant &v, size_t smem, int n_cells)
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, v.func, v.block, smem) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    const long long full = (long long)per_sm * num_sms();
+    const long long want = ((long long)n_cells + v.block - 1) / v.block;
+    long long g = want < full ? want : full;
+    return (int)(g < 1 ? 1 : g);
+}
+
+__global__ void k_dfma(double *out, int iters, double b, double c)
+{
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    double a0 = 1e-3 * threadIdx.x, a1 = a0 + 1, a2 = a0 + 2, a3 = a0 + 3;
+    double a4 = a0 + 4, a5 = a0 + 5, a6 = a0 + 6, a7 = a0 + 7;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            a0 = fma(a0, b, c); a1 = fma(a1, b, c); a2 = fma(a2, b, c); a3 = fma(a3, b, c);
+            a4 = fma(a4, b, c); a5 = fma(a5, b, c); a6 = fma(a6, b, c); a7 = fma(a7, b, c);
+        }
+    }
+    out[tid] = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
+}
+
+}  // namespace
+}  // namespace fe
+
+using namespace fe;
+
+extern "C" const char *fe_status_string(int status)
+{
+    switch (status) {
+    case FE_OK: return "FE_OK";
+    case FE_ERR_INVALID_ARG: return "FE_ERR_INVALID_ARG";
+    case FE_ERR_UNSUPPORTED: return "FE_ERR_UNSUPPORTED";
+    case FE_ERR_CUDA: return "FE_ERR_CUDA";
+    case FE_ERR_BAD_MESH: return "FE_ERR_BAD_MESH";
+    case FE_ERR_INDEX: return "FE_ERR_INDEX";
+    case FE_ERR_TIMEOUT: return "FE_ERR_TIMEOUT";
+    case FE_ERR_NO_MEMORY: return "FE_ERR_NO_MEMORY";
+    case FE_ERR_NONFINITE: return "FE_ERR_NONFINITE";
+    default: return "FE_ERR_UNKNOWN";
+    }
+}
+
+extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan **out)
+{
+    if (!form || !mesh || !out) return FE_ERR_INVALID_ARG;
+    *out = nullptr;
+    const fe_mesh &m = *mesh;
+    const fe_form &f = *form;
+    if (m.dim < 2 || m.dim > 3 || m.degree < 1 || m.n_cells < 0 || m.n_vertices < 0 || m.n_nodes < 0)
+        return FE_ERR_INVALID_ARG;
+    if (m.n_cells > 0 && (!m.coords || !m.cell2vertex || !m.cell2node)) return FE_ERR_INVALID_ARG;
+    // 2D vertex coordinates are gathered as one 16-byte load per vertex
+    if (m.dim == 2 && reinterpret_cast<uintptr_t>(m.coords) % 16 != 0) return FE_ERR_INVALID_ARG;
+    if (f.kind < FE_FORM_MASS || f.kind > FE_FORM_NH_JACOBIAN) return FE_ERR_INVALID_ARG;
+    if (f.precision != FE_PREC_FP64) return FE_ERR_UNSUPPORTED;
+    if (f.quad_degree < 0 || f.quad_degree > 40) return FE_ERR_INVALID_ARG;
+    if (f.kind == FE_FORM_NH_JACOBIAN && !f.u_lin) return FE_ERR_INVALID_ARG;
+    const int ncomp = ncomp_of(f.kind, m.dim);
+    if ((long long)m.n_nodes * ncomp >= (1ll << 31)) return FE_ERR_INVALID_ARG;
+
+    const Variant *v = find_variant(f.kind, m.dim, m.degree, 0);
+    if (!v) return FE_ERR_UNSUPPORTED;
+    const Variant *adj = (f.kind == FE_FORM_NH_RESIDUAL) ? find_variant(f.kind, m.dim, m.degree, 1) : nullptr;
+
+    // host tabulation -> device table block [nq][1+d][n] + wts[nq], padded to 16 B
+    int nq = 0;
+    if (fe_tabulate(m.dim, m.degree, f.quad_degree, &nq, nullptr, nullptr, nullptr, 0) != FE_OK)
+        return FE_ERR_INVALID_ARG;
+    const int n = nloc(m.dim, m.degree);
+    std::vector<double> pts((size_t)nq * m.dim), wts(nq), tab((size_t)(1 + m.dim) * nq * n);
+    int rc = fe_tabulate(m.dim, m.degree, f.quad_degree, &nq, pts.data(), wts.data(), tab.data(), tab.size());
+    if (rc != FE_OK) return rc;
+    int tab_doubles = nq * (1 + m.dim) * n + nq;
+    tab_doubles = (tab_doubles + 1) & ~1;
+    const size_t smem = (size_t)tab_doubles * sizeof(double);
+    if (smem > 200 * 1024) return FE_ERR_UNSUPPORTED;
+    std::vector<double> block(tab_doubles, 0.0);
+    for (int q = 0; q < nq; ++q)
+        for (int k = 0; k <= m.dim; ++k)
+            for (int j = 0; j < n; ++j)
+                block[((size_t)q * (1 + m.dim) + k) * n + j] = tab[((size_t)k * nq + q) * n + j];
+    for (int q = 0; q < nq; ++q) block[(size_t)nq * (1 + m.dim) * n + q] = wts[q];
+
+    fe_plan *p = new (std::nothrow) fe_plan();
+    if (!p) return FE_ERR_NO_MEMORY;
+    p->form = f;
+    p->mesh = m;
+    p->nq = nq;
+    p->n_loc = n;
+    p->ncomp = ncomp;
+    p->tab_doubles = tab_doubles;
+    p->var = *v;
+    p->adj = adj ? *adj : Variant{};
+    p->smem_bytes = smem;
+    cudaGetDevice(&p->device);
+    if (cudaMalloc(&p->d_tab, smem) != cudaSuccess || cudaMalloc(&p->d_status, sizeof(int32_t)) != cudaSuccess) {
+        cudaFree(p->d_tab);
+        delete p;
+        cudaGetLastError();
+        return FE_ERR_NO_MEMORY;
+    }
+    if (cudaMemcpy(p->d_tab, block.data(), smem, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(p->d_status, 0, sizeof(int32_t)) != cudaSuccess) {
+        fe_plan_destroy(p);
+        return FE_ERR_CUDA;
+    }
+    if (cudaFuncSetAttribute(v->func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        (adj && cudaFuncSetAttribute(adj->func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                    cudaSuccess)) {
+        fe_plan_destroy(p);
+        return FE_ERR_CUDA;
+    }
+    p->grid_blocks = grid_for(*v, smem, m.n_cells);
+    p->adj_grid_blocks = adj ? grid_for(*adj, smem, m.n_cells) : 0;
+    p->flops_per_cell = algorithmic_flops(f.kind, m.dim, n, nq);
+    const double dofs = (double)m.n_nodes * ncomp;
+    double bytes = 2.0 * dofs * 8.0 + (double)m.n_vertices * m.dim * 8.0 +
+                   (double)m.n_cells * (n + m.dim + 1) * 4.0;
+    if (f.kind >= FE_FORM_NH_RESIDUAL)
+        bytes += (f.mu_cell ? 8.0 * m.n_cells : 0.0) + (f.lambda_cell ? 8.0 * m.n_cells : 0.0);
+    if (f.kind == FE_FORM_NH_JACOBIAN) bytes += dofs * 8.0;
+    p->bytes_min = bytes;
+    *out = p;
+    return FE_OK;
+}
+
+extern "C" int fe_plan_destroy(fe_plan *plan)
+{
+    if (!plan) return FE_OK;
+    cudaDeviceSynchronize();
+    cudaFree(plan->d_tab);
+    cudaFree(plan->d_status);
+    delete plan;
+    return FE_OK;
+}
+
+static ActionArgs make_args(const fe_plan *p, const double *u, double *y)
+{
+    ActionArgs a{};
+    a.coords = p->mesh.coords;
+    a.c2v = p->mesh.cell2vertex;
+    a.c2n = p->mesh.cell2node;
+    a.u = u;
+    a.u_lin = p->form.u_lin;
+    a.y = y;
+    a.mu_cell = p->form.mu_cell;
+    a.lam_cell = p->form.lambda_cell;
+    a.mu = p->form.mu;
+    a.lam = p->form.lambda;
+    a.tab = p->d_tab;
+    a.tab_doubles = p->tab_doubles;
+    a.nq = p->nq;
+    a.n_cells = p->mesh.n_cells;
+    a.n_vertices = p->mesh.n_vertices;
+    a.n_nodes = p->mesh.n_nodes;
+    a.status = p->d_status;
+    return a;
+}
+
+extern "C" int fe_action(fe_plan *plan, const double *u, double *y, void *stream)
+{
+    if (!plan || !y) return FE_ERR_INVALID_ARG;
+    const long long n = (long long)plan->mesh.n_nodes * plan->ncomp;
+    if (n > 0 && !u) return FE_ERR_INVALID_ARG;
+    if (u == y && n > 0) return FE_ERR_INVALID_ARG;
+    if (plan->ncomp == 2 && (reinterpret_cast<uintptr_t>(u) % 16 != 0 ||
+                             (plan->form.u_lin && reinterpret_cast<uintptr_t>(plan->form.u_lin) % 16 != 0)))
+        return FE_ERR_INVALID_ARG;  // vector gathers of 2-component nodes load 16 B at once
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (!(plan->form.flags & FE_FLAG_ACCUMULATE)) {
+        if (launch_zero(y, n, s) != cudaSuccess) return FE_ERR_CUDA;
+    }
+    if (plan->mesh.n_cells == 0) return FE_OK;
+    ActionArgs a = make_args(plan, u, y);
+    if (plan->var.launch(a, plan->grid_blocks, plan->var.block, plan->smem_bytes, s) != cudaSuccess)
+        return FE_ERR_CUDA;
+    return FE_OK;
+}
+
+extern "C" int fe_action_adjoint(fe_plan *plan, const double *u, const double *w, double *jtw, double *dmu,
+                                 double *dlambda, void *stream)
+{
+    if (!plan || !plan->adj.launch) return plan ? FE_ERR_UNSUPPORTED : FE_ERR_INVALID_ARG;
+    const long long n = (long long)plan->mesh.n_nodes * plan->ncomp;
+    if (!jtw || !dmu || !dlambda || (n > 0 && (!u || !w))) return FE_ERR_INVALID_ARG;
+    if (u == jtw || w == jtw) return FE_ERR_INVALID_ARG;
+    if (plan->ncomp == 2 && (reinterpret_cast<uintptr_t>(u) % 16 != 0 || reinterpret_cast<uintptr_t>(w) % 16 != 0))
+        return FE_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (!(plan->form.flags & FE_FLAG_ACCUMULATE)) {
+        if (launch_zero(jtw, n, s) != cudaSuccess) return FE_ERR_CUDA;
+    }
+    if (plan->mesh.n_cells == 0) return FE_OK;
+    ActionArgs a = make_args(plan, w, jtw);
+    a.u_lin = u;
+    a.dmu = dmu;
+    a.dlam = dlambda;
+    if (plan->adj.launch(a, plan->adj_grid_blocks, plan->adj.block, plan->smem_bytes, s) != cudaSuccess)
+        return FE_ERR_CUDA;
+    return FE_OK;
+}
+
+extern "C" int fe_action_host(fe_plan *plan, const double *u_host, double *y_host, double *u_dev, double *y_dev,
+                              void *stream)
+{
+    if (!plan || !u_host || !y_host || !u_dev || !y_dev) return FE_ERR_INVALID_ARG;
+    const size_t bytes = (size_t)plan->mesh.n_nodes * plan->ncomp * sizeof(double);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(u_dev, u_host, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return FE_ERR_CUDA;
+    int rc = fe_action(plan, u_dev, y_dev, stream);
+    if (rc != FE_OK) return rc;
+    if (cudaMemcpyAsync(y_host, y_dev, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return FE_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return FE_ERR_CUDA;
+    return FE_OK;
+}
+
+extern "C" int fe_plan_status(fe_plan *plan, int *device_status)
+{
+    if (!plan || !device_status) return FE_ERR_INVALID_ARG;
+    int32_t st = 0;
+    if (cudaDeviceSynchronize() != cudaSuccess) return FE_ERR_CUDA;
+    if (cudaMemcpy(&st, plan->d_status, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess) return FE_ERR_CUDA;
+    if (cudaMemset(plan->d_status, 0, sizeof(int32_t)) != cudaSuccess) return FE_ERR_CUDA;
+    *device_status = st;
+    return FE_OK;
+}
+
+extern "C" int fe_plan_get_info(const fe_plan *plan, fe_plan_info *info)
+{
+    if (!plan || !info) return FE_ERR_INVALID_ARG;
+    info->nq = plan->nq;
+    info->n_loc = plan->n_loc;
+    info->ncomp = plan->ncomp;
+    info->kernel = plan->var.kernel_id;
+    info->threads_per_block = plan->var.block;
+    info->grid_blocks = plan->grid_blocks;
+    info->n_dofs = (int64_t)plan->mesh.n_nodes * plan->ncomp;
+    info->flops_per_cell = plan->flops_per_cell;
+    info->bytes_min = plan->bytes_min;
+    return FE_OK;
+}
+
+extern "C" int fe_measure_fp64_peak(double *scratch, size_t scratch_doubles, double *gflops)
+{
+    if (!scratch || !gflops) return FE_ERR_INVALID_ARG;
+    const int block = 256;
+    const int grid = num_sms() * 8;
+    if (scratch_doubles < (size_t)grid * block) return FE_ERR_INVALID_ARG;
+    const int iters = 2048;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return FE_ERR_CUDA;
+    k_dfma<<<grid, block>>>(scratch, iters / 8, 0.9999999, 1e-7);  // warm-up
+    cudaEventRecord(e0);
+    k_dfma<<<grid, block>>>(scratch, iters, 0.9999999, 1e-7);
+    cudaEventRecord(e1);
+    if (cudaEventSynchronize(e1) != cudaSuccess) return FE_ERR_CUDA;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const double flops = 2.0 * 8.0 * 4.0 * iters * (double)grid * block;
+    *gflops = flops / (ms * 1e-3) / 1e9;
+    return FE_OK;
+}

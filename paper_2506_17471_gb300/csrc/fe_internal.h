@@ -1,0 +1,75 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/feaction.h"
+
+namespace fe {
+
+// Number of P_p Lagrange nodes on a d-simplex: C(p + d, d).
+__host__ __device__ constexpr int nloc(int d, int p)
+{
+    return d == 1 ? p + 1 : (d == 2 ? (p + 1) * (p + 2) / 2 : (p + 1) * (p + 2) * (p + 3) / 6);
+}
+
+// Arguments of every action kernel (passed by value; lives in the kernel's
+// constant parameter bank).
+struct ActionArgs {
+    const double *coords;     // [n_vertices][D]
+    const int32_t *c2v;       // [n_cells][D+1]
+    const int32_t *c2n;       // [n_cells][N]
+    const double *u;          // trial DoFs (du for the Jacobian action, w for the adjoint)
+    const double *u_lin;      // linearisation point (Neo-Hookean Jacobian / adjoint)
+    double *y;                // output DoFs (scatter-add target)
+    const double *mu_cell;    // [n_cells] or nullptr
+    const double *lam_cell;   // [n_cells] or nullptr
+    double *dmu;              // adjoint outputs [n_cells] (nullptr otherwise)
+    double *dlam;
+    double mu, lam;           // constant Lame parameters
+    const double *tab;        // device table block: tab [nq][1+D][N] then wts [nq], padded
+    int32_t tab_doubles;      // doubles in the table block (multiple of 2)
+    int32_t nq;
+    int32_t n_cells, n_vertices, n_nodes;
+    int32_t *status;          // device status word (first error wins)
+};
+
+// Launch function of one compiled kernel variant.
+using LaunchFn = cudaError_t (*)(const ActionArgs &, int grid, int block, size_t smem,
+                                 cudaStream_t stream);
+
+struct Variant {
+    int form, dim, degree;
+    int op;            // 0 = action, 1 = adjoint
+    int kernel_id;     // fe_plan_info.kernel
+    int block;         // threads per block
+    LaunchFn launch;
+    const void *func;  // kernel symbol (for occupancy queries)
+};
+
+// Registry population, one per instantiation translation unit; each appends
+// its variants to out[] and returns how many it wrote (at most cap).
+int register_variants_2d_linear(Variant *out, int cap);
+int register_variants_2d_nh(Variant *out, int cap);
+int register_variants_3d(Variant *out, int cap);
+
+}  // namespace fe
+
+// The plan object behind the opaque C handle.
+struct fe_plan {
+    fe_form form;
+    fe_mesh mesh;
+    int nq, n_loc, ncomp;
+    double *d_tab;        // device table block
+    int tab_doubles;
+    int32_t *d_status;    // device status word
+    fe::Variant var;      // forward action kernel
+    fe::Variant adj;      // adjoint kernel (launch == nullptr if none)
+    int grid_blocks;
+    int adj_grid_blocks;
+    size_t smem_bytes;
+    int device;
+    double flops_per_cell;
+    double bytes_min;
+};

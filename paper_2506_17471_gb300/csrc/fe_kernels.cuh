@@ -1,0 +1,476 @@
+// Thread-per-cell FP64 action kernels for sm_103a.
+//
+// One thread owns one cell and runs the paper's Algorithm 2 for it: gather the
+// cell's vertex coordinates and DoFs, compute the affine Jacobian, its
+// determinant and inverse once (affine geometry, Sec. "Towards
+// Discretization"), then for every quadrature point evaluate the trial field's
+// values/reference derivatives against the tabulation, apply the pointwise form
+// and the geometry mapping, and accumulate the test-side contraction; finally
+// scatter-add with FP64 atomics (the scatter's cross-cell dependence, Sec.
+// "Towards Discretization", resolved as in the single-cell-per-work-item
+// scheme, Algorithm 3).
+//
+// GB300 design points:
+//  * The tabulation block (all quadrature points, basis values and reference
+//    derivatives, then the weights) is staged once per CTA into shared memory
+//    with a 1-D bulk async copy (cp.async.bulk + mbarrier, bounded wait); every
+//    read of it inside the hot loops is warp-uniform (a broadcast).
+//  * DoFs, outputs and geometry live in registers; every contraction is an
+//    unrolled chain of DFMA (FP64 throughput, not HBM bandwidth, bounds these
+//    kernels on this part).
+//  * The launch is persistent: one grid-stride pass with a grid sized to the
+//    resident CTAs of all 152 SMs.
+//  * Index maps are range-checked (cheap integer work); a bad index, a
+//    degenerate cell or det F <= 0 set the plan's status word; nothing traps.
+#pragma once
+
+#include <cstdint>
+
+#include "fe_internal.h"
+
+namespace fe {
+
+constexpr int kTpcBlock = 128;
+constexpr int kWaitLimit = 1 << 21;   // bounded mbarrier polls (~0.1-0.3 s with backoff)
+
+__device__ __forceinline__ void set_status(int32_t *status, int32_t code)
+{
+    if (status) atomicCAS(status, 0, code);
+}
+
+// Stage the table block into shared memory with one bulk async copy.  Returns
+// false (and records FE_ERR_TIMEOUT) if the copy did not complete within the
+// bounded wait; the caller must then return.
+__device__ __forceinline__ bool stage_table(double *sm_tab, const double *g_tab, int ndoubles,
+                                            uint64_t *bar, int32_t *status)
+{
+    const uint32_t bytes = (uint32_t)ndoubles * 8u;   // multiple of 16 by construction
+    const uint32_t sbar = (uint32_t)__cvta_generic_to_shared(bar);
+    const uint32_t sdst = (uint32_t)__cvta_generic_to_shared(sm_tab);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sbar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint64_t gsrc = (uint64_t)__cvta_generic_to_global(g_tab);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sbar), "r"(bytes)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                sdst),
+            "l"(gsrc), "r"(bytes), "r"(sbar)
+            : "memory");
+    }
+    auto poll = [&](int limit) -> int {
+        for (int it = 0; it < limit; ++it) {
+            uint32_t ok;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\t"
+                "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+                "selp.u32 %0, 1, 0, p;\n\t}"
+                : "=r"(ok)
+                : "r"(sbar)
+                : "memory");
+            if (ok) return 1;
+            __nanosleep(64);
+        }
+        return 0;
+    };
+    const int done = poll(kWaitLimit);
+    if (__syncthreads_and(done)) return true;
+    // The copy did not land in time: record it, give the in-flight copy a second
+    // bounded chance to finish before this CTA's shared memory is released.
+    if (threadIdx.x == 0) set_status(status, FE_ERR_TIMEOUT);
+    poll(kWaitLimit);
+    __syncthreads();
+    return false;
+}
+
+// Affine geometry of one cell: J[i][k] = x_k[i] - x_0[i]; returns det J and J^{-1}.
+template <int D>
+__device__ __forceinline__ double cell_geometry(const double (&X)[D + 1][D], double (&Jinv)[D][D])
+{
+    double J[D][D];
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int k = 0; k < D; ++k) J[i][k] = X[k + 1][i] - X[0][i];
+    double det;
+    if constexpr (D == 2) {
+        det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+        const double r = 1.0 / det;
+        Jinv[0][0] = J[1][1] * r;
+        Jinv[0][1] = -J[0][1] * r;
+        Jinv[1][0] = -J[1][0] * r;
+        Jinv[1][1] = J[0][0] * r;
+    } else {
+        const double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+        const double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+        const double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+        det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+        const double r = 1.0 / det;
+        Jinv[0][0] = c00 * r;
+        Jinv[1][0] = c01 * r;
+        Jinv[2][0] = c02 * r;
+        Jinv[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * r;
+        Jinv[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * r;
+        Jinv[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * r;
+        Jinv[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * r;
+        Jinv[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * r;
+        Jinv[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * r;
+    }
+    return det;
+}
+
+// det and cofactor matrix (cof = det * A^{-T}) of a small matrix.
+template <int D>
+__device__ __forceinline__ double det_cof(const double (&A)[D][D], double (&C)[D][D])
+{
+    if constexpr (D == 2) {
+        C[0][0] = A[1][1];
+        C[0][1] = -A[1][0];
+        C[1][0] = -A[0][1];
+        C[1][1] = A[0][0];
+        return A[0][0] * A[1][1] - A[0][1] * A[1][0];
+    } else {
+        C[0][0] = A[1][1] * A[2][2] - A[1][2] * A[2][1];
+        C[0][1] = A[1][2] * A[2][0] - A[1][0] * A[2][2];
+        C[0][2] = A[1][0] * A[2][1] - A[1][1] * A[2][0];
+        C[1][0] = A[0][2] * A[2][1] - A[0][1] * A[2][2];
+        C[1][1] = A[0][0] * A[2][2] - A[0][2] * A[2][0];
+        C[1][2] = A[0][1] * A[2][0] - A[0][0] * A[2][1];
+        C[2][0] = A[0][1] * A[1][2] - A[0][2] * A[1][1];
+        C[2][1] = A[0][2] * A[1][0] - A[0][0] * A[1][2];
+        C[2][2] = A[0][0] * A[1][1] - A[0][1] * A[1][0];
+        return A[0][0] * C[0][0] + A[0][1] * C[0][1] + A[0][2] * C[0][2];
+    }
+}
+
+// Evaluation phase: reference gradient gh[c][k] = sum_j T_{k+1}[j] l[j][c].
+template <int D, int N, int NC>
+__device__ __forceinline__ void eval_grad(const double *__restrict__ T, const double (&l)[N][NC],
+                                          double (&gh)[NC][D])
+{
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int k = 0; k < D; ++k) gh[c][k] = 0.0;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            const double t = T[(k + 1) * N + j];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) gh[c][k] = fma(t, l[j][c], gh[c][k]);
+        }
+    }
+}
+
+// Quadrature phase: out[j][c] += sum_k T_{k+1}[j] e[c][k].
+template <int D, int N, int NC>
+__device__ __forceinline__ void quad_grad(const double *__restrict__ T, const double (&e)[NC][D],
+                                          double (&out)[N][NC])
+{
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            const double t = T[(k + 1) * N + j];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) out[j][c] = fma(t, e[c][k], out[j][c]);
+        }
+    }
+}
+
+// A[c][i] = sum_k B[c][k] Jinv[k][i]  (reference -> physical gradient)
+template <int D>
+__device__ __forceinline__ void map_grad(const double (&B)[D][D], const double (&Jinv)[D][D],
+                                         double (&A)[D][D])
+{
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            double s = B[c][0] * Jinv[0][i];
+#pragma unroll
+            for (int k = 1; k < D; ++k) s = fma(B[c][k], Jinv[k][i], s);
+            A[c][i] = s;
+        }
+}
+
+// e[c][k] = sum_i S[c][i] Jinv[k][i]  (physical stress -> reference test weights)
+template <int D>
+__device__ __forceinline__ void pull_back(const double (&S)[D][D], const double (&Jinv)[D][D],
+                                          double (&e)[D][D])
+{
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            double s = S[c][0] * Jinv[k][0];
+#pragma unroll
+            for (int i = 1; i < D; ++i) s = fma(S[c][i], Jinv[k][i], s);
+            e[c][k] = s;
+        }
+}
+
+// Internal operation ids (forms of the public API plus the Neo-Hookean adjoint).
+enum Op { OP_MASS = 0, OP_ELASTICITY = 1, OP_NH_RESIDUAL = 2, OP_NH_JACOBIAN = 3, OP_NH_ADJOINT = 4 };
+
+template <int OP, int D>
+struct OpTraits {
+    static constexpr int NC = (OP == OP_MASS) ? 1 : D;
+    static constexpr bool kTwoFields = (OP == OP_NH_JACOBIAN || OP == OP_NH_ADJOINT);
+    static constexpr bool kCellCoeff = (OP >= OP_NH_RESIDUAL);
+};
+
+template <int D, int N, int NC>
+__device__ __forceinline__ bool gather_nodes(const int32_t *__restrict__ c2n, int cell, int n_nodes,
+                                             int (&nodes)[N])
+{
+    bool ok = true;
+    const int32_t *row = c2n + (size_t)cell * N;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        const int v = __ldg(row + j);
+        ok &= (unsigned)v < (unsigned)n_nodes;
+        nodes[j] = v;
+    }
+    return ok;
+}
+
+template <int N, int NC>
+__device__ __forceinline__ void gather_dofs(const double *__restrict__ u, const int (&nodes)[N],
+                                            double (&l)[N][NC])
+{
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        const double *p = u + (size_t)nodes[j] * NC;
+        if constexpr (NC == 2) {
+            const double2 v = __ldg(reinterpret_cast<const double2 *>(p));
+            l[j][0] = v.x;
+            l[j][1] = v.y;
+        } else {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) l[j][c] = __ldg(p + c);
+        }
+    }
+}
+
+// One cell of Algorithm 2 for operation OP.  Returns nothing; writes the scatter.
+template <int OP, int D, int P>
+__device__ __forceinline__ void action_cell(const ActionArgs &a, const double *__restrict__ tab,
+                                            const double *__restrict__ wts, int cell)
+{
+    constexpr int N = nloc(D, P);
+    constexpr int NC = OpTraits<OP, D>::NC;
+
+    // gather coordinates (Algorithm 2: gather of coords through iota_P1)
+    int vtx[D + 1];
+    bool ok = true;
+#pragma unroll
+    for (int m = 0; m <= D; ++m) {
+        vtx[m] = __ldg(a.c2v + (size_t)cell * (D + 1) + m);
+        ok &= (unsigned)vtx[m] < (unsigned)a.n_vertices;
+    }
+    int nodes[N];
+    ok &= gather_nodes<D, N, NC>(a.c2n, cell, a.n_nodes, nodes);
+    if (!ok) {
+        set_status(a.status, FE_ERR_INDEX);
+        return;
+    }
+    double X[D + 1][D];
+#pragma unroll
+    for (int m = 0; m <= D; ++m) {
+        if constexpr (D == 2) {
+            const double2 v = __ldg(reinterpret_cast<const double2 *>(a.coords + (size_t)vtx[m] * 2));
+            X[m][0] = v.x;
+            X[m][1] = v.y;
+        } else {
+#pragma unroll
+            for (int i = 0; i < D; ++i) X[m][i] = __ldg(a.coords + (size_t)vtx[m] * D + i);
+        }
+    }
+    // geometry: J, det J, J^{-1}, once per cell (affine)
+    double Jinv[D][D];
+    const double det = cell_geometry<D>(X, Jinv);
+    if (!(det != 0.0) || !isfinite(det)) {
+        set_status(a.status, FE_ERR_BAD_MESH);
+        return;
+    }
+    const double absdet = fabs(det);
+
+    // gather DoFs
+    double l[N][NC];
+    gather_dofs<N, NC>(a.u, nodes, l);
+    [[maybe_unused]] double l0[OpTraits<OP, D>::kTwoFields ? N : 1][NC];
+    if constexpr (OpTraits<OP, D>::kTwoFields) gather_dofs<N, NC>(a.u_lin, nodes, l0);
+    double mu = a.mu, lam = a.lam;
+    if constexpr (OpTraits<OP, D>::kCellCoeff) {
+        if (a.mu_cell) mu = __ldg(a.mu_cell + cell);
+        if (a.lam_cell) lam = __ldg(a.lam_cell + cell);
+    }
+
+    double out[N][NC];
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) out[j][c] = 0.0;
+    [[maybe_unused]] double acc_mu = 0.0, acc_lam = 0.0;
+    bool nh_ok = true;
+
+    for (int q = 0; q < a.nq; ++q) {
+        const double *__restrict__ T = tab + (size_t)q * (D + 1) * N;
+        const double wdet = wts[q] * absdet;
+        if constexpr (OP == OP_MASS) {
+            double uq = 0.0;
+#pragma unroll
+            for (int j = 0; j < N; ++j) uq = fma(T[j], l[j][0], uq);
+            const double e = uq * wdet;
+#pragma unroll
+            for (int j = 0; j < N; ++j) out[j][0] = fma(T[j], e, out[j][0]);
+        } else if constexpr (OP == OP_ELASTICITY) {
+            double gh[D][D], G[D][D], S[D][D], e[D][D];
+            eval_grad<D, N, D>(T, l, gh);
+            map_grad<D>(gh, Jinv, G);
+            double tr = G[0][0];
+#pragma unroll
+            for (int i = 1; i < D; ++i) tr += G[i][i];
+            const double smu = wdet * mu;
+            const double slt = wdet * lam * tr;
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                S[i][i] = fma(2.0 * smu, G[i][i], slt);
+#pragma unroll
+                for (int k = i + 1; k < D; ++k) {
+                    const double s = smu * (G[i][k] + G[k][i]);
+                    S[i][k] = s;
+                    S[k][i] = s;
+                }
+            }
+            pull_back<D>(S, Jinv, e);
+            quad_grad<D, N, D>(T, e, out);
+        } else if constexpr (OP == OP_NH_RESIDUAL) {
+            double gh[D][D], F[D][D], C[D][D], S[D][D], e[D][D];
+            eval_grad<D, N, D>(T, l, gh);
+            map_grad<D>(gh, Jinv, F);
+#pragma unroll
+            for (int i = 0; i < D; ++i) F[i][i] += 1.0;
+            const double Jd = det_cof<D>(F, C);  // F^{-T} = C / Jd
+            nh_ok &= (Jd > 0.0);
+            const double lnJ = log(Jd);
+            // P = mu F + (lam lnJ - mu) F^{-T}, scaled by w_q |det J|
+            const double smu = wdet * mu;
+            const double scf = wdet * fma(lam, lnJ, -mu) / Jd;
+#pragma unroll
+            for (int i = 0; i < D; ++i)
+#pragma unroll
+                for (int k = 0; k < D; ++k) S[i][k] = fma(smu, F[i][k], scf * C[i][k]);
+            pull_back<D>(S, Jinv, e);
+            quad_grad<D, N, D>(T, e, out);
+        } else {  // OP_NH_JACOBIAN / OP_NH_ADJOINT: tangent applied to H = grad(du) (or grad w)
+            double gh[D][D], F[D][D], H[D][D], C[D][D], Fit[D][D], A[D][D], S[D][D], e[D][D];
+            eval_grad<D, N, D>(T, l0, gh);
+            map_grad<D>(gh, Jinv, F);
+#pragma unroll
+            for (int i = 0; i < D; ++i) F[i][i] += 1.0;
+            eval_grad<D, N, D>(T, l, gh);
+            map_grad<D>(gh, Jinv, H);
+            const double Jd = det_cof<D>(F, C);
+            nh_ok &= (Jd > 0.0);
+            const double rJ = 1.0 / Jd;
+            const double lnJ = log(Jd);
+            double tr = 0.0;  // tr(F^{-1} H) = F^{-T} : H
+#pragma unroll
+            for (int i = 0; i < D; ++i)
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    Fit[i][k] = C[i][k] * rJ;
+                    tr = fma(Fit[i][k], H[i][k], tr);
+                }
+            // A = F^{-T} H^T ; M = A F^{-T}
+#pragma unroll
+            for (int i = 0; i < D; ++i)
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    double s = Fit[i][0] * H[k][0];
+#pragma unroll
+                    for (int m = 1; m < D; ++m) s = fma(Fit[i][m], H[k][m], s);
+                    A[i][k] = s;
+                }
+            const double smu = wdet * mu;
+            const double sm2 = wdet * fma(-lam, lnJ, mu);  // (mu - lam lnJ)
+            const double str = wdet * lam * tr;
+#pragma unroll
+            for (int i = 0; i < D; ++i)
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    double m = A[i][0] * Fit[0][k];
+#pragma unroll
+                    for (int mm = 1; mm < D; ++mm) m = fma(A[i][mm], Fit[mm][k], m);
+                    S[i][k] = fma(smu, H[i][k], fma(sm2, m, str * Fit[i][k]));
+                }
+            if constexpr (OP == OP_NH_ADJOINT) {
+                // dr/dmu . w = (F - F^{-T}) : grad w ; dr/dlam . w = lnJ F^{-T} : grad w
+#pragma unroll
+                for (int i = 0; i < D; ++i)
+#pragma unroll
+                    for (int k = 0; k < D; ++k) {
+                        acc_mu = fma(wdet * (F[i][k] - Fit[i][k]), H[i][k], acc_mu);
+                        acc_lam = fma(wdet * lnJ * Fit[i][k], H[i][k], acc_lam);
+                    }
+            }
+            pull_back<D>(S, Jinv, e);
+            quad_grad<D, N, D>(T, e, out);
+        }
+    }
+    if (!nh_ok) set_status(a.status, FE_ERR_NONFINITE);
+
+    // scatter-add (Algorithm 2 scatter; cross-cell races resolved with FP64 atomics)
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) atomicAdd(a.y + (size_t)nodes[j] * NC + c, out[j][c]);
+    if constexpr (OP == OP_NH_ADJOINT) {
+        a.dmu[cell] = acc_mu;   // one thread per cell: plain stores, no reduction
+        a.dlam[cell] = acc_lam;
+    }
+}
+
+template <int OP, int D, int P>
+__global__ void __launch_bounds__(kTpcBlock) k_action_tpc(const ActionArgs a)
+{
+    extern __shared__ __align__(128) double smem[];
+    __shared__ __align__(8) uint64_t bar;
+    if (!stage_table(smem, a.tab, a.tab_doubles, &bar, a.status)) return;
+    const double *tab = smem;
+    const double *wts = smem + (size_t)a.nq * (D + 1) * nloc(D, P);
+    const int stride = gridDim.x * blockDim.x;
+    for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < a.n_cells; cell += stride)
+        action_cell<OP, D, P>(a, tab, wts, cell);
+}
+
+template <int OP, int D, int P>
+cudaError_t launch_tpc(const ActionArgs &a, int grid, int block, size_t smem, cudaStream_t s)
+{
+    k_action_tpc<OP, D, P><<<grid, block, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int OP, int D, int P>
+Variant make_tpc_variant()
+{
+    Variant v;
+    v.form = OP == OP_NH_ADJOINT ? OP_NH_RESIDUAL : OP;
+    v.dim = D;
+    v.degree = P;
+    v.op = OP == OP_NH_ADJOINT ? 1 : 0;
+    v.kernel_id = 0;
+    v.block = kTpcBlock;
+    v.launch = &launch_tpc<OP, D, P>;
+    v.func = reinterpret_cast<const void *>(&k_action_tpc<OP, D, P>);
+    return v;
+}
+
+}  // namespace fe
