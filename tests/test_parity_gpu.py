@@ -16,6 +16,12 @@ from feinputs.fields import sinusoid_displacement
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-12
+# The Neo-Hookean residual at the smooth sum-of-sinusoids displacement on the
+# 256^2 P4 mesh is ill-conditioned in FP64: the displacement gradient is a sum of
+# nodal terms ~1e3 times larger than the result, so a half-ulp change of the
+# tabulation alone moves the oracle's own output by 1.5e-12 relative
+# (tests/test_oracle_conditioning.py pins this).  Parity there is 1e-11.
+TOL_NH_SMOOTH = 1e-11
 
 
 @pytest.fixture(scope="module")
@@ -136,7 +142,7 @@ def test_full_nh_p4_2d_n256(fe):
     w = uniform_field(m.n_nodes * 2, 5)
     plan = fe.Plan(M, fe.NH_RESIDUAL, 8, mu_cell=mu, lam_cell=lam)
     r = plan.apply(cuda(u))
-    assert rel(r, o.nh_residual(u, mu, lam, threads=16)) <= TOL
+    assert rel(r, o.nh_residual(u, mu, lam, threads=16)) <= TOL_NH_SMOOTH
     jtw, dmu, dlam = plan.adjoint(cuda(u), cuda(w))
     # J^T w over the whole mesh against the oracle's Jacobian action (the two are
     # equal by the tangent's symmetry, pinned on the CPU) ...
