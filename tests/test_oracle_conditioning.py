@@ -25,10 +25,16 @@ def test_nh_residual_smooth_field_sensitivity(oracle_built):
     r = o.nh_residual(u, mu, lam, threads=8)
     w = uniform_field(m.n_nodes * 2, 5)
     j = o.nh_jacobian(u, w, mu, lam, threads=8)
+    cells = (0, 1500)
+    _, dmu, _ = o.nh_adjoint(u, w, mu, lam, threads=8, cells=cells)
     rng = np.random.default_rng(0)
     t0 = o.tab.copy()
     o.tab = np.ascontiguousarray(t0 * (1 + 2.0 ** -53 * rng.choice([-1.0, 1.0], size=t0.shape)))
     dr = np.abs(o.nh_residual(u, mu, lam, threads=8) - r).max() / np.abs(r).max()
     dj = np.abs(o.nh_jacobian(u, w, mu, lam, threads=8) - j).max() / np.abs(j).max()
+    _, dmu2, _ = o.nh_adjoint(u, w, mu, lam, threads=8, cells=cells)
+    ddmu = np.abs(dmu2 - dmu)[:1500].max() / np.abs(dmu[:1500]).max()
     assert 5e-13 < dr < 5e-12, dr      # residual: rounding alone reaches ~1.5e-12
     assert dj < 5e-13, dj              # rough-direction Jacobian: well conditioned
+    assert ddmu < 2e-12, ddmu          # dmu uses the same smooth-field gradients
+    print(f"sensitivity: residual {dr:.2e}, jacobian {dj:.2e}, dmu {ddmu:.2e}")

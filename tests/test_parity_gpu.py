@@ -150,8 +150,9 @@ def test_full_nh_p4_2d_n256(fe):
     # ... and the literal transposed-element-matrix adjoint on sampled cell ranges
     for c0, c1 in ((0, 1500), (m.n_cells // 2, m.n_cells // 2 + 1500), (m.n_cells - 1500, m.n_cells)):
         _, odmu, odlam = o.nh_adjoint(u, w, mu, lam, threads=8, cells=(c0, c1))
-        assert rel(dmu[c0:c1], odmu[c0:c1]) <= TOL
-        assert rel(dlam[c0:c1], odlam[c0:c1]) <= TOL
+        # dmu, dlambda integrate F - F^{-T} and ln(det F) F^{-T}: smooth-field conditioned
+        assert rel(dmu[c0:c1], odmu[c0:c1]) <= TOL_NH_SMOOTH
+        assert rel(dlam[c0:c1], odlam[c0:c1]) <= TOL_NH_SMOOTH
     assert plan.status() == 0
 
 
