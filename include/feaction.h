@@ -167,7 +167,13 @@ int fe_action_host(fe_plan *plan, const double *u_host, double *y_host, double *
                    double *y_dev, void *stream);
 
 /* Reads and clears the plan's device status word (synchronises the device).
- * *device_status receives FE_OK or the first device-detected error. */
+ * *device_status receives FE_OK or the first device-detected error; it is
+ * FE_ERR_CUDA if a launch left the plan's work-queue counters inconsistent.
+ *
+ * Concurrency: a plan's kernels pull cells from a plan-owned work queue (two
+ * counters per kernel, reset by the last warp of each launch).  Launches of the
+ * same plan must therefore not overlap in time: issue them on one stream, or
+ * order them with events.  Different plans are independent. */
 int fe_plan_status(fe_plan *plan, int *device_status);
 
 /* Plan facts for callers and benchmarks. */

@@ -216,14 +216,16 @@ extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan 
     p->adj = adj ? *adj : Variant{};
     p->smem_bytes = smem;
     cudaGetDevice(&p->device);
-    if (cudaMalloc(&p->d_tab, smem) != cudaSuccess || cudaMalloc(&p->d_status, sizeof(int32_t)) != cudaSuccess) {
+    if (cudaMalloc(&p->d_tab, smem) != cudaSuccess ||
+        cudaMalloc(&p->d_status, 8 * sizeof(int32_t)) != cudaSuccess) {
         cudaFree(p->d_tab);
         delete p;
         cudaGetLastError();
         return FE_ERR_NO_MEMORY;
     }
+    p->d_sched = p->d_status + 4;  // status word, padding, then the queue counters
     if (cudaMemcpy(p->d_tab, block.data(), smem, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemset(p->d_status, 0, sizeof(int32_t)) != cudaSuccess) {
+        cudaMemset(p->d_status, 0, 8 * sizeof(int32_t)) != cudaSuccess) {
         fe_plan_destroy(p);
         return FE_ERR_CUDA;
     }
@@ -277,6 +279,7 @@ static ActionArgs make_args(const fe_plan *p, const double *u, double *y)
     a.n_vertices = p->mesh.n_vertices;
     a.n_nodes = p->mesh.n_nodes;
     a.status = p->d_status;
+    a.sched = p->d_sched;
     return a;
 }
 
@@ -316,6 +319,7 @@ extern "C" int fe_action_adjoint(fe_plan *plan, const double *u, const double *w
     if (plan->mesh.n_cells == 0) return FE_OK;
     ActionArgs a = make_args(plan, w, jtw);
     a.u_lin = u;
+    a.sched = plan->d_sched + 2;
     a.dmu = dmu;
     a.dlam = dlambda;
     if (plan->adj.launch(a, plan->adj_grid_blocks, plan->adj.block, plan->smem_bytes, s) != cudaSuccess)
@@ -340,10 +344,17 @@ extern "C" int fe_action_host(fe_plan *plan, const double *u_host, double *y_hos
 extern "C" int fe_plan_status(fe_plan *plan, int *device_status)
 {
     if (!plan || !device_status) return FE_ERR_INVALID_ARG;
-    int32_t st = 0;
+    int32_t words[8] = {0};
     if (cudaDeviceSynchronize() != cudaSuccess) return FE_ERR_CUDA;
-    if (cudaMemcpy(&st, plan->d_status, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess) return FE_ERR_CUDA;
-    if (cudaMemset(plan->d_status, 0, sizeof(int32_t)) != cudaSuccess) return FE_ERR_CUDA;
+    if (cudaMemcpy(words, plan->d_status, sizeof(words), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return FE_ERR_CUDA;
+    int32_t st = words[0];
+    // With the device idle, every launch has left the work queue and its last
+    // warp reset the counters; anything else means a launch did not complete.
+    if (words[4] || words[5] || words[6] || words[7]) {
+        if (st == FE_OK) st = FE_ERR_CUDA;
+    }
+    if (cudaMemset(plan->d_status, 0, sizeof(words)) != cudaSuccess) return FE_ERR_CUDA;
     *device_status = st;
     return FE_OK;
 }

@@ -33,6 +33,7 @@ struct ActionArgs {
     int32_t nq;
     int32_t n_cells, n_vertices, n_nodes;
     int32_t *status;          // device status word (first error wins)
+    int32_t *sched;           // [2] work-queue counters: next chunk, warps finished (self-resetting)
 };
 
 // Launch function of one compiled kernel variant.
@@ -64,6 +65,7 @@ struct fe_plan {
     double *d_tab;        // device table block
     int tab_doubles;
     int32_t *d_status;    // device status word
+    int32_t *d_sched;     // [4] work-queue counters: forward kernel [0..1], adjoint kernel [2..3]
     fe::Variant var;      // forward action kernel
     fe::Variant adj;      // adjoint kernel (launch == nullptr if none)
     int grid_blocks;

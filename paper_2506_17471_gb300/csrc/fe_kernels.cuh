@@ -18,8 +18,9 @@
 //  * DoFs, outputs and geometry live in registers; every contraction is an
 //    unrolled chain of DFMA (FP64 throughput, not HBM bandwidth, bounds these
 //    kernels on this part).
-//  * The launch is persistent: one grid-stride pass with a grid sized to the
-//    resident CTAs of all 152 SMs.
+//  * The launch is persistent (grid = resident CTAs of all 152 SMs) and warps
+//    pull 32-cell chunks from a work queue, which keeps the FP64 pipe of every
+//    SM busy until the last chunk.
 //  * Index maps are range-checked (cheap integer work); a bad index, a
 //    degenerate cell or det F <= 0 set the plan's status word; nothing traps.
 #pragma once
@@ -438,17 +439,45 @@ __device__ __forceinline__ void action_cell(const ActionArgs &a, const double *_
     }
 }
 
+// Warp-level work queue: each warp takes chunks of 32 consecutive cells (one per
+// lane) from a global counter until the cells run out, so SMs that finish early
+// take more work and the tail is at most one chunk.  The last warp to leave
+// resets both counters, so every launch starts from zero without a memset.
+__device__ __forceinline__ void leave_queue(int32_t *sched)
+{
+    if ((threadIdx.x & 31) == 0) {
+        const int total_warps = (int)(gridDim.x * (blockDim.x >> 5));
+        __threadfence();
+        if (atomicAdd(sched + 1, 1) == total_warps - 1) {
+            sched[0] = 0;
+            sched[1] = 0;
+            __threadfence();
+        }
+    }
+}
+
 template <int OP, int D, int P>
 __global__ void __launch_bounds__(kTpcBlock) k_action_tpc(const ActionArgs a)
 {
     extern __shared__ __align__(128) double smem[];
     __shared__ __align__(8) uint64_t bar;
-    if (!stage_table(smem, a.tab, a.tab_doubles, &bar, a.status)) return;
+    if (!stage_table(smem, a.tab, a.tab_doubles, &bar, a.status)) {
+        leave_queue(a.sched);
+        return;
+    }
     const double *tab = smem;
     const double *wts = smem + (size_t)a.nq * (D + 1) * nloc(D, P);
-    const int stride = gridDim.x * blockDim.x;
-    for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < a.n_cells; cell += stride)
-        action_cell<OP, D, P>(a, tab, wts, cell);
+    const int lane = threadIdx.x & 31;
+    const int n_chunks = (a.n_cells + 31) >> 5;
+    for (;;) {
+        int chunk = 0;
+        if (lane == 0) chunk = atomicAdd(a.sched, 1);
+        chunk = __shfl_sync(0xffffffffu, chunk, 0);
+        if (chunk >= n_chunks) break;
+        const int cell = (chunk << 5) + lane;
+        if (cell < a.n_cells) action_cell<OP, D, P>(a, tab, wts, cell);
+    }
+    leave_queue(a.sched);
 }
 
 template <int OP, int D, int P>
