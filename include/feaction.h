@@ -27,8 +27,9 @@
  *   DoF index = node * d + component.  Scalar fields: DoF index = node.
  * - All index arrays are int32, row-major; all real arrays are IEEE double.
  * - Device pointers are CUDA device (or managed) memory on the current device.
- *   The caller owns every array; a plan owns only its device tabulation and its
- *   device status word.  No entry point allocates on the action path.
+ *   The caller owns every array; a plan owns only its device tabulation, its
+ *   device status word and its work-queue counters (allocated once, at plan
+ *   creation).  No entry point allocates on the action path.
  * - Calls that take a stream enqueue work on that stream (a cudaStream_t passed
  *   as void*; NULL means the legacy default stream) and return without
  *   synchronising.  Host-detectable errors are returned immediately and nothing
