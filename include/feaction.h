@@ -193,6 +193,41 @@ typedef struct fe_plan_info {
 
 int fe_plan_get_info(const fe_plan *plan, fe_plan_info *info);
 
+/* ------------------------------------------------------------------ no-allocation variant */
+/* fe_action for callers that cannot allocate device memory (the paper has no
+ * counterpart; this is a deployment convenience).  Such callers include
+ * applications whose device memory is owned up front by their own pool
+ * allocator and hosts that forbid device allocations after start-up: they
+ * cannot create a plan, because fe_plan_create calls cudaMalloc for the table
+ * block, the status word and the work-queue counters.
+ *
+ * This entry point runs the same thread-per-cell kernel as fe_action and
+ * allocates nothing: no cudaMalloc, cudaFree or allocating library call.  Its
+ * scratch (table block, status word, queue counters) is a file-scope device
+ * array of 256 bytes plus FE_NOALLOC_TABLE_DOUBLES doubles (96 KB), which every
+ * GPU that loads the library holds until the process exits.
+ *   form, mesh: as for fe_plan_create (device pointers inside them).
+ *   tab_host, wts_host, nq: the host tabulation exactly as fe_tabulate writes it
+ *     for (mesh->dim, mesh->degree, form->quad_degree): tab [(1+dim)][nq][n_loc],
+ *     wts [nq].  Read before the call returns.
+ *   u, y: device DoF vectors as for fe_action (y is overwritten unless
+ *     FE_FLAG_ACCUMULATE).
+ *   device_status: NULL, or a host int that receives the device status word
+ *     (FE_OK or the first device-detected error); a non-NULL pointer makes the
+ *     call synchronise the stream.
+ * Set-up: the first call on each device (with that device current) looks up the
+ * device address of the scratch array; make that first call before any stream
+ * capture.  Every call clears the status word and the counters before it
+ * launches, and keeps its table in the array afterwards.  Calls whose GPU work
+ * overlaps (unordered streams, several host threads) race on the shared array.
+ * Errors: FE_ERR_INVALID_ARG (bad arguments, or a table block larger than
+ * FE_NOALLOC_TABLE_DOUBLES doubles), FE_ERR_UNSUPPORTED (no thread-per-cell
+ * kernel for this form/dim/degree), FE_ERR_CUDA. */
+#define FE_NOALLOC_TABLE_DOUBLES 12288
+int fe_action_noalloc(const fe_form *form, const fe_mesh *mesh, const double *tab_host,
+                      const double *wts_host, int nq, const double *u, double *y,
+                      int *device_status, void *stream);
+
 /* ------------------------------------------------------------------ diagnostics */
 /* Measures the device's FP64 FMA throughput with an unrolled independent-chain
  * kernel: writes the achieved FP64 GFLOP/s (an FMA counts 2) to *gflops.

@@ -28,7 +28,7 @@ FE_FLAG_ACCUMULATE = 1
 # every symbol declared in include/feaction.h
 EXPORTS = ("fe_status_string", "fe_tabulate", "fe_plan_create", "fe_plan_destroy", "fe_action",
            "fe_action_adjoint", "fe_action_host", "fe_plan_status", "fe_plan_get_info",
-           "fe_measure_fp64_peak")
+           "fe_measure_fp64_peak", "fe_action_noalloc")
 
 
 class FeMesh(ctypes.Structure):
@@ -77,6 +77,8 @@ def _load() -> ctypes.CDLL:
     lib.fe_plan_status.argtypes = [P, ctypes.POINTER(I)]
     lib.fe_plan_get_info.argtypes = [P, ctypes.POINTER(FePlanInfo)]
     lib.fe_measure_fp64_peak.argtypes = [P, Z, ctypes.POINTER(D)]
+    lib.fe_action_noalloc.argtypes = [ctypes.POINTER(FeForm), ctypes.POINTER(FeMesh), P, P, I, P, P,
+                                      ctypes.POINTER(I), P]
     for name in EXPORTS:
         if name != "fe_status_string":
             getattr(lib, name).restype = I

@@ -19,7 +19,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfeaction.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["fe_api.cu", "fe_inst_2d_linear.cu", "fe_inst_2d_nh.cu", "fe_inst_3d.cu", "fe_tabulate.cpp"]
+SOURCES = ["fe_api.cu", "fe_inst_2d_linear.cu", "fe_inst_2d_nh.cu", "fe_inst_3d.cu", "fe_tabulate.cpp",
+           "fe_noalloc.cu"]
 GENCODE = "arch=compute_103a,code=sm_103a"
 
 
