@@ -176,10 +176,14 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- GPU arm
-def time_secondary(fe, torch, flush):
-    """Mass P2 2D (N=64) and Neo-Hookean P4 2D (N=256) forward + adjoint, FP64."""
+def time_secondary(fe, torch, flush, M_el, u_el, y64_el):
+    """Secondary measurements: mass P2 2D (N=64), Neo-Hookean P4 2D (N=256)
+    forward + adjoint, FP32-contraction (mixed) kernels, and CG with FP64
+    iterative refinement on the clamped elasticity system."""
+    import numpy as np
     from feinputs import lame_fields, structured_mesh, uniform_field
     from feinputs.fields import sinusoid_displacement
+    from paper_2506_17471_gb300 import solvers
     out = {}
 
     def timed(fn, reps=10):
@@ -197,6 +201,9 @@ def time_secondary(fe, torch, flush):
             ts.append(e0.elapsed_time(e1))
         return statistics.mean(ts) * 1e-3
 
+    def rel(a, b):
+        return float((a - b).abs().max() / b.abs().max())
+
     m = structured_mesh(2, 64, 2, jitter=0.2, seed=20250617)
     M = fe.Mesh(2, 2, m.coords, m.cell2vertex, m.cell2node, m.n_nodes)
     plan = fe.Plan(M, fe.MASS, 4)
@@ -209,18 +216,75 @@ def time_secondary(fe, torch, flush):
     m = structured_mesh(2, 256, 4, jitter=0.2, seed=20250619)
     M = fe.Mesh(2, 4, m.coords, m.cell2vertex, m.cell2node, m.n_nodes)
     mu, lam = lame_fields(m.n_cells, 3)
-    plan = fe.Plan(M, fe.NH_RESIDUAL, 8, mu_cell=mu, lam_cell=lam)
     u = torch.from_numpy(sinusoid_displacement(m, 4)).cuda()
     w = torch.from_numpy(uniform_field(m.n_nodes * 2, 5)).cuda()
-    y = torch.empty_like(u)
-    tf = timed(lambda: plan.apply(u, y))
-    ta = timed(lambda: plan.adjoint(u, w))
     n = m.n_nodes * 2
-    out["nh_p4_2d_n256"] = {"dofs": n, "fwd_ms": tf * 1e3, "adj_ms": ta * 1e3,
-                            "fwd_dofs_per_s": n / tf, "adj_dofs_per_s": n / ta,
-                            "adj_over_fwd": ta / tf, "fwd_gflops": plan.flops() / tf / 1e9,
-                            "nq": plan.info.nq}
+    res = {}
+    for prec in ("fp64", "fp32"):
+        plan = fe.Plan(M, fe.NH_RESIDUAL, 8, mu_cell=mu, lam_cell=lam, precision=prec)
+        y = torch.empty_like(u)
+        tf = timed(lambda: plan.apply(u, y))
+        ta = timed(lambda: plan.adjoint(u, w))
+        res[prec] = (tf, ta, y.clone(), plan.adjoint(u, w)[0])
+        out[f"nh_p4_2d_n256_{prec}"] = {
+            "dofs": n, "fwd_ms": tf * 1e3, "adj_ms": ta * 1e3, "fwd_dofs_per_s": n / tf,
+            "adj_dofs_per_s": n / ta, "adj_over_fwd": ta / tf,
+            "fwd_gflops": plan.flops() / tf / 1e9, "nq": plan.info.nq}
+    out["nh_p4_2d_n256_fp32"]["fwd_speedup_vs_fp64"] = res["fp64"][0] / res["fp32"][0]
+    out["nh_p4_2d_n256_fp32"]["adj_speedup_vs_fp64"] = res["fp64"][1] / res["fp32"][1]
+    out["nh_p4_2d_n256_fp32"]["rel_dev_fwd_vs_fp64"] = rel(res["fp32"][2], res["fp64"][2])
+    out["nh_p4_2d_n256_fp32"]["rel_dev_adj_vs_fp64"] = rel(res["fp32"][3], res["fp64"][3])
+
+    # elasticity P2 3D (the headline workload) with FP32 contractions
+    p64 = fe.Plan(M_el, fe.ELASTICITY, 2, lam=1.25, mu=1.0)
+    p32 = fe.Plan(M_el, fe.ELASTICITY, 2, lam=1.25, mu=1.0, precision="fp32")
+    y32 = torch.empty_like(u_el)
+    t64 = timed(lambda: p64.apply(u_el, y64_el))
+    t32 = timed(lambda: p32.apply(u_el, y32))
+    nd = p32.n_dofs
+    out["elasticity_p2_3d_n32_fp32"] = {
+        "ms": t32 * 1e3, "dofs_per_s": nd / t32, "speedup_vs_fp64": t64 / t32,
+        "rel_dev_vs_fp64": rel(y32, y64_el)}
+
+    # CG with FP64 iterative refinement, clamped boundary, b = M A_64 x*
+    free = torch.from_numpy(np.repeat(~_BOUNDARY[0], 3).astype(np.uint8)).cuda()
+    xs = torch.from_numpy(uniform_field(nd, 5)).cuda() * free
+    b = torch.empty_like(xs)
+    p64.apply(xs, b)
+    b *= free
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, st64 = solvers.cg(lambda a, c: p64.apply(a, c), b, free, rtol=1e-10)
+    torch.cuda.synchronize()
+    t_cg = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    _, stir = solvers.cg_ir(lambda a, c: p64.apply(a, c), lambda a, c: p32.apply(a, c), b, free,
+                            tol=1e-10)
+    torch.cuda.synchronize()
+    t_ir = time.perf_counter() - t0
+    out["cg_ir_elasticity_p2_3d_n32"] = {
+        "fp64_cg_s": t_cg, "fp64_cg_iters": st64.iterations, "fp64_cg_rel_residual": st64.rel_residual,
+        "ir_s": t_ir, "ir_outer": stir.outer, "ir_inner_iters": stir.iterations,
+        "ir_rel_residual_fp64": stir.rel_residual, "speedup": t_cg / t_ir,
+        "note": "relative residuals are true FP64 residuals ||M(b - A_64 x)|| / ||M b||"}
+
+    # mass P3 2D at ~4M DoFs (hp sweep point), FP64 vs FP32 contractions
+    m = structured_mesh(2, 667, 3, jitter=0.2, seed=20250620)
+    M = fe.Mesh(2, 3, m.coords, m.cell2vertex, m.cell2node, m.n_nodes)
+    u = torch.from_numpy(uniform_field(m.n_nodes, 6)).cuda()
+    ys = {}
+    for prec in ("fp64", "fp32"):
+        plan = fe.Plan(M, fe.MASS, 6, precision=prec)
+        ys[prec] = torch.empty_like(u)
+        t = timed(lambda: plan.apply(u, ys[prec]))
+        out[f"mass_p3_2d_n667_{prec}"] = {"dofs": m.n_nodes, "ms": t * 1e3,
+                                          "dofs_per_s": m.n_nodes / t,
+                                          "gflops": plan.flops() / t / 1e9}
+    out["mass_p3_2d_n667_fp32"]["rel_dev_vs_fp64"] = rel(ys["fp32"], ys["fp64"])
     return out
+
+
+_BOUNDARY = []
 
 
 def run_ours(args):
@@ -242,6 +306,7 @@ def run_ours(args):
     import paper_2506_17471_gb300 as fe
 
     m, u_np = make_inputs()
+    _BOUNDARY[:] = [m.boundary_nodes()]
     M = fe.Mesh(3, 2, m.coords, m.cell2vertex, m.cell2node, m.n_nodes, device=dev)
     plan = fe.Plan(M, fe.ELASTICITY, 2, lam=1.25, mu=1.0)
     n_dofs = plan.n_dofs
@@ -324,7 +389,7 @@ def run_ours(args):
         dfma = fe.measure_fp64_peak()
         extra["fp64_dfma_measured_gflops"] = dfma
         if not args.no_extra:
-            extra.update(time_secondary(fe, torch, flush))
+            extra.update(time_secondary(fe, torch, flush, M, u, y))
         hbm_bound = flops / plan.info.bytes_min * peaks.get("hbm_gbs", 6800.0)
         extra["roofline_min_gflops"] = min(FP64_NOMINAL_GFLOPS, hbm_bound)
         extra["arithmetic_intensity_flop_per_byte"] = flops / plan.info.bytes_min

@@ -75,7 +75,13 @@ enum fe_form_kind {
 };
 
 enum fe_precision {
-    FE_PREC_FP64 = 0         /* every operation in IEEE double */
+    FE_PREC_FP64 = 0,        /* every operation in IEEE double                           */
+    FE_PREC_FP32 = 1         /* evaluation and quadrature contractions (tables, DoFs,
+                                accumulators) in IEEE single with FP32 accumulation;
+                                geometry (det J, J^{-1}), quadrature weights, the
+                                Neo-Hookean kinematics, log det F and stress, and the
+                                scatter-add stay FP64.  The linear elasticity stress is
+                                evaluated in single.  Error: see fe_plan_create.        */
 };
 
 /* Flags for fe_form.flags */
@@ -192,6 +198,39 @@ typedef struct fe_plan_info {
 } fe_plan_info;
 
 int fe_plan_get_info(const fe_plan *plan, fe_plan_info *info);
+
+/* ------------------------------------------------------------------ Krylov building blocks */
+/* Vector kernels for conjugate gradients with FP64 iterative refinement around
+ * a reduced-precision action (the action is the operator; these supply one
+ * CG iteration's vector work).  All vectors are device FP64 arrays of n
+ * entries; mask is NULL (every DoF free) or a device uint8 array of n entries,
+ * 1 for a free DoF and 0 for a Dirichlet DoF (the masked system is
+ * M A M + (I - M) with M = diag(mask)).  Every scalar stays on the device in
+ * the caller's workspace ws of FE_CG_WORKSPACE_DOUBLES doubles, which must be
+ * zero-filled once before first use; scalars live at ws[FE_CG_PARTIALS + s]
+ * with s: 0 rr, 1 pq, 2 alpha, 3 beta, 4 rr after the update, 5..14 free slots
+ * for fe_vec_dot, 15 reserved (reduction counter, self-resetting).
+ * Reductions are deterministic (fixed grid, fixed summation order).  Calls
+ * sharing one ws must be ordered (one stream).  All are asynchronous on stream.
+ * Errors: FE_ERR_INVALID_ARG, FE_ERR_CUDA. */
+#define FE_CG_PARTIALS 1024
+#define FE_CG_WORKSPACE_DOUBLES (FE_CG_PARTIALS + 16)
+/* r = M (b - Ax); p = r; rr = r . r */
+int fe_cg_start(long long n, const double *b, const double *Ax, const uint8_t *mask, double *r,
+                double *p, double *ws, void *stream);
+/* q <- M q; pq = p . q; alpha = rr / pq   (q = A p from the action on entry) */
+int fe_cg_direction(long long n, const double *p, double *q, const uint8_t *mask, double *ws,
+                    void *stream);
+/* x += alpha p; r -= alpha q; beta = (r . r) / rr; rr = r . r */
+int fe_cg_update(long long n, double *x, double *r, const double *p, const double *q, double *ws,
+                 void *stream);
+/* p = r + beta p */
+int fe_cg_new_direction(long long n, const double *r, double *p, const double *ws, void *stream);
+/* y += a x (a on the host) */
+int fe_vec_axpy(long long n, double a, const double *x, double *y, void *stream);
+/* ws scalar slot (5..14) = (M x) . y */
+int fe_vec_dot(long long n, const double *x, const double *y, const uint8_t *mask, double *ws,
+               int slot, void *stream);
 
 /* ------------------------------------------------------------------ no-allocation variant */
 /* fe_action for callers that cannot allocate device memory (the paper has no

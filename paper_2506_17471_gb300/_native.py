@@ -23,12 +23,16 @@ FE_FORM_ELASTICITY = 1
 FE_FORM_NH_RESIDUAL = 2
 FE_FORM_NH_JACOBIAN = 3
 FE_PREC_FP64 = 0
+FE_PREC_FP32 = 1
 FE_FLAG_ACCUMULATE = 1
 
 # every symbol declared in include/feaction.h
 EXPORTS = ("fe_status_string", "fe_tabulate", "fe_plan_create", "fe_plan_destroy", "fe_action",
            "fe_action_adjoint", "fe_action_host", "fe_plan_status", "fe_plan_get_info",
-           "fe_measure_fp64_peak", "fe_action_noalloc")
+           "fe_measure_fp64_peak", "fe_action_noalloc", "fe_cg_start", "fe_cg_direction",
+           "fe_cg_update", "fe_cg_new_direction", "fe_vec_axpy", "fe_vec_dot")
+FE_CG_PARTIALS = 1024
+FE_CG_WORKSPACE_DOUBLES = FE_CG_PARTIALS + 16
 
 
 class FeMesh(ctypes.Structure):
@@ -79,6 +83,13 @@ def _load() -> ctypes.CDLL:
     lib.fe_measure_fp64_peak.argtypes = [P, Z, ctypes.POINTER(D)]
     lib.fe_action_noalloc.argtypes = [ctypes.POINTER(FeForm), ctypes.POINTER(FeMesh), P, P, I, P, P,
                                       ctypes.POINTER(I), P]
+    LL = ctypes.c_longlong
+    lib.fe_cg_start.argtypes = [LL, P, P, P, P, P, P, P]
+    lib.fe_cg_direction.argtypes = [LL, P, P, P, P, P]
+    lib.fe_cg_update.argtypes = [LL, P, P, P, P, P, P]
+    lib.fe_cg_new_direction.argtypes = [LL, P, P, P, P]
+    lib.fe_vec_axpy.argtypes = [LL, D, P, P, P]
+    lib.fe_vec_dot.argtypes = [LL, P, P, P, P, I, P]
     for name in EXPORTS:
         if name != "fe_status_string":
             getattr(lib, name).restype = I

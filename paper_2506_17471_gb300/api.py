@@ -20,6 +20,8 @@ NH_RESIDUAL = N.FE_FORM_NH_RESIDUAL
 NH_JACOBIAN = N.FE_FORM_NH_JACOBIAN
 FORM_NAMES = {MASS: "mass", ELASTICITY: "elasticity", NH_RESIDUAL: "nh_residual",
               NH_JACOBIAN: "nh_jacobian"}
+# contraction precision of a plan (include/feaction.h, enum fe_precision)
+PRECISIONS = {"fp64": N.FE_PREC_FP64, "fp32": N.FE_PREC_FP32}
 
 
 def _stream_ptr(stream=None) -> ctypes.c_void_p:
@@ -100,7 +102,7 @@ class Plan:
 
     def __init__(self, mesh: Mesh, kind: int, quad_degree: int, *, lam: float = 0.0,
                  mu: float = 0.0, mu_cell=None, lam_cell=None, u_lin=None,
-                 accumulate: bool = False):
+                 accumulate: bool = False, precision: str = "fp64"):
         self.mesh = mesh
         self.kind = int(kind)
         self.ncomp = 1 if kind == MASS else mesh.dim
@@ -112,7 +114,10 @@ class Plan:
         self.u_lin = None if u_lin is None else torch.as_tensor(
             u_lin, dtype=torch.float64, device=dev).clone().contiguous()
         flags = N.FE_FLAG_ACCUMULATE if accumulate else 0
-        self._form = N.FeForm(self.kind, int(quad_degree), N.FE_PREC_FP64, flags, float(lam),
+        if precision not in PRECISIONS:
+            raise ValueError(f"precision must be one of {sorted(PRECISIONS)}")
+        self.precision = precision
+        self._form = N.FeForm(self.kind, int(quad_degree), PRECISIONS[precision], flags, float(lam),
                               float(mu), _dptr(self.lam_cell).value or 0,
                               _dptr(self.mu_cell).value or 0, _dptr(self.u_lin).value or 0)
         self._mesh_c = mesh._c()

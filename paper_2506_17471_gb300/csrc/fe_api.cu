@@ -26,12 +26,13 @@ void init_registry()
     g_nvariants = n;
 }
 
-const Variant *find_variant(int form, int dim, int degree, int op)
+const Variant *find_variant(int form, int dim, int degree, int op, int precision)
 {
     std::call_once(g_once, init_registry);
     for (int i = 0; i < g_nvariants; ++i) {
         const Variant &v = g_variants[i];
-        if (v.form == form && v.dim == dim && v.degree == degree && v.op == op) return &v;
+        if (v.form == form && v.dim == dim && v.degree == degree && v.op == op && v.precision == precision)
+            return &v;
     }
     return nullptr;
 }
@@ -175,15 +176,16 @@ extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan 
     // 2D vertex coordinates are gathered as one 16-byte load per vertex
     if (m.dim == 2 && reinterpret_cast<uintptr_t>(m.coords) % 16 != 0) return FE_ERR_INVALID_ARG;
     if (f.kind < FE_FORM_MASS || f.kind > FE_FORM_NH_JACOBIAN) return FE_ERR_INVALID_ARG;
-    if (f.precision != FE_PREC_FP64) return FE_ERR_UNSUPPORTED;
+    if (f.precision != FE_PREC_FP64 && f.precision != FE_PREC_FP32) return FE_ERR_UNSUPPORTED;
     if (f.quad_degree < 0 || f.quad_degree > 40) return FE_ERR_INVALID_ARG;
     if (f.kind == FE_FORM_NH_JACOBIAN && !f.u_lin) return FE_ERR_INVALID_ARG;
     const int ncomp = ncomp_of(f.kind, m.dim);
     if ((long long)m.n_nodes * ncomp >= (1ll << 31)) return FE_ERR_INVALID_ARG;
 
-    const Variant *v = find_variant(f.kind, m.dim, m.degree, 0);
+    const Variant *v = find_variant(f.kind, m.dim, m.degree, 0, f.precision);
     if (!v) return FE_ERR_UNSUPPORTED;
-    const Variant *adj = (f.kind == FE_FORM_NH_RESIDUAL) ? find_variant(f.kind, m.dim, m.degree, 1) : nullptr;
+    const Variant *adj =
+        (f.kind == FE_FORM_NH_RESIDUAL) ? find_variant(f.kind, m.dim, m.degree, 1, f.precision) : nullptr;
 
     // host tabulation -> device table block [nq][1+d][n] + wts[nq], padded to 16 B
     int nq = 0;
@@ -193,16 +195,33 @@ extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan 
     std::vector<double> pts((size_t)nq * m.dim), wts(nq), tab((size_t)(1 + m.dim) * nq * n);
     int rc = fe_tabulate(m.dim, m.degree, f.quad_degree, &nq, pts.data(), wts.data(), tab.data(), tab.size());
     if (rc != FE_OK) return rc;
-    int tab_doubles = nq * (1 + m.dim) * n + nq;
-    tab_doubles = (tab_doubles + 1) & ~1;
-    const size_t smem = (size_t)tab_doubles * sizeof(double);
+    // table block: tab [nq][1+d][n] in the contraction precision, padded to 8 B,
+    // the weights [nq] in double, the weights [nq] in the contraction precision;
+    // the block is padded to 16 B (bulk copy)
+    const size_t esz = f.precision == FE_PREC_FP32 ? sizeof(float) : sizeof(double);
+    const size_t woff = ((size_t)nq * (1 + m.dim) * n * esz + 7) & ~(size_t)7;
+    const size_t smem = (woff + (size_t)nq * (sizeof(double) + esz) + 15) & ~(size_t)15;
+    const int tab_doubles = (int)(smem / sizeof(double));
     if (smem > 200 * 1024) return FE_ERR_UNSUPPORTED;
     std::vector<double> block(tab_doubles, 0.0);
+    unsigned char *blk = reinterpret_cast<unsigned char *>(block.data());
     for (int q = 0; q < nq; ++q)
         for (int k = 0; k <= m.dim; ++k)
-            for (int j = 0; j < n; ++j)
-                block[((size_t)q * (1 + m.dim) + k) * n + j] = tab[((size_t)k * nq + q) * n + j];
-    for (int q = 0; q < nq; ++q) block[(size_t)nq * (1 + m.dim) * n + q] = wts[q];
+            for (int j = 0; j < n; ++j) {
+                const double t = tab[((size_t)k * nq + q) * n + j];
+                const size_t idx = ((size_t)q * (1 + m.dim) + k) * n + j;
+                if (esz == sizeof(float))
+                    reinterpret_cast<float *>(blk)[idx] = (float)t;
+                else
+                    reinterpret_cast<double *>(blk)[idx] = t;
+            }
+    for (int q = 0; q < nq; ++q) {
+        reinterpret_cast<double *>(blk + woff)[q] = wts[q];
+        if (esz == sizeof(float))
+            reinterpret_cast<float *>(blk + woff + (size_t)nq * sizeof(double))[q] = (float)wts[q];
+        else
+            reinterpret_cast<double *>(blk + woff + (size_t)nq * sizeof(double))[q] = wts[q];
+    }
 
     fe_plan *p = new (std::nothrow) fe_plan();
     if (!p) return FE_ERR_NO_MEMORY;

@@ -43,6 +43,7 @@ using LaunchFn = cudaError_t (*)(const ActionArgs &, int grid, int block, size_t
 struct Variant {
     int form, dim, degree;
     int op;            // 0 = action, 1 = adjoint
+    int precision;     // enum fe_precision of the contractions
     int kernel_id;     // fe_plan_info.kernel
     int block;         // threads per block
     LaunchFn launch;

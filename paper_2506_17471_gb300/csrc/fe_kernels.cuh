@@ -26,6 +26,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 
 #include "fe_internal.h"
 
@@ -148,20 +149,20 @@ __device__ __forceinline__ double det_cof(const double (&A)[D][D], double (&C)[D
     }
 }
 
-// Evaluation phase: reference gradient gh[c][k] = sum_j T_{k+1}[j] l[j][c].
-template <int D, int N, int NC>
-__device__ __forceinline__ void eval_grad(const double *__restrict__ T, const double (&l)[N][NC],
-                                          double (&gh)[NC][D])
+// Evaluation phase: reference gradient gh[c][k] = sum_j T_{k+1}[j] l[j][c], in
+// the contraction type R (double, or float for the mixed-precision variant).
+template <int D, int N, int NC, typename R>
+__device__ __forceinline__ void eval_grad(const R *__restrict__ T, const R (&l)[N][NC], R (&gh)[NC][D])
 {
 #pragma unroll
     for (int c = 0; c < NC; ++c)
 #pragma unroll
-        for (int k = 0; k < D; ++k) gh[c][k] = 0.0;
+        for (int k = 0; k < D; ++k) gh[c][k] = R(0);
 #pragma unroll
     for (int j = 0; j < N; ++j) {
 #pragma unroll
         for (int k = 0; k < D; ++k) {
-            const double t = T[(k + 1) * N + j];
+            const R t = T[(k + 1) * N + j];
 #pragma unroll
             for (int c = 0; c < NC; ++c) gh[c][k] = fma(t, l[j][c], gh[c][k]);
         }
@@ -169,15 +170,14 @@ __device__ __forceinline__ void eval_grad(const double *__restrict__ T, const do
 }
 
 // Quadrature phase: out[j][c] += sum_k T_{k+1}[j] e[c][k].
-template <int D, int N, int NC>
-__device__ __forceinline__ void quad_grad(const double *__restrict__ T, const double (&e)[NC][D],
-                                          double (&out)[N][NC])
+template <int D, int N, int NC, typename R>
+__device__ __forceinline__ void quad_grad(const R *__restrict__ T, const R (&e)[NC][D], R (&out)[N][NC])
 {
 #pragma unroll
     for (int j = 0; j < N; ++j) {
 #pragma unroll
         for (int k = 0; k < D; ++k) {
-            const double t = T[(k + 1) * N + j];
+            const R t = T[(k + 1) * N + j];
 #pragma unroll
             for (int c = 0; c < NC; ++c) out[j][c] = fma(t, e[c][k], out[j][c]);
         }
@@ -185,15 +185,14 @@ __device__ __forceinline__ void quad_grad(const double *__restrict__ T, const do
 }
 
 // A[c][i] = sum_k B[c][k] Jinv[k][i]  (reference -> physical gradient)
-template <int D>
-__device__ __forceinline__ void map_grad(const double (&B)[D][D], const double (&Jinv)[D][D],
-                                         double (&A)[D][D])
+template <int D, typename R>
+__device__ __forceinline__ void map_grad(const R (&B)[D][D], const R (&Jinv)[D][D], R (&A)[D][D])
 {
 #pragma unroll
     for (int c = 0; c < D; ++c)
 #pragma unroll
         for (int i = 0; i < D; ++i) {
-            double s = B[c][0] * Jinv[0][i];
+            R s = B[c][0] * Jinv[0][i];
 #pragma unroll
             for (int k = 1; k < D; ++k) s = fma(B[c][k], Jinv[k][i], s);
             A[c][i] = s;
@@ -201,19 +200,27 @@ __device__ __forceinline__ void map_grad(const double (&B)[D][D], const double (
 }
 
 // e[c][k] = sum_i S[c][i] Jinv[k][i]  (physical stress -> reference test weights)
-template <int D>
-__device__ __forceinline__ void pull_back(const double (&S)[D][D], const double (&Jinv)[D][D],
-                                          double (&e)[D][D])
+template <int D, typename R>
+__device__ __forceinline__ void pull_back(const R (&S)[D][D], const R (&Jinv)[D][D], R (&e)[D][D])
 {
 #pragma unroll
     for (int c = 0; c < D; ++c)
 #pragma unroll
         for (int k = 0; k < D; ++k) {
-            double s = S[c][0] * Jinv[k][0];
+            R s = S[c][0] * Jinv[k][0];
 #pragma unroll
             for (int i = 1; i < D; ++i) s = fma(S[c][i], Jinv[k][i], s);
             e[c][k] = s;
         }
+}
+
+template <int A, int B, typename T, typename U>
+__device__ __forceinline__ void convert(const T (&x)[A][B], U (&y)[A][B])
+{
+#pragma unroll
+    for (int i = 0; i < A; ++i)
+#pragma unroll
+        for (int k = 0; k < B; ++k) y[i][k] = U(x[i][k]);
 }
 
 // Internal operation ids (forms of the public API plus the Neo-Hookean adjoint).
@@ -241,31 +248,45 @@ __device__ __forceinline__ bool gather_nodes(const int32_t *__restrict__ c2n, in
     return ok;
 }
 
-template <int N, int NC>
+// Gather DoFs (double in memory) into the contraction type R.
+template <int N, int NC, typename R>
 __device__ __forceinline__ void gather_dofs(const double *__restrict__ u, const int (&nodes)[N],
-                                            double (&l)[N][NC])
+                                            R (&l)[N][NC])
 {
 #pragma unroll
     for (int j = 0; j < N; ++j) {
         const double *p = u + (size_t)nodes[j] * NC;
         if constexpr (NC == 2) {
             const double2 v = __ldg(reinterpret_cast<const double2 *>(p));
-            l[j][0] = v.x;
-            l[j][1] = v.y;
+            l[j][0] = R(v.x);
+            l[j][1] = R(v.y);
         } else {
 #pragma unroll
-            for (int c = 0; c < NC; ++c) l[j][c] = __ldg(p + c);
+            for (int c = 0; c < NC; ++c) l[j][c] = R(__ldg(p + c));
         }
     }
 }
 
-// One cell of Algorithm 2 for operation OP.  Returns nothing; writes the scatter.
-template <int OP, int D, int P>
-__device__ __forceinline__ void action_cell(const ActionArgs &a, const double *__restrict__ tab,
-                                            const double *__restrict__ wts, int cell)
+// Table block layout in shared memory: tab [nq][1+D][N] in R, padded to a
+// multiple of 8 bytes, then the weights [nq] in double, then the weights [nq]
+// again in R (used by forms whose pointwise work runs in R).
+template <typename R>
+__host__ __device__ constexpr size_t table_weights_offset_bytes(int nq, int d, int n)
+{
+    return ((size_t)nq * (d + 1) * n * sizeof(R) + 7) & ~(size_t)7;
+}
+
+// One cell of Algorithm 2 for operation OP, contractions in R.  Geometry, the
+// quadrature weights, the Neo-Hookean kinematics/stress and the scatter are
+// always FP64.
+template <int OP, int D, int P, typename R>
+__device__ __forceinline__ void action_cell(const ActionArgs &a, const R *__restrict__ tab,
+                                            const double *__restrict__ wts, const R *__restrict__ wts_r,
+                                            int cell)
 {
     constexpr int N = nloc(D, P);
     constexpr int NC = OpTraits<OP, D>::NC;
+    constexpr bool kMixed = !std::is_same<R, double>::value;
 
     // gather coordinates (Algorithm 2: gather of coords through iota_P1)
     int vtx[D + 1];
@@ -293,7 +314,7 @@ __device__ __forceinline__ void action_cell(const ActionArgs &a, const double *_
             for (int i = 0; i < D; ++i) X[m][i] = __ldg(a.coords + (size_t)vtx[m] * D + i);
         }
     }
-    // geometry: J, det J, J^{-1}, once per cell (affine)
+    // geometry: J, det J, J^{-1}, once per cell (affine), in FP64
     double Jinv[D][D];
     const double det = cell_geometry<D>(X, Jinv);
     if (!(det != 0.0) || !isfinite(det)) {
@@ -301,61 +322,76 @@ __device__ __forceinline__ void action_cell(const ActionArgs &a, const double *_
         return;
     }
     const double absdet = fabs(det);
+    const R absdet_r = R(absdet);
+    [[maybe_unused]] R Jinv_r[D][D];
+    if constexpr (kMixed) convert<D, D>(Jinv, Jinv_r);
 
     // gather DoFs
-    double l[N][NC];
-    gather_dofs<N, NC>(a.u, nodes, l);
-    [[maybe_unused]] double l0[OpTraits<OP, D>::kTwoFields ? N : 1][NC];
-    if constexpr (OpTraits<OP, D>::kTwoFields) gather_dofs<N, NC>(a.u_lin, nodes, l0);
+    R l[N][NC];
+    gather_dofs<N, NC, R>(a.u, nodes, l);
+    [[maybe_unused]] R l0[OpTraits<OP, D>::kTwoFields ? N : 1][NC];
+    if constexpr (OpTraits<OP, D>::kTwoFields) gather_dofs<N, NC, R>(a.u_lin, nodes, l0);
     double mu = a.mu, lam = a.lam;
     if constexpr (OpTraits<OP, D>::kCellCoeff) {
         if (a.mu_cell) mu = __ldg(a.mu_cell + cell);
         if (a.lam_cell) lam = __ldg(a.lam_cell + cell);
     }
 
-    double out[N][NC];
+    R out[N][NC];
 #pragma unroll
     for (int j = 0; j < N; ++j)
 #pragma unroll
-        for (int c = 0; c < NC; ++c) out[j][c] = 0.0;
+        for (int c = 0; c < NC; ++c) out[j][c] = R(0);
     [[maybe_unused]] double acc_mu = 0.0, acc_lam = 0.0;
     bool nh_ok = true;
 
+    [[maybe_unused]] const R mu_r = R(mu), lam_r = R(lam);
     for (int q = 0; q < a.nq; ++q) {
-        const double *__restrict__ T = tab + (size_t)q * (D + 1) * N;
-        const double wdet = wts[q] * absdet;
+        const R *__restrict__ T = tab + (size_t)q * (D + 1) * N;
+        // w_q |det J| in R for the forms evaluated in R, in FP64 for Neo-Hookean
+        const R wdet_r = wts_r[q] * absdet_r;
         if constexpr (OP == OP_MASS) {
-            double uq = 0.0;
+            R uq = R(0);
 #pragma unroll
             for (int j = 0; j < N; ++j) uq = fma(T[j], l[j][0], uq);
-            const double e = uq * wdet;
+            const R e = uq * wdet_r;
 #pragma unroll
             for (int j = 0; j < N; ++j) out[j][0] = fma(T[j], e, out[j][0]);
         } else if constexpr (OP == OP_ELASTICITY) {
-            double gh[D][D], G[D][D], S[D][D], e[D][D];
-            eval_grad<D, N, D>(T, l, gh);
-            map_grad<D>(gh, Jinv, G);
-            double tr = G[0][0];
+            // linear stress: evaluated in the contraction type
+            R gh[D][D], G[D][D], S[D][D], e[D][D];
+            eval_grad<D, N, D, R>(T, l, gh);
+            if constexpr (kMixed)
+                map_grad<D, R>(gh, Jinv_r, G);
+            else
+                map_grad<D, R>(gh, Jinv, G);
+            R tr = G[0][0];
 #pragma unroll
             for (int i = 1; i < D; ++i) tr += G[i][i];
-            const double smu = wdet * mu;
-            const double slt = wdet * lam * tr;
+            const R smu = wdet_r * mu_r;
+            const R slt = wdet_r * lam_r * tr;
 #pragma unroll
             for (int i = 0; i < D; ++i) {
-                S[i][i] = fma(2.0 * smu, G[i][i], slt);
+                S[i][i] = fma(R(2) * smu, G[i][i], slt);
 #pragma unroll
                 for (int k = i + 1; k < D; ++k) {
-                    const double s = smu * (G[i][k] + G[k][i]);
+                    const R s = smu * (G[i][k] + G[k][i]);
                     S[i][k] = s;
                     S[k][i] = s;
                 }
             }
-            pull_back<D>(S, Jinv, e);
-            quad_grad<D, N, D>(T, e, out);
+            if constexpr (kMixed)
+                pull_back<D, R>(S, Jinv_r, e);
+            else
+                pull_back<D, R>(S, Jinv, e);
+            quad_grad<D, N, D, R>(T, e, out);
         } else if constexpr (OP == OP_NH_RESIDUAL) {
+            const double wdet = wts[q] * absdet;
+            R ghr[D][D], er[D][D];
             double gh[D][D], F[D][D], C[D][D], S[D][D], e[D][D];
-            eval_grad<D, N, D>(T, l, gh);
-            map_grad<D>(gh, Jinv, F);
+            eval_grad<D, N, D, R>(T, l, ghr);
+            convert<D, D>(ghr, gh);
+            map_grad<D, double>(gh, Jinv, F);
 #pragma unroll
             for (int i = 0; i < D; ++i) F[i][i] += 1.0;
             const double Jd = det_cof<D>(F, C);  // F^{-T} = C / Jd
@@ -368,16 +404,21 @@ __device__ __forceinline__ void action_cell(const ActionArgs &a, const double *_
             for (int i = 0; i < D; ++i)
 #pragma unroll
                 for (int k = 0; k < D; ++k) S[i][k] = fma(smu, F[i][k], scf * C[i][k]);
-            pull_back<D>(S, Jinv, e);
-            quad_grad<D, N, D>(T, e, out);
+            pull_back<D, double>(S, Jinv, e);
+            convert<D, D>(e, er);
+            quad_grad<D, N, D, R>(T, er, out);
         } else {  // OP_NH_JACOBIAN / OP_NH_ADJOINT: tangent applied to H = grad(du) (or grad w)
+            const double wdet = wts[q] * absdet;
+            R ghr[D][D], er[D][D];
             double gh[D][D], F[D][D], H[D][D], C[D][D], Fit[D][D], A[D][D], S[D][D], e[D][D];
-            eval_grad<D, N, D>(T, l0, gh);
-            map_grad<D>(gh, Jinv, F);
+            eval_grad<D, N, D, R>(T, l0, ghr);
+            convert<D, D>(ghr, gh);
+            map_grad<D, double>(gh, Jinv, F);
 #pragma unroll
             for (int i = 0; i < D; ++i) F[i][i] += 1.0;
-            eval_grad<D, N, D>(T, l, gh);
-            map_grad<D>(gh, Jinv, H);
+            eval_grad<D, N, D, R>(T, l, ghr);
+            convert<D, D>(ghr, gh);
+            map_grad<D, double>(gh, Jinv, H);
             const double Jd = det_cof<D>(F, C);
             nh_ok &= (Jd > 0.0);
             const double rJ = 1.0 / Jd;
@@ -422,17 +463,18 @@ __device__ __forceinline__ void action_cell(const ActionArgs &a, const double *_
                         acc_lam = fma(wdet * lnJ * Fit[i][k], H[i][k], acc_lam);
                     }
             }
-            pull_back<D>(S, Jinv, e);
-            quad_grad<D, N, D>(T, e, out);
+            pull_back<D, double>(S, Jinv, e);
+            convert<D, D>(e, er);
+            quad_grad<D, N, D, R>(T, er, out);
         }
     }
     if (!nh_ok) set_status(a.status, FE_ERR_NONFINITE);
 
-    // scatter-add (Algorithm 2 scatter; cross-cell races resolved with FP64 atomics)
+    // scatter-add in FP64 (Algorithm 2 scatter; cross-cell races resolved with atomics)
 #pragma unroll
     for (int j = 0; j < N; ++j)
 #pragma unroll
-        for (int c = 0; c < NC; ++c) atomicAdd(a.y + (size_t)nodes[j] * NC + c, out[j][c]);
+        for (int c = 0; c < NC; ++c) atomicAdd(a.y + (size_t)nodes[j] * NC + c, double(out[j][c]));
     if constexpr (OP == OP_NH_ADJOINT) {
         a.dmu[cell] = acc_mu;   // one thread per cell: plain stores, no reduction
         a.dlam[cell] = acc_lam;
@@ -456,7 +498,7 @@ __device__ __forceinline__ void leave_queue(int32_t *sched)
     }
 }
 
-template <int OP, int D, int P>
+template <int OP, int D, int P, typename R>
 __global__ void __launch_bounds__(kTpcBlock) k_action_tpc(const ActionArgs a)
 {
     extern __shared__ __align__(128) double smem[];
@@ -465,8 +507,11 @@ __global__ void __launch_bounds__(kTpcBlock) k_action_tpc(const ActionArgs a)
         leave_queue(a.sched);
         return;
     }
-    const double *tab = smem;
-    const double *wts = smem + (size_t)a.nq * (D + 1) * nloc(D, P);
+    constexpr int N = nloc(D, P);
+    const R *tab = reinterpret_cast<const R *>(smem);
+    const double *wts = reinterpret_cast<const double *>(
+        reinterpret_cast<const char *>(smem) + table_weights_offset_bytes<R>(a.nq, D, N));
+    const R *wts_r = reinterpret_cast<const R *>(wts + a.nq);
     const int lane = threadIdx.x & 31;
     const int n_chunks = (a.n_cells + 31) >> 5;
     for (;;) {
@@ -475,19 +520,19 @@ __global__ void __launch_bounds__(kTpcBlock) k_action_tpc(const ActionArgs a)
         chunk = __shfl_sync(0xffffffffu, chunk, 0);
         if (chunk >= n_chunks) break;
         const int cell = (chunk << 5) + lane;
-        if (cell < a.n_cells) action_cell<OP, D, P>(a, tab, wts, cell);
+        if (cell < a.n_cells) action_cell<OP, D, P, R>(a, tab, wts, wts_r, cell);
     }
     leave_queue(a.sched);
 }
 
-template <int OP, int D, int P>
+template <int OP, int D, int P, typename R>
 cudaError_t launch_tpc(const ActionArgs &a, int grid, int block, size_t smem, cudaStream_t s)
 {
-    k_action_tpc<OP, D, P><<<grid, block, smem, s>>>(a);
+    k_action_tpc<OP, D, P, R><<<grid, block, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-template <int OP, int D, int P>
+template <int OP, int D, int P, typename R = double>
 Variant make_tpc_variant()
 {
     Variant v;
@@ -495,10 +540,11 @@ Variant make_tpc_variant()
     v.dim = D;
     v.degree = P;
     v.op = OP == OP_NH_ADJOINT ? 1 : 0;
+    v.precision = std::is_same<R, double>::value ? FE_PREC_FP64 : FE_PREC_FP32;
     v.kernel_id = 0;
     v.block = kTpcBlock;
-    v.launch = &launch_tpc<OP, D, P>;
-    v.func = reinterpret_cast<const void *>(&k_action_tpc<OP, D, P>);
+    v.launch = &launch_tpc<OP, D, P, R>;
+    v.func = reinterpret_cast<const void *>(&k_action_tpc<OP, D, P, R>);
     return v;
 }
 

@@ -52,7 +52,8 @@ const Variant *noalloc_variant(int form, int dim, int degree)
     std::call_once(g_na_once, init_noalloc_registry);
     for (int i = 0; i < g_na_nvariants; ++i) {
         const Variant &v = g_na_variants[i];
-        if (v.form == form && v.dim == dim && v.degree == degree && v.op == 0) return &v;
+        if (v.form == form && v.dim == dim && v.degree == degree && v.op == 0 && v.precision == FE_PREC_FP64)
+            return &v;
     }
     return nullptr;
 }
@@ -107,7 +108,7 @@ extern "C" int fe_action_noalloc(const fe_form *form, const fe_mesh *mesh, const
     if (!v) return FE_ERR_UNSUPPORTED;
 
     const int n = nloc(m.dim, m.degree);
-    long long tab_doubles = (long long)nq * (1 + m.dim) * n + nq;
+    long long tab_doubles = (long long)nq * (1 + m.dim) * n + 2ll * nq;  // table, weights twice
     tab_doubles = (tab_doubles + 1) & ~1ll;
     if (tab_doubles > FE_NOALLOC_TABLE_DOUBLES) return FE_ERR_INVALID_ARG;  // beyond the scratch
     const size_t smem = (size_t)tab_doubles * sizeof(double);
@@ -125,7 +126,8 @@ extern "C" int fe_action_noalloc(const fe_form *form, const fe_mesh *mesh, const
 
     // Clear the status word and the queue counters (the array keeps the last
     // call's contents), then lay the caller's [1+d][nq][n] table out as the
-    // kernel's [nq][1+d][n] block followed by the weights.
+    // kernel's [nq][1+d][n] block followed by the weights (twice: the kernel
+    // reads one copy in FP64 and one in its contraction type, here also FP64).
     if (cudaMemsetAsync(scratch, 0, kNoallocHeaderBytes, s) != cudaSuccess) return FE_ERR_CUDA;
     for (int k = 0; k <= m.dim; ++k) {
         if (cudaMemcpy2DAsync(table + (size_t)k * n, (size_t)(1 + m.dim) * n * sizeof(double),
@@ -134,9 +136,11 @@ extern "C" int fe_action_noalloc(const fe_form *form, const fe_mesh *mesh, const
                               s) != cudaSuccess)
             return FE_ERR_CUDA;
     }
-    if (cudaMemcpyAsync(table + (size_t)nq * (1 + m.dim) * n, wts_host, (size_t)nq * sizeof(double),
-                        cudaMemcpyHostToDevice, s) != cudaSuccess)
-        return FE_ERR_CUDA;
+    for (int copy = 0; copy < 2; ++copy) {
+        if (cudaMemcpyAsync(table + (size_t)nq * (1 + m.dim) * n + (size_t)copy * nq, wts_host,
+                            (size_t)nq * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return FE_ERR_CUDA;
+    }
 
     if (!(f.flags & FE_FLAG_ACCUMULATE) && n_dofs > 0) {
         if (cudaMemsetAsync(y, 0, (size_t)n_dofs * sizeof(double), s) != cudaSuccess) return FE_ERR_CUDA;

@@ -1,0 +1,96 @@
+"""GPU parity of the FP32-contraction (mixed-precision) kernels against the FP64 oracle.
+
+Stated bound: tables, DoFs and accumulators are IEEE single (unit roundoff
+u = 2^-24 = 6.0e-8); each evaluation contraction has at most d*n_loc <= 105
+terms and each quadrature contraction at most Q(1+d) <= 256 terms, so the
+forward error of each contraction is at most gamma_256 = 256u/(1-256u) = 1.5e-5
+of the sum of the absolute terms.  For the random inputs below the absolute
+terms exceed the result by a small factor, and the parity tolerance is
+TOL32 = 5e-5 (norm-wise, relative to ||y_ref||_inf).  Geometry, the
+Neo-Hookean kinematics/stress/log and the scatter are FP64 and add nothing at
+this level.  The Neo-Hookean residual at a smooth displacement is evaluated
+from gradients ~1e3 times smaller than their terms (see
+tests/test_oracle_conditioning.py), so its mixed tolerance is 1e3 x TOL32.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from feinputs import lame_fields, structured_mesh, uniform_field
+from feinputs.fields import sinusoid_displacement
+
+pytestmark = pytest.mark.gpu
+TOL32 = 5e-5
+
+
+@pytest.fixture(scope="module")
+def fe():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2506_17471_gb300 as fe
+    return fe
+
+
+def rel(a, b):
+    a = a.detach().cpu().numpy() if torch.is_tensor(a) else a
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def cuda(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def make(fe, dim, N, p, seed):
+    m = structured_mesh(dim, N, p, jitter=0.2 if dim == 2 else 0.15, seed=seed)
+    return m, fe.Mesh(dim, p, m.coords, m.cell2vertex, m.cell2node, m.n_nodes)
+
+
+@pytest.mark.parametrize("dim,N,p", [(2, 13, 1), (2, 13, 2), (2, 13, 3), (2, 9, 6), (3, 5, 2), (3, 4, 4)])
+def test_mass_fp32(fe, dim, N, p):
+    m, M = make(fe, dim, N, p, 100 + p)
+    q = 2 * p
+    o = oracle.Oracle.from_mesh(m, q)
+    u = uniform_field(m.n_nodes, 1)
+    y = fe.Plan(M, fe.MASS, q, precision="fp32").apply(cuda(u))
+    err = rel(y, o.mass(u))
+    assert err <= TOL32 and err > 1e-12   # really computed in single
+
+
+@pytest.mark.parametrize("dim,N,p", [(2, 11, 2), (2, 11, 4), (3, 5, 1), (3, 5, 2)])
+def test_elasticity_fp32(fe, dim, N, p):
+    m, M = make(fe, dim, N, p, 110 + p)
+    q = 2 * (p - 1)
+    o = oracle.Oracle.from_mesh(m, q)
+    u = uniform_field(m.n_nodes * dim, 2)
+    y = fe.Plan(M, fe.ELASTICITY, q, lam=1.25, mu=1.0, precision="fp32").apply(cuda(u))
+    assert rel(y, o.elasticity(u, 1.25, 1.0)) <= TOL32
+
+
+@pytest.mark.parametrize("dim,N,p", [(2, 9, 2), (2, 9, 4), (3, 5, 2)])
+def test_nh_fp32(fe, dim, N, p):
+    m, M = make(fe, dim, N, p, 120 + p)
+    q = 2 * p
+    o = oracle.Oracle.from_mesh(m, q)
+    mu, lam = lame_fields(m.n_cells, 3)
+    u = sinusoid_displacement(m, 4)
+    w = uniform_field(m.n_nodes * dim, 5)
+    res = fe.Plan(M, fe.NH_RESIDUAL, q, mu_cell=mu, lam_cell=lam, precision="fp32")
+    assert rel(res.apply(cuda(u)), o.nh_residual(u, mu, lam)) <= 1e3 * TOL32
+    jac = fe.Plan(M, fe.NH_JACOBIAN, q, mu_cell=mu, lam_cell=lam, u_lin=cuda(u), precision="fp32")
+    assert rel(jac.apply(cuda(w)), o.nh_jacobian(u, w, mu, lam)) <= TOL32
+    jtw, dmu, dlam = res.adjoint(cuda(u), cuda(w))
+    ojtw, odmu, odlam = o.nh_adjoint(u, w, mu, lam)
+    assert rel(jtw, ojtw) <= TOL32
+    assert rel(dmu, odmu) <= 1e3 * TOL32 and rel(dlam, odlam) <= 1e3 * TOL32
+
+
+def test_full_elasticity_p2_3d_fp32(fe):
+    m, M = make(fe, 3, 32, 2, 20250618)
+    o = oracle.Oracle.from_mesh(m, 2)
+    u = uniform_field(m.n_nodes * 3, 2)
+    plan = fe.Plan(M, fe.ELASTICITY, 2, lam=1.25, mu=1.0, precision="fp32")
+    y = plan.apply(cuda(u))
+    assert rel(y, o.elasticity(u, 1.25, 1.0, threads=16)) <= TOL32
+    assert plan.status() == 0
