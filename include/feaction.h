@@ -274,6 +274,15 @@ int fe_action_noalloc(const fe_form *form, const fe_mesh *mesh, const double *ta
  * there so the work cannot be elided).  Synchronous. */
 int fe_measure_fp64_peak(double *scratch, size_t scratch_doubles, double *gflops);
 
+/* Self-test of the mixed-precision kernels' binary64<->binary32 conversions
+ * (integer bit-pattern conversions with round-to-nearest-even, used instead of
+ * the hardware conversion, which issues on the slow FP64 pipe of this part)
+ * against the hardware conversions, over the device array x [n]:
+ * count[0] += binary64->binary32 mismatches, count[1] += binary32->binary64
+ * mismatches; count is a device array of 2 zero-initialised uint64.
+ * Asynchronous on stream. */
+int fe_selftest_conversions(const double *x, long long n, unsigned long long *count, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

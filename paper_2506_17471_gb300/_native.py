@@ -30,7 +30,8 @@ FE_FLAG_ACCUMULATE = 1
 EXPORTS = ("fe_status_string", "fe_tabulate", "fe_plan_create", "fe_plan_destroy", "fe_action",
            "fe_action_adjoint", "fe_action_host", "fe_plan_status", "fe_plan_get_info",
            "fe_measure_fp64_peak", "fe_action_noalloc", "fe_cg_start", "fe_cg_direction",
-           "fe_cg_update", "fe_cg_new_direction", "fe_vec_axpy", "fe_vec_dot")
+           "fe_cg_update", "fe_cg_new_direction", "fe_vec_axpy", "fe_vec_dot",
+           "fe_selftest_conversions")
 FE_CG_PARTIALS = 1024
 FE_CG_WORKSPACE_DOUBLES = FE_CG_PARTIALS + 16
 
@@ -90,6 +91,7 @@ def _load() -> ctypes.CDLL:
     lib.fe_cg_new_direction.argtypes = [LL, P, P, P, P]
     lib.fe_vec_axpy.argtypes = [LL, D, P, P, P]
     lib.fe_vec_dot.argtypes = [LL, P, P, P, P, I, P]
+    lib.fe_selftest_conversions.argtypes = [P, LL, P, P]
     for name in EXPORTS:
         if name != "fe_status_string":
             getattr(lib, name).restype = I

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "fe_internal.h"
+#include "fe_kernels.cuh"
 
 namespace fe {
 namespace {
@@ -414,4 +415,37 @@ extern "C" int fe_measure_fp64_peak(double *scratch, size_t scratch_doubles, dou
     const double flops = 2.0 * 8.0 * 4.0 * iters * (double)grid * block;
     *gflops = flops / (ms * 1e-3) / 1e9;
     return FE_OK;
+}
+
+namespace fe {
+namespace {
+// Self-test of the bit-pattern conversions against the hardware conversions:
+// count[0] += binary64->binary32 mismatches, count[1] += binary32->binary64
+// mismatches (NaN results compare equal to NaN).
+__global__ void k_selftest_conversions(const double *x, long long n, unsigned long long *count)
+{
+    unsigned long long bad32 = 0, bad64 = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double v = x[i];
+        const float a = f64_to_f32_rn(v), b = __double2float_rn(v);
+        if (__float_as_uint(a) != __float_as_uint(b) && !(isnan(a) && isnan(b))) ++bad32;
+        const double c = f32_to_f64(b), d = (double)b;
+        if (__double_as_longlong(c) != __double_as_longlong(d) && !(isnan(c) && isnan(d))) ++bad64;
+    }
+    if (bad32) atomicAdd(count, bad32);
+    if (bad64) atomicAdd(count + 1, bad64);
+}
+
+}  // namespace
+}  // namespace fe
+
+extern "C" int fe_selftest_conversions(const double *x, long long n, unsigned long long *count, void *stream)
+{
+    if (!x || !count || n < 0) return FE_ERR_INVALID_ARG;
+    if (n == 0) return FE_OK;
+    long long g = (n + 255) / 256;
+    if (g > 4096) g = 4096;
+    k_selftest_conversions<<<(int)g, 256, 0, static_cast<cudaStream_t>(stream)>>>(x, n, count);
+    return cudaGetLastError() == cudaSuccess ? FE_OK : FE_ERR_CUDA;
 }

@@ -149,6 +149,47 @@ __device__ __forceinline__ double det_cof(const double (&A)[D][D], double (&C)[D
     }
 }
 
+// IEEE 754 binary64 -> binary32 with round-to-nearest-even, computed with
+// integer operations on the bit patterns.  On this part the hardware
+// conversion issues on the FP64 pipe (about 1/64 of the FP32 rate), so the
+// mixed-precision kernels convert DoFs, outputs and geometry this way.  Inputs
+// whose binary32 result would be zero, subnormal or not finite (and NaN) take
+// the hardware conversion.
+__device__ __forceinline__ float f64_to_f32_rn(double x)
+{
+    const unsigned hi = (unsigned)__double2hiint(x);
+    const unsigned lo = (unsigned)__double2loint(x);
+    const int fexp = (int)((hi >> 20) & 0x7FFu) - 896;   // binary32 biased exponent
+    if ((unsigned)(fexp - 1) >= 254u) return __double2float_rn(x);
+    unsigned bits = (hi & 0x80000000u) | ((unsigned)fexp << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+    const unsigned rest = lo & 0x1FFFFFFFu;               // the 29 discarded mantissa bits
+    const unsigned up = (rest > 0x10000000u) || (rest == 0x10000000u && (bits & 1u));
+    return __uint_as_float(bits + up);                    // a carry may round up to infinity
+}
+
+// IEEE 754 binary32 -> binary64 (exact), by re-biasing the exponent and
+// widening the mantissa; zero, subnormal, infinite and NaN inputs take the
+// hardware conversion.
+__device__ __forceinline__ double f32_to_f64(float f)
+{
+    const unsigned b = __float_as_uint(f);
+    const unsigned e = (b >> 23) & 0xFFu;
+    if (e == 0u || e == 255u) return (double)f;
+    const unsigned hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7FFFFFu) >> 3);
+    return __hiloint2double((int)hi, (int)(b << 29));
+}
+
+template <typename U, typename T>
+__device__ __forceinline__ U cvt(T x)
+{
+    if constexpr (std::is_same<U, T>::value)
+        return x;
+    else if constexpr (std::is_same<U, float>::value)
+        return f64_to_f32_rn(x);
+    else
+        return f32_to_f64(x);
+}
+
 // Evaluation phase: reference gradient gh[c][k] = sum_j T_{k+1}[j] l[j][c], in
 // the contraction type R (double, or float for the mixed-precision variant).
 template <int D, int N, int NC, typename R>
@@ -220,7 +261,7 @@ __device__ __forceinline__ void convert(const T (&x)[A][B], U (&y)[A][B])
 #pragma unroll
     for (int i = 0; i < A; ++i)
 #pragma unroll
-        for (int k = 0; k < B; ++k) y[i][k] = U(x[i][k]);
+        for (int k = 0; k < B; ++k) y[i][k] = cvt<U>(x[i][k]);
 }
 
 // Internal operation ids (forms of the public API plus the Neo-Hookean adjoint).
@@ -258,11 +299,11 @@ __device__ __forceinline__ void gather_dofs(const double *__restrict__ u, const 
         const double *p = u + (size_t)nodes[j] * NC;
         if constexpr (NC == 2) {
             const double2 v = __ldg(reinterpret_cast<const double2 *>(p));
-            l[j][0] = R(v.x);
-            l[j][1] = R(v.y);
+            l[j][0] = cvt<R>(v.x);
+            l[j][1] = cvt<R>(v.y);
         } else {
 #pragma unroll
-            for (int c = 0; c < NC; ++c) l[j][c] = R(__ldg(p + c));
+            for (int c = 0; c < NC; ++c) l[j][c] = cvt<R>(__ldg(p + c));
         }
     }
 }
@@ -322,7 +363,7 @@ __device__ __forceinline__ void action_cell(const ActionArgs &a, const R *__rest
         return;
     }
     const double absdet = fabs(det);
-    const R absdet_r = R(absdet);
+    const R absdet_r = cvt<R>(absdet);
     [[maybe_unused]] R Jinv_r[D][D];
     if constexpr (kMixed) convert<D, D>(Jinv, Jinv_r);
 
@@ -345,7 +386,7 @@ __device__ __forceinline__ void action_cell(const ActionArgs &a, const R *__rest
     [[maybe_unused]] double acc_mu = 0.0, acc_lam = 0.0;
     bool nh_ok = true;
 
-    [[maybe_unused]] const R mu_r = R(mu), lam_r = R(lam);
+    [[maybe_unused]] const R mu_r = cvt<R>(mu), lam_r = cvt<R>(lam);
     for (int q = 0; q < a.nq; ++q) {
         const R *__restrict__ T = tab + (size_t)q * (D + 1) * N;
         // w_q |det J| in R for the forms evaluated in R, in FP64 for Neo-Hookean
@@ -474,7 +515,7 @@ __device__ __forceinline__ void action_cell(const ActionArgs &a, const R *__rest
 #pragma unroll
     for (int j = 0; j < N; ++j)
 #pragma unroll
-        for (int c = 0; c < NC; ++c) atomicAdd(a.y + (size_t)nodes[j] * NC + c, double(out[j][c]));
+        for (int c = 0; c < NC; ++c) atomicAdd(a.y + (size_t)nodes[j] * NC + c, cvt<double>(out[j][c]));
     if constexpr (OP == OP_NH_ADJOINT) {
         a.dmu[cell] = acc_mu;   // one thread per cell: plain stores, no reduction
         a.dlam[cell] = acc_lam;

@@ -94,3 +94,25 @@ def test_full_elasticity_p2_3d_fp32(fe):
     y = plan.apply(cuda(u))
     assert rel(y, o.elasticity(u, 1.25, 1.0, threads=16)) <= TOL32
     assert plan.status() == 0
+
+
+def test_bit_conversions_match_hardware(fe):
+    """The mixed kernels convert binary64 <-> binary32 with integer bit operations
+    (round to nearest even); they must agree bit for bit with CUDA's conversion."""
+    import ctypes
+    from paper_2506_17471_gb300 import _native as N
+    rng = np.random.default_rng(0)
+    vals = [rng.standard_normal(200_000) * 10.0 ** rng.integers(-45, 45, 200_000),
+            rng.uniform(-1, 1, 100_000),
+            np.array([0.0, -0.0, np.inf, -np.inf, np.nan, 1e-310, -1e-320, 3.4028234663852886e38,
+                      3.4028235677973366e38, 3.402823669209385e38, 1.1754943508222875e-38,
+                      1.1754942106924411e-38, 1.401298464324817e-45, 7e-46, 1e300, -1e300])]
+    f = rng.standard_normal(100_000).astype(np.float32)
+    nxt = np.nextafter(f, np.float32(np.inf))
+    vals.append((f.astype(np.float64) + nxt.astype(np.float64)) / 2)     # exact ties
+    x = torch.from_numpy(np.concatenate(vals)).cuda()
+    count = torch.zeros(2, dtype=torch.int64, device="cuda")
+    rc = N.lib.fe_selftest_conversions(ctypes.c_void_p(x.data_ptr()), x.numel(),
+                                       ctypes.c_void_p(count.data_ptr()), None)
+    assert rc == 0
+    assert count.tolist() == [0, 0]
