@@ -86,6 +86,9 @@ enum fe_precision {
 
 /* Flags for fe_form.flags */
 #define FE_FLAG_ACCUMULATE 1u  /* y += A(u) instead of y = A(u) */
+#define FE_FLAG_COOPERATIVE 2u /* use the cells-per-CTA kernel even where a
+                                  thread-per-cell kernel exists for the degree
+                                  (it is always used where none exists)      */
 
 /* Mesh: affine simplices with P_degree Lagrange DoFs (Sec. "Background",
  * Ciarlet triple and local-to-global maps iota_T).  All pointers are device
@@ -188,7 +191,7 @@ typedef struct fe_plan_info {
     int32_t nq;               /* quadrature points per cell                        */
     int32_t n_loc;            /* local nodes per cell                              */
     int32_t ncomp;            /* components per node                               */
-    int32_t kernel;           /* variant id: 0 thread-per-cell                     */
+    int32_t kernel;           /* variant id: 0 thread-per-cell, 1 cells-per-CTA    */
     int32_t threads_per_block;
     int32_t grid_blocks;      /* blocks launched per action                        */
     int64_t n_dofs;           /* n_nodes * ncomp                                   */

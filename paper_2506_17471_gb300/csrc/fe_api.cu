@@ -8,7 +8,7 @@
 #include <vector>
 
 #include "fe_internal.h"
-#include "fe_kernels.cuh"
+#include "fe_coop.cuh"
 
 namespace fe {
 namespace {
@@ -24,18 +24,37 @@ void init_registry()
     n += register_variants_2d_linear(g_variants + n, kMaxVariants - n);
     n += register_variants_2d_nh(g_variants + n, kMaxVariants - n);
     n += register_variants_3d(g_variants + n, kMaxVariants - n);
+    n += register_variants_coop(g_variants + n, kMaxVariants - n);
     g_nvariants = n;
 }
 
-const Variant *find_variant(int form, int dim, int degree, int op, int precision)
+// The thread-per-cell variant compiled for exactly this degree, else (or when
+// forced) the cooperative variant, which serves every degree.
+const Variant *find_variant(int form, int dim, int degree, int op, int precision, bool force_coop)
 {
     std::call_once(g_once, init_registry);
+    const Variant *coop = nullptr;
     for (int i = 0; i < g_nvariants; ++i) {
         const Variant &v = g_variants[i];
-        if (v.form == form && v.dim == dim && v.degree == degree && v.op == op && v.precision == precision)
-            return &v;
+        if (v.form != form || v.dim != dim || v.op != op || v.precision != precision) continue;
+        if (v.kernel_id == 1) coop = &v;
+        else if (v.degree == degree && !force_coop) return &v;
     }
-    return nullptr;
+    return coop;
+}
+
+// Largest cell batch whose shared-memory plan leaves room for two CTAs per SM
+// (at most 64 cells, at least 1).
+int coop_cells_for(int n, int nq, int dim, int ncomp, int fields, size_t esz, size_t budget)
+{
+    int best = 1;
+    for (int C = 1; C <= 64; ++C) {
+        const size_t total = esz == sizeof(float)
+                                 ? coop_layout<float>(n, nq, dim, ncomp, C, fields).total
+                                 : coop_layout<double>(n, nq, dim, ncomp, C, fields).total;
+        if (total <= budget) best = C;
+    }
+    return best;
 }
 
 // Algorithmic FP64 flops of Algorithm 2 for one cell (multiply and add count 1
@@ -117,14 +136,14 @@ cudaError_t launch_zero(double *y, long long n, cudaStream_t s)
 
 int ncomp_of(int kind, int dim) { return kind == FE_FORM_MASS ? 1 : dim; }
 
-int grid_for(const Variant &v, size_t smem, int n_cells)
+int grid_for(const Variant &v, size_t smem, int n_cells, int cells_per_cta)
 {
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, v.func, v.block, smem) != cudaSuccess ||
         per_sm < 1)
         per_sm = 1;
     const long long full = (long long)per_sm * num_sms();
-    const long long want = ((long long)n_cells + v.block - 1) / v.block;
+    const long long want = ((long long)n_cells + cells_per_cta - 1) / cells_per_cta;
     long long g = want < full ? want : full;
     return (int)(g < 1 ? 1 : g);
 }
@@ -183,10 +202,13 @@ extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan 
     const int ncomp = ncomp_of(f.kind, m.dim);
     if ((long long)m.n_nodes * ncomp >= (1ll << 31)) return FE_ERR_INVALID_ARG;
 
-    const Variant *v = find_variant(f.kind, m.dim, m.degree, 0, f.precision);
+    const bool force_coop = (f.flags & FE_FLAG_COOPERATIVE) != 0;
+    const Variant *v = find_variant(f.kind, m.dim, m.degree, 0, f.precision, force_coop);
     if (!v) return FE_ERR_UNSUPPORTED;
-    const Variant *adj =
-        (f.kind == FE_FORM_NH_RESIDUAL) ? find_variant(f.kind, m.dim, m.degree, 1, f.precision) : nullptr;
+    const Variant *adj = (f.kind == FE_FORM_NH_RESIDUAL)
+                             ? find_variant(f.kind, m.dim, m.degree, 1, f.precision, force_coop)
+                             : nullptr;
+    if (adj && adj->kernel_id != v->kernel_id) adj = find_variant(f.kind, m.dim, m.degree, 1, f.precision, true);
 
     // host tabulation -> device table block [nq][1+d][n] + wts[nq], padded to 16 B
     int nq = 0;
@@ -196,13 +218,31 @@ extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan 
     std::vector<double> pts((size_t)nq * m.dim), wts(nq), tab((size_t)(1 + m.dim) * nq * n);
     int rc = fe_tabulate(m.dim, m.degree, f.quad_degree, &nq, pts.data(), wts.data(), tab.data(), tab.size());
     if (rc != FE_OK) return rc;
-    // table block: tab [nq][1+d][n] in the contraction precision, padded to 8 B,
-    // the weights [nq] in double, the weights [nq] in the contraction precision;
-    // the block is padded to 16 B (bulk copy)
+    // table block.  Thread-per-cell: tab [nq][1+d][n] in the contraction
+    // precision, padded to 8 B, the weights [nq] in double, the weights [nq] in
+    // the contraction precision, padded to 16 B.  Cooperative: the same with the
+    // per-point row stride padded to an odd element count, followed in shared
+    // memory by the batch scratch (not staged).
     const size_t esz = f.precision == FE_PREC_FP32 ? sizeof(float) : sizeof(double);
-    const size_t woff = ((size_t)nq * (1 + m.dim) * n * esz + 7) & ~(size_t)7;
-    const size_t smem = (woff + (size_t)nq * (sizeof(double) + esz) + 15) & ~(size_t)15;
-    const int tab_doubles = (int)(smem / sizeof(double));
+    const bool coop = v->kernel_id == 1;
+    const int fields_max = (f.kind == FE_FORM_NH_JACOBIAN || (adj != nullptr)) ? 2 : 1;
+    int coop_cells = 0;
+    size_t rs = (size_t)(1 + m.dim) * n, woff, smem, block_bytes;
+    if (coop) {
+        coop_cells = coop_cells_for(n, nq, m.dim, ncomp, fields_max, esz, 100 * 1024);
+        if (esz == sizeof(float)) {
+            const CoopLayout L = coop_layout<float>(n, nq, m.dim, ncomp, coop_cells, fields_max);
+            rs = L.rs; woff = L.wts_off; block_bytes = L.table_block_bytes; smem = L.total;
+        } else {
+            const CoopLayout L = coop_layout<double>(n, nq, m.dim, ncomp, coop_cells, fields_max);
+            rs = L.rs; woff = L.wts_off; block_bytes = L.table_block_bytes; smem = L.total;
+        }
+    } else {
+        woff = ((size_t)nq * rs * esz + 7) & ~(size_t)7;
+        block_bytes = (woff + (size_t)nq * (sizeof(double) + esz) + 15) & ~(size_t)15;
+        smem = block_bytes;
+    }
+    const int tab_doubles = (int)(block_bytes / sizeof(double));
     if (smem > 200 * 1024) return FE_ERR_UNSUPPORTED;
     std::vector<double> block(tab_doubles, 0.0);
     unsigned char *blk = reinterpret_cast<unsigned char *>(block.data());
@@ -210,7 +250,7 @@ extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan 
         for (int k = 0; k <= m.dim; ++k)
             for (int j = 0; j < n; ++j) {
                 const double t = tab[((size_t)k * nq + q) * n + j];
-                const size_t idx = ((size_t)q * (1 + m.dim) + k) * n + j;
+                const size_t idx = (size_t)q * rs + (size_t)k * n + j;
                 if (esz == sizeof(float))
                     reinterpret_cast<float *>(blk)[idx] = (float)t;
                 else
@@ -236,7 +276,8 @@ extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan 
     p->adj = adj ? *adj : Variant{};
     p->smem_bytes = smem;
     cudaGetDevice(&p->device);
-    if (cudaMalloc(&p->d_tab, smem) != cudaSuccess ||
+    p->coop_cells = coop_cells;
+    if (cudaMalloc(&p->d_tab, block_bytes) != cudaSuccess ||
         cudaMalloc(&p->d_status, 8 * sizeof(int32_t)) != cudaSuccess) {
         cudaFree(p->d_tab);
         delete p;
@@ -244,7 +285,7 @@ extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan 
         return FE_ERR_NO_MEMORY;
     }
     p->d_sched = p->d_status + 4;  // status word, padding, then the queue counters
-    if (cudaMemcpy(p->d_tab, block.data(), smem, cudaMemcpyHostToDevice) != cudaSuccess ||
+    if (cudaMemcpy(p->d_tab, block.data(), block_bytes, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(p->d_status, 0, 8 * sizeof(int32_t)) != cudaSuccess) {
         fe_plan_destroy(p);
         return FE_ERR_CUDA;
@@ -255,8 +296,8 @@ extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan 
         fe_plan_destroy(p);
         return FE_ERR_CUDA;
     }
-    p->grid_blocks = grid_for(*v, smem, m.n_cells);
-    p->adj_grid_blocks = adj ? grid_for(*adj, smem, m.n_cells) : 0;
+    p->grid_blocks = grid_for(*v, smem, m.n_cells, coop ? coop_cells : v->block);
+    p->adj_grid_blocks = adj ? grid_for(*adj, smem, m.n_cells, coop ? coop_cells : adj->block) : 0;
     p->flops_per_cell = algorithmic_flops(f.kind, m.dim, n, nq);
     const double dofs = (double)m.n_nodes * ncomp;
     double bytes = 2.0 * dofs * 8.0 + (double)m.n_vertices * m.dim * 8.0 +
@@ -300,6 +341,8 @@ static ActionArgs make_args(const fe_plan *p, const double *u, double *y)
     a.n_nodes = p->mesh.n_nodes;
     a.status = p->d_status;
     a.sched = p->d_sched;
+    a.coop_n = p->n_loc;
+    a.coop_cells = p->coop_cells;
     return a;
 }
 

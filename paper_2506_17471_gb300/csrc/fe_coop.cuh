@@ -1,0 +1,348 @@
+// Cooperative (cells-per-CTA) action kernel for high-degree elements.
+//
+// Thread-per-cell keeps a cell's DoFs and outputs in registers; from about 60
+// doubles of per-cell state upwards (Neo-Hookean Jacobian P6 in 2D,
+// elasticity P3+ in 3D) that spills.  This kernel splits Algorithm 2's phases
+// across the threads of a CTA instead, for a batch of C cells at a time (the
+// role of the paper's multi-level tiling with N_c cells per work-group, Sec.
+// "Multi-level Tiling"; here the whole tabulation fits in shared memory, so the
+// tables are not tiled):
+//   A  gather: nodes, vertex coordinates and DoFs of the batch into shared
+//      memory; one thread per cell forms J^{-1}, |det J| (FP64);
+//   B  evaluation + pointwise: one thread per (cell, quadrature point) computes
+//      the reference gradients from the shared DoFs, maps them, evaluates the
+//      pointwise form and writes e[c][q][k][comp] to shared memory;
+//   C  quadrature + scatter: one thread per (cell, node) contracts e with the
+//      test tabulation and scatter-adds its components with FP64 atomics.
+// The degree and the rule are runtime values, so one instantiation per
+// (operation, dimension, contraction type) serves every degree.
+// Shared-memory strides are odd (in 8-byte words for double, 4-byte for float)
+// so that threads reading consecutive quadrature points or cells hit distinct
+// banks.
+#pragma once
+
+#include "fe_kernels.cuh"
+
+namespace fe {
+
+constexpr int kCoopBlock = 256;
+
+// Shared-memory plan of one CTA, computed identically on host and device.
+struct CoopLayout {
+    int n, nq, D, NC, C, fields;
+    int rs;        // table row stride per quadrature point (elements), odd
+    int ls;        // per-cell DoF stride (doubles), odd
+    int es;        // per-(cell, q) stride of e (elements), odd
+    size_t tab_bytes, wts_off, wtsr_off, table_block_bytes;   // the staged table block
+    size_t off_l, off_e, off_nodes, off_geo, off_acc, total;
+};
+
+template <typename R>
+__host__ __device__ inline CoopLayout coop_layout(int n, int nq, int D, int NC, int C, int fields)
+{
+    CoopLayout L;
+    L.n = n;
+    L.nq = nq;
+    L.D = D;
+    L.NC = NC;
+    L.C = C;
+    L.fields = fields;
+    L.rs = ((1 + D) * n) | 1;
+    L.ls = (fields * n * NC) | 1;
+    L.es = (D * NC) | 1;
+    L.tab_bytes = (size_t)nq * L.rs * sizeof(R);
+    L.wts_off = (L.tab_bytes + 7) & ~(size_t)7;
+    L.wtsr_off = L.wts_off + (size_t)nq * sizeof(double);
+    L.table_block_bytes = (L.wtsr_off + (size_t)nq * sizeof(R) + 15) & ~(size_t)15;
+    L.off_l = L.table_block_bytes;
+    L.off_e = (L.off_l + (size_t)C * L.ls * sizeof(double) + 15) & ~(size_t)15;
+    L.off_nodes = (L.off_e + (size_t)C * nq * L.es * sizeof(R) + 15) & ~(size_t)15;
+    L.off_geo = (L.off_nodes + (size_t)C * n * sizeof(int) + 15) & ~(size_t)15;
+    // per cell: Jinv (D*D), |det J|, mu, lam, a validity flag -> 16 doubles
+    L.off_acc = L.off_geo + (size_t)C * 16 * sizeof(double);
+    // adjoint accumulators dmu, dlam per cell
+    L.total = (L.off_acc + (size_t)C * 2 * sizeof(double) + 15) & ~(size_t)15;
+    return L;
+}
+
+template <int OP, int D, typename R>
+__global__ void __launch_bounds__(kCoopBlock) k_action_coop(const ActionArgs a, const int n, const int C)
+{
+    constexpr int NC = OpTraits<OP, D>::NC;
+    constexpr int FIELDS = OpTraits<OP, D>::kTwoFields ? 2 : 1;
+    extern __shared__ __align__(128) double smem[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int s_chunk;
+    const CoopLayout L = coop_layout<R>(n, a.nq, D, NC, C, FIELDS);
+    unsigned char *base = reinterpret_cast<unsigned char *>(smem);
+    if (!stage_table(smem, a.tab, a.tab_doubles, &bar, a.status)) {
+        leave_queue(a.sched);
+        return;
+    }
+    const R *tab = reinterpret_cast<const R *>(base);
+    const double *wts = reinterpret_cast<const double *>(base + L.wts_off);
+    const R *wts_r = reinterpret_cast<const R *>(base + L.wtsr_off);
+    double *sl = reinterpret_cast<double *>(base + L.off_l);
+    R *se = reinterpret_cast<R *>(base + L.off_e);
+    int *snodes = reinterpret_cast<int *>(base + L.off_nodes);
+    double *sgeo = reinterpret_cast<double *>(base + L.off_geo);
+    double *sacc = reinterpret_cast<double *>(base + L.off_acc);
+    const int nq = a.nq;
+    const int n_batches = (a.n_cells + C - 1) / C;
+
+    for (;;) {
+        if (threadIdx.x == 0) s_chunk = atomicAdd(a.sched, 1);
+        __syncthreads();
+        const int batch = s_chunk;
+        if (batch >= n_batches) break;
+        const int cell0 = batch * C;
+        const int nb = min(C, a.n_cells - cell0);
+
+        // ---- A: gather nodes and DoFs; geometry (one thread per cell)
+        for (int i = threadIdx.x; i < nb * n; i += blockDim.x) {
+            const int c = i / n, j = i - c * n;
+            const int node = __ldg(a.c2n + (size_t)(cell0 + c) * n + j);
+            const bool ok = (unsigned)node < (unsigned)a.n_nodes;
+            if (!ok) set_status(a.status, FE_ERR_INDEX);
+            snodes[c * n + j] = ok ? node : -1;
+#pragma unroll
+            for (int f = 0; f < FIELDS; ++f) {
+                const double *src = (f == 0) ? a.u : a.u_lin;
+#pragma unroll
+                for (int m = 0; m < NC; ++m)
+                    sl[c * L.ls + (f * n + j) * NC + m] = ok ? __ldg(src + (size_t)node * NC + m) : 0.0;
+            }
+        }
+        for (int c = threadIdx.x; c < nb; c += blockDim.x) {
+            const int cell = cell0 + c;
+            double X[D + 1][D];
+            bool ok = true;
+#pragma unroll
+            for (int m = 0; m <= D; ++m) {
+                const int v = __ldg(a.c2v + (size_t)cell * (D + 1) + m);
+                ok &= (unsigned)v < (unsigned)a.n_vertices;
+#pragma unroll
+                for (int i = 0; i < D; ++i) X[m][i] = ok ? __ldg(a.coords + (size_t)v * D + i) : 0.0;
+            }
+            double Jinv[D][D];
+            const double det = cell_geometry<D>(X, Jinv);
+            double *g = sgeo + c * 16;
+            const bool good = ok && (det != 0.0) && isfinite(det);
+            if (!ok) set_status(a.status, FE_ERR_INDEX);
+            else if (!good) set_status(a.status, FE_ERR_BAD_MESH);
+#pragma unroll
+            for (int i = 0; i < D; ++i)
+#pragma unroll
+                for (int k = 0; k < D; ++k) g[i * D + k] = good ? Jinv[i][k] : 0.0;
+            g[D * D] = good ? fabs(det) : 0.0;
+            g[D * D + 1] = (OpTraits<OP, D>::kCellCoeff && a.mu_cell) ? __ldg(a.mu_cell + cell) : a.mu;
+            g[D * D + 2] = (OpTraits<OP, D>::kCellCoeff && a.lam_cell) ? __ldg(a.lam_cell + cell) : a.lam;
+            g[D * D + 3] = good ? 1.0 : 0.0;
+            sacc[2 * c] = 0.0;
+            sacc[2 * c + 1] = 0.0;
+        }
+        __syncthreads();
+
+        // ---- B: evaluation + pointwise per (cell, quadrature point)
+        bool nh_ok = true;
+        for (int i = threadIdx.x; i < nb * nq; i += blockDim.x) {
+            const int c = i / nq, q = i - c * nq;
+            const double *g = sgeo + c * 16;
+            const R *T = tab + (size_t)q * L.rs;
+            const double *lc = sl + c * L.ls;
+            R *e = se + ((size_t)c * nq + q) * L.es;
+            const double absdet = g[D * D];
+            double Jinv[D][D];
+#pragma unroll
+            for (int ii = 0; ii < D; ++ii)
+#pragma unroll
+                for (int k = 0; k < D; ++k) Jinv[ii][k] = g[ii * D + k];
+            const double mu = g[D * D + 1], lam = g[D * D + 2];
+            if constexpr (OP == OP_MASS) {
+                R uq = R(0);
+                for (int j = 0; j < n; ++j) uq = fma(T[j], cvt<R>(lc[j]), uq);
+                e[0] = uq * (wts_r[q] * cvt<R>(absdet));
+            } else {
+                // reference gradients of the field(s) at q
+                R gh[FIELDS][NC][D];
+#pragma unroll
+                for (int f = 0; f < FIELDS; ++f)
+#pragma unroll
+                    for (int m = 0; m < NC; ++m)
+#pragma unroll
+                        for (int k = 0; k < D; ++k) gh[f][m][k] = R(0);
+                for (int j = 0; j < n; ++j) {
+                    R t[D];
+#pragma unroll
+                    for (int k = 0; k < D; ++k) t[k] = T[(k + 1) * n + j];
+#pragma unroll
+                    for (int f = 0; f < FIELDS; ++f)
+#pragma unroll
+                        for (int m = 0; m < NC; ++m) {
+                            const R lv = cvt<R>(lc[(f * n + j) * NC + m]);
+#pragma unroll
+                            for (int k = 0; k < D; ++k) gh[f][m][k] = fma(t[k], lv, gh[f][m][k]);
+                        }
+                }
+                if constexpr (OP == OP_ELASTICITY) {
+                    R Jr[D][D], G[D][D], S[D][D], er[D][D];
+                    convert<D, D>(Jinv, Jr);
+                    map_grad<D, R>(gh[0], Jr, G);
+                    R tr = G[0][0];
+#pragma unroll
+                    for (int ii = 1; ii < D; ++ii) tr += G[ii][ii];
+                    const R wdet_r = wts_r[q] * cvt<R>(absdet);
+                    const R smu = wdet_r * cvt<R>(mu);
+                    const R slt = wdet_r * cvt<R>(lam) * tr;
+#pragma unroll
+                    for (int ii = 0; ii < D; ++ii) {
+                        S[ii][ii] = fma(R(2) * smu, G[ii][ii], slt);
+#pragma unroll
+                        for (int k = ii + 1; k < D; ++k) {
+                            const R s = smu * (G[ii][k] + G[k][ii]);
+                            S[ii][k] = s;
+                            S[k][ii] = s;
+                        }
+                    }
+                    pull_back<D, R>(S, Jr, er);
+#pragma unroll
+                    for (int m = 0; m < NC; ++m)
+#pragma unroll
+                        for (int k = 0; k < D; ++k) e[m * D + k] = er[m][k];
+                } else {
+                    const double wdet = wts[q] * absdet;
+                    double ghd[D][D], F[D][D], C2[D][D], S[D][D], ed[D][D];
+                    // the field whose gradient forms F: u (residual) or u_lin (tangent)
+                    convert<D, D>(gh[FIELDS - 1], ghd);
+                    map_grad<D, double>(ghd, Jinv, F);
+#pragma unroll
+                    for (int ii = 0; ii < D; ++ii) F[ii][ii] += 1.0;
+                    const double Jd = det_cof<D>(F, C2);
+                    nh_ok &= (Jd > 0.0);
+                    const double lnJ = log(Jd);
+                    if constexpr (OP == OP_NH_RESIDUAL) {
+                        const double smu = wdet * mu;
+                        const double scf = wdet * fma(lam, lnJ, -mu) / Jd;
+#pragma unroll
+                        for (int ii = 0; ii < D; ++ii)
+#pragma unroll
+                            for (int k = 0; k < D; ++k) S[ii][k] = fma(smu, F[ii][k], scf * C2[ii][k]);
+                    } else {
+                        double H[D][D], Fit[D][D], A[D][D];
+                        convert<D, D>(gh[0], ghd);
+                        map_grad<D, double>(ghd, Jinv, H);
+                        const double rJ = 1.0 / Jd;
+                        double tr = 0.0;
+#pragma unroll
+                        for (int ii = 0; ii < D; ++ii)
+#pragma unroll
+                            for (int k = 0; k < D; ++k) {
+                                Fit[ii][k] = C2[ii][k] * rJ;
+                                tr = fma(Fit[ii][k], H[ii][k], tr);
+                            }
+#pragma unroll
+                        for (int ii = 0; ii < D; ++ii)
+#pragma unroll
+                            for (int k = 0; k < D; ++k) {
+                                double s = Fit[ii][0] * H[k][0];
+#pragma unroll
+                                for (int mm = 1; mm < D; ++mm) s = fma(Fit[ii][mm], H[k][mm], s);
+                                A[ii][k] = s;
+                            }
+                        const double smu = wdet * mu;
+                        const double sm2 = wdet * fma(-lam, lnJ, mu);
+                        const double str = wdet * lam * tr;
+#pragma unroll
+                        for (int ii = 0; ii < D; ++ii)
+#pragma unroll
+                            for (int k = 0; k < D; ++k) {
+                                double m = A[ii][0] * Fit[0][k];
+#pragma unroll
+                                for (int mm = 1; mm < D; ++mm) m = fma(A[ii][mm], Fit[mm][k], m);
+                                S[ii][k] = fma(smu, H[ii][k], fma(sm2, m, str * Fit[ii][k]));
+                            }
+                        if constexpr (OP == OP_NH_ADJOINT) {
+                            double amu = 0.0, alam = 0.0;
+#pragma unroll
+                            for (int ii = 0; ii < D; ++ii)
+#pragma unroll
+                                for (int k = 0; k < D; ++k) {
+                                    amu = fma(wdet * (F[ii][k] - Fit[ii][k]), H[ii][k], amu);
+                                    alam = fma(wdet * lnJ * Fit[ii][k], H[ii][k], alam);
+                                }
+                            atomicAdd(sacc + 2 * c, amu);       // shared-memory FP64 atomics
+                            atomicAdd(sacc + 2 * c + 1, alam);
+                        }
+                    }
+                    pull_back<D, double>(S, Jinv, ed);
+#pragma unroll
+                    for (int m = 0; m < NC; ++m)
+#pragma unroll
+                        for (int k = 0; k < D; ++k) e[m * D + k] = cvt<R>(ed[m][k]);
+                }
+            }
+        }
+        if (!nh_ok) set_status(a.status, FE_ERR_NONFINITE);
+        __syncthreads();
+
+        // ---- C: quadrature contraction + scatter per (cell, node)
+        for (int i = threadIdx.x; i < nb * n; i += blockDim.x) {
+            const int c = i / n, j = i - c * n;
+            const int node = snodes[c * n + j];
+            if (node < 0 || sgeo[c * 16 + D * D + 3] == 0.0) continue;
+            R out[NC];
+#pragma unroll
+            for (int m = 0; m < NC; ++m) out[m] = R(0);
+            const R *ec = se + (size_t)c * nq * L.es;
+            for (int q = 0; q < nq; ++q) {
+                const R *T = tab + (size_t)q * L.rs;
+                const R *e = ec + (size_t)q * L.es;
+                if constexpr (OP == OP_MASS) {
+                    out[0] = fma(T[j], e[0], out[0]);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < D; ++k) {
+                        const R t = T[(k + 1) * n + j];
+#pragma unroll
+                        for (int m = 0; m < NC; ++m) out[m] = fma(t, e[m * D + k], out[m]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int m = 0; m < NC; ++m) atomicAdd(a.y + (size_t)node * NC + m, cvt<double>(out[m]));
+        }
+        if constexpr (OP == OP_NH_ADJOINT) {
+            for (int c = threadIdx.x; c < nb; c += blockDim.x) {
+                a.dmu[cell0 + c] = sacc[2 * c];
+                a.dlam[cell0 + c] = sacc[2 * c + 1];
+            }
+        }
+        __syncthreads();   // the batch's shared state is reused by the next batch
+    }
+    leave_queue(a.sched);
+}
+
+template <int OP, int D, typename R>
+cudaError_t launch_coop(const ActionArgs &a, int grid, int block, size_t smem, cudaStream_t s)
+{
+    k_action_coop<OP, D, R><<<grid, block, smem, s>>>(a, a.coop_n, a.coop_cells);
+    return cudaGetLastError();
+}
+
+template <int OP, int D, typename R = double>
+Variant make_coop_variant()
+{
+    Variant v;
+    v.form = OP == OP_NH_ADJOINT ? OP_NH_RESIDUAL : OP;
+    v.dim = D;
+    v.degree = 0;   // any degree
+    v.op = OP == OP_NH_ADJOINT ? 1 : 0;
+    v.precision = std::is_same<R, double>::value ? FE_PREC_FP64 : FE_PREC_FP32;
+    v.kernel_id = 1;
+    v.block = kCoopBlock;
+    v.launch = &launch_coop<OP, D, R>;
+    v.func = reinterpret_cast<const void *>(&k_action_coop<OP, D, R>);
+    return v;
+}
+
+}  // namespace fe

@@ -34,6 +34,8 @@ struct ActionArgs {
     int32_t n_cells, n_vertices, n_nodes;
     int32_t *status;          // device status word (first error wins)
     int32_t *sched;           // [2] work-queue counters: next chunk, warps finished (self-resetting)
+    int32_t coop_n;           // cooperative kernel: local nodes per cell
+    int32_t coop_cells;       // cooperative kernel: cells per CTA batch
 };
 
 // Launch function of one compiled kernel variant.
@@ -55,6 +57,7 @@ struct Variant {
 int register_variants_2d_linear(Variant *out, int cap);
 int register_variants_2d_nh(Variant *out, int cap);
 int register_variants_3d(Variant *out, int cap);
+int register_variants_coop(Variant *out, int cap);
 
 }  // namespace fe
 
@@ -72,6 +75,7 @@ struct fe_plan {
     int grid_blocks;
     int adj_grid_blocks;
     size_t smem_bytes;
+    int coop_cells;       // cells per CTA batch (cooperative kernel), else 0
     int device;
     double flops_per_cell;
     double bytes_min;
