@@ -30,6 +30,7 @@
  */
 #include <math.h>
 #include <stdint.h>
+#include <stdlib.h>
 #include <string.h>
 
 #define ORC_MAXD 3
@@ -387,23 +388,24 @@ int orc_nh_adjoint(int dim, int nloc, int nq, const double *wts, const double *t
                    const double *u, const double *w, double *jtw, double *dmu, double *dlam,
                    long c0, long c1)
 {
-    if (!check_args(dim, nloc) || nloc * dim > 96) return 3;
-    enum { NMAX = 96 };
-    double K[NMAX][NMAX]; /* element tangent, on the stack: callers may run in threads */
+    if (!check_args(dim, nloc)) return 3;
+    enum { NMAX = ORC_MAXLOC * ORC_MAXD };
+    const int nd = nloc * dim;
+    double *K = (double *)malloc(sizeof(double) * (size_t)nd * nd); /* element tangent, per call */
+    if (!K) return 3;
     double X[ORC_MAXD + 1][ORC_MAXD], J[ORC_MAXD][ORC_MAXD], Jinv[ORC_MAXD][ORC_MAXD], detJ;
     double l[NMAX], wl[NMAX], out[NMAX];
     double gh[ORC_MAXD][ORC_MAXD], G[ORC_MAXD][ORC_MAXD], F[ORC_MAXD][ORC_MAXD],
         Finv[ORC_MAXD][ORC_MAXD], W[ORC_MAXD][ORC_MAXD];
     double dphi[ORC_MAXLOC][ORC_MAXD];
-    const int nd = nloc * dim;
-    for (long c = c0; c < c1; ++c) {
+    int rc = 0;
+    for (long c = c0; c < c1 && rc == 0; ++c) {
         gather_coords(dim, c, c2v, coords, X);
         gather_dofs(dim, nloc, c, c2n, u, l);
         gather_dofs(dim, nloc, c, c2n, w, wl);
         const double mu = mu_cell[c], lam = lam_cell[c];
-        if (!geometry(dim, X, J, &detJ, Jinv)) return 1;
-        for (int r = 0; r < nd; ++r)
-            for (int s = 0; s < nd; ++s) K[r][s] = 0.0;
+        if (!geometry(dim, X, J, &detJ, Jinv)) { rc = 1; break; }
+        for (int r = 0; r < nd * nd; ++r) K[r] = 0.0;
         double smu = 0.0, slam = 0.0;
         for (int q = 0; q < nq; ++q) {
             const double meas = wts[q] * fabs(detJ);
@@ -412,7 +414,7 @@ int orc_nh_adjoint(int dim, int nloc, int nq, const double *wts, const double *t
             eval_ref_grad(dim, dim, nloc, nq, tab, q, wl, gh);
             to_physical(dim, dim, gh, Jinv, W);
             double Jd;
-            if (!nh_kinematics(dim, G, F, &Jd, Finv)) return 2;
+            if (!nh_kinematics(dim, G, F, &Jd, Finv)) { rc = 2; break; }
             const double lnJ = log(Jd);
             for (int a = 0; a < dim; ++a)
                 for (int b = 0; b < dim; ++b) {
@@ -438,17 +440,19 @@ int orc_nh_adjoint(int dim, int nloc, int nq, const double *wts, const double *t
                                              + lam * Finv[i][a] * Finv[k][b];
                                     s += dphi[j][i] * A * dphi[m][k];
                                 }
-                            K[j * dim + a][m * dim + b] += meas * s;
+                            K[(size_t)(j * dim + a) * nd + m * dim + b] += meas * s;
                         }
         }
+        if (rc) break;
         for (int s = 0; s < nd; ++s) {
             double acc = 0.0;
-            for (int r = 0; r < nd; ++r) acc += K[r][s] * wl[r];
+            for (int r = 0; r < nd; ++r) acc += K[(size_t)r * nd + s] * wl[r];
             out[s] = acc;
         }
         scatter_dofs(dim, nloc, c, c2n, out, jtw);
         dmu[c] += smu;
         dlam[c] += slam;
     }
-    return 0;
+    free(K);
+    return rc;
 }

@@ -18,6 +18,11 @@ from feinputs.fields import sinusoid_displacement
 pytestmark = pytest.mark.gpu
 TOL = 1e-12
 TOL32 = 5e-5
+# Neo-Hookean tangent linearised at the smooth sinusoid field on the fine P6 mesh:
+# FP64 conditioning (tests/test_oracle_conditioning.py) puts independent
+# evaluations ~1e-12 apart; parity there is 1e-11, and a small random
+# linearisation point (well conditioned) is held to 1e-12.
+TOL_NH_SMOOTH = 1e-11
 
 
 @pytest.fixture(scope="module")
@@ -131,13 +136,20 @@ def test_hp_sweep_full_size(fe, name, dim, p, N, q):
         fn = lambda o, cells: o.nh_jacobian(ul, du, mu[cells] if len(cells) < m.n_cells else mu,
                                             lam[cells] if len(cells) < m.n_cells else lam, threads=16)
         ncomp = 2
+    tol = TOL_NH_SMOOTH if name == "nh_jacobian_p6_2d" else TOL
     if not big:
         o = oracle.Oracle.from_mesh(m, q)
         ref = fn(o, np.arange(m.n_cells))
-        assert rel(y, ref) <= TOL
+        assert rel(y, ref) <= tol
+        if name == "nh_jacobian_p6_2d":
+            # well-conditioned linearisation point: random, small enough for det F > 0
+            ur = uniform_field(m.n_nodes * 2, 5) * (0.1 / (p * N))
+            plan.set_linearisation(cuda(ur))
+            yr = plan.apply(cuda(du)).cpu().numpy()
+            assert rel(yr, o.nh_jacobian(ur, du, mu, lam, threads=16)) <= TOL
     else:
         rng = np.random.default_rng(N)
         nodes = rng.choice(m.n_nodes, size=64, replace=False)
         ref = sampled_oracle(m, q, nodes, fn)
         idx = (nodes[:, None] * ncomp + np.arange(ncomp)[None, :]).reshape(-1)
-        assert np.abs(y[idx] - ref[idx]).max() <= TOL * np.abs(y).max()
+        assert np.abs(y[idx] - ref[idx]).max() <= tol * np.abs(y).max()

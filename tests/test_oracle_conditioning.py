@@ -38,3 +38,21 @@ def test_nh_residual_smooth_field_sensitivity(oracle_built):
     assert dj < 5e-13, dj              # rough-direction Jacobian: well conditioned
     assert ddmu < 2e-12, ddmu          # dmu uses the same smooth-field gradients
     print(f"sensitivity: residual {dr:.2e}, jacobian {dj:.2e}, dmu {ddmu:.2e}")
+
+
+def test_nh_jacobian_p6_smooth_linearisation_sensitivity(oracle_built):
+    """hp-sweep Neo-Hookean Jacobian (P6 triangles, 236^2 x 2 cells): linearised at
+    the smooth sinusoid field, a half-ulp tabulation change moves the oracle's own
+    result by ~5e-13, so an independent FP64 evaluation differing in operation
+    order lands at ~1e-12; the parity tolerance there is 1e-11."""
+    m = structured_mesh(2, 236, 6, jitter=0.2, seed=20250620 + 236)
+    o = oracle.Oracle.from_mesh(m, 12)
+    mu, lam = lame_fields(m.n_cells, 2)
+    ul = sinusoid_displacement(m, 3)
+    du = uniform_field(m.n_nodes * 2, 4)
+    j = o.nh_jacobian(ul, du, mu, lam, threads=8)
+    rng = np.random.default_rng(0)
+    t0 = o.tab.copy()
+    o.tab = np.ascontiguousarray(t0 * (1 + 2.0 ** -53 * rng.choice([-1.0, 1.0], size=t0.shape)))
+    dj = np.abs(o.nh_jacobian(ul, du, mu, lam, threads=8) - j).max() / np.abs(j).max()
+    assert 1e-13 < dj < 5e-12, dj
