@@ -281,6 +281,60 @@ def time_secondary(fe, torch, flush, M_el, u_el, y64_el):
                                           "dofs_per_s": m.n_nodes / t,
                                           "gflops": plan.flops() / t / 1e9}
     out["mass_p3_2d_n667_fp32"]["rel_dev_vs_fp64"] = rel(ys["fp32"], ys["fp64"])
+
+    # CG with FP64 refinement on the P3 mass system (~4M DoFs)
+    p64 = fe.Plan(M, fe.MASS, 6)
+    p32 = fe.Plan(M, fe.MASS, 6, precision="fp32")
+    xs = torch.from_numpy(uniform_field(m.n_nodes, 7)).cuda()
+    b = torch.empty_like(xs)
+    p64.apply(xs, b)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, st64 = solvers.cg(lambda a, c: p64.apply(a, c), b, rtol=1e-10)
+    torch.cuda.synchronize()
+    t_cg = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    _, stir = solvers.cg_ir(lambda a, c: p64.apply(a, c), lambda a, c: p32.apply(a, c), b, tol=1e-10)
+    torch.cuda.synchronize()
+    t_ir = time.perf_counter() - t0
+    out["cg_ir_mass_p3_2d_n667"] = {
+        "fp64_cg_s": t_cg, "fp64_cg_iters": st64.iterations, "fp64_cg_rel_residual": st64.rel_residual,
+        "ir_s": t_ir, "ir_outer": stir.outer, "ir_inner_iters": stir.iterations,
+        "ir_rel_residual_fp64": stir.rel_residual, "speedup": t_cg / t_ir}
+
+    # hp sweep at ~4M and ~16M DoFs, FP64 and FP32 contractions
+    hp = {}
+    for name, dim, p, N, q in (("nh_jacobian_p6_2d", 2, 6, 236, 12), ("nh_jacobian_p6_2d", 2, 6, 471, 12),
+                               ("elasticity_p4_3d", 3, 4, 27, 6), ("elasticity_p4_3d", 3, 4, 43, 6),
+                               ("mass_p3_2d", 2, 3, 667, 6), ("mass_p3_2d", 2, 3, 1333, 6)):
+        m = structured_mesh(dim, N, p, jitter=0.2 if dim == 2 else 0.15, seed=20250620 + N)
+        M = fe.Mesh(dim, p, m.coords, m.cell2vertex, m.cell2node, m.n_nodes)
+        extra_kw = {}
+        if name.startswith("nh"):
+            mu, lam = lame_fields(m.n_cells, 2)
+            extra_kw = dict(mu_cell=mu, lam_cell=lam,
+                            u_lin=torch.from_numpy(sinusoid_displacement(m, 3)).cuda())
+            kind, nc = fe.NH_JACOBIAN, 2
+        elif name.startswith("elasticity"):
+            extra_kw = dict(lam=1.25, mu=1.0)
+            kind, nc = fe.ELASTICITY, 3
+        else:
+            kind, nc = fe.MASS, 1
+        u = torch.from_numpy(uniform_field(m.n_nodes * nc, 4)).cuda()
+        row = {"dofs": m.n_nodes * nc, "cells": m.n_cells}
+        ys = {}
+        for prec in ("fp64", "fp32"):
+            plan = fe.Plan(M, kind, q, precision=prec, **extra_kw)
+            ys[prec] = torch.empty_like(u)
+            t = timed(lambda: plan.apply(u, ys[prec]), reps=5)
+            row[prec] = {"ms": t * 1e3, "dofs_per_s": m.n_nodes * nc / t,
+                         "gflops": plan.flops() / t / 1e9, "kernel": plan.info.kernel,
+                         "nq": plan.info.nq}
+        row["fp64"]["frac_of_fp64_peak"] = row["fp64"]["gflops"] / FP64_NOMINAL_GFLOPS
+        row["fp32_speedup"] = row["fp64"]["ms"] / row["fp32"]["ms"]
+        row["fp32_rel_dev_vs_fp64"] = rel(ys["fp32"], ys["fp64"])
+        hp[f"{name}_n{N}"] = row
+    out["hp_sweep"] = hp
     return out
 
 

@@ -143,7 +143,7 @@ def test_hp_sweep_full_size(fe, name, dim, p, N, q):
         assert rel(y, ref) <= tol
         if name == "nh_jacobian_p6_2d":
             # well-conditioned linearisation point: random, small enough for det F > 0
-            ur = uniform_field(m.n_nodes * 2, 5) * (0.1 / (p * N))
+            ur = uniform_field(m.n_nodes * 2, 5) * (0.004 / (p * N))
             plan.set_linearisation(cuda(ur))
             yr = plan.apply(cuda(du)).cpu().numpy()
             assert rel(yr, o.nh_jacobian(ur, du, mu, lam, threads=16)) <= TOL
