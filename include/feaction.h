@@ -118,6 +118,10 @@ typedef struct fe_form {
     const double *lambda_cell;   /* [n_cells] or NULL                              */
     const double *mu_cell;       /* [n_cells] or NULL                              */
     const double *u_lin;         /* [n_nodes*dim] for NH_JACOBIAN, else NULL       */
+    int32_t tile_cells;          /* cells per CTA batch of the cells-per-CTA kernel
+                                    (0: the largest that leaves room for two CTAs
+                                    per SM); ignored by the thread-per-cell kernel  */
+    int32_t reserved;
 } fe_form;
 
 /* ------------------------------------------------------------------ tabulation */
@@ -201,6 +205,47 @@ typedef struct fe_plan_info {
 } fe_plan_info;
 
 int fe_plan_get_info(const fe_plan *plan, fe_plan_info *info);
+
+/* ------------------------------------------------------------------ batched persistent action */
+/* Many independent problems (meshes of uneven size, degree and form) in one
+ * persistent launch.  Each problem is a FP64 MASS, ELASTICITY or NH_RESIDUAL
+ * form on its own mesh with its own device input u and output y (same layouts
+ * as fe_action; y is overwritten).  kernel selects the device code used for
+ * the problem's tiles: -1 automatic (thread-per-cell where compiled for the
+ * degree, else cells-per-CTA), 0 thread-per-cell (tiles of 128 cells), 1
+ * cells-per-CTA with tile_cells cells per tile (0: 16).
+ * fe_batch_create validates, tabulates every problem, uploads the tables and
+ * the cost-ordered work list, and allocates the batch's device memory
+ * (synchronous).  Pointers inside the problems are borrowed and must outlive
+ * the batch.  fe_batch_run enqueues two kernels on stream: one that zeroes
+ * every y, and the persistent kernel whose CTAs pull tiles from the work list
+ * (a CTA restages a problem's table only when the problem changes).  Runs of
+ * one batch must not overlap in time.  fe_batch_status reads and clears the
+ * batch's device status word (synchronises).
+ * Errors: FE_ERR_INVALID_ARG, FE_ERR_UNSUPPORTED, FE_ERR_NO_MEMORY, FE_ERR_CUDA. */
+typedef struct fe_batch_problem {
+    fe_form form;
+    fe_mesh mesh;
+    const double *u;             /* device, n_nodes * ncomp                        */
+    double *y;                   /* device, n_nodes * ncomp                        */
+    int32_t kernel;              /* -1 auto, 0 thread-per-cell, 1 cells-per-CTA    */
+    int32_t tile_cells;          /* cells per tile for kernel 1 (0: 16)            */
+} fe_batch_problem;
+
+typedef struct fe_batch fe_batch;
+
+typedef struct fe_batch_info {
+    int32_t problems, items, grid_blocks, pad;
+    int64_t smem_bytes;
+    int64_t dofs;                /* sum of the problems' DoFs                      */
+    double contraction_flops;    /* contraction flops of all problems (Ops_usable) */
+} fe_batch_info;
+
+int fe_batch_create(const fe_batch_problem *problems, int count, fe_batch **out);
+int fe_batch_run(fe_batch *batch, void *stream);
+int fe_batch_status(fe_batch *batch, int *device_status);
+int fe_batch_get_info(const fe_batch *batch, fe_batch_info *info);
+int fe_batch_destroy(fe_batch *batch);
 
 /* ------------------------------------------------------------------ Krylov building blocks */
 /* Vector kernels for conjugate gradients with FP64 iterative refinement around

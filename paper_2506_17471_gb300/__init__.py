@@ -9,8 +9,8 @@ shared library and raises ImportError if it has not been built.
 from ._native import FeError, LIB_PATH, EXPORTS
 from .api import (MASS, ELASTICITY, NH_RESIDUAL, NH_JACOBIAN, FORM_NAMES, PRECISIONS, Mesh, Plan,
                   PlanInfo,
-                  NeoHookeanResidual, tabulate, measure_fp64_peak)
+                  NeoHookeanResidual, Batch, tabulate, measure_fp64_peak)
 
 __all__ = ["FeError", "LIB_PATH", "EXPORTS", "MASS", "ELASTICITY", "NH_RESIDUAL", "NH_JACOBIAN",
-           "FORM_NAMES", "PRECISIONS", "Mesh", "Plan", "PlanInfo", "NeoHookeanResidual", "tabulate",
+           "FORM_NAMES", "PRECISIONS", "Mesh", "Plan", "PlanInfo", "NeoHookeanResidual", "Batch", "tabulate",
            "measure_fp64_peak"]

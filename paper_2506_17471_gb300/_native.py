@@ -32,7 +32,8 @@ EXPORTS = ("fe_status_string", "fe_tabulate", "fe_plan_create", "fe_plan_destroy
            "fe_action_adjoint", "fe_action_host", "fe_plan_status", "fe_plan_get_info",
            "fe_measure_fp64_peak", "fe_action_noalloc", "fe_cg_start", "fe_cg_direction",
            "fe_cg_update", "fe_cg_new_direction", "fe_vec_axpy", "fe_vec_dot",
-           "fe_selftest_conversions")
+           "fe_selftest_conversions", "fe_batch_create", "fe_batch_run", "fe_batch_status",
+           "fe_batch_get_info", "fe_batch_destroy")
 FE_CG_PARTIALS = 1024
 FE_CG_WORKSPACE_DOUBLES = FE_CG_PARTIALS + 16
 
@@ -49,7 +50,20 @@ class FeForm(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("flags", ctypes.c_uint32),
                 ("lambda_", ctypes.c_double), ("mu", ctypes.c_double),
                 ("lambda_cell", ctypes.c_void_p), ("mu_cell", ctypes.c_void_p),
-                ("u_lin", ctypes.c_void_p)]
+                ("u_lin", ctypes.c_void_p), ("tile_cells", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class FeBatchProblem(ctypes.Structure):
+    _fields_ = [("form", FeForm), ("mesh", FeMesh), ("u", ctypes.c_void_p), ("y", ctypes.c_void_p),
+                ("kernel", ctypes.c_int32), ("tile_cells", ctypes.c_int32)]
+
+
+class FeBatchInfo(ctypes.Structure):
+    _fields_ = [("problems", ctypes.c_int32), ("items", ctypes.c_int32),
+                ("grid_blocks", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("smem_bytes", ctypes.c_int64), ("dofs", ctypes.c_int64),
+                ("contraction_flops", ctypes.c_double)]
 
 
 class FePlanInfo(ctypes.Structure):
@@ -93,6 +107,11 @@ def _load() -> ctypes.CDLL:
     lib.fe_vec_axpy.argtypes = [LL, D, P, P, P]
     lib.fe_vec_dot.argtypes = [LL, P, P, P, P, I, P]
     lib.fe_selftest_conversions.argtypes = [P, LL, P, P]
+    lib.fe_batch_create.argtypes = [ctypes.POINTER(FeBatchProblem), I, ctypes.POINTER(P)]
+    lib.fe_batch_run.argtypes = [P, P]
+    lib.fe_batch_status.argtypes = [P, ctypes.POINTER(I)]
+    lib.fe_batch_get_info.argtypes = [P, ctypes.POINTER(FeBatchInfo)]
+    lib.fe_batch_destroy.argtypes = [P]
     for name in EXPORTS:
         if name != "fe_status_string":
             getattr(lib, name).restype = I

@@ -102,7 +102,8 @@ class Plan:
 
     def __init__(self, mesh: Mesh, kind: int, quad_degree: int, *, lam: float = 0.0,
                  mu: float = 0.0, mu_cell=None, lam_cell=None, u_lin=None,
-                 accumulate: bool = False, precision: str = "fp64", cooperative: bool = False):
+                 accumulate: bool = False, precision: str = "fp64", cooperative: bool = False,
+                 tile_cells: int = 0):
         self.mesh = mesh
         self.kind = int(kind)
         self.ncomp = 1 if kind == MASS else mesh.dim
@@ -119,7 +120,8 @@ class Plan:
         self.precision = precision
         self._form = N.FeForm(self.kind, int(quad_degree), PRECISIONS[precision], flags, float(lam),
                               float(mu), _dptr(self.lam_cell).value or 0,
-                              _dptr(self.mu_cell).value or 0, _dptr(self.u_lin).value or 0)
+                              _dptr(self.mu_cell).value or 0, _dptr(self.u_lin).value or 0,
+                              int(tile_cells), 0)
         self._mesh_c = mesh._c()
         handle = ctypes.c_void_p(0)
         N.check(N.lib.fe_plan_create(ctypes.byref(self._form), ctypes.byref(self._mesh_c),
@@ -238,3 +240,70 @@ class NeoHookeanResidual(torch.autograd.Function):
         (u,) = ctx.saved_tensors
         jtw, dmu, dlam = ctx.plan.adjoint(u, w.contiguous())
         return jtw, dmu, dlam, None
+
+
+class Batch:
+    """Many independent problems in one persistent launch (``fe_batch_*``).
+
+    ``problems``: list of dicts with keys mesh (Mesh), kind (MASS, ELASTICITY or
+    NH_RESIDUAL), quad_degree, u (device tensor), optional lam, mu, mu_cell,
+    lam_cell, kernel (-1 auto, 0 thread-per-cell, 1 cells-per-CTA) and
+    tile_cells.  Outputs are allocated here (``self.y[i]``)."""
+
+    def __init__(self, problems):
+        self._keep = []
+        self.y = []
+        arr = (N.FeBatchProblem * len(problems))()
+        for i, pb in enumerate(problems):
+            mesh = pb["mesh"]
+            kind = int(pb["kind"])
+            nc = 1 if kind == MASS else mesh.dim
+            u = pb["u"]
+            if u.dtype != torch.float64 or not u.is_cuda or u.numel() != mesh.n_nodes * nc:
+                raise ValueError(f"problem {i}: u must be a float64 CUDA tensor of {mesh.n_nodes * nc}")
+            y = torch.empty_like(u)
+            mu_cell = pb.get("mu_cell")
+            lam_cell = pb.get("lam_cell")
+            mu_cell = None if mu_cell is None else torch.as_tensor(mu_cell, dtype=torch.float64,
+                                                                   device=u.device).contiguous()
+            lam_cell = None if lam_cell is None else torch.as_tensor(lam_cell, dtype=torch.float64,
+                                                                     device=u.device).contiguous()
+            self._keep += [mesh, u, y, mu_cell, lam_cell]
+            self.y.append(y)
+            arr[i].form = N.FeForm(kind, int(pb["quad_degree"]), N.FE_PREC_FP64, 0,
+                                   float(pb.get("lam", 0.0)), float(pb.get("mu", 0.0)),
+                                   _dptr(lam_cell).value or 0, _dptr(mu_cell).value or 0, 0, 0, 0)
+            arr[i].mesh = mesh._c()
+            arr[i].u = u.data_ptr()
+            arr[i].y = y.data_ptr()
+            arr[i].kernel = int(pb.get("kernel", -1))
+            arr[i].tile_cells = int(pb.get("tile_cells", 0))
+        self._arr = arr
+        h = ctypes.c_void_p(0)
+        N.check(N.lib.fe_batch_create(arr, len(problems), ctypes.byref(h)), "fe_batch_create")
+        self._h = h
+        info = N.FeBatchInfo()
+        N.check(N.lib.fe_batch_get_info(self._h, ctypes.byref(info)), "fe_batch_get_info")
+        self.info = {"problems": info.problems, "items": info.items, "grid_blocks": info.grid_blocks,
+                     "smem_bytes": info.smem_bytes, "dofs": info.dofs,
+                     "contraction_flops": info.contraction_flops}
+
+    def run(self, stream=None):
+        N.check(N.lib.fe_batch_run(self._h, _stream_ptr(stream)), "fe_batch_run")
+        return self.y
+
+    def status(self) -> int:
+        st = ctypes.c_int(0)
+        N.check(N.lib.fe_batch_status(self._h, ctypes.byref(st)), "fe_batch_status")
+        return st.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            N.lib.fe_batch_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

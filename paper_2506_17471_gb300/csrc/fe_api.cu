@@ -199,6 +199,7 @@ extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan 
     if (f.precision != FE_PREC_FP64 && f.precision != FE_PREC_FP32) return FE_ERR_UNSUPPORTED;
     if (f.quad_degree < 0 || f.quad_degree > 40) return FE_ERR_INVALID_ARG;
     if (f.kind == FE_FORM_NH_JACOBIAN && !f.u_lin) return FE_ERR_INVALID_ARG;
+    if (f.tile_cells < 0 || f.tile_cells > 4096) return FE_ERR_INVALID_ARG;
     const int ncomp = ncomp_of(f.kind, m.dim);
     if ((long long)m.n_nodes * ncomp >= (1ll << 31)) return FE_ERR_INVALID_ARG;
 
@@ -229,7 +230,8 @@ extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan 
     int coop_cells = 0;
     size_t rs = (size_t)(1 + m.dim) * n, woff, smem, block_bytes;
     if (coop) {
-        coop_cells = coop_cells_for(n, nq, m.dim, ncomp, fields_max, esz, 100 * 1024);
+        coop_cells = f.tile_cells > 0 ? f.tile_cells
+                                      : coop_cells_for(n, nq, m.dim, ncomp, fields_max, esz, 100 * 1024);
         if (esz == sizeof(float)) {
             const CoopLayout L = coop_layout<float>(n, nq, m.dim, ncomp, coop_cells, fields_max);
             rs = L.rs; woff = L.wts_off; block_bytes = L.table_block_bytes; smem = L.total;

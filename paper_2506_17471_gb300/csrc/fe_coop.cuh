@@ -65,6 +65,274 @@ __host__ __device__ inline CoopLayout coop_layout(int n, int nq, int D, int NC, 
     return L;
 }
 
+// Shared-memory pointers of one CTA's cooperative scratch.
+template <typename R>
+struct CoopSmem {
+    const R *tab;
+    const double *wts;
+    const R *wts_r;
+    double *l;
+    R *e;
+    int *nodes;
+    double *geo;
+    double *acc;
+};
+
+template <typename R>
+__device__ __forceinline__ CoopSmem<R> coop_smem(unsigned char *base, const CoopLayout &L)
+{
+    CoopSmem<R> S;
+    S.tab = reinterpret_cast<const R *>(base);
+    S.wts = reinterpret_cast<const double *>(base + L.wts_off);
+    S.wts_r = reinterpret_cast<const R *>(base + L.wtsr_off);
+    S.l = reinterpret_cast<double *>(base + L.off_l);
+    S.e = reinterpret_cast<R *>(base + L.off_e);
+    S.nodes = reinterpret_cast<int *>(base + L.off_nodes);
+    S.geo = reinterpret_cast<double *>(base + L.off_geo);
+    S.acc = reinterpret_cast<double *>(base + L.off_acc);
+    return S;
+}
+
+// One batch of cells [cell0, cell0 + nb) through phases A-C by the whole CTA.
+// Must be called by every thread of the CTA; ends with a barrier.
+template <int OP, int D, typename R>
+__device__ __forceinline__ void coop_batch(const ActionArgs &a, const CoopLayout &L, const CoopSmem<R> &S,
+                                           const int cell0, const int nb)
+{
+    constexpr int NC = OpTraits<OP, D>::NC;
+    constexpr int FIELDS = OpTraits<OP, D>::kTwoFields ? 2 : 1;
+    const int n = L.n;
+    const int nq = L.nq;
+    const R *tab = S.tab;
+    const double *wts = S.wts;
+    const R *wts_r = S.wts_r;
+    double *sl = S.l;
+    R *se = S.e;
+    int *snodes = S.nodes;
+    double *sgeo = S.geo;
+    double *sacc = S.acc;
+    // ---- A: gather nodes and DoFs; geometry (one thread per cell)
+    for (int i = threadIdx.x; i < nb * n; i += blockDim.x) {
+        const int c = i / n, j = i - c * n;
+        const int node = __ldg(a.c2n + (size_t)(cell0 + c) * n + j);
+        const bool ok = (unsigned)node < (unsigned)a.n_nodes;
+        if (!ok) set_status(a.status, FE_ERR_INDEX);
+        snodes[c * n + j] = ok ? node : -1;
+#pragma unroll
+        for (int f = 0; f < FIELDS; ++f) {
+            const double *src = (f == 0) ? a.u : a.u_lin;
+#pragma unroll
+            for (int m = 0; m < NC; ++m)
+                sl[c * L.ls + (f * n + j) * NC + m] = ok ? __ldg(src + (size_t)node * NC + m) : 0.0;
+        }
+    }
+    for (int c = threadIdx.x; c < nb; c += blockDim.x) {
+        const int cell = cell0 + c;
+        double X[D + 1][D];
+        bool ok = true;
+#pragma unroll
+        for (int m = 0; m <= D; ++m) {
+            const int v = __ldg(a.c2v + (size_t)cell * (D + 1) + m);
+            ok &= (unsigned)v < (unsigned)a.n_vertices;
+#pragma unroll
+            for (int i = 0; i < D; ++i) X[m][i] = ok ? __ldg(a.coords + (size_t)v * D + i) : 0.0;
+        }
+        double Jinv[D][D];
+        const double det = cell_geometry<D>(X, Jinv);
+        double *g = sgeo + c * 16;
+        const bool good = ok && (det != 0.0) && isfinite(det);
+        if (!ok) set_status(a.status, FE_ERR_INDEX);
+        else if (!good) set_status(a.status, FE_ERR_BAD_MESH);
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int k = 0; k < D; ++k) g[i * D + k] = good ? Jinv[i][k] : 0.0;
+        g[D * D] = good ? fabs(det) : 0.0;
+        g[D * D + 1] = (OpTraits<OP, D>::kCellCoeff && a.mu_cell) ? __ldg(a.mu_cell + cell) : a.mu;
+        g[D * D + 2] = (OpTraits<OP, D>::kCellCoeff && a.lam_cell) ? __ldg(a.lam_cell + cell) : a.lam;
+        g[D * D + 3] = good ? 1.0 : 0.0;
+        sacc[2 * c] = 0.0;
+        sacc[2 * c + 1] = 0.0;
+    }
+    __syncthreads();
+
+    // ---- B: evaluation + pointwise per (cell, quadrature point)
+    bool nh_ok = true;
+    for (int i = threadIdx.x; i < nb * nq; i += blockDim.x) {
+        const int c = i / nq, q = i - c * nq;
+        const double *g = sgeo + c * 16;
+        const R *T = tab + (size_t)q * L.rs;
+        const double *lc = sl + c * L.ls;
+        R *e = se + ((size_t)c * nq + q) * L.es;
+        const double absdet = g[D * D];
+        double Jinv[D][D];
+#pragma unroll
+        for (int ii = 0; ii < D; ++ii)
+#pragma unroll
+            for (int k = 0; k < D; ++k) Jinv[ii][k] = g[ii * D + k];
+        const double mu = g[D * D + 1], lam = g[D * D + 2];
+        if constexpr (OP == OP_MASS) {
+            R uq = R(0);
+            for (int j = 0; j < n; ++j) uq = fma(T[j], cvt<R>(lc[j]), uq);
+            e[0] = uq * (wts_r[q] * cvt<R>(absdet));
+        } else {
+            // reference gradients of the field(s) at q
+            R gh[FIELDS][NC][D];
+#pragma unroll
+            for (int f = 0; f < FIELDS; ++f)
+#pragma unroll
+                for (int m = 0; m < NC; ++m)
+#pragma unroll
+                    for (int k = 0; k < D; ++k) gh[f][m][k] = R(0);
+            for (int j = 0; j < n; ++j) {
+                R t[D];
+#pragma unroll
+                for (int k = 0; k < D; ++k) t[k] = T[(k + 1) * n + j];
+#pragma unroll
+                for (int f = 0; f < FIELDS; ++f)
+#pragma unroll
+                    for (int m = 0; m < NC; ++m) {
+                        const R lv = cvt<R>(lc[(f * n + j) * NC + m]);
+#pragma unroll
+                        for (int k = 0; k < D; ++k) gh[f][m][k] = fma(t[k], lv, gh[f][m][k]);
+                    }
+            }
+            if constexpr (OP == OP_ELASTICITY) {
+                R Jr[D][D], G[D][D], S[D][D], er[D][D];
+                convert<D, D>(Jinv, Jr);
+                map_grad<D, R>(gh[0], Jr, G);
+                R tr = G[0][0];
+#pragma unroll
+                for (int ii = 1; ii < D; ++ii) tr += G[ii][ii];
+                const R wdet_r = wts_r[q] * cvt<R>(absdet);
+                const R smu = wdet_r * cvt<R>(mu);
+                const R slt = wdet_r * cvt<R>(lam) * tr;
+#pragma unroll
+                for (int ii = 0; ii < D; ++ii) {
+                    S[ii][ii] = fma(R(2) * smu, G[ii][ii], slt);
+#pragma unroll
+                    for (int k = ii + 1; k < D; ++k) {
+                        const R s = smu * (G[ii][k] + G[k][ii]);
+                        S[ii][k] = s;
+                        S[k][ii] = s;
+                    }
+                }
+                pull_back<D, R>(S, Jr, er);
+#pragma unroll
+                for (int m = 0; m < NC; ++m)
+#pragma unroll
+                    for (int k = 0; k < D; ++k) e[m * D + k] = er[m][k];
+            } else {
+                const double wdet = wts[q] * absdet;
+                double ghd[D][D], F[D][D], C2[D][D], S[D][D], ed[D][D];
+                // the field whose gradient forms F: u (residual) or u_lin (tangent)
+                convert<D, D>(gh[FIELDS - 1], ghd);
+                map_grad<D, double>(ghd, Jinv, F);
+#pragma unroll
+                for (int ii = 0; ii < D; ++ii) F[ii][ii] += 1.0;
+                const double Jd = det_cof<D>(F, C2);
+                nh_ok &= (Jd > 0.0);
+                const double lnJ = log(Jd);
+                if constexpr (OP == OP_NH_RESIDUAL) {
+                    const double smu = wdet * mu;
+                    const double scf = wdet * fma(lam, lnJ, -mu) / Jd;
+#pragma unroll
+                    for (int ii = 0; ii < D; ++ii)
+#pragma unroll
+                        for (int k = 0; k < D; ++k) S[ii][k] = fma(smu, F[ii][k], scf * C2[ii][k]);
+                } else {
+                    double H[D][D], Fit[D][D], A[D][D];
+                    convert<D, D>(gh[0], ghd);
+                    map_grad<D, double>(ghd, Jinv, H);
+                    const double rJ = 1.0 / Jd;
+                    double tr = 0.0;
+#pragma unroll
+                    for (int ii = 0; ii < D; ++ii)
+#pragma unroll
+                        for (int k = 0; k < D; ++k) {
+                            Fit[ii][k] = C2[ii][k] * rJ;
+                            tr = fma(Fit[ii][k], H[ii][k], tr);
+                        }
+#pragma unroll
+                    for (int ii = 0; ii < D; ++ii)
+#pragma unroll
+                        for (int k = 0; k < D; ++k) {
+                            double s = Fit[ii][0] * H[k][0];
+#pragma unroll
+                            for (int mm = 1; mm < D; ++mm) s = fma(Fit[ii][mm], H[k][mm], s);
+                            A[ii][k] = s;
+                        }
+                    const double smu = wdet * mu;
+                    const double sm2 = wdet * fma(-lam, lnJ, mu);
+                    const double str = wdet * lam * tr;
+#pragma unroll
+                    for (int ii = 0; ii < D; ++ii)
+#pragma unroll
+                        for (int k = 0; k < D; ++k) {
+                            double m = A[ii][0] * Fit[0][k];
+#pragma unroll
+                            for (int mm = 1; mm < D; ++mm) m = fma(A[ii][mm], Fit[mm][k], m);
+                            S[ii][k] = fma(smu, H[ii][k], fma(sm2, m, str * Fit[ii][k]));
+                        }
+                    if constexpr (OP == OP_NH_ADJOINT) {
+                        double amu = 0.0, alam = 0.0;
+#pragma unroll
+                        for (int ii = 0; ii < D; ++ii)
+#pragma unroll
+                            for (int k = 0; k < D; ++k) {
+                                amu = fma(wdet * (F[ii][k] - Fit[ii][k]), H[ii][k], amu);
+                                alam = fma(wdet * lnJ * Fit[ii][k], H[ii][k], alam);
+                            }
+                        atomicAdd(sacc + 2 * c, amu);       // shared-memory FP64 atomics
+                        atomicAdd(sacc + 2 * c + 1, alam);
+                    }
+                }
+                pull_back<D, double>(S, Jinv, ed);
+#pragma unroll
+                for (int m = 0; m < NC; ++m)
+#pragma unroll
+                    for (int k = 0; k < D; ++k) e[m * D + k] = cvt<R>(ed[m][k]);
+            }
+        }
+    }
+    if (!nh_ok) set_status(a.status, FE_ERR_NONFINITE);
+    __syncthreads();
+
+    // ---- C: quadrature contraction + scatter per (cell, node)
+    for (int i = threadIdx.x; i < nb * n; i += blockDim.x) {
+        const int c = i / n, j = i - c * n;
+        const int node = snodes[c * n + j];
+        if (node < 0 || sgeo[c * 16 + D * D + 3] == 0.0) continue;
+        R out[NC];
+#pragma unroll
+        for (int m = 0; m < NC; ++m) out[m] = R(0);
+        const R *ec = se + (size_t)c * nq * L.es;
+        for (int q = 0; q < nq; ++q) {
+            const R *T = tab + (size_t)q * L.rs;
+            const R *e = ec + (size_t)q * L.es;
+            if constexpr (OP == OP_MASS) {
+                out[0] = fma(T[j], e[0], out[0]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    const R t = T[(k + 1) * n + j];
+#pragma unroll
+                    for (int m = 0; m < NC; ++m) out[m] = fma(t, e[m * D + k], out[m]);
+                }
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < NC; ++m) atomicAdd(a.y + (size_t)node * NC + m, cvt<double>(out[m]));
+    }
+    if constexpr (OP == OP_NH_ADJOINT) {
+        for (int c = threadIdx.x; c < nb; c += blockDim.x) {
+            a.dmu[cell0 + c] = sacc[2 * c];
+            a.dlam[cell0 + c] = sacc[2 * c + 1];
+        }
+    }
+    __syncthreads();   // the batch's shared state is reused by the next batch
+}
+
 template <int OP, int D, typename R>
 __global__ void __launch_bounds__(kCoopBlock) k_action_coop(const ActionArgs a, const int n, const int C)
 {
@@ -74,250 +342,19 @@ __global__ void __launch_bounds__(kCoopBlock) k_action_coop(const ActionArgs a, 
     __shared__ __align__(8) uint64_t bar;
     __shared__ int s_chunk;
     const CoopLayout L = coop_layout<R>(n, a.nq, D, NC, C, FIELDS);
-    unsigned char *base = reinterpret_cast<unsigned char *>(smem);
     if (!stage_table(smem, a.tab, a.tab_doubles, &bar, a.status)) {
         leave_queue(a.sched);
         return;
     }
-    const R *tab = reinterpret_cast<const R *>(base);
-    const double *wts = reinterpret_cast<const double *>(base + L.wts_off);
-    const R *wts_r = reinterpret_cast<const R *>(base + L.wtsr_off);
-    double *sl = reinterpret_cast<double *>(base + L.off_l);
-    R *se = reinterpret_cast<R *>(base + L.off_e);
-    int *snodes = reinterpret_cast<int *>(base + L.off_nodes);
-    double *sgeo = reinterpret_cast<double *>(base + L.off_geo);
-    double *sacc = reinterpret_cast<double *>(base + L.off_acc);
-    const int nq = a.nq;
+    const CoopSmem<R> S = coop_smem<R>(reinterpret_cast<unsigned char *>(smem), L);
     const int n_batches = (a.n_cells + C - 1) / C;
-
     for (;;) {
         if (threadIdx.x == 0) s_chunk = atomicAdd(a.sched, 1);
         __syncthreads();
         const int batch = s_chunk;
         if (batch >= n_batches) break;
         const int cell0 = batch * C;
-        const int nb = min(C, a.n_cells - cell0);
-
-        // ---- A: gather nodes and DoFs; geometry (one thread per cell)
-        for (int i = threadIdx.x; i < nb * n; i += blockDim.x) {
-            const int c = i / n, j = i - c * n;
-            const int node = __ldg(a.c2n + (size_t)(cell0 + c) * n + j);
-            const bool ok = (unsigned)node < (unsigned)a.n_nodes;
-            if (!ok) set_status(a.status, FE_ERR_INDEX);
-            snodes[c * n + j] = ok ? node : -1;
-#pragma unroll
-            for (int f = 0; f < FIELDS; ++f) {
-                const double *src = (f == 0) ? a.u : a.u_lin;
-#pragma unroll
-                for (int m = 0; m < NC; ++m)
-                    sl[c * L.ls + (f * n + j) * NC + m] = ok ? __ldg(src + (size_t)node * NC + m) : 0.0;
-            }
-        }
-        for (int c = threadIdx.x; c < nb; c += blockDim.x) {
-            const int cell = cell0 + c;
-            double X[D + 1][D];
-            bool ok = true;
-#pragma unroll
-            for (int m = 0; m <= D; ++m) {
-                const int v = __ldg(a.c2v + (size_t)cell * (D + 1) + m);
-                ok &= (unsigned)v < (unsigned)a.n_vertices;
-#pragma unroll
-                for (int i = 0; i < D; ++i) X[m][i] = ok ? __ldg(a.coords + (size_t)v * D + i) : 0.0;
-            }
-            double Jinv[D][D];
-            const double det = cell_geometry<D>(X, Jinv);
-            double *g = sgeo + c * 16;
-            const bool good = ok && (det != 0.0) && isfinite(det);
-            if (!ok) set_status(a.status, FE_ERR_INDEX);
-            else if (!good) set_status(a.status, FE_ERR_BAD_MESH);
-#pragma unroll
-            for (int i = 0; i < D; ++i)
-#pragma unroll
-                for (int k = 0; k < D; ++k) g[i * D + k] = good ? Jinv[i][k] : 0.0;
-            g[D * D] = good ? fabs(det) : 0.0;
-            g[D * D + 1] = (OpTraits<OP, D>::kCellCoeff && a.mu_cell) ? __ldg(a.mu_cell + cell) : a.mu;
-            g[D * D + 2] = (OpTraits<OP, D>::kCellCoeff && a.lam_cell) ? __ldg(a.lam_cell + cell) : a.lam;
-            g[D * D + 3] = good ? 1.0 : 0.0;
-            sacc[2 * c] = 0.0;
-            sacc[2 * c + 1] = 0.0;
-        }
-        __syncthreads();
-
-        // ---- B: evaluation + pointwise per (cell, quadrature point)
-        bool nh_ok = true;
-        for (int i = threadIdx.x; i < nb * nq; i += blockDim.x) {
-            const int c = i / nq, q = i - c * nq;
-            const double *g = sgeo + c * 16;
-            const R *T = tab + (size_t)q * L.rs;
-            const double *lc = sl + c * L.ls;
-            R *e = se + ((size_t)c * nq + q) * L.es;
-            const double absdet = g[D * D];
-            double Jinv[D][D];
-#pragma unroll
-            for (int ii = 0; ii < D; ++ii)
-#pragma unroll
-                for (int k = 0; k < D; ++k) Jinv[ii][k] = g[ii * D + k];
-            const double mu = g[D * D + 1], lam = g[D * D + 2];
-            if constexpr (OP == OP_MASS) {
-                R uq = R(0);
-                for (int j = 0; j < n; ++j) uq = fma(T[j], cvt<R>(lc[j]), uq);
-                e[0] = uq * (wts_r[q] * cvt<R>(absdet));
-            } else {
-                // reference gradients of the field(s) at q
-                R gh[FIELDS][NC][D];
-#pragma unroll
-                for (int f = 0; f < FIELDS; ++f)
-#pragma unroll
-                    for (int m = 0; m < NC; ++m)
-#pragma unroll
-                        for (int k = 0; k < D; ++k) gh[f][m][k] = R(0);
-                for (int j = 0; j < n; ++j) {
-                    R t[D];
-#pragma unroll
-                    for (int k = 0; k < D; ++k) t[k] = T[(k + 1) * n + j];
-#pragma unroll
-                    for (int f = 0; f < FIELDS; ++f)
-#pragma unroll
-                        for (int m = 0; m < NC; ++m) {
-                            const R lv = cvt<R>(lc[(f * n + j) * NC + m]);
-#pragma unroll
-                            for (int k = 0; k < D; ++k) gh[f][m][k] = fma(t[k], lv, gh[f][m][k]);
-                        }
-                }
-                if constexpr (OP == OP_ELASTICITY) {
-                    R Jr[D][D], G[D][D], S[D][D], er[D][D];
-                    convert<D, D>(Jinv, Jr);
-                    map_grad<D, R>(gh[0], Jr, G);
-                    R tr = G[0][0];
-#pragma unroll
-                    for (int ii = 1; ii < D; ++ii) tr += G[ii][ii];
-                    const R wdet_r = wts_r[q] * cvt<R>(absdet);
-                    const R smu = wdet_r * cvt<R>(mu);
-                    const R slt = wdet_r * cvt<R>(lam) * tr;
-#pragma unroll
-                    for (int ii = 0; ii < D; ++ii) {
-                        S[ii][ii] = fma(R(2) * smu, G[ii][ii], slt);
-#pragma unroll
-                        for (int k = ii + 1; k < D; ++k) {
-                            const R s = smu * (G[ii][k] + G[k][ii]);
-                            S[ii][k] = s;
-                            S[k][ii] = s;
-                        }
-                    }
-                    pull_back<D, R>(S, Jr, er);
-#pragma unroll
-                    for (int m = 0; m < NC; ++m)
-#pragma unroll
-                        for (int k = 0; k < D; ++k) e[m * D + k] = er[m][k];
-                } else {
-                    const double wdet = wts[q] * absdet;
-                    double ghd[D][D], F[D][D], C2[D][D], S[D][D], ed[D][D];
-                    // the field whose gradient forms F: u (residual) or u_lin (tangent)
-                    convert<D, D>(gh[FIELDS - 1], ghd);
-                    map_grad<D, double>(ghd, Jinv, F);
-#pragma unroll
-                    for (int ii = 0; ii < D; ++ii) F[ii][ii] += 1.0;
-                    const double Jd = det_cof<D>(F, C2);
-                    nh_ok &= (Jd > 0.0);
-                    const double lnJ = log(Jd);
-                    if constexpr (OP == OP_NH_RESIDUAL) {
-                        const double smu = wdet * mu;
-                        const double scf = wdet * fma(lam, lnJ, -mu) / Jd;
-#pragma unroll
-                        for (int ii = 0; ii < D; ++ii)
-#pragma unroll
-                            for (int k = 0; k < D; ++k) S[ii][k] = fma(smu, F[ii][k], scf * C2[ii][k]);
-                    } else {
-                        double H[D][D], Fit[D][D], A[D][D];
-                        convert<D, D>(gh[0], ghd);
-                        map_grad<D, double>(ghd, Jinv, H);
-                        const double rJ = 1.0 / Jd;
-                        double tr = 0.0;
-#pragma unroll
-                        for (int ii = 0; ii < D; ++ii)
-#pragma unroll
-                            for (int k = 0; k < D; ++k) {
-                                Fit[ii][k] = C2[ii][k] * rJ;
-                                tr = fma(Fit[ii][k], H[ii][k], tr);
-                            }
-#pragma unroll
-                        for (int ii = 0; ii < D; ++ii)
-#pragma unroll
-                            for (int k = 0; k < D; ++k) {
-                                double s = Fit[ii][0] * H[k][0];
-#pragma unroll
-                                for (int mm = 1; mm < D; ++mm) s = fma(Fit[ii][mm], H[k][mm], s);
-                                A[ii][k] = s;
-                            }
-                        const double smu = wdet * mu;
-                        const double sm2 = wdet * fma(-lam, lnJ, mu);
-                        const double str = wdet * lam * tr;
-#pragma unroll
-                        for (int ii = 0; ii < D; ++ii)
-#pragma unroll
-                            for (int k = 0; k < D; ++k) {
-                                double m = A[ii][0] * Fit[0][k];
-#pragma unroll
-                                for (int mm = 1; mm < D; ++mm) m = fma(A[ii][mm], Fit[mm][k], m);
-                                S[ii][k] = fma(smu, H[ii][k], fma(sm2, m, str * Fit[ii][k]));
-                            }
-                        if constexpr (OP == OP_NH_ADJOINT) {
-                            double amu = 0.0, alam = 0.0;
-#pragma unroll
-                            for (int ii = 0; ii < D; ++ii)
-#pragma unroll
-                                for (int k = 0; k < D; ++k) {
-                                    amu = fma(wdet * (F[ii][k] - Fit[ii][k]), H[ii][k], amu);
-                                    alam = fma(wdet * lnJ * Fit[ii][k], H[ii][k], alam);
-                                }
-                            atomicAdd(sacc + 2 * c, amu);       // shared-memory FP64 atomics
-                            atomicAdd(sacc + 2 * c + 1, alam);
-                        }
-                    }
-                    pull_back<D, double>(S, Jinv, ed);
-#pragma unroll
-                    for (int m = 0; m < NC; ++m)
-#pragma unroll
-                        for (int k = 0; k < D; ++k) e[m * D + k] = cvt<R>(ed[m][k]);
-                }
-            }
-        }
-        if (!nh_ok) set_status(a.status, FE_ERR_NONFINITE);
-        __syncthreads();
-
-        // ---- C: quadrature contraction + scatter per (cell, node)
-        for (int i = threadIdx.x; i < nb * n; i += blockDim.x) {
-            const int c = i / n, j = i - c * n;
-            const int node = snodes[c * n + j];
-            if (node < 0 || sgeo[c * 16 + D * D + 3] == 0.0) continue;
-            R out[NC];
-#pragma unroll
-            for (int m = 0; m < NC; ++m) out[m] = R(0);
-            const R *ec = se + (size_t)c * nq * L.es;
-            for (int q = 0; q < nq; ++q) {
-                const R *T = tab + (size_t)q * L.rs;
-                const R *e = ec + (size_t)q * L.es;
-                if constexpr (OP == OP_MASS) {
-                    out[0] = fma(T[j], e[0], out[0]);
-                } else {
-#pragma unroll
-                    for (int k = 0; k < D; ++k) {
-                        const R t = T[(k + 1) * n + j];
-#pragma unroll
-                        for (int m = 0; m < NC; ++m) out[m] = fma(t, e[m * D + k], out[m]);
-                    }
-                }
-            }
-#pragma unroll
-            for (int m = 0; m < NC; ++m) atomicAdd(a.y + (size_t)node * NC + m, cvt<double>(out[m]));
-        }
-        if constexpr (OP == OP_NH_ADJOINT) {
-            for (int c = threadIdx.x; c < nb; c += blockDim.x) {
-                a.dmu[cell0 + c] = sacc[2 * c];
-                a.dlam[cell0 + c] = sacc[2 * c + 1];
-            }
-        }
-        __syncthreads();   // the batch's shared state is reused by the next batch
+        coop_batch<OP, D, R>(a, L, S, cell0, min(C, a.n_cells - cell0));
     }
     leave_queue(a.sched);
 }

@@ -1,0 +1,54 @@
+"""Host logic of the autotuner (no GPU): candidate space, pruning, cost model,
+Spearman rank correlation (the paper's Eq. "spearmann_rho")."""
+
+import math
+
+import pytest
+
+
+@pytest.fixture(scope="module")
+def at():
+    import __graft_entry__
+    __graft_entry__.build_library()
+    from paper_2506_17471_gb300 import autotune
+    return autotune
+
+
+def test_eta_simd_closed_form(at):
+    # the paper's eta_simd = N_c N_WI / (32 ceil(N_c N_WI / 32)) with 32-wide groups
+    for items in (1, 31, 32, 33, 64, 100):
+        assert at.eta_simd(items, 32) == pytest.approx(items / (32 * math.ceil(items / 32)))
+    assert at.eta_simd(256) == 1.0 and at.eta_simd(257) == pytest.approx(257 / 512)
+
+
+def test_candidates_follow_tile_constraint_and_pruning(at):
+    from paper_2506_17471_gb300 import _native as N
+    cands = at.candidates(N.FE_FORM_ELASTICITY, 3, 4, nq=64, n_loc=35, ncomp=3)
+    assert all(c.kernel == 1 for c in cands)          # no thread-per-cell kernel for P4 tets
+    tiles = [c.tile_cells for c in cands]
+    assert tiles == sorted(tiles, reverse=True)
+    cmax = max(tiles)
+    assert all(any(t == math.ceil(cmax / k) for k in range(1, 64)) for t in tiles)
+    for t in tiles:
+        assert t == cmax or at.eta_simd(t * 64) >= 0.3
+        assert at._coop_total_bytes(35, 64, 3, 3, t, 1) <= at.SMEM_BUDGET
+    assert at._coop_total_bytes(35, 64, 3, 3, cmax + 1, 1) > at.SMEM_BUDGET
+    c2 = at.candidates(N.FE_FORM_MASS, 2, 2, nq=9, n_loc=6, ncomp=1)
+    assert c2[0].kernel == 0                           # thread-per-cell exists for P2 mass
+
+
+def test_cost_model_monotone(at):
+    c = at.Candidate(0)
+    t1 = at.model_time(c, 1000, 1e8, 1e6, 8, 10)
+    t2 = at.model_time(c, 1000, 2e8, 1e6, 8, 10)
+    assert t2 > t1
+    # memory-bound regime: time follows bytes
+    t3 = at.model_time(c, 1000, 1.0, 1e9, 8, 10)
+    assert t3 == pytest.approx(1e9 / (at.HBM_GBS * 1e9) + at.T_LAUNCH_S
+                               + math.ceil(1000 / 128) * at.T_BATCH_S / (at.N_SMS * 2))
+
+
+def test_spearman(at):
+    assert at.spearman([1, 2, 3, 4], [10, 20, 30, 40]) == 1.0
+    assert at.spearman([1, 2, 3, 4], [4, 3, 2, 1]) == -1.0
+    assert at.spearman([1, 2, 3, 4, 5], [2, 1, 4, 3, 5]) == pytest.approx(0.8)
