@@ -292,9 +292,7 @@ extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan 
         fe_plan_destroy(p);
         return FE_ERR_CUDA;
     }
-    if (cudaFuncSetAttribute(v->func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-        (adj && cudaFuncSetAttribute(adj->func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-                    cudaSuccess)) {
+    if (allow_max_dynamic_smem(v->func) != cudaSuccess || (adj && allow_max_dynamic_smem(adj->func) != cudaSuccess)) {
         fe_plan_destroy(p);
         return FE_ERR_CUDA;
     }

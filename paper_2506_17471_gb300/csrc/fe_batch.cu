@@ -360,8 +360,7 @@ extern "C" int fe_batch_create(const fe_batch_problem *problems, int count, fe_b
                                       cudaMemcpyHostToDevice) != cudaSuccess) ||
         cudaMemcpy(b->d_spans, spans.data(), sizeof(ZeroSpan) * count, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(b->d_words, 0, 8 * sizeof(int32_t)) != cudaSuccess ||
-        cudaFuncSetAttribute(k_action_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess) {
+        allow_max_dynamic_smem(reinterpret_cast<const void *>(k_action_batched)) != cudaSuccess) {
         batch_free(b);
         return FE_ERR_CUDA;
     }

@@ -52,6 +52,23 @@ struct Variant {
     const void *func;  // kernel symbol (for occupancy queries)
 };
 
+// Raise a kernel's dynamic shared-memory limit to the device's opt-in maximum.
+// The limit is an attribute of the kernel function, shared by every plan that
+// uses it, so it must never be lowered to one plan's need.
+inline cudaError_t allow_max_dynamic_smem(const void *func)
+{
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes attr;
+    e = cudaFuncGetAttributes(&attr, func);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                optin - (int)attr.sharedSizeBytes);
+}
+
 // Registry population, one per instantiation translation unit; each appends
 // its variants to out[] and returns how many it wrote (at most cap).
 int register_variants_2d_linear(Variant *out, int cap);

@@ -146,8 +146,7 @@ extern "C" int fe_action_noalloc(const fe_form *form, const fe_mesh *mesh, const
         if (cudaMemsetAsync(y, 0, (size_t)n_dofs * sizeof(double), s) != cudaSuccess) return FE_ERR_CUDA;
     }
     if (m.n_cells > 0) {
-        if (cudaFuncSetAttribute(v->func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-            return FE_ERR_CUDA;
+        if (allow_max_dynamic_smem(v->func) != cudaSuccess) return FE_ERR_CUDA;
         int per_sm = 0, sms = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, v->func, v->block, smem) != cudaSuccess ||
             per_sm < 1)

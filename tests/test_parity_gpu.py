@@ -283,3 +283,22 @@ def test_autograd_function_matches_oracle_and_fd(fe):
         fd = float(((rp - rm) * cuda(w)).sum()) / (2 * h)
     an = float((ut.grad * cuda(d)).sum())
     assert abs(fd - an) <= 1e-7 * abs(an)
+
+
+def test_plans_of_one_kernel_keep_their_shared_memory(fe):
+    """A later plan of the same kernel with a smaller table must not break an
+    earlier plan that needs more dynamic shared memory."""
+    m, M = make(fe, 2, 6, 4, seed=3)
+    o_big = oracle.Oracle.from_mesh(m, 30)
+    big = fe.Plan(M, fe.MASS, 30)      # 256-point rule: ~95 KB table
+    small = fe.Plan(M, fe.MASS, 2)     # 4-point rule: ~1.6 KB table
+    u = uniform_field(m.n_nodes, 1)
+    assert rel(big.apply(cuda(u)), o_big.mass(u)) <= TOL
+    assert rel(small.apply(cuda(u)), oracle.Oracle.from_mesh(m, 2).mass(u)) <= TOL
+    c = structured_mesh(3, 3, 4, jitter=0.15, seed=2)
+    C = fe.Mesh(3, 4, c.coords, c.cell2vertex, c.cell2node, c.n_nodes)
+    wide = fe.Plan(C, fe.ELASTICITY, 6, lam=1.25, mu=1.0, tile_cells=5)
+    narrow = fe.Plan(C, fe.ELASTICITY, 6, lam=1.25, mu=1.0, tile_cells=1)
+    v = uniform_field(c.n_nodes * 3, 2)
+    ref = oracle.Oracle.from_mesh(c, 6).elasticity(v, 1.25, 1.0)
+    assert rel(wide.apply(cuda(v)), ref) <= TOL and rel(narrow.apply(cuda(v)), ref) <= TOL
