@@ -370,7 +370,8 @@ def time_batched(fe, torch):
             u = torch.from_numpy(sinusoid_displacement(m, s_["seed"])).cuda()
 
         def make_plan(c, M=M, kind=kind, q=q, kw=kw):
-            return fe.Plan(M, kind, q, cooperative=c.kernel == 1, tile_cells=c.tile_cells, **kw)
+            return fe.Plan(M, kind, q, cooperative=c.kernel == 1, tile_cells=c.tile_cells,
+                           tables_global=c.tables_global, **kw)
 
         best, rep = autotune.tune(make_plan, u, "", kind, dim, p, use_cache=False)
         if "spearman" in rep:
@@ -380,7 +381,7 @@ def time_batched(fe, torch):
         flops += plan.flops()
         dofs += plan.n_dofs
         problems.append(dict(mesh=M, kind=kind, quad_degree=q, u=u, kernel=best.kernel,
-                             tile_cells=best.tile_cells, **kw))
+                             tile_cells=best.tile_cells, tables_global=best.tables_global, **kw))
     batch = fe.Batch(problems)
     stream = torch.cuda.current_stream()
 

@@ -89,6 +89,10 @@ enum fe_precision {
 #define FE_FLAG_COOPERATIVE 2u /* use the cells-per-CTA kernel even where a
                                   thread-per-cell kernel exists for the degree
                                   (it is always used where none exists)      */
+#define FE_FLAG_TABLES_GLOBAL 4u /* cells-per-CTA kernel: keep the tabulation in
+                                  global memory (L2/L1 resident, two coalesced
+                                  layouts) instead of shared memory; the default
+                                  does so only for tables above 96 KB          */
 
 /* Mesh: affine simplices with P_degree Lagrange DoFs (Sec. "Background",
  * Ciarlet triple and local-to-global maps iota_T).  All pointers are device

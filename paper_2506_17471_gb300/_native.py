@@ -26,6 +26,7 @@ FE_PREC_FP64 = 0
 FE_PREC_FP32 = 1
 FE_FLAG_ACCUMULATE = 1
 FE_FLAG_COOPERATIVE = 2
+FE_FLAG_TABLES_GLOBAL = 4
 
 # every symbol declared in include/feaction.h
 EXPORTS = ("fe_status_string", "fe_tabulate", "fe_plan_create", "fe_plan_destroy", "fe_action",

@@ -103,7 +103,7 @@ class Plan:
     def __init__(self, mesh: Mesh, kind: int, quad_degree: int, *, lam: float = 0.0,
                  mu: float = 0.0, mu_cell=None, lam_cell=None, u_lin=None,
                  accumulate: bool = False, precision: str = "fp64", cooperative: bool = False,
-                 tile_cells: int = 0):
+                 tile_cells: int = 0, tables_global: bool = False):
         self.mesh = mesh
         self.kind = int(kind)
         self.ncomp = 1 if kind == MASS else mesh.dim
@@ -114,7 +114,8 @@ class Plan:
             lam_cell, dtype=torch.float64, device=dev).clone().contiguous()
         self.u_lin = None if u_lin is None else torch.as_tensor(
             u_lin, dtype=torch.float64, device=dev).clone().contiguous()
-        flags = (N.FE_FLAG_ACCUMULATE if accumulate else 0) | (N.FE_FLAG_COOPERATIVE if cooperative else 0)
+        flags = ((N.FE_FLAG_ACCUMULATE if accumulate else 0) | (N.FE_FLAG_COOPERATIVE if cooperative else 0)
+                 | (N.FE_FLAG_TABLES_GLOBAL if tables_global else 0))
         if precision not in PRECISIONS:
             raise ValueError(f"precision must be one of {sorted(PRECISIONS)}")
         self.precision = precision
@@ -270,7 +271,8 @@ class Batch:
                                                                      device=u.device).contiguous()
             self._keep += [mesh, u, y, mu_cell, lam_cell]
             self.y.append(y)
-            arr[i].form = N.FeForm(kind, int(pb["quad_degree"]), N.FE_PREC_FP64, 0,
+            flags = N.FE_FLAG_TABLES_GLOBAL if pb.get("tables_global") else 0
+            arr[i].form = N.FeForm(kind, int(pb["quad_degree"]), N.FE_PREC_FP64, flags,
                                    float(pb.get("lam", 0.0)), float(pb.get("mu", 0.0)),
                                    _dptr(lam_cell).value or 0, _dptr(mu_cell).value or 0, 0, 0, 0)
             arr[i].mesh = mesh._c()

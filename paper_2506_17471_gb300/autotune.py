@@ -48,23 +48,32 @@ T_LAUNCH_S = 4e-6
 T_BATCH_S = 1.5e-6
 COOP_BLOCK = 256
 SMEM_BUDGET = 100 * 1024
+SMEM_TABLE_MAX = 96 * 1024    # the library keeps larger tables in global memory
 
 
 @dataclass(frozen=True)
 class Candidate:
-    kernel: int          # 0 thread-per-cell, 1 cells-per-CTA
-    tile_cells: int = 0  # cells per CTA batch (cells-per-CTA only)
+    kernel: int                  # 0 thread-per-cell, 1 cells-per-CTA
+    tile_cells: int = 0          # cells per CTA batch (cells-per-CTA only)
+    tables_global: bool = False  # cells-per-CTA: tables in global memory instead of shared
 
     def label(self) -> str:
-        return "tpc" if self.kernel == 0 else f"coop{self.tile_cells}"
+        if self.kernel == 0:
+            return "tpc"
+        return f"coop{self.tile_cells}" + ("g" if self.tables_global else "")
 
 
-def _coop_total_bytes(n, nq, dim, ncomp, C, fields, esz=8):
+
+
+
+def _coop_total_bytes(n, nq, dim, ncomp, C, fields, esz=8, tables_global=None):
     """Shared memory of the cells-per-CTA plan (mirrors the kernel's layout)."""
+    if tables_global is None:
+        tables_global = nq * (1 + dim) * n * esz > SMEM_TABLE_MAX
     rs = ((1 + dim) * n) | 1
     ls = (fields * n * ncomp) | 1
     es = (dim * ncomp) | 1
-    tab = nq * rs * esz
+    tab = 0 if tables_global else nq * rs * esz
     woff = (tab + 7) & ~7
     block = (woff + nq * 8 + nq * esz + 15) & ~15
     off_e = (block + C * ls * 8 + 15) & ~15
@@ -90,20 +99,25 @@ def candidates(kind, dim, degree, nq, n_loc, ncomp, fields=1, eta_min=0.3, max_t
     out = []
     if tpc_available(kind, dim, degree):
         out.append(Candidate(0))
-    cmax = 1
-    for C in range(1, 65):
-        if _coop_total_bytes(n_loc, nq, dim, ncomp, C, fields) <= SMEM_BUDGET:
-            cmax = C
-    seen = set()
-    for k in range(1, 64):
-        C = math.ceil(cmax / k)
-        if C in seen:
-            continue
-        seen.add(C)
-        if C == cmax or eta_simd(C * nq) >= eta_min:
-            out.append(Candidate(1, C))
-        if len(seen) >= max_tiles or C == 1:
-            break
+    # table residency: shared memory when the table fits, always also global memory
+    residencies = [True]
+    if nq * (1 + dim) * n_loc * 8 <= SMEM_TABLE_MAX:
+        residencies.insert(0, False)
+    for gt in residencies:
+        cmax = 1
+        for C in range(1, 65):
+            if _coop_total_bytes(n_loc, nq, dim, ncomp, C, fields, tables_global=gt) <= SMEM_BUDGET:
+                cmax = C
+        seen = set()
+        for k in range(1, 64):
+            C = math.ceil(cmax / k)
+            if C in seen:
+                continue
+            seen.add(C)
+            if C == cmax or eta_simd(C * nq) >= eta_min:
+                out.append(Candidate(1, C, gt))
+            if len(seen) >= max_tiles or C == 1:
+                break
     return out
 
 

@@ -45,13 +45,13 @@ const Variant *find_variant(int form, int dim, int degree, int op, int precision
 
 // Largest cell batch whose shared-memory plan leaves room for two CTAs per SM
 // (at most 64 cells, at least 1).
-int coop_cells_for(int n, int nq, int dim, int ncomp, int fields, size_t esz, size_t budget)
+int coop_cells_for(int n, int nq, int dim, int ncomp, int fields, size_t esz, size_t budget, bool gt)
 {
     int best = 1;
     for (int C = 1; C <= 64; ++C) {
         const size_t total = esz == sizeof(float)
-                                 ? coop_layout<float>(n, nq, dim, ncomp, C, fields).total
-                                 : coop_layout<double>(n, nq, dim, ncomp, C, fields).total;
+                                 ? coop_layout<float>(n, nq, dim, ncomp, C, fields, gt).total
+                                 : coop_layout<double>(n, nq, dim, ncomp, C, fields, gt).total;
         if (total <= budget) best = C;
     }
     return best;
@@ -228,17 +228,21 @@ extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan 
     const bool coop = v->kernel_id == 1;
     const int fields_max = (f.kind == FE_FORM_NH_JACOBIAN || (adj != nullptr)) ? 2 : 1;
     int coop_cells = 0;
+    bool global_tab = false;
     size_t rs = (size_t)(1 + m.dim) * n, woff, smem, block_bytes;
     if (coop) {
+        const bool gt = (f.flags & FE_FLAG_TABLES_GLOBAL) ||
+                        (esz == sizeof(float) ? coop_default_global<float>(n, nq, m.dim)
+                                              : coop_default_global<double>(n, nq, m.dim));
         coop_cells = f.tile_cells > 0 ? f.tile_cells
-                                      : coop_cells_for(n, nq, m.dim, ncomp, fields_max, esz, 100 * 1024);
-        if (esz == sizeof(float)) {
-            const CoopLayout L = coop_layout<float>(n, nq, m.dim, ncomp, coop_cells, fields_max);
-            rs = L.rs; woff = L.wts_off; block_bytes = L.table_block_bytes; smem = L.total;
-        } else {
-            const CoopLayout L = coop_layout<double>(n, nq, m.dim, ncomp, coop_cells, fields_max);
-            rs = L.rs; woff = L.wts_off; block_bytes = L.table_block_bytes; smem = L.total;
-        }
+                                      : coop_cells_for(n, nq, m.dim, ncomp, fields_max, esz, 100 * 1024, gt);
+        CoopLayout L = esz == sizeof(float) ? coop_layout<float>(n, nq, m.dim, ncomp, coop_cells, fields_max, gt)
+                                            : coop_layout<double>(n, nq, m.dim, ncomp, coop_cells, fields_max, gt);
+        rs = L.rs;
+        woff = L.wts_off;
+        block_bytes = L.table_block_bytes;
+        smem = L.total;
+        global_tab = L.global_tab != 0;
     } else {
         woff = ((size_t)nq * rs * esz + 7) & ~(size_t)7;
         block_bytes = (woff + (size_t)nq * (sizeof(double) + esz) + 15) & ~(size_t)15;
@@ -246,24 +250,32 @@ extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan 
     }
     const int tab_doubles = (int)(block_bytes / sizeof(double));
     if (smem > 200 * 1024) return FE_ERR_UNSUPPORTED;
-    std::vector<double> block(tab_doubles, 0.0);
+    // global-memory tables of the cooperative kernel follow the staged block:
+    // phase B [1+d][n][nq], then phase C [nq][1+d][n], each 16-byte aligned
+    const size_t gsz = global_tab ? (((size_t)(1 + m.dim) * n * nq * esz + 15) & ~(size_t)15) : 0;
+    const size_t alloc_bytes = block_bytes + 2 * gsz;
+    std::vector<double> block(alloc_bytes / sizeof(double), 0.0);
     unsigned char *blk = reinterpret_cast<unsigned char *>(block.data());
+    auto put = [&](size_t byte_off, size_t idx, double t) {
+        if (esz == sizeof(float))
+            reinterpret_cast<float *>(blk + byte_off)[idx] = (float)t;
+        else
+            reinterpret_cast<double *>(blk + byte_off)[idx] = t;
+    };
     for (int q = 0; q < nq; ++q)
         for (int k = 0; k <= m.dim; ++k)
             for (int j = 0; j < n; ++j) {
                 const double t = tab[((size_t)k * nq + q) * n + j];
-                const size_t idx = (size_t)q * rs + (size_t)k * n + j;
-                if (esz == sizeof(float))
-                    reinterpret_cast<float *>(blk)[idx] = (float)t;
-                else
-                    reinterpret_cast<double *>(blk)[idx] = t;
+                if (global_tab) {
+                    put(block_bytes, ((size_t)k * n + j) * nq + q, t);
+                    put(block_bytes + gsz, ((size_t)q * (1 + m.dim) + k) * n + j, t);
+                } else {
+                    put(0, (size_t)q * rs + (size_t)k * n + j, t);
+                }
             }
     for (int q = 0; q < nq; ++q) {
         reinterpret_cast<double *>(blk + woff)[q] = wts[q];
-        if (esz == sizeof(float))
-            reinterpret_cast<float *>(blk + woff + (size_t)nq * sizeof(double))[q] = (float)wts[q];
-        else
-            reinterpret_cast<double *>(blk + woff + (size_t)nq * sizeof(double))[q] = wts[q];
+        put(woff + (size_t)nq * sizeof(double), q, wts[q]);
     }
 
     fe_plan *p = new (std::nothrow) fe_plan();
@@ -279,7 +291,7 @@ extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan 
     p->smem_bytes = smem;
     cudaGetDevice(&p->device);
     p->coop_cells = coop_cells;
-    if (cudaMalloc(&p->d_tab, block_bytes) != cudaSuccess ||
+    if (cudaMalloc(&p->d_tab, alloc_bytes) != cudaSuccess ||
         cudaMalloc(&p->d_status, 8 * sizeof(int32_t)) != cudaSuccess) {
         cudaFree(p->d_tab);
         delete p;
@@ -287,7 +299,9 @@ extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan 
         return FE_ERR_NO_MEMORY;
     }
     p->d_sched = p->d_status + 4;  // status word, padding, then the queue counters
-    if (cudaMemcpy(p->d_tab, block.data(), block_bytes, cudaMemcpyHostToDevice) != cudaSuccess ||
+    p->d_tab_b = global_tab ? reinterpret_cast<unsigned char *>(p->d_tab) + block_bytes : nullptr;
+    p->d_tab_c = global_tab ? reinterpret_cast<unsigned char *>(p->d_tab) + block_bytes + gsz : nullptr;
+    if (cudaMemcpy(p->d_tab, block.data(), alloc_bytes, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(p->d_status, 0, 8 * sizeof(int32_t)) != cudaSuccess) {
         fe_plan_destroy(p);
         return FE_ERR_CUDA;
@@ -343,6 +357,8 @@ static ActionArgs make_args(const fe_plan *p, const double *u, double *y)
     a.sched = p->d_sched;
     a.coop_n = p->n_loc;
     a.coop_cells = p->coop_cells;
+    a.tab_b = p->d_tab_b;
+    a.tab_c = p->d_tab_c;
     return a;
 }
 

@@ -80,8 +80,8 @@ template <int OP, int D>
 __device__ __forceinline__ void run_coop(const BatchProblemDev &P, unsigned char *base, int cell0)
 {
     constexpr int NC = OpTraits<OP, D>::NC;
-    const CoopLayout L = coop_layout<double>(P.a.coop_n, P.a.nq, D, NC, P.coop_cells, 1);
-    const CoopSmem<double> S = coop_smem<double>(base, L);
+    const CoopLayout L = coop_layout<double>(P.a.coop_n, P.a.nq, D, NC, P.coop_cells, 1, P.a.tab_b != nullptr);
+    const CoopSmem<double> S = coop_smem<double>(base, L, P.a);
     coop_batch<OP, D, double>(P.a, L, S, cell0, min(P.coop_cells, P.a.n_cells - cell0));
 }
 
@@ -230,6 +230,8 @@ extern "C" int fe_batch_create(const fe_batch_problem *problems, int count, fe_b
     std::vector<size_t> offsets(count);
     std::vector<double> cost(count);
     std::vector<ZeroSpan> spans(count);
+    std::vector<size_t> staged_doubles(count), gsizes(count);
+    std::vector<long long> global_off(count);
     size_t table_doubles = 0, smem = 0;
     for (int i = 0; i < count; ++i) {
         const fe_batch_problem &pb = problems[i];
@@ -238,7 +240,7 @@ extern "C" int fe_batch_create(const fe_batch_problem *problems, int count, fe_b
         if (m.dim < 2 || m.dim > 3 || m.degree < 1 || m.n_cells < 0 || m.n_nodes < 0 || !pb.y ||
             (m.n_cells > 0 && (!m.coords || !m.cell2vertex || !m.cell2node || !pb.u)) ||
             f.precision != FE_PREC_FP64 || f.kind < FE_FORM_MASS || f.kind > FE_FORM_NH_RESIDUAL ||
-            f.quad_degree < 0 || f.quad_degree > 40 || (f.flags & FE_FLAG_ACCUMULATE) ||
+            f.quad_degree < 0 || f.quad_degree > 40 || (f.flags & ~(uint32_t)FE_FLAG_TABLES_GLOBAL) ||
             (m.dim == 2 && reinterpret_cast<uintptr_t>(m.coords) % 16 != 0) ||
             (m.dim == 2 && f.kind != FE_FORM_MASS && reinterpret_cast<uintptr_t>(pb.u) % 16 != 0)) {
             batch_free(b);
@@ -261,12 +263,15 @@ extern "C" int fe_batch_create(const fe_batch_problem *problems, int count, fe_b
         }
         int C = 0;
         size_t rs, block_bytes, need;
+        bool global_tab = false;
         if (kind == 1) {
             C = pb.tile_cells > 0 ? pb.tile_cells : 16;
-            const CoopLayout L = coop_layout<double>(n, nq, m.dim, ncomp, C, 1);
+            const bool gt = (f.flags & FE_FLAG_TABLES_GLOBAL) || coop_default_global<double>(n, nq, m.dim);
+            const CoopLayout L = coop_layout<double>(n, nq, m.dim, ncomp, C, 1, gt);
             rs = L.rs;
             block_bytes = L.table_block_bytes;
             need = L.total;
+            global_tab = L.global_tab != 0;
         } else {
             rs = (size_t)(1 + m.dim) * n;
             block_bytes = ((size_t)nq * rs * 8 + (size_t)nq * 16 + 15) & ~(size_t)15;
@@ -277,18 +282,33 @@ extern "C" int fe_batch_create(const fe_batch_problem *problems, int count, fe_b
             return FE_ERR_UNSUPPORTED;
         }
         smem = std::max(smem, need);
+        // staged block (table rows unless kept in global memory, then the weights
+        // twice), followed for global-table problems by the phase-B [1+d][n][nq]
+        // and phase-C [nq][1+d][n] tables; every piece an even number of doubles
+        const size_t tdoubles = global_tab ? 0 : (size_t)nq * rs;
+        const size_t gdoubles = global_tab ? (((size_t)(1 + m.dim) * n * nq + 1) & ~(size_t)1) : 0;
         std::vector<double> &blk = blocks[i];
-        blk.assign(block_bytes / 8, 0.0);
+        blk.assign(block_bytes / 8 + 2 * gdoubles, 0.0);
         for (int q = 0; q < nq; ++q)
             for (int k = 0; k <= m.dim; ++k)
-                for (int j = 0; j < n; ++j) blk[(size_t)q * rs + (size_t)k * n + j] = tab[((size_t)k * nq + q) * n + j];
-        const size_t woff = (((size_t)nq * rs * 8 + 7) & ~(size_t)7) / 8;
+                for (int j = 0; j < n; ++j) {
+                    const double t = tab[((size_t)k * nq + q) * n + j];
+                    if (global_tab) {
+                        blk[block_bytes / 8 + ((size_t)k * n + j) * nq + q] = t;
+                        blk[block_bytes / 8 + gdoubles + ((size_t)q * (1 + m.dim) + k) * n + j] = t;
+                    } else {
+                        blk[(size_t)q * rs + (size_t)k * n + j] = t;
+                    }
+                }
         for (int q = 0; q < nq; ++q) {
-            blk[woff + q] = wts[q];
-            blk[woff + nq + q] = wts[q];
+            blk[tdoubles + q] = wts[q];
+            blk[tdoubles + nq + q] = wts[q];
         }
         offsets[i] = table_doubles;
-        table_doubles += blk.size();   // multiple of 2: every block stays 16-byte aligned
+        table_doubles += blk.size();   // multiple of 2: every piece stays 16-byte aligned
+        staged_doubles[i] = block_bytes / 8;
+        global_off[i] = global_tab ? (long long)(block_bytes / 8) : -1;
+        gsizes[i] = gdoubles;
 
         BatchProblemDev &P = probs[i];
         std::memset(&P, 0, sizeof(P));
@@ -302,7 +322,7 @@ extern "C" int fe_batch_create(const fe_batch_problem *problems, int count, fe_b
         a.lam_cell = f.lambda_cell;
         a.mu = f.mu;
         a.lam = f.lambda;
-        a.tab_doubles = (int32_t)blk.size();
+        a.tab_doubles = (int32_t)staged_doubles[i];
         a.nq = nq;
         a.n_cells = m.n_cells;
         a.n_vertices = m.n_vertices;
@@ -347,6 +367,10 @@ extern "C" int fe_batch_create(const fe_batch_problem *problems, int count, fe_b
     }
     for (int i = 0; i < count; ++i) {
         probs[i].a.tab = b->d_tables + offsets[i];
+        if (global_off[i] >= 0) {
+            probs[i].a.tab_b = b->d_tables + offsets[i] + global_off[i];
+            probs[i].a.tab_c = b->d_tables + offsets[i] + global_off[i] + gsizes[i];
+        }
         probs[i].a.status = b->d_words;
         probs[i].a.sched = nullptr;   // the batched kernel uses the batch's queue
         if (cudaMemcpy(b->d_tables + offsets[i], blocks[i].data(), blocks[i].size() * 8, cudaMemcpyHostToDevice) !=

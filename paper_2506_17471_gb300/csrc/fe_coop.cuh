@@ -18,7 +18,10 @@
 // (operation, dimension, contraction type) serves every degree.
 // Shared-memory strides are odd (in 8-byte words for double, 4-byte for float)
 // so that threads reading consecutive quadrature points or cells hit distinct
-// banks.
+// banks.  Tables larger than kCoopSmemTableBytes stay in global memory (L2/L1
+// resident) in two layouts, [1+D][N][nq] for phase B (consecutive threads read
+// consecutive quadrature points) and [nq][1+D][N] for phase C (consecutive
+// nodes), so shared memory holds only the batch scratch and the weights.
 #pragma once
 
 #include "fe_kernels.cuh"
@@ -26,10 +29,12 @@
 namespace fe {
 
 constexpr int kCoopBlock = 256;
+constexpr size_t kCoopSmemTableBytes = 96 * 1024;   // larger tables stay in global memory
 
 // Shared-memory plan of one CTA, computed identically on host and device.
 struct CoopLayout {
     int n, nq, D, NC, C, fields;
+    int global_tab;   // 1: the tables stay in global memory (only the weights are staged)
     int rs;        // table row stride per quadrature point (elements), odd
     int ls;        // per-cell DoF stride (doubles), odd
     int es;        // per-(cell, q) stride of e (elements), odd
@@ -37,8 +42,17 @@ struct CoopLayout {
     size_t off_l, off_e, off_nodes, off_geo, off_acc, total;
 };
 
+// Default table residency of the cells-per-CTA kernel: shared memory unless the
+// table is larger than kCoopSmemTableBytes (a plan may also ask for global).
 template <typename R>
-__host__ __device__ inline CoopLayout coop_layout(int n, int nq, int D, int NC, int C, int fields)
+__host__ __device__ inline bool coop_default_global(int n, int nq, int D)
+{
+    return (size_t)nq * (1 + D) * n * sizeof(R) > kCoopSmemTableBytes;
+}
+
+template <typename R>
+__host__ __device__ inline CoopLayout coop_layout(int n, int nq, int D, int NC, int C, int fields,
+                                                  bool global_tab)
 {
     CoopLayout L;
     L.n = n;
@@ -50,7 +64,8 @@ __host__ __device__ inline CoopLayout coop_layout(int n, int nq, int D, int NC, 
     L.rs = ((1 + D) * n) | 1;
     L.ls = (fields * n * NC) | 1;
     L.es = (D * NC) | 1;
-    L.tab_bytes = (size_t)nq * L.rs * sizeof(R);
+    L.global_tab = global_tab ? 1 : 0;
+    L.tab_bytes = L.global_tab ? 0 : (size_t)nq * L.rs * sizeof(R);
     L.wts_off = (L.tab_bytes + 7) & ~(size_t)7;
     L.wtsr_off = L.wts_off + (size_t)nq * sizeof(double);
     L.table_block_bytes = (L.wtsr_off + (size_t)nq * sizeof(R) + 15) & ~(size_t)15;
@@ -69,6 +84,8 @@ __host__ __device__ inline CoopLayout coop_layout(int n, int nq, int D, int NC, 
 template <typename R>
 struct CoopSmem {
     const R *tab;
+    const R *tab_b;     // global-memory tables (global_tab == 1)
+    const R *tab_c;
     const double *wts;
     const R *wts_r;
     double *l;
@@ -79,10 +96,13 @@ struct CoopSmem {
 };
 
 template <typename R>
-__device__ __forceinline__ CoopSmem<R> coop_smem(unsigned char *base, const CoopLayout &L)
+__device__ __forceinline__ CoopSmem<R> coop_smem(unsigned char *base, const CoopLayout &L,
+                                                 const ActionArgs &a)
 {
     CoopSmem<R> S;
     S.tab = reinterpret_cast<const R *>(base);
+    S.tab_b = reinterpret_cast<const R *>(a.tab_b);
+    S.tab_c = reinterpret_cast<const R *>(a.tab_c);
     S.wts = reinterpret_cast<const double *>(base + L.wts_off);
     S.wts_r = reinterpret_cast<const R *>(base + L.wtsr_off);
     S.l = reinterpret_cast<double *>(base + L.off_l);
@@ -162,6 +182,8 @@ __device__ __forceinline__ void coop_batch(const ActionArgs &a, const CoopLayout
         const int c = i / nq, q = i - c * nq;
         const double *g = sgeo + c * 16;
         const R *T = tab + (size_t)q * L.rs;
+        const bool gtab = L.global_tab;
+        const R *TB = S.tab_b + q;   // [k][j][q]: element (k, j) at TB[(k * n + j) * nq]
         const double *lc = sl + c * L.ls;
         R *e = se + ((size_t)c * nq + q) * L.es;
         const double absdet = g[D * D];
@@ -173,7 +195,8 @@ __device__ __forceinline__ void coop_batch(const ActionArgs &a, const CoopLayout
         const double mu = g[D * D + 1], lam = g[D * D + 2];
         if constexpr (OP == OP_MASS) {
             R uq = R(0);
-            for (int j = 0; j < n; ++j) uq = fma(T[j], cvt<R>(lc[j]), uq);
+            for (int j = 0; j < n; ++j)
+                uq = fma(gtab ? __ldg(TB + (size_t)j * nq) : T[j], cvt<R>(lc[j]), uq);
             e[0] = uq * (wts_r[q] * cvt<R>(absdet));
         } else {
             // reference gradients of the field(s) at q
@@ -187,7 +210,8 @@ __device__ __forceinline__ void coop_batch(const ActionArgs &a, const CoopLayout
             for (int j = 0; j < n; ++j) {
                 R t[D];
 #pragma unroll
-                for (int k = 0; k < D; ++k) t[k] = T[(k + 1) * n + j];
+                for (int k = 0; k < D; ++k)
+                    t[k] = gtab ? __ldg(TB + ((size_t)(k + 1) * n + j) * nq) : T[(k + 1) * n + j];
 #pragma unroll
                 for (int f = 0; f < FIELDS; ++f)
 #pragma unroll
@@ -307,15 +331,16 @@ __device__ __forceinline__ void coop_batch(const ActionArgs &a, const CoopLayout
 #pragma unroll
         for (int m = 0; m < NC; ++m) out[m] = R(0);
         const R *ec = se + (size_t)c * nq * L.es;
+        const bool gtab = L.global_tab;
         for (int q = 0; q < nq; ++q) {
-            const R *T = tab + (size_t)q * L.rs;
+            const R *T = gtab ? S.tab_c + (size_t)q * (D + 1) * n : tab + (size_t)q * L.rs;
             const R *e = ec + (size_t)q * L.es;
             if constexpr (OP == OP_MASS) {
-                out[0] = fma(T[j], e[0], out[0]);
+                out[0] = fma(gtab ? __ldg(T + j) : T[j], e[0], out[0]);
             } else {
 #pragma unroll
                 for (int k = 0; k < D; ++k) {
-                    const R t = T[(k + 1) * n + j];
+                    const R t = gtab ? __ldg(T + (k + 1) * n + j) : T[(k + 1) * n + j];
 #pragma unroll
                     for (int m = 0; m < NC; ++m) out[m] = fma(t, e[m * D + k], out[m]);
                 }
@@ -341,12 +366,12 @@ __global__ void __launch_bounds__(kCoopBlock) k_action_coop(const ActionArgs a, 
     extern __shared__ __align__(128) double smem[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ int s_chunk;
-    const CoopLayout L = coop_layout<R>(n, a.nq, D, NC, C, FIELDS);
+    const CoopLayout L = coop_layout<R>(n, a.nq, D, NC, C, FIELDS, a.tab_b != nullptr);
     if (!stage_table(smem, a.tab, a.tab_doubles, &bar, a.status)) {
         leave_queue(a.sched);
         return;
     }
-    const CoopSmem<R> S = coop_smem<R>(reinterpret_cast<unsigned char *>(smem), L);
+    const CoopSmem<R> S = coop_smem<R>(reinterpret_cast<unsigned char *>(smem), L, a);
     const int n_batches = (a.n_cells + C - 1) / C;
     for (;;) {
         if (threadIdx.x == 0) s_chunk = atomicAdd(a.sched, 1);

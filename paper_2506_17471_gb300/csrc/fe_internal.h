@@ -36,6 +36,8 @@ struct ActionArgs {
     int32_t *sched;           // [2] work-queue counters: next chunk, warps finished (self-resetting)
     int32_t coop_n;           // cooperative kernel: local nodes per cell
     int32_t coop_cells;       // cooperative kernel: cells per CTA batch
+    const void *tab_b;        // cooperative kernel, large tables: [1+D][N][nq] in global memory
+    const void *tab_c;        // cooperative kernel, large tables: [nq][1+D][N] in global memory
 };
 
 // Launch function of one compiled kernel variant.
@@ -83,7 +85,10 @@ struct fe_plan {
     fe_form form;
     fe_mesh mesh;
     int nq, n_loc, ncomp;
-    double *d_tab;        // device table block
+    double *d_tab;        // device table block (cooperative kernel, large tables: then the
+                          // phase-B and phase-C tables follow it in the same allocation)
+    const void *d_tab_b;  // cooperative kernel, large tables (else nullptr)
+    const void *d_tab_c;
     int tab_doubles;
     int32_t *d_status;    // device status word
     int32_t *d_sched;     // [4] work-queue counters: forward kernel [0..1], adjoint kernel [2..3]

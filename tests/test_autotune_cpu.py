@@ -25,14 +25,18 @@ def test_candidates_follow_tile_constraint_and_pruning(at):
     from paper_2506_17471_gb300 import _native as N
     cands = at.candidates(N.FE_FORM_ELASTICITY, 3, 4, nq=64, n_loc=35, ncomp=3)
     assert all(c.kernel == 1 for c in cands)          # no thread-per-cell kernel for P4 tets
+    assert {c.tables_global for c in cands} == {False, True}
+    cands = [c for c in cands if not c.tables_global]
     tiles = [c.tile_cells for c in cands]
     assert tiles == sorted(tiles, reverse=True)
     cmax = max(tiles)
     assert all(any(t == math.ceil(cmax / k) for k in range(1, 64)) for t in tiles)
     for t in tiles:
         assert t == cmax or at.eta_simd(t * 64) >= 0.3
-        assert at._coop_total_bytes(35, 64, 3, 3, t, 1) <= at.SMEM_BUDGET
-    assert at._coop_total_bytes(35, 64, 3, 3, cmax + 1, 1) > at.SMEM_BUDGET
+        assert at._coop_total_bytes(35, 64, 3, 3, t, 1, tables_global=False) <= at.SMEM_BUDGET
+    assert at._coop_total_bytes(35, 64, 3, 3, cmax + 1, 1, tables_global=False) > at.SMEM_BUDGET
+    big = at.candidates(N.FE_FORM_NH_RESIDUAL, 3, 4, nq=125, n_loc=35, ncomp=3)
+    assert big and all(c.tables_global for c in big)     # a 140 KB table never goes to shared
     c2 = at.candidates(N.FE_FORM_MASS, 2, 2, nq=9, n_loc=6, ncomp=1)
     assert c2[0].kernel == 0                           # thread-per-cell exists for P2 mass
 

@@ -24,14 +24,15 @@ def fe():
     return fe
 
 
-def build(fe, specs, kernel=-1, tile=0):
+def build(fe, specs, kernel=-1, tile=0, tables_global=False):
     problems, refs = [], []
     for s in specs:
         dim, p, N, q = s["dim"], s["degree"], s["N"], s["quad_degree"]
         m = structured_mesh(dim, N, p, jitter=0.2 if dim == 2 else 0.15, seed=s["seed"])
         M = fe.Mesh(dim, p, m.coords, m.cell2vertex, m.cell2node, m.n_nodes)
         o = oracle.Oracle.from_mesh(m, q)
-        pb = {"mesh": M, "quad_degree": q, "kernel": kernel, "tile_cells": tile}
+        pb = {"mesh": M, "quad_degree": q, "kernel": kernel, "tile_cells": tile,
+              "tables_global": tables_global}
         if s["form"] == "mass":
             u = uniform_field(m.n_nodes, s["seed"])
             pb.update(kind=fe.MASS)
@@ -51,10 +52,11 @@ def build(fe, specs, kernel=-1, tile=0):
     return problems, refs
 
 
-@pytest.mark.parametrize("kernel,tile", [(-1, 0), (1, 8), (1, 3)])
-def test_batched_matches_oracle(fe, kernel, tile):
+@pytest.mark.parametrize("kernel,tile,tables_global", [(-1, 0, False), (1, 8, False), (1, 3, False),
+                                                       (1, 5, True)])
+def test_batched_matches_oracle(fe, kernel, tile, tables_global):
     specs = batch_specs(count=18, seed=77, cells_min=40, cells_max=2500)
-    problems, refs = build(fe, specs, kernel, tile)
+    problems, refs = build(fe, specs, kernel, tile, tables_global)
     batch = fe.Batch(problems)
     assert batch.info["problems"] == len(specs)
     for rep in range(2):

@@ -153,3 +153,27 @@ def test_hp_sweep_full_size(fe, name, dim, p, N, q):
         ref = sampled_oracle(m, q, nodes, fn)
         idx = (nodes[:, None] * ncomp + np.arange(ncomp)[None, :]).reshape(-1)
         assert np.abs(y[idx] - ref[idx]).max() <= tol * np.abs(y).max()
+
+
+@pytest.mark.parametrize("dim,N,p", [(2, 5, 6), (3, 3, 3), (3, 2, 4)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_coop_tables_in_global_memory(fe, dim, N, p, prec):
+    """Cells-per-CTA kernel with the tabulation kept in global memory (two
+    coalesced layouts) instead of shared memory."""
+    m, M = make(fe, dim, N, p, 400 + p)
+    tol = TOL if prec == "fp64" else TOL32
+    q = 2 * p
+    o = oracle.Oracle.from_mesh(m, q)
+    mu, lam = lame_fields(m.n_cells, 3)
+    u = sinusoid_displacement(m, 4)
+    w = uniform_field(m.n_nodes * dim, 5)
+    res = fe.Plan(M, fe.NH_RESIDUAL, q, mu_cell=mu, lam_cell=lam, precision=prec, cooperative=True,
+                  tables_global=True)
+    assert rel(res.apply(cuda(u)), o.nh_residual(u, mu, lam)) <= (tol if prec == "fp64" else 1e3 * tol)
+    jtw, dmu, _ = res.adjoint(cuda(u), cuda(w))
+    ojtw, odmu, _ = o.nh_adjoint(u, w, mu, lam)
+    assert rel(jtw, ojtw) <= tol
+    s = uniform_field(m.n_nodes, 6)
+    mp = fe.Plan(M, fe.MASS, q, precision=prec, cooperative=True, tables_global=True, tile_cells=7)
+    assert rel(mp.apply(cuda(s)), o.mass(s)) <= tol
+    assert res.status() == 0 and mp.status() == 0
