@@ -23,11 +23,11 @@ the largest tile is always kept.
 Cost model: on GB300 the FP64 pipe, not memory, binds (machine balance 0.18
 flop/B), so the paper's global + local memory time t_heur is extended with an
 FP64 term and kept as the memory bound:
-    t = max(flops / (F_peak eta), bytes / beta_HBM) + t_launch + batches x t_batch / (SMs x resident)
-with eta = eta_tail (thread-per-cell: 32-cell warp chunks over the resident
-warps) or the flop-weighted mean of eta_B and eta_C (cells-per-CTA; evaluation
-and quadrature carry equal contraction flops), and t_batch the latency of one
-gather/barrier round.  ``spearman`` measures how well the model ranks measured candidates
+    t = max(flops / (F_peak eta), bytes / beta_HBM) + t_launch + rounds x t_round
+where eta combines how well the launch fills the machine (and its last round,
+the tail) with the lane efficiency of the cells-per-CTA phases (evaluation and
+quadrature carry equal contraction flops; co-resident CTAs fill idle lanes);
+see :func:`model_time`.  ``spearman`` measures how well the model ranks measured candidates
 (the paper's Eq. "spearmann_rho").
 """
 
@@ -121,18 +121,37 @@ def candidates(kind, dim, degree, nq, n_loc, ncomp, fields=1, eta_min=0.3, max_t
     return out
 
 
-def model_time(c: Candidate, n_cells, flops, bytes_min, nq, n_loc, resident_per_sm=2):
+SMEM_PER_SM = 228 * 1024
+WARPS_TO_FILL_SM = 8          # warps per SM that keep the FP64 pipe busy (measured: 95 % at 8)
+
+
+def model_time(c: Candidate, n_cells, flops, bytes_min, nq, n_loc, ncomp=1, fields=1, dim=2):
+    """Modelled time of one action.
+
+    Thread-per-cell: one thread per cell in 32-cell warp chunks; the machine is
+    full at WARPS_TO_FILL_SM warps per SM, and the last round of chunks is the
+    tail: eta = warps / (W ceil(warps / W)), W = SMs x WARPS_TO_FILL_SM.
+    Cells-per-CTA: ceil(n_cells / C) CTAs of 256 threads over SMs x resident
+    slots (resident CTAs per SM from the shared-memory plan, at most 4), the
+    same fill/tail factor over slots, times the lane efficiency of its two
+    phases, whose idle lanes co-resident CTAs partly fill."""
     t_mem = bytes_min / (HBM_GBS * 1e9)
     if c.kernel == 0:
-        chunks = math.ceil(n_cells / 32)
-        warps = N_SMS * 4 * resident_per_sm
-        eta = chunks / (warps * math.ceil(chunks / warps)) if chunks else 1.0
-        batches = math.ceil(n_cells / 128)
+        warps = max(1, math.ceil(n_cells / 32))
+        full = N_SMS * WARPS_TO_FILL_SM
+        eta = warps / (full * math.ceil(warps / full))
+        rounds = math.ceil(warps / full)
     else:
-        eta = eta_simd(c.tile_cells * nq) * 0.5 + 0.5 * eta_simd(c.tile_cells * n_loc)
-        batches = math.ceil(n_cells / c.tile_cells)
+        smem = _coop_total_bytes(n_loc, nq, dim, ncomp, c.tile_cells, fields, tables_global=c.tables_global)
+        resident = max(1, min(4, SMEM_PER_SM // max(smem, 1)))
+        ctas = max(1, math.ceil(n_cells / c.tile_cells))
+        slots = N_SMS * resident
+        eta_par = ctas / (slots * math.ceil(ctas / slots))
+        lanes = 0.5 * eta_simd(c.tile_cells * nq) + 0.5 * eta_simd(c.tile_cells * n_loc)
+        eta = eta_par * (1.0 - (1.0 - lanes) / resident)
+        rounds = math.ceil(ctas / slots)
     t_fp = flops / (F_PEAK_GFLOPS * 1e9 * max(eta, 1e-3))
-    return max(t_fp, t_mem) + T_LAUNCH_S + batches * T_BATCH_S / (N_SMS * resident_per_sm)
+    return max(t_fp, t_mem) + T_LAUNCH_S + rounds * T_BATCH_S
 
 
 def spearman(xs, ys) -> float:
@@ -181,7 +200,8 @@ def tune(make_plan, u, key: str, kind, dim, degree, top_b: int = 3, reps: int = 
     flops, bytes_min, n_cells = probe.flops(), probe.info.bytes_min, probe.mesh.n_cells
     del probe
     cands = candidates(kind, dim, degree, nq, n_loc, ncomp)
-    ranked = sorted(cands, key=lambda c: model_time(c, n_cells, flops, bytes_min, nq, n_loc))
+    mt = lambda c: model_time(c, n_cells, flops, bytes_min, nq, n_loc, ncomp, dim=dim)  # noqa: E731
+    ranked = sorted(cands, key=mt)
     chosen = ranked if time_all else ranked[:top_b]
     measured = {}
     stream = torch.cuda.current_stream()
@@ -201,12 +221,11 @@ def tune(make_plan, u, key: str, kind, dim, degree, top_b: int = 3, reps: int = 
         measured[c] = statistics.median(ts)
     best = min(measured, key=measured.get)
     report = {"candidates": [c.label() for c in ranked],
-              "model_s": {c.label(): model_time(c, n_cells, flops, bytes_min, nq, n_loc) for c in ranked},
+              "model_s": {c.label(): mt(c) for c in ranked},
               "measured_s": {c.label(): t for c, t in measured.items()}, "best": best.label()}
     if len(measured) >= 3:
         cs = list(measured)
-        report["spearman"] = spearman([model_time(c, n_cells, flops, bytes_min, nq, n_loc) for c in cs],
-                                      [measured[c] for c in cs])
+        report["spearman"] = spearman([mt(c) for c in cs], [measured[c] for c in cs])
     if use_cache:
         cache = _load_cache()
         cache[key] = {"kernel": best.kernel, "tile_cells": best.tile_cells}

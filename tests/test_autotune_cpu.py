@@ -48,8 +48,11 @@ def test_cost_model_monotone(at):
     assert t2 > t1
     # memory-bound regime: time follows bytes
     t3 = at.model_time(c, 1000, 1.0, 1e9, 8, 10)
-    assert t3 == pytest.approx(1e9 / (at.HBM_GBS * 1e9) + at.T_LAUNCH_S
-                               + math.ceil(1000 / 128) * at.T_BATCH_S / (at.N_SMS * 2))
+    assert t3 == pytest.approx(1e9 / (at.HBM_GBS * 1e9) + at.T_LAUNCH_S + at.T_BATCH_S)
+    # a mesh too small to fill the machine favours the cells-per-CTA kernel
+    small_tpc = at.model_time(at.Candidate(0), 2000, 1e8, 1e6, 27, 20, 1, dim=3)
+    small_coop = at.model_time(at.Candidate(1, 4), 2000, 1e8, 1e6, 27, 20, 1, dim=3)
+    assert small_coop < small_tpc
 
 
 def test_spearman(at):
