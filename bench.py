@@ -4,7 +4,7 @@ Workload (one step = one full matrix-free action, every hot-path step):
 linear elasticity, vector P2 Lagrange on tetrahedra, unit cube cut into 32^3
 cubes x 6 Kuhn tets (196,608 cells, 3 x 274,625 DoFs), interior vertices
 jittered by U[-0.15h, 0.15h], lambda = 1.25, mu = 1, quadrature exact to degree
-2 (8-point conical-product rule), u ~ U[-1, 1], FP64 throughout.
+2 (the 4-point fully symmetric rule), u ~ U[-1, 1], FP64 throughout.
 
 Timing: W untimed warm-up steps, then K steps; each step's kernels are bracketed
 by CUDA events on the launch stream and a 256 MB buffer is written between steps
@@ -41,9 +41,10 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP64 FMA peak from the part's unit counts and clocks: 1.25 TFLOP/s nominal for a
 # GB300 (152 SMs at up to 2070 MHz, about 4 FP64 flops per SM per clock).
 FP64_NOMINAL_GFLOPS = 1250.0
+QUAD_SCHEME = "symmetric"   # the 4-point fully symmetric degree-2 rule
 WORKLOAD = ("linear elasticity, vector P2 tets, unit cube 32^3 x 6 Kuhn tets (196,608 cells, "
-            "823,875 DoFs), jitter 0.15h, lambda=1.25 mu=1, quadrature degree 2 (8-point "
-            "conical-product rule), FP64")
+            "823,875 DoFs), jitter 0.15h, lambda=1.25 mu=1, quadrature degree 2 (4-point fully "
+            "symmetric rule), FP64")
 
 
 def parse():
@@ -77,7 +78,7 @@ def cpu_oracle_rate(m, u, budget_cpu_s=12.0, threads=None):
     about ``budget_cpu_s`` CPU-seconds were spent (bounded sample)."""
     import oracle
     threads = threads or os.cpu_count() or 1
-    o = oracle.Oracle.from_mesh(m, 2)
+    o = oracle.Oracle.from_mesh(m, 2, QUAD_SCHEME)
     o.elasticity(u, 1.25, 1.0, threads=threads, cells=(0, min(m.n_cells, 2048)))  # warm
     reps, t0 = 0, time.perf_counter()
     while True:
@@ -99,7 +100,7 @@ def run_reference(args):
     m, u = make_inputs()
     threads = os.cpu_count() or 1
     import oracle
-    o = oracle.Oracle.from_mesh(m, 2)
+    o = oracle.Oracle.from_mesh(m, 2, QUAD_SCHEME)
     # each step: the oracle action on a fixed sample of 1/4 of the cells
     c1 = m.n_cells // 4
     for _ in range(args.warmup):
@@ -235,9 +236,15 @@ def time_secondary(fe, torch, flush, M_el, u_el, y64_el):
     out["nh_p4_2d_n256_fp32"]["rel_dev_fwd_vs_fp64"] = rel(res["fp32"][2], res["fp64"][2])
     out["nh_p4_2d_n256_fp32"]["rel_dev_adj_vs_fp64"] = rel(res["fp32"][3], res["fp64"][3])
 
-    # elasticity P2 3D (the headline workload) with FP32 contractions
-    p64 = fe.Plan(M_el, fe.ELASTICITY, 2, lam=1.25, mu=1.0)
-    p32 = fe.Plan(M_el, fe.ELASTICITY, 2, lam=1.25, mu=1.0, precision="fp32")
+    # elasticity P2 3D (the headline workload) with FP32 contractions, and with the
+    # 8-point conical-product rule for comparison
+    p64 = fe.Plan(M_el, fe.ELASTICITY, 2, lam=1.25, mu=1.0, quad_scheme=QUAD_SCHEME)
+    p32 = fe.Plan(M_el, fe.ELASTICITY, 2, lam=1.25, mu=1.0, precision="fp32", quad_scheme=QUAD_SCHEME)
+    pcon = fe.Plan(M_el, fe.ELASTICITY, 2, lam=1.25, mu=1.0)
+    ycon = torch.empty_like(u_el)
+    tcon = timed(lambda: pcon.apply(u_el, ycon))
+    out["elasticity_p2_3d_n32_conical8"] = {"ms": tcon * 1e3, "dofs_per_s": pcon.n_dofs / tcon,
+                                             "gflops": pcon.flops() / tcon / 1e9, "nq": pcon.info.nq}
     y32 = torch.empty_like(u_el)
     t64 = timed(lambda: p64.apply(u_el, y64_el))
     t32 = timed(lambda: p32.apply(u_el, y32))
@@ -451,7 +458,7 @@ def run_ours(args):
     m, u_np = make_inputs()
     _BOUNDARY[:] = [m.boundary_nodes()]
     M = fe.Mesh(3, 2, m.coords, m.cell2vertex, m.cell2node, m.n_nodes, device=dev)
-    plan = fe.Plan(M, fe.ELASTICITY, 2, lam=1.25, mu=1.0)
+    plan = fe.Plan(M, fe.ELASTICITY, 2, lam=1.25, mu=1.0, quad_scheme=QUAD_SCHEME)
     n_dofs = plan.n_dofs
     u = torch.from_numpy(u_np).to(dev)
     y = torch.empty_like(u)
@@ -488,7 +495,7 @@ def run_ours(args):
     step_ms = [a.elapsed_time(b) for a, b in ev]
 
     # the action kernel alone (accumulate plan: no zero kernel) for the roofline
-    plan_acc = fe.Plan(M, fe.ELASTICITY, 2, lam=1.25, mu=1.0, accumulate=True)
+    plan_acc = fe.Plan(M, fe.ELASTICITY, 2, lam=1.25, mu=1.0, accumulate=True, quad_scheme=QUAD_SCHEME)
     kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
     for i in range(args.steps):

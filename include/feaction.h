@@ -125,7 +125,7 @@ typedef struct fe_form {
     int32_t tile_cells;          /* cells per CTA batch of the cells-per-CTA kernel
                                     (0: the largest that leaves room for two CTAs
                                     per SM); ignored by the thread-per-cell kernel  */
-    int32_t reserved;
+    int32_t quad_scheme;         /* enum fe_quad_scheme (0: conical product)        */
 } fe_form;
 
 /* ------------------------------------------------------------------ tabulation */
@@ -144,6 +144,24 @@ typedef struct fe_form {
  * or > 40, cap too small). */
 int fe_tabulate(int dim, int degree, int quad_degree, int *nq, double *pts, double *wts,
                 double *tab, size_t cap);
+
+/* Quadrature families (fe_form.quad_scheme). */
+enum fe_quad_scheme {
+    FE_QUAD_CONICAL = 0,   /* collapsed conical-product Gauss-Jacobi rule (as fe_tabulate) */
+    FE_QUAD_SYMMETRIC = 1  /* fully symmetric rule (invariant under every permutation of the
+                              barycentric coordinates, positive weights, interior points) of
+                              the smallest tabulated degree >= quad_degree, derived at run
+                              time by Gauss-Newton on the moment equations from a stated
+                              orbit structure; tabulated: triangles degree 2, 4, 6, 8 (3, 6,
+                              12, 16 points), tetrahedra degree 2, 5 (4, 14 points).  Other
+                              requests fall back to FE_QUAD_CONICAL.  Points are ordered
+                              lexicographically by (xhat_1, xhat_2, xhat_3).            */
+};
+
+/* fe_tabulate for either quadrature family; same outputs and errors
+ * (FE_ERR_INVALID_ARG also for an unknown scheme). */
+int fe_tabulate_scheme(int dim, int degree, int quad_degree, int scheme, int *nq, double *pts,
+                       double *wts, double *tab, size_t cap);
 
 /* ------------------------------------------------------------------ plans */
 typedef struct fe_plan fe_plan;

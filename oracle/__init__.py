@@ -7,6 +7,7 @@ code, headers, tables or helpers.
 
 * ``quadrature.py``: conical-product Gauss-Jacobi rules (Golub-Welsch, numpy).
 * ``basis.py``: Silvester-product Lagrange basis and tabulation (numpy).
+* ``symmetric.py``: fully symmetric rules from the moment equations (scipy).
 * ``oracle.c``: literal sequential Algorithm 2 loops for every form, built with
   gcc into ``oracle/_build/liboracle.so`` by :func:`build`.
 
@@ -88,23 +89,24 @@ class Oracle:
     the layout conventions of ``oracle.c``; ``n_nodes`` is the global node count.
     """
 
-    def __init__(self, dim, degree, quad_degree, coords, cell2vertex, cell2node, n_nodes):
+    def __init__(self, dim, degree, quad_degree, coords, cell2vertex, cell2node, n_nodes,
+                 scheme="conical"):
         self.dim, self.degree, self.quad_degree = int(dim), int(degree), int(quad_degree)
         self.coords = np.ascontiguousarray(coords, dtype=np.float64)
         self.c2v = np.ascontiguousarray(cell2vertex, dtype=np.int32)
         self.c2n = np.ascontiguousarray(cell2node, dtype=np.int32)
         self.n_nodes = int(n_nodes)
         self.n_cells = int(self.c2v.shape[0])
-        self.pts, self.wts, tab = tabulate(self.dim, self.degree, self.quad_degree)
+        self.pts, self.wts, tab = tabulate(self.dim, self.degree, self.quad_degree, scheme)
         self.tab = np.ascontiguousarray(tab)
         self.nloc = int(self.tab.shape[2])
         self.nq = int(self.wts.shape[0])
         assert self.c2n.shape == (self.n_cells, self.nloc)
 
     @classmethod
-    def from_mesh(cls, mesh, quad_degree):
+    def from_mesh(cls, mesh, quad_degree, scheme="conical"):
         return cls(mesh.dim, mesh.degree, quad_degree, mesh.coords, mesh.cell2vertex,
-                   mesh.cell2node, mesh.n_nodes)
+                   mesh.cell2node, mesh.n_nodes, scheme)
 
     # ------------------------------------------------------------------ driver
     def _common(self):

@@ -85,9 +85,14 @@ def basis_at(dim: int, degree: int, x: np.ndarray) -> tuple[np.ndarray, np.ndarr
     return val, grad
 
 
-def tabulate(dim: int, degree: int, quad_degree: int):
-    """(points [Q,d], weights [Q], tab [1+d, Q, n]) for the oracle's own rule."""
-    pts, wts = simplex_rule(dim, quad_degree)
+def tabulate(dim: int, degree: int, quad_degree: int, scheme: str = "conical"):
+    """(points [Q,d], weights [Q], tab [1+d, Q, n]) for the oracle's own rule
+    (``scheme``: "conical" product rule or "symmetric" rule family)."""
+    if scheme == "symmetric":
+        from .symmetric import symmetric_rule
+        pts, wts = symmetric_rule(dim, quad_degree)
+    else:
+        pts, wts = simplex_rule(dim, quad_degree)
     n = len(multi_indices(dim, degree))
     tab = np.empty((1 + dim, len(wts), n))
     for q in range(len(wts)):

@@ -7,10 +7,11 @@ shared library and raises ImportError if it has not been built.
 """
 
 from ._native import FeError, LIB_PATH, EXPORTS
-from .api import (MASS, ELASTICITY, NH_RESIDUAL, NH_JACOBIAN, FORM_NAMES, PRECISIONS, Mesh, Plan,
+from .api import (MASS, ELASTICITY, NH_RESIDUAL, NH_JACOBIAN, FORM_NAMES, PRECISIONS, QUAD_SCHEMES,
+                  Mesh, Plan,
                   PlanInfo,
                   NeoHookeanResidual, Batch, tabulate, measure_fp64_peak)
 
 __all__ = ["FeError", "LIB_PATH", "EXPORTS", "MASS", "ELASTICITY", "NH_RESIDUAL", "NH_JACOBIAN",
-           "FORM_NAMES", "PRECISIONS", "Mesh", "Plan", "PlanInfo", "NeoHookeanResidual", "Batch", "tabulate",
+           "FORM_NAMES", "PRECISIONS", "QUAD_SCHEMES", "Mesh", "Plan", "PlanInfo", "NeoHookeanResidual", "Batch", "tabulate",
            "measure_fp64_peak"]

@@ -29,7 +29,10 @@ FE_FLAG_COOPERATIVE = 2
 FE_FLAG_TABLES_GLOBAL = 4
 
 # every symbol declared in include/feaction.h
-EXPORTS = ("fe_status_string", "fe_tabulate", "fe_plan_create", "fe_plan_destroy", "fe_action",
+FE_QUAD_CONICAL = 0
+FE_QUAD_SYMMETRIC = 1
+
+EXPORTS = ("fe_status_string", "fe_tabulate", "fe_tabulate_scheme", "fe_plan_create", "fe_plan_destroy", "fe_action",
            "fe_action_adjoint", "fe_action_host", "fe_plan_status", "fe_plan_get_info",
            "fe_measure_fp64_peak", "fe_action_noalloc", "fe_cg_start", "fe_cg_direction",
            "fe_cg_update", "fe_cg_new_direction", "fe_vec_axpy", "fe_vec_dot",
@@ -52,7 +55,7 @@ class FeForm(ctypes.Structure):
                 ("lambda_", ctypes.c_double), ("mu", ctypes.c_double),
                 ("lambda_cell", ctypes.c_void_p), ("mu_cell", ctypes.c_void_p),
                 ("u_lin", ctypes.c_void_p), ("tile_cells", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("quad_scheme", ctypes.c_int32)]
 
 
 class FeBatchProblem(ctypes.Structure):
@@ -90,6 +93,7 @@ def _load() -> ctypes.CDLL:
     lib.fe_status_string.argtypes = [I]
     lib.fe_status_string.restype = ctypes.c_char_p
     lib.fe_tabulate.argtypes = [I, I, I, ctypes.POINTER(I), P, P, P, Z]
+    lib.fe_tabulate_scheme.argtypes = [I, I, I, I, ctypes.POINTER(I), P, P, P, Z]
     lib.fe_plan_create.argtypes = [ctypes.POINTER(FeForm), ctypes.POINTER(FeMesh), ctypes.POINTER(P)]
     lib.fe_plan_destroy.argtypes = [P]
     lib.fe_action.argtypes = [P, P, P, P]

@@ -33,20 +33,24 @@ def _dptr(t: torch.Tensor | None) -> ctypes.c_void_p:
     return ctypes.c_void_p(0 if t is None else t.data_ptr())
 
 
-def tabulate(dim: int, degree: int, quad_degree: int):
+QUAD_SCHEMES = {"conical": N.FE_QUAD_CONICAL, "symmetric": N.FE_QUAD_SYMMETRIC}
+
+
+def tabulate(dim: int, degree: int, quad_degree: int, scheme: str = "conical"):
     """Quadrature points [nq,d], weights [nq], tabulation [1+d, nq, n_loc] (host)."""
+    sc = QUAD_SCHEMES[scheme]
     nq = ctypes.c_int(0)
-    N.check(N.lib.fe_tabulate(dim, degree, quad_degree, ctypes.byref(nq), None, None, None, 0),
+    N.check(N.lib.fe_tabulate_scheme(dim, degree, quad_degree, sc, ctypes.byref(nq), None, None, None, 0),
             "fe_tabulate")
     from math import comb
     n = comb(degree + dim, dim)
     pts = np.zeros((nq.value, dim))
     wts = np.zeros(nq.value)
     tab = np.zeros((1 + dim, nq.value, n))
-    N.check(N.lib.fe_tabulate(dim, degree, quad_degree, ctypes.byref(nq),
-                              pts.ctypes.data_as(ctypes.c_void_p),
-                              wts.ctypes.data_as(ctypes.c_void_p),
-                              tab.ctypes.data_as(ctypes.c_void_p), tab.size), "fe_tabulate")
+    N.check(N.lib.fe_tabulate_scheme(dim, degree, quad_degree, sc, ctypes.byref(nq),
+                                     pts.ctypes.data_as(ctypes.c_void_p),
+                                     wts.ctypes.data_as(ctypes.c_void_p),
+                                     tab.ctypes.data_as(ctypes.c_void_p), tab.size), "fe_tabulate")
     return pts, wts, tab
 
 
@@ -103,7 +107,7 @@ class Plan:
     def __init__(self, mesh: Mesh, kind: int, quad_degree: int, *, lam: float = 0.0,
                  mu: float = 0.0, mu_cell=None, lam_cell=None, u_lin=None,
                  accumulate: bool = False, precision: str = "fp64", cooperative: bool = False,
-                 tile_cells: int = 0, tables_global: bool = False):
+                 tile_cells: int = 0, tables_global: bool = False, quad_scheme: str = "conical"):
         self.mesh = mesh
         self.kind = int(kind)
         self.ncomp = 1 if kind == MASS else mesh.dim
@@ -122,7 +126,7 @@ class Plan:
         self._form = N.FeForm(self.kind, int(quad_degree), PRECISIONS[precision], flags, float(lam),
                               float(mu), _dptr(self.lam_cell).value or 0,
                               _dptr(self.mu_cell).value or 0, _dptr(self.u_lin).value or 0,
-                              int(tile_cells), 0)
+                              int(tile_cells), QUAD_SCHEMES[quad_scheme])
         self._mesh_c = mesh._c()
         handle = ctypes.c_void_p(0)
         N.check(N.lib.fe_plan_create(ctypes.byref(self._form), ctypes.byref(self._mesh_c),
@@ -274,7 +278,8 @@ class Batch:
             flags = N.FE_FLAG_TABLES_GLOBAL if pb.get("tables_global") else 0
             arr[i].form = N.FeForm(kind, int(pb["quad_degree"]), N.FE_PREC_FP64, flags,
                                    float(pb.get("lam", 0.0)), float(pb.get("mu", 0.0)),
-                                   _dptr(lam_cell).value or 0, _dptr(mu_cell).value or 0, 0, 0, 0)
+                                   _dptr(lam_cell).value or 0, _dptr(mu_cell).value or 0, 0, 0,
+                                   QUAD_SCHEMES[pb.get("quad_scheme", "conical")])
             arr[i].mesh = mesh._c()
             arr[i].u = u.data_ptr()
             arr[i].y = y.data_ptr()

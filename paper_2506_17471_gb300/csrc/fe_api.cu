@@ -213,11 +213,12 @@ extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan 
 
     // host tabulation -> device table block [nq][1+d][n] + wts[nq], padded to 16 B
     int nq = 0;
-    if (fe_tabulate(m.dim, m.degree, f.quad_degree, &nq, nullptr, nullptr, nullptr, 0) != FE_OK)
+    if (fe_tabulate_scheme(m.dim, m.degree, f.quad_degree, f.quad_scheme, &nq, nullptr, nullptr, nullptr, 0) != FE_OK)
         return FE_ERR_INVALID_ARG;
     const int n = nloc(m.dim, m.degree);
     std::vector<double> pts((size_t)nq * m.dim), wts(nq), tab((size_t)(1 + m.dim) * nq * n);
-    int rc = fe_tabulate(m.dim, m.degree, f.quad_degree, &nq, pts.data(), wts.data(), tab.data(), tab.size());
+    int rc = fe_tabulate_scheme(m.dim, m.degree, f.quad_degree, f.quad_scheme, &nq, pts.data(), wts.data(), tab.data(),
+                           tab.size());
     if (rc != FE_OK) return rc;
     // table block.  Thread-per-cell: tab [nq][1+d][n] in the contraction
     // precision, padded to 8 B, the weights [nq] in double, the weights [nq] in

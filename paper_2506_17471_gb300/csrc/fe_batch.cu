@@ -247,14 +247,15 @@ extern "C" int fe_batch_create(const fe_batch_problem *problems, int count, fe_b
             return FE_ERR_INVALID_ARG;
         }
         int nq = 0;
-        if (fe_tabulate(m.dim, m.degree, f.quad_degree, &nq, nullptr, nullptr, nullptr, 0) != FE_OK) {
+        if (fe_tabulate_scheme(m.dim, m.degree, f.quad_degree, f.quad_scheme, &nq, nullptr, nullptr, nullptr, 0) != FE_OK) {
             batch_free(b);
             return FE_ERR_INVALID_ARG;
         }
         const int n = nloc(m.dim, m.degree);
         const int ncomp = f.kind == FE_FORM_MASS ? 1 : m.dim;
         std::vector<double> pts((size_t)nq * m.dim), wts(nq), tab((size_t)(1 + m.dim) * nq * n);
-        fe_tabulate(m.dim, m.degree, f.quad_degree, &nq, pts.data(), wts.data(), tab.data(), tab.size());
+        fe_tabulate_scheme(m.dim, m.degree, f.quad_degree, f.quad_scheme, &nq, pts.data(), wts.data(), tab.data(),
+                           tab.size());
         int kind = pb.kernel;
         if (kind < 0) kind = tpc_available(f.kind, m.dim, m.degree) ? 0 : 1;
         if (kind == 0 && !tpc_available(f.kind, m.dim, m.degree)) {

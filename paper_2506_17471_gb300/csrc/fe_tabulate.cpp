@@ -23,6 +23,10 @@
 
 #include "fe_internal.h"
 
+namespace fe {
+bool symmetric_rule(int dim, int q, std::vector<double> &pts, std::vector<double> &wts);
+}
+
 namespace {
 
 // Recurrence of the monic Jacobi polynomials for (1-x)^a (1+x)^b on [-1,1]:
@@ -210,14 +214,24 @@ void tabulate_at(int dim, int p, const double *x, const std::vector<int> &mi, in
 
 }  // namespace
 
-extern "C" int fe_tabulate(int dim, int degree, int quad_degree, int *nq, double *pts, double *wts,
-                           double *tab, size_t cap)
+extern "C" int fe_tabulate_scheme(int dim, int degree, int quad_degree, int scheme, int *nq, double *pts,
+                                  double *wts, double *tab, size_t cap)
 {
     if (dim < 1 || dim > 3 || degree < 1 || degree > 10 || quad_degree < 0 || quad_degree > 40 ||
-        nq == nullptr)
+        nq == nullptr || scheme < FE_QUAD_CONICAL || scheme > FE_QUAD_SYMMETRIC)
         return FE_ERR_INVALID_ARG;
     Rule r;
-    if (!simplex_rule(dim, quad_degree, r)) return FE_ERR_INVALID_ARG;
+    bool have = false;
+    if (scheme == FE_QUAD_SYMMETRIC && dim >= 2) {
+        std::vector<double> p, w;
+        if (fe::symmetric_rule(dim, quad_degree, p, w)) {
+            r.nq = (int)w.size();
+            r.pts = p;
+            r.wts = w;
+            have = true;
+        }
+    }
+    if (!have && !simplex_rule(dim, quad_degree, r)) return FE_ERR_INVALID_ARG;
     *nq = r.nq;
     if (tab == nullptr) return FE_OK;
     if (pts == nullptr || wts == nullptr) return FE_ERR_INVALID_ARG;
@@ -236,4 +250,10 @@ extern "C" int fe_tabulate(int dim, int degree, int quad_degree, int *nq, double
                 tab[((size_t)(k + 1) * r.nq + q) * nl + j] = grad[(size_t)k * nl + j];
     }
     return FE_OK;
+}
+
+extern "C" int fe_tabulate(int dim, int degree, int quad_degree, int *nq, double *pts, double *wts,
+                           double *tab, size_t cap)
+{
+    return fe_tabulate_scheme(dim, degree, quad_degree, FE_QUAD_CONICAL, nq, pts, wts, tab, cap);
 }

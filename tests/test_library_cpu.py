@@ -92,3 +92,17 @@ def test_plan_create_validates_before_cuda(fe):
     assert N.lib.fe_plan_create(None, ctypes.byref(mesh), ctypes.byref(h)) == 1
     assert N.lib.fe_action(None, None, None, None) == 1
     assert N.lib.fe_plan_destroy(None) == 0
+
+
+@pytest.mark.parametrize("dim,q", [(2, 2), (2, 4), (2, 6), (2, 8), (3, 2), (3, 4), (3, 5), (3, 6)])
+@pytest.mark.parametrize("degree", [1, 2, 4])
+def test_symmetric_tabulation_matches_oracle(fe, dim, q, degree):
+    import oracle
+    pts, wts, tab = fe.tabulate(dim, degree, q, "symmetric")
+    p2, w2, t2 = oracle.tabulate(dim, degree, q, "symmetric")
+    if (dim, q) in ((3, 6),):   # no tabulated symmetric rule: the conical-product fallback
+        np.testing.assert_allclose(pts, p2, rtol=0, atol=1e-15)
+        np.testing.assert_allclose(wts, w2, rtol=1e-14)
+    else:                        # both sides round the extended-precision solution once
+        assert np.array_equal(pts, p2) and np.array_equal(wts, w2)
+    assert np.abs(tab - t2).max() <= 1e-14 * np.abs(t2).max()

@@ -132,3 +132,45 @@ def test_table_sizes_match_paper():
         if row["kind"] == "helmholtz":
             terms = 1 + row["d"]
         assert terms == row["n_deriv"], row
+
+
+# ---------------------------------------------------------------- symmetric rules
+SYM = [(2, 2, 3), (2, 4, 6), (2, 6, 12), (2, 8, 16), (3, 2, 4), (3, 5, 14)]
+
+
+@pytest.mark.parametrize("dim,q,npts", SYM)
+def test_symmetric_rules_exact_positive_invariant(dim, q, npts):
+    from oracle.symmetric import symmetric_rule
+    pts, wts = symmetric_rule(dim, q)
+    assert len(wts) == npts
+    assert np.all(wts > 0) and np.all(pts > 0) and np.all(pts.sum(axis=1) < 1)
+    assert abs(wts.sum() - 1.0 / factorial(dim)) < 1e-15
+    for total in range(q + 1):
+        for alpha in itertools.product(range(total + 1), repeat=dim):
+            if sum(alpha) != total:
+                continue
+            val = np.sum(wts * np.prod(pts ** np.asarray(alpha), axis=1))
+            assert abs(val - monomial_integral(alpha)) < 1e-15, (alpha, val)
+    # invariance: permuting the barycentric coordinates maps the rule onto itself
+    lam = np.concatenate([1 - pts.sum(axis=1, keepdims=True), pts], axis=1)
+    key = {tuple(np.round(l, 13)): w for l, w in zip(lam, wts)}
+    for perm in itertools.permutations(range(dim + 1)):
+        for l, w in zip(lam[:, perm], wts):
+            assert abs(key[tuple(np.round(l, 13))] - w) < 1e-16
+
+
+def test_symmetric_rule_sizes_match_paper_point_counts():
+    """Table "action_param_space": Mass P3 and P4 on triangles use Q = 12 and 16 points,
+    the sizes of the degree-6 and degree-8 fully symmetric rules (2p for mass)."""
+    from oracle.symmetric import symmetric_rule
+    with open(os.path.join(GOLDEN, "action_param_space.json")) as f:
+        rows = {(r["d"], r["kind"], r["degree"]): r for r in json.load(f)["rows"]}
+    for p in (3, 4):
+        assert len(symmetric_rule(2, 2 * p)[1]) == rows[(2, "mass", p)]["Q_paper"]
+
+
+def test_symmetric_family_falls_back_to_conical():
+    from oracle.symmetric import symmetric_rule
+    pts, wts = symmetric_rule(3, 6)
+    p2, w2 = quadrature.simplex_rule(3, 6)
+    assert np.array_equal(pts, p2) and np.array_equal(wts, w2)

@@ -302,3 +302,45 @@ def test_plans_of_one_kernel_keep_their_shared_memory(fe):
     v = uniform_field(c.n_nodes * 3, 2)
     ref = oracle.Oracle.from_mesh(c, 6).elasticity(v, 1.25, 1.0)
     assert rel(wide.apply(cuda(v)), ref) <= TOL and rel(narrow.apply(cuda(v)), ref) <= TOL
+
+
+# ---------------------------------------------------------------- fully symmetric rules
+@pytest.mark.parametrize("dim,N,p,form,q", [(2, 13, 2, "mass", 4), (2, 9, 3, "mass", 6),
+                                            (3, 5, 2, "elasticity", 2), (2, 11, 4, "elasticity", 6),
+                                            (3, 4, 3, "mass", 5), (2, 9, 4, "nh", 8), (3, 5, 2, "nh", 4)])
+def test_symmetric_rules_parity(fe, dim, N, p, form, q):
+    m, M = make(fe, dim, N, p, seed=500 + p)
+    o = oracle.Oracle.from_mesh(m, q, "symmetric")
+    if form == "mass":
+        u = uniform_field(m.n_nodes, 1)
+        plan = fe.Plan(M, fe.MASS, q, quad_scheme="symmetric")
+        assert plan.info.nq == o.nq
+        assert rel(plan.apply(cuda(u)), o.mass(u)) <= TOL
+    elif form == "elasticity":
+        u = uniform_field(m.n_nodes * dim, 2)
+        plan = fe.Plan(M, fe.ELASTICITY, q, lam=1.25, mu=1.0, quad_scheme="symmetric")
+        assert rel(plan.apply(cuda(u)), o.elasticity(u, 1.25, 1.0)) <= TOL
+    else:
+        mu, lam = lame_fields(m.n_cells, 3)
+        u = sinusoid_displacement(m, 4)
+        w = uniform_field(m.n_nodes * dim, 5)
+        res = fe.Plan(M, fe.NH_RESIDUAL, q, mu_cell=mu, lam_cell=lam, quad_scheme="symmetric")
+        assert rel(res.apply(cuda(u)), o.nh_residual(u, mu, lam)) <= TOL
+        jtw, dmu, dlam = res.adjoint(cuda(u), cuda(w))
+        ojtw, odmu, odlam = o.nh_adjoint(u, w, mu, lam)
+        assert rel(jtw, ojtw) <= TOL and rel(dmu, odmu) <= TOL
+        coop = fe.Plan(M, fe.NH_RESIDUAL, q, mu_cell=mu, lam_cell=lam, quad_scheme="symmetric",
+                       cooperative=True)
+        assert rel(coop.apply(cuda(u)), o.nh_residual(u, mu, lam)) <= TOL
+
+
+def test_full_elasticity_p2_3d_n32_symmetric_rule(fe):
+    """The benchmark workload with the 4-point degree-2 rule."""
+    m, M = make(fe, 3, 32, 2, seed=20250618)
+    o = oracle.Oracle.from_mesh(m, 2, "symmetric")
+    assert o.nq == 4
+    u = uniform_field(m.n_nodes * 3, 2)
+    plan = fe.Plan(M, fe.ELASTICITY, 2, lam=1.25, mu=1.0, quad_scheme="symmetric")
+    assert plan.info.nq == 4
+    assert rel(plan.apply(cuda(u)), o.elasticity(u, 1.25, 1.0, threads=16)) <= TOL
+    assert plan.status() == 0
