@@ -41,6 +41,10 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP64 FMA peak from the part's unit counts and clocks: 1.25 TFLOP/s nominal for a
 # GB300 (152 SMs at up to 2070 MHz, about 4 FP64 flops per SM per clock).
 FP64_NOMINAL_GFLOPS = 1250.0
+# DRAM traffic of the benchmark kernel per launch (dram__bytes_read.sum + dram__bytes_write.sum)
+# from the ncu capture summarised in profiles/elasticity_p2_3d_n32_fp64_sym4.md; reported only
+# while the kernel source still hashes to the captured version.
+MEASURED_TRAFFIC = {"source_hash": "dea944c9e368eb2a", "bytes": 25096448}
 QUAD_SCHEME = "symmetric"   # the 4-point fully symmetric degree-2 rule
 WORKLOAD = ("linear elasticity, vector P2 tets, unit cube 32^3 x 6 Kuhn tets (196,608 cells, "
             "823,875 DoFs), jitter 0.15h, lambda=1.25 mu=1, quadrature degree 2 (4-point fully "
@@ -63,6 +67,15 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("fe_kernels.cuh", "fe_internal.h"):
+        with open(os.path.join(ROOT, "paper_2506_17471_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def make_inputs():
@@ -561,7 +574,9 @@ def run_ours(args):
                    "l2": "flushed between steps (256 MB write, outside the timed events)"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_GFLOPS,
                      "unit": "GFLOP/s", "frac": achieved / FP64_NOMINAL_GFLOPS,
-                     "traffic": None, "kernel": "k_action_tpc<ELASTICITY,3,2>",
+                     "traffic": (MEASURED_TRAFFIC["bytes"]
+                                 if kernel_source_hash() == MEASURED_TRAFFIC["source_hash"] else None),
+                     "traffic_unit": "bytes per launch", "kernel": "k_action_tpc<ELASTICITY,3,2>",
                      "flops_per_launch": flops,
                      "peak_note": "FP64 FMA peak from unit counts and clocks (1.25 TFLOP/s "
                                   "nominal); measured DFMA loop in extra"},
