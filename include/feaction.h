@@ -76,12 +76,21 @@ enum fe_form_kind {
 
 enum fe_precision {
     FE_PREC_FP64 = 0,        /* every operation in IEEE double                           */
-    FE_PREC_FP32 = 1         /* evaluation and quadrature contractions (tables, DoFs,
+    FE_PREC_FP32 = 1,        /* evaluation and quadrature contractions (tables, DoFs,
                                 accumulators) in IEEE single with FP32 accumulation;
                                 geometry (det J, J^{-1}), quadrature weights, the
                                 Neo-Hookean kinematics, log det F and stress, and the
                                 scatter-add stay FP64.  The linear elasticity stress is
                                 evaluated in single.  Error: see fe_plan_create.        */
+    FE_PREC_BF16 = 2,        /* tensor-core kernel (mass, elasticity): both contractions on
+                                tcgen05 tensor cores with bfloat16 operands (tables, DoFs
+                                scaled per cell by a power of two, pointwise results) and
+                                FP32 accumulation in tensor memory; geometry FP64, linear
+                                stress FP32, scatter-add FP64.  Any degree with at most
+                                256 local nodes.  Error: see fe_plan_create.            */
+    FE_PREC_FP16 = 3         /* as FE_PREC_BF16 with IEEE binary16 operands (3 more
+                                significand bits, smaller range; the per-cell power-of-two
+                                scaling keeps the operands O(1))                        */
 };
 
 /* Flags for fe_form.flags */
@@ -217,7 +226,8 @@ typedef struct fe_plan_info {
     int32_t nq;               /* quadrature points per cell                        */
     int32_t n_loc;            /* local nodes per cell                              */
     int32_t ncomp;            /* components per node                               */
-    int32_t kernel;           /* variant id: 0 thread-per-cell, 1 cells-per-CTA    */
+    int32_t kernel;           /* variant id: 0 thread-per-cell, 1 cells-per-CTA,
+                                 2 tensor core (128-cell tiles)                    */
     int32_t threads_per_block;
     int32_t grid_blocks;      /* blocks launched per action                        */
     int64_t n_dofs;           /* n_nodes * ncomp                                   */
@@ -352,6 +362,21 @@ int fe_measure_fp64_peak(double *scratch, size_t scratch_doubles, double *gflops
  * mismatches; count is a device array of 2 zero-initialised uint64.
  * Asynchronous on stream. */
 int fe_selftest_conversions(const double *x, long long n, unsigned long long *count, void *stream);
+
+/* Device self-test of the tensor-core kernel's integer conversions binary64 ->
+ * bfloat16 and binary64 -> binary16 (round to nearest even, done without the
+ * FP64 pipe) against CUDA's __double2bfloat16 / __double2half: x device
+ * [n]; count device [2] unsigned 64-bit, count[0] += bfloat16 mismatches,
+ * count[1] += binary16 mismatches (NaN results compare equal).  Asynchronous.
+ * Errors: FE_ERR_INVALID_ARG, FE_ERR_CUDA. */
+int fe_selftest_conversions16(const double *x, long long n, unsigned long long *count, void *stream);
+
+/* Host function.  Rounds x[n] (host) to the 16-bit type of precision
+ * (FE_PREC_BF16 or FE_PREC_FP16) to nearest even, exactly as plans round their
+ * tabulation for the tensor-core kernel; bits[n] (host, caller-owned) receives
+ * the bit patterns.  Errors: FE_ERR_INVALID_ARG (NULL with n > 0),
+ * FE_ERR_UNSUPPORTED (another precision). */
+int fe_round16(const double *x, size_t n, int precision, uint16_t *bits);
 
 #ifdef __cplusplus
 }

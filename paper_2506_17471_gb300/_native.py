@@ -17,6 +17,7 @@ FE_OK = 0
 STATUS_NAMES = {0: "FE_OK", 1: "FE_ERR_INVALID_ARG", 2: "FE_ERR_UNSUPPORTED", 3: "FE_ERR_CUDA",
                 4: "FE_ERR_BAD_MESH", 5: "FE_ERR_INDEX", 6: "FE_ERR_TIMEOUT", 7: "FE_ERR_NO_MEMORY",
                 8: "FE_ERR_NONFINITE"}
+globals().update({name: code for code, name in STATUS_NAMES.items()})
 
 FE_FORM_MASS = 0
 FE_FORM_ELASTICITY = 1
@@ -24,6 +25,8 @@ FE_FORM_NH_RESIDUAL = 2
 FE_FORM_NH_JACOBIAN = 3
 FE_PREC_FP64 = 0
 FE_PREC_FP32 = 1
+FE_PREC_BF16 = 2
+FE_PREC_FP16 = 3
 FE_FLAG_ACCUMULATE = 1
 FE_FLAG_COOPERATIVE = 2
 FE_FLAG_TABLES_GLOBAL = 4
@@ -37,7 +40,7 @@ EXPORTS = ("fe_status_string", "fe_tabulate", "fe_tabulate_scheme", "fe_plan_cre
            "fe_measure_fp64_peak", "fe_action_noalloc", "fe_cg_start", "fe_cg_direction",
            "fe_cg_update", "fe_cg_new_direction", "fe_vec_axpy", "fe_vec_dot",
            "fe_selftest_conversions", "fe_batch_create", "fe_batch_run", "fe_batch_status",
-           "fe_batch_get_info", "fe_batch_destroy")
+           "fe_batch_get_info", "fe_batch_destroy", "fe_selftest_conversions16", "fe_round16")
 FE_CG_PARTIALS = 1024
 FE_CG_WORKSPACE_DOUBLES = FE_CG_PARTIALS + 16
 
@@ -112,6 +115,8 @@ def _load() -> ctypes.CDLL:
     lib.fe_vec_axpy.argtypes = [LL, D, P, P, P]
     lib.fe_vec_dot.argtypes = [LL, P, P, P, P, I, P]
     lib.fe_selftest_conversions.argtypes = [P, LL, P, P]
+    lib.fe_selftest_conversions16.argtypes = [P, LL, P, P]
+    lib.fe_round16.argtypes = [P, ctypes.c_size_t, I, P]
     lib.fe_batch_create.argtypes = [ctypes.POINTER(FeBatchProblem), I, ctypes.POINTER(P)]
     lib.fe_batch_run.argtypes = [P, P]
     lib.fe_batch_status.argtypes = [P, ctypes.POINTER(I)]

@@ -21,7 +21,8 @@ NH_JACOBIAN = N.FE_FORM_NH_JACOBIAN
 FORM_NAMES = {MASS: "mass", ELASTICITY: "elasticity", NH_RESIDUAL: "nh_residual",
               NH_JACOBIAN: "nh_jacobian"}
 # contraction precision of a plan (include/feaction.h, enum fe_precision)
-PRECISIONS = {"fp64": N.FE_PREC_FP64, "fp32": N.FE_PREC_FP32}
+PRECISIONS = {"fp64": N.FE_PREC_FP64, "fp32": N.FE_PREC_FP32, "bf16": N.FE_PREC_BF16,
+              "fp16": N.FE_PREC_FP16}
 
 
 def _stream_ptr(stream=None) -> ctypes.c_void_p:

@@ -1,4 +1,5 @@
 // C-ABI of the action library: plans, launches, status, diagnostics.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -9,6 +10,7 @@
 
 #include "fe_internal.h"
 #include "fe_coop.cuh"
+#include "fe_tc.cuh"
 
 namespace fe {
 namespace {
@@ -25,11 +27,13 @@ void init_registry()
     n += register_variants_2d_nh(g_variants + n, kMaxVariants - n);
     n += register_variants_3d(g_variants + n, kMaxVariants - n);
     n += register_variants_coop(g_variants + n, kMaxVariants - n);
+    n += register_variants_tc(g_variants + n, kMaxVariants - n);
     g_nvariants = n;
 }
 
 // The thread-per-cell variant compiled for exactly this degree, else (or when
 // forced) the cooperative variant, which serves every degree.
+// The 16-bit precisions have only the tensor-core kernel (any degree).
 const Variant *find_variant(int form, int dim, int degree, int op, int precision, bool force_coop)
 {
     std::call_once(g_once, init_registry);
@@ -37,6 +41,7 @@ const Variant *find_variant(int form, int dim, int degree, int op, int precision
     for (int i = 0; i < g_nvariants; ++i) {
         const Variant &v = g_variants[i];
         if (v.form != form || v.dim != dim || v.op != op || v.precision != precision) continue;
+        if (v.kernel_id == 2) return &v;
         if (v.kernel_id == 1) coop = &v;
         else if (v.degree == degree && !force_coop) return &v;
     }
@@ -55,6 +60,24 @@ int coop_cells_for(int n, int nq, int dim, int ncomp, int fields, size_t esz, si
         if (total <= budget) best = C;
     }
     return best;
+}
+
+// Tensor-core tile shape: two 128-cell pipelines per CTA if their tables,
+// operands and accumulators fit (256 TMEM columns each), else one; the fewest
+// quadrature-point chunks that fit.  Returns false if nothing fits.
+bool tc_choose(int n, int nq, int ncomp, int kd, int fields, size_t smem_cap, TcLayout *out)
+{
+    if (n > 256 || nq < 1) return false;
+    for (int halves = 2; halves >= 1; --halves)
+        for (int nch = 1; nch <= nq; ++nch) {
+            const int qc = (nq + nch - 1) / nch;
+            const TcLayout L = tc_layout(n, nq, ncomp, kd, fields, qc, halves);
+            if (L.N1p > 256 || L.N2p > 256 || L.tmem_cols > 512) continue;
+            if (L.total > smem_cap || L.staged_bytes >= (1u << 20)) continue;
+            *out = L;
+            return true;
+        }
+    return false;
 }
 
 // Algorithmic FP64 flops of Algorithm 2 for one cell (multiply and add count 1
@@ -184,6 +207,99 @@ extern "C" const char *fe_status_string(int status)
     }
 }
 
+// Plan of the tensor-core kernel: the staged block holds Phi (evaluation GEMM
+// B operand, rows = chunk columns (q, k), K = node j) and Phi^T (quadrature
+// GEMM B operand, rows = node j, K = (q, k) over all chunks) rounded to the
+// 16-bit type, in the K-major core-matrix layout, then the weights in FP64 and
+// FP32.
+template <typename T16>
+static void tc_fill_block(const TcLayout &L, int kind, const std::vector<double> &wts,
+                          const std::vector<double> &tab, std::vector<unsigned char> &blk)
+{
+    blk.assign(L.staged_bytes, 0);
+    uint16_t *B1 = reinterpret_cast<uint16_t *>(blk.data() + L.b1_off);
+    uint16_t *B2 = reinterpret_cast<uint16_t *>(blk.data() + L.b2_off);
+    for (int ch = 0; ch < L.nch; ++ch)
+        for (int ql = 0; ql < L.qc; ++ql) {
+            const int q = ch * L.qc + ql;
+            if (q >= L.nq) break;
+            for (int k = 0; k < L.KD; ++k) {
+                const int row = ch * L.N1p + ql * L.KDP + k;
+                const int kt = kind == FE_FORM_MASS ? 0 : 1 + k;
+                for (int j = 0; j < L.n; ++j) {
+                    const uint16_t bits = to16_bits<T16>(tab[((size_t)kt * L.nq + q) * L.n + j]);
+                    B1[tc_off(row, j, L.K1p)] = bits;
+                    B2[tc_off(j, row, L.K2)] = bits;
+                }
+            }
+        }
+    for (int q = 0; q < L.nq; ++q) {
+        reinterpret_cast<double *>(blk.data() + L.wd_off)[q] = wts[q];
+        reinterpret_cast<float *>(blk.data() + L.wf_off)[q] = (float)wts[q];
+    }
+}
+
+static int plan_create_tc(const fe_form &f, const fe_mesh &m, const Variant &v, int nq, int n, int ncomp,
+                          const std::vector<double> &wts, const std::vector<double> &tab, fe_plan **out)
+{
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return FE_ERR_CUDA;
+    const int kd = f.kind == FE_FORM_MASS ? 1 : m.dim;
+    TcLayout L;
+    if (!tc_choose(n, nq, ncomp, kd, 1, (size_t)optin - 256, &L)) return FE_ERR_UNSUPPORTED;
+    std::vector<unsigned char> blk;
+    if (f.precision == FE_PREC_BF16)
+        tc_fill_block<__nv_bfloat16>(L, f.kind, wts, tab, blk);
+    else
+        tc_fill_block<__half>(L, f.kind, wts, tab, blk);
+
+    fe_plan *p = new (std::nothrow) fe_plan();
+    if (!p) return FE_ERR_NO_MEMORY;
+    p->form = f;
+    p->mesh = m;
+    p->nq = nq;
+    p->n_loc = n;
+    p->ncomp = ncomp;
+    p->tab_doubles = (int)(L.staged_bytes / sizeof(double));
+    p->var = v;
+    p->var.block = kTcRows * L.halves;
+    p->adj = Variant{};
+    p->smem_bytes = L.total;
+    p->device = dev;
+    p->tc_qc = L.qc;
+    p->tc_halves = L.halves;
+    if (cudaMalloc(&p->d_tab, L.staged_bytes) != cudaSuccess ||
+        cudaMalloc(&p->d_status, 8 * sizeof(int32_t)) != cudaSuccess) {
+        cudaFree(p->d_tab);
+        delete p;
+        cudaGetLastError();
+        return FE_ERR_NO_MEMORY;
+    }
+    p->d_sched = p->d_status + 4;
+    if (cudaMemcpy(p->d_tab, blk.data(), L.staged_bytes, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(p->d_status, 0, 8 * sizeof(int32_t)) != cudaSuccess || allow_max_dynamic_smem(v.func) != cudaSuccess) {
+        fe_plan_destroy(p);
+        return FE_ERR_CUDA;
+    }
+    // resident CTAs per SM: shared memory and registers, and the 512 TMEM
+    // columns (a CTA whose allocation does not fit would wait for another to exit)
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, v.func, p->var.block, L.total) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    per_sm = std::min(per_sm, 512 / L.tmem_cols);
+    const long long tiles = ((long long)m.n_cells + kTcRows - 1) / kTcRows;
+    const long long want = (tiles + L.halves - 1) / L.halves;
+    p->grid_blocks = (int)std::max(1LL, std::min(want, (long long)per_sm * num_sms()));
+    p->flops_per_cell = algorithmic_flops(f.kind, m.dim, n, nq);
+    const double dofs = (double)m.n_nodes * ncomp;
+    p->bytes_min = 2.0 * dofs * 8.0 + (double)m.n_vertices * m.dim * 8.0 + (double)m.n_cells * (n + m.dim + 1) * 4.0;
+    *out = p;
+    return FE_OK;
+}
+
 extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan **out)
 {
     if (!form || !mesh || !out) return FE_ERR_INVALID_ARG;
@@ -196,7 +312,9 @@ extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan 
     // 2D vertex coordinates are gathered as one 16-byte load per vertex
     if (m.dim == 2 && reinterpret_cast<uintptr_t>(m.coords) % 16 != 0) return FE_ERR_INVALID_ARG;
     if (f.kind < FE_FORM_MASS || f.kind > FE_FORM_NH_JACOBIAN) return FE_ERR_INVALID_ARG;
-    if (f.precision != FE_PREC_FP64 && f.precision != FE_PREC_FP32) return FE_ERR_UNSUPPORTED;
+    if (f.precision < FE_PREC_FP64 || f.precision > FE_PREC_FP16) return FE_ERR_UNSUPPORTED;
+    const bool tc = f.precision == FE_PREC_BF16 || f.precision == FE_PREC_FP16;
+    if (tc && f.kind != FE_FORM_MASS && f.kind != FE_FORM_ELASTICITY) return FE_ERR_UNSUPPORTED;
     if (f.quad_degree < 0 || f.quad_degree > 40) return FE_ERR_INVALID_ARG;
     if (f.kind == FE_FORM_NH_JACOBIAN && !f.u_lin) return FE_ERR_INVALID_ARG;
     if (f.tile_cells < 0 || f.tile_cells > 4096) return FE_ERR_INVALID_ARG;
@@ -225,6 +343,7 @@ extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan 
     // the contraction precision, padded to 16 B.  Cooperative: the same with the
     // per-point row stride padded to an odd element count, followed in shared
     // memory by the batch scratch (not staged).
+    if (tc) return plan_create_tc(f, m, *v, nq, n, ncomp, wts, tab, out);
     const size_t esz = f.precision == FE_PREC_FP32 ? sizeof(float) : sizeof(double);
     const bool coop = v->kernel_id == 1;
     const int fields_max = (f.kind == FE_FORM_NH_JACOBIAN || (adj != nullptr)) ? 2 : 1;
@@ -360,6 +479,8 @@ static ActionArgs make_args(const fe_plan *p, const double *u, double *y)
     a.coop_cells = p->coop_cells;
     a.tab_b = p->d_tab_b;
     a.tab_c = p->d_tab_c;
+    a.tc_qc = p->tc_qc;
+    a.tc_halves = p->tc_halves;
     return a;
 }
 
@@ -497,8 +618,49 @@ __global__ void k_selftest_conversions(const double *x, long long n, unsigned lo
     if (bad64) atomicAdd(count + 1, bad64);
 }
 
+// Self-test of the integer binary64 -> bfloat16 / binary16 conversions of the
+// tensor-core kernel against CUDA's conversions: count[0] += bfloat16
+// mismatches, count[1] += binary16 mismatches (NaN compares equal to NaN).
+__global__ void k_selftest_conversions16(const double *x, long long n, unsigned long long *count)
+{
+    unsigned long long bad_b = 0, bad_h = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double v = x[i];
+        const __nv_bfloat16 hb = __double2bfloat16(v);
+        const __half hh = __double2half(v);
+        const uint16_t rb = *reinterpret_cast<const uint16_t *>(&hb), rh = *reinterpret_cast<const uint16_t *>(&hh);
+        const uint16_t mb = to16_bits<__nv_bfloat16>(v), mh = to16_bits<__half>(v);
+        const bool nan_b = (rb & 0x7F80) == 0x7F80 && (rb & 0x7F), nan_mb = (mb & 0x7F80) == 0x7F80 && (mb & 0x7F);
+        const bool nan_h = (rh & 0x7C00) == 0x7C00 && (rh & 0x3FF), nan_mh = (mh & 0x7C00) == 0x7C00 && (mh & 0x3FF);
+        if (rb != mb && !(nan_b && nan_mb)) ++bad_b;
+        if (rh != mh && !(nan_h && nan_mh)) ++bad_h;
+    }
+    if (bad_b) atomicAdd(count, bad_b);
+    if (bad_h) atomicAdd(count + 1, bad_h);
+}
+
 }  // namespace
 }  // namespace fe
+
+extern "C" int fe_selftest_conversions16(const double *x, long long n, unsigned long long *count, void *stream)
+{
+    if (!x || !count || n < 0) return FE_ERR_INVALID_ARG;
+    if (n == 0) return FE_OK;
+    long long g = (n + 255) / 256;
+    if (g > 4096) g = 4096;
+    k_selftest_conversions16<<<(int)g, 256, 0, static_cast<cudaStream_t>(stream)>>>(x, n, count);
+    return cudaGetLastError() == cudaSuccess ? FE_OK : FE_ERR_CUDA;
+}
+
+extern "C" int fe_round16(const double *x, size_t n, int precision, uint16_t *bits)
+{
+    if ((n > 0 && (!x || !bits))) return FE_ERR_INVALID_ARG;
+    if (precision != FE_PREC_BF16 && precision != FE_PREC_FP16) return FE_ERR_UNSUPPORTED;
+    for (size_t i = 0; i < n; ++i)
+        bits[i] = precision == FE_PREC_BF16 ? to16_bits<__nv_bfloat16>(x[i]) : to16_bits<__half>(x[i]);
+    return FE_OK;
+}
 
 extern "C" int fe_selftest_conversions(const double *x, long long n, unsigned long long *count, void *stream)
 {

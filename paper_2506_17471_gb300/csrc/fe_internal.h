@@ -38,6 +38,8 @@ struct ActionArgs {
     int32_t coop_cells;       // cooperative kernel: cells per CTA batch
     const void *tab_b;        // cooperative kernel, large tables: [1+D][N][nq] in global memory
     const void *tab_c;        // cooperative kernel, large tables: [nq][1+D][N] in global memory
+    int32_t tc_qc;            // tensor-core kernel: quadrature points per chunk
+    int32_t tc_halves;        // tensor-core kernel: 128-cell pipelines per CTA (1 or 2)
 };
 
 // Launch function of one compiled kernel variant.
@@ -77,6 +79,7 @@ int register_variants_2d_linear(Variant *out, int cap);
 int register_variants_2d_nh(Variant *out, int cap);
 int register_variants_3d(Variant *out, int cap);
 int register_variants_coop(Variant *out, int cap);
+int register_variants_tc(Variant *out, int cap);
 
 }  // namespace fe
 
@@ -98,6 +101,8 @@ struct fe_plan {
     int adj_grid_blocks;
     size_t smem_bytes;
     int coop_cells;       // cells per CTA batch (cooperative kernel), else 0
+    int tc_qc;            // tensor-core kernel: quadrature points per chunk, else 0
+    int tc_halves;        // tensor-core kernel: 128-cell pipelines per CTA, else 0
     int device;
     double flops_per_cell;
     double bytes_min;

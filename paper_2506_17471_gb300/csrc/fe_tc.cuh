@@ -1,0 +1,589 @@
+// Tensor-core (tcgen05) action with 16-bit contractions for high-degree cells.
+//
+// A tile of 128 cells runs the two contractions of Algorithm 2 as GEMMs with
+// the cells on the M dimension:
+//   evaluation:  E_m[c, (q,k)] = sum_j  U_m[c, j] Phi_k[q][j]          (per component m)
+//   quadrature:  Y_m[c, j]     = sum_{(q,k)} E'_m[c, (q,k)] Phi_k[q][j]
+// U_m holds the tile's gathered DoFs, E'_m the weighted pointwise stress pulled
+// back to the reference cell (Sec. "Towards Discretization": evaluation,
+// pointwise and quadrature phases).  Row c of every GEMM is cell c, which is
+// TMEM lane c and thread c of the tile: a thread gathers its cell, computes its
+// geometry, reads its own accumulator row with tcgen05.ld, evaluates the
+// pointwise form for its cell at every point and scatter-adds its own result,
+// exactly like the thread-per-cell kernel, while the contractions run on the
+// tensor cores (tcgen05.mma kind::f16, BF16 or FP16 operands, FP32 accumulators
+// in TMEM, issued by one thread, completion through tcgen05.commit and an
+// mbarrier with a bounded wait).
+//
+// The tabulation operands (Phi as the evaluation GEMM's B, Phi^T as the
+// quadrature GEMM's B) are laid out by the plan in the tensor cores' K-major
+// core-matrix layout and staged once per CTA by one bulk copy.  Quadrature
+// points are processed in chunks of qc points so the evaluation accumulators of
+// a chunk and the quadrature accumulators of the whole tile fit in TMEM; the
+// quadrature GEMM accumulates over the chunks.  A CTA runs one or two
+// independent 128-cell pipelines ("halves", 128 threads each) that share the
+// staged tables and synchronise with named barriers.
+//
+// Precision: the DoFs are scaled per cell by a power of two s_u >= max |u|
+// and rounded to 16 bits; for elasticity J^{-1} is scaled by a power of two
+// s_J >= max |J^{-1}_ik|.  The pointwise values then stay O(1) whatever the
+// mesh size and field magnitude (FP16 neither overflows nor goes subnormal),
+// and the output factor |det J| s_u s_J^2 is applied in FP64 at the scatter.
+// Geometry is FP64, the linear stress FP32, the scatter-add FP64.
+//
+// Operand layout (K-major, no swizzle): 8x8 core matrices of 16-bit elements
+// (128 bytes), ordered [row group][K group][row][col]; LBO = 128 B between
+// K-adjacent core matrices, SBO = (Kp/8) * 128 B between row groups.
+#pragma once
+
+#include <cstring>
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "fe_kernels.cuh"
+
+namespace fe {
+
+constexpr int kTcRows = 128;   // cells (threads, TMEM lanes) per half
+
+__host__ __device__ inline int tc_round_up(int x, int m) { return (x + m - 1) / m * m; }
+__host__ __device__ inline size_t tc_round_up_sz(size_t x, size_t m) { return (x + m - 1) / m * m; }
+
+// Tile geometry, computed identically by the plan and the kernel.
+struct TcLayout {
+    int n, nq, NC, KD, KDP, F;   // KD derivative terms per point (KDP: padded to 1, 2 or 4); F fields
+    int qc, nch;                 // points per chunk, chunks
+    int N1p, K1p;                // evaluation GEMM: N (chunk columns), K (n padded to 16)
+    int N2p, K2;                 // quadrature GEMM: N (n padded to 16), K (nch * N1p)
+    int halves;
+    size_t b1_off, b2_off, wd_off, wf_off, staged_bytes;   // staged block
+    size_t a1_off, a2_off, nodes_off, half_bytes;          // per-half scratch (from its base)
+    size_t total;                                          // dynamic shared memory
+    int acc1_cols, acc2_cols, half_cols, tmem_cols;
+};
+
+__host__ __device__ inline int tc_kdp(int kd) { return kd == 1 ? 1 : (kd == 2 ? 2 : 4); }
+
+__host__ __device__ inline TcLayout tc_layout(int n, int nq, int NC, int KD, int F, int qc, int halves)
+{
+    TcLayout L;
+    L.n = n;
+    L.nq = nq;
+    L.NC = NC;
+    L.KD = KD;
+    L.KDP = tc_kdp(KD);
+    L.F = F;
+    L.qc = qc < 1 ? 1 : qc;
+    L.nch = (nq + L.qc - 1) / L.qc;
+    L.N1p = tc_round_up(L.qc * L.KDP, 16);
+    L.K1p = tc_round_up(n, 16);
+    L.N2p = tc_round_up(n, 16);
+    L.K2 = L.nch * L.N1p;
+    L.halves = halves;
+    L.b1_off = 0;
+    L.b2_off = (size_t)L.nch * L.N1p * L.K1p * 2;
+    L.wd_off = L.b2_off + (size_t)L.N2p * L.K2 * 2;
+    L.wf_off = L.wd_off + (size_t)nq * 8;
+    L.staged_bytes = tc_round_up_sz(L.wf_off + (size_t)nq * 4, 128);
+    L.a1_off = 0;
+    L.a2_off = L.a1_off + (size_t)F * NC * kTcRows * L.K1p * 2;
+    L.nodes_off = L.a2_off + (size_t)NC * kTcRows * L.N1p * 2;
+    L.half_bytes = tc_round_up_sz(L.nodes_off + (size_t)n * kTcRows * 4, 128);
+    L.total = L.staged_bytes + (size_t)halves * L.half_bytes;
+    L.acc1_cols = F * NC * L.N1p;
+    L.acc2_cols = NC * L.N2p;
+    L.half_cols = L.acc1_cols + L.acc2_cols;
+    // each half owns tmem_cols / halves columns (a power of two >= 32 in total)
+    int t = 32;
+    while (t / halves < L.half_cols) t <<= 1;
+    L.tmem_cols = t;
+    return L;
+}
+
+// Element offset of (row r, k) in a K-major no-swizzle operand with Kp columns.
+__host__ __device__ inline size_t tc_off(int r, int k, int Kp)
+{
+    return (size_t)(r >> 3) * (Kp >> 3) * 64 + (size_t)(k >> 3) * 64 + (r & 7) * 8 + (k & 7);
+}
+
+// Round-to-nearest-even conversion of an IEEE binary64 value to a binary16-
+// family format with EB exponent and MB fraction bits (binary16: 5, 10;
+// bfloat16: 8, 7), done on the integer bit pattern (no FP64-pipe conversion).
+// NaN maps to a quiet NaN, overflow to infinity, results below half the
+// smallest subnormal to signed zero.
+template <int EB, int MB>
+__host__ __device__ __forceinline__ uint16_t f64_to_small_rn(double x)
+{
+    uint64_t b;
+#ifdef __CUDA_ARCH__
+    b = (uint64_t)__double_as_longlong(x);
+#else
+    std::memcpy(&b, &x, 8);
+#endif
+    constexpr int kBias = (1 << (EB - 1)) - 1;
+    constexpr uint32_t kInf = ((1u << EB) - 1u) << MB;
+    const uint32_t sign = (uint32_t)(b >> 63) << (EB + MB);
+    const uint64_t frac = b & 0xFFFFFFFFFFFFFull;
+    const int e = (int)((b >> 52) & 0x7FF);
+    if (e == 0x7FF) return (uint16_t)(sign | kInf | (frac ? (1u << (MB - 1)) : 0u));
+    const int te = e - 1023 + kBias;   // biased exponent in the target format
+    uint64_t m;
+    int shift;
+    if (te >= 1) {
+        m = ((uint64_t)te << 52) | frac;   // exponent and fraction: a carry rounds into the exponent
+        shift = 52 - MB;
+    } else {
+        m = frac | (e ? (1ull << 52) : 0ull);
+        shift = 52 - MB + 1 - te;
+        if (shift > 62) return (uint16_t)sign;
+    }
+    uint64_t r = m >> shift;
+    const uint64_t rem = m & ((1ull << shift) - 1ull), halfway = 1ull << (shift - 1);
+    if (rem > halfway || (rem == halfway && (r & 1ull))) ++r;
+    if (r >= kInf) return (uint16_t)(sign | kInf);
+    return (uint16_t)(sign | (uint32_t)r);
+}
+
+template <typename T16>
+__host__ __device__ __forceinline__ uint16_t to16_bits(double x);
+template <>
+__host__ __device__ __forceinline__ uint16_t to16_bits<__nv_bfloat16>(double x) { return f64_to_small_rn<8, 7>(x); }
+template <>
+__host__ __device__ __forceinline__ uint16_t to16_bits<__half>(double x) { return f64_to_small_rn<5, 10>(x); }
+
+// Two FP32 values to a packed pair of 16-bit values (round to nearest even);
+// the first value lands at the lower address.
+template <typename T16>
+__device__ __forceinline__ uint32_t pack2(float lo, float hi);
+template <>
+__device__ __forceinline__ uint32_t pack2<__nv_bfloat16>(float lo, float hi)
+{
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+template <>
+__device__ __forceinline__ uint32_t pack2<__half>(float lo, float hi)
+{
+    const __half2 v = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+__device__ __forceinline__ uint64_t tc_smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)((lbo & 0x3FFFF) >> 4) << 16) |
+           ((uint64_t)((sbo & 0x3FFFF) >> 4) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor of tcgen05.mma kind::f16: FP32 accumulator, A and B of
+// the same 16-bit type (fmt 0 = F16, 1 = BF16), both K-major.
+__host__ __device__ constexpr uint32_t tc_idesc(int fmt, int M, int N)
+{
+    return (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(da), "l"(db), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t sbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(sbar)
+                 : "memory");
+}
+
+// 16 consecutive accumulator columns of this warp's 32 lanes (no wait).
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Barrier over the 128 threads of one half (named barrier 1 + half).
+__device__ __forceinline__ void half_sync(int half)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + half), "r"(kTcRows) : "memory");
+}
+
+// Barrier over one half that also returns whether pred held on all its threads.
+__device__ __forceinline__ bool half_all(int half, bool pred)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, %2, %3, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "r"(1 + half), "r"(kTcRows)
+        : "memory");
+    return r != 0;
+}
+
+// Bounded wait on an mbarrier phase; true if it completed.
+__device__ __forceinline__ bool tc_wait(uint32_t sbar, uint32_t parity)
+{
+    for (int it = 0; it < kWaitLimit; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(sbar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        __nanosleep(32);
+    }
+    return false;
+}
+
+// Power of two s = 2^e with 2^(e-1) <= x < 2^e for finite x > 0, else 1.
+__device__ __forceinline__ void pow2_above(double x, double &s, double &inv_s)
+{
+    if (!(x > 0.0) || !isfinite(x)) {
+        s = 1.0;
+        inv_s = 1.0;
+        return;
+    }
+    int e = 0;
+    frexp(x, &e);
+    s = ldexp(1.0, e);
+    inv_s = ldexp(1.0, -e);
+}
+
+template <int OP, int D, typename T16>
+__global__ void __launch_bounds__(2 * kTcRows, 1) k_action_tc(const ActionArgs a)
+{
+    constexpr int NC = OpTraits<OP, D>::NC;
+    constexpr int KD = (OP == OP_MASS) ? 1 : D;
+    constexpr int KDP = (KD == 1) ? 1 : (KD == 2 ? 2 : 4);
+    constexpr int F = 1;
+    constexpr int PPB = 16 / KDP;   // quadrature points per 16 accumulator columns
+    constexpr int FMT = std::is_same<T16, __nv_bfloat16>::value ? 1 : 0;
+    extern __shared__ __align__(128) unsigned char tc_smem[];
+    __shared__ __align__(8) uint64_t bars[3];   // table copy; one MMA barrier per half
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_tile[2];
+
+    const TcLayout L = tc_layout(a.coop_n, a.nq, NC, KD, F, a.tc_qc, a.tc_halves);
+    const int tid = threadIdx.x, half = tid >> 7, t = tid & (kTcRows - 1), warp = tid >> 5;
+    const int n = L.n;
+    const uint32_t bar0 = (uint32_t)__cvta_generic_to_shared(&bars[0]);
+    const uint32_t barh = (uint32_t)__cvta_generic_to_shared(&bars[1 + half]);
+
+    if (tid == 0) {
+        for (int i = 0; i < 3; ++i) {
+            const uint32_t b = (uint32_t)__cvta_generic_to_shared(&bars[i]);
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&s_tmem);
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst),
+                     "r"((uint32_t)L.tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = s_tmem;
+    if (tid == 0) {
+        const uint32_t bytes = (uint32_t)L.staged_bytes;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar0), "r"(bytes) : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                (uint32_t)__cvta_generic_to_shared(tc_smem)),
+            "l"((uint64_t)__cvta_generic_to_global(a.tab)), "r"(bytes), "r"(bar0)
+            : "memory");
+    }
+    bool ok = __syncthreads_and(tc_wait(bar0, 0));
+    if (!ok) tc_wait(bar0, 0);   // let a late copy land before the CTA exits
+
+    const unsigned char *staged = tc_smem;
+    unsigned char *hb = tc_smem + L.staged_bytes + (size_t)half * L.half_bytes;
+    const float *wf = reinterpret_cast<const float *>(staged + L.wf_off);
+    int *snodes = reinterpret_cast<int *>(hb + L.nodes_off);   // [n][128]
+    const uint32_t b1s = (uint32_t)__cvta_generic_to_shared(staged + L.b1_off);
+    const uint32_t b2s = (uint32_t)__cvta_generic_to_shared(staged + L.b2_off);
+    const uint32_t a1s = (uint32_t)__cvta_generic_to_shared(hb + L.a1_off);
+    const uint32_t a2s = (uint32_t)__cvta_generic_to_shared(hb + L.a2_off);
+    const uint32_t thalf = tbase + (uint32_t)(half * (L.tmem_cols / L.halves));
+    const uint32_t tlane = thalf + ((uint32_t)((warp & 3) * 32) << 16);   // this warp's TMEM lanes
+    const int n_tiles = (a.n_cells + kTcRows - 1) / kTcRows;
+    [[maybe_unused]] const float lam_f = f64_to_f32_rn(a.lam), mu_f = f64_to_f32_rn(a.mu);
+    uint32_t phase = 0;
+    bool timed_out = false;
+
+    while (ok) {
+        if (t == 0) s_tile[half] = atomicAdd(a.sched, 1);
+        half_sync(half);
+        const int tile = s_tile[half];
+        if (tile >= n_tiles) break;
+        const int cell = tile * kTcRows + t;
+
+        // ---- gather (Algorithm 2): vertices, geometry in FP64, nodes, scaled DoFs
+        double scale = 0.0;   // output factor; 0 marks a cell that is skipped
+        [[maybe_unused]] float Jh[D][D];
+        double inv_su = 1.0;
+        bool good = cell < a.n_cells;
+        if (good) {
+            double X[D + 1][D];
+#pragma unroll
+            for (int m = 0; m <= D; ++m) {
+                const int v = __ldg(a.c2v + (size_t)cell * (D + 1) + m);
+                const bool in = (unsigned)v < (unsigned)a.n_vertices;
+                good &= in;
+#pragma unroll
+                for (int i = 0; i < D; ++i) X[m][i] = in ? __ldg(a.coords + (size_t)v * D + i) : 0.0;
+            }
+            double Jinv[D][D];
+            const double det = cell_geometry<D>(X, Jinv);
+            double umax = 0.0;
+            bool nodes_ok = true;
+            for (int j = 0; j < n; ++j) {
+                const int node = __ldg(a.c2n + (size_t)cell * n + j);
+                const bool in = (unsigned)node < (unsigned)a.n_nodes;
+                nodes_ok &= in;
+                snodes[j * kTcRows + t] = in ? node : -1;
+                if (in) {
+#pragma unroll
+                    for (int m = 0; m < NC; ++m) umax = fmax(umax, fabs(__ldg(a.u + (size_t)node * NC + m)));
+                }
+            }
+            if (!good || !nodes_ok) {
+                set_status(a.status, FE_ERR_INDEX);
+                good = false;
+            } else if (!(det != 0.0) || !isfinite(det)) {
+                set_status(a.status, FE_ERR_BAD_MESH);
+                good = false;
+            }
+            if (good) {
+                double su;
+                pow2_above(umax, su, inv_su);
+                scale = fabs(det) * su;
+                if constexpr (OP == OP_ELASTICITY) {
+                    double jmax = 0.0;
+#pragma unroll
+                    for (int i = 0; i < D; ++i)
+#pragma unroll
+                        for (int k = 0; k < D; ++k) jmax = fmax(jmax, fabs(Jinv[i][k]));
+                    double sj, inv_sj;
+                    pow2_above(jmax, sj, inv_sj);
+                    scale *= sj * sj;
+#pragma unroll
+                    for (int i = 0; i < D; ++i)
+#pragma unroll
+                        for (int k = 0; k < D; ++k) Jh[i][k] = f64_to_f32_rn(Jinv[i][k] * inv_sj);
+                }
+            }
+        }
+        if (!good) {
+            for (int j = 0; j < n; ++j) snodes[j * kTcRows + t] = -1;
+        }
+        // A operand of the evaluation GEMM: row t = this cell, K = local node j
+#pragma unroll
+        for (int m = 0; m < NC; ++m) {
+            T16 *A1 = reinterpret_cast<T16 *>(hb + L.a1_off) + (size_t)m * kTcRows * L.K1p;
+            for (int j8 = 0; j8 < L.K1p; j8 += 8) {
+                uint32_t w[4];
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    uint32_t pair = 0;
+#pragma unroll
+                    for (int s = 0; s < 2; ++s) {
+                        const int j = j8 + 2 * h + s;
+                        double v = 0.0;
+                        if (good && j < n) {
+                            const int node = snodes[j * kTcRows + t];
+                            v = __ldg(a.u + (size_t)node * NC + m) * inv_su;
+                        }
+                        pair |= (uint32_t)to16_bits<T16>(v) << (16 * s);
+                    }
+                    w[h] = pair;
+                }
+                *reinterpret_cast<uint4 *>(A1 + tc_off(t, j8, L.K1p)) = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        }
+        fence_async_smem();
+        tc_fence_before();
+        half_sync(half);
+        tc_fence_after();
+
+        const uint32_t id1 = tc_idesc(FMT, kTcRows, L.N1p), id2 = tc_idesc(FMT, kTcRows, L.N2p);
+        for (int ch = 0; ch < L.nch; ++ch) {
+            // ---- evaluation GEMM of chunk ch (its commit also covers the previous chunk's quadrature GEMM)
+            if (t == 0) {
+                const uint32_t sbo = (uint32_t)L.K1p * 16u;
+                for (int m = 0; m < NC; ++m)
+                    for (int s = 0; s < L.K1p / 16; ++s) {
+                        const uint64_t da =
+                            tc_smem_desc(a1s + (uint32_t)(m * kTcRows * L.K1p * 2) + (uint32_t)s * 256u, 128u, sbo);
+                        const uint64_t db =
+                            tc_smem_desc(b1s + (uint32_t)(ch * L.N1p * L.K1p * 2) + (uint32_t)s * 256u, 128u, sbo);
+                        tc_mma(thalf + (uint32_t)(m * L.N1p), da, db, id1, s > 0 ? 1u : 0u);
+                    }
+                tc_commit(barh);
+            }
+            if (!half_all(half, tc_wait(barh, phase))) {
+                tc_wait(barh, phase);
+                timed_out = true;
+                break;
+            }
+            phase ^= 1u;
+            tc_fence_after();
+
+            // ---- pointwise: this thread's cell at the chunk's points, E' into the quadrature A operand
+            for (int blk = 0; blk < L.N1p / 16; ++blk) {
+                uint32_t r[NC][16];
+#pragma unroll
+                for (int m = 0; m < NC; ++m) tc_ld16(tlane + (uint32_t)(m * L.N1p + blk * 16), r[m]);
+                tc_wait_ld();
+                float v[NC][16];
+#pragma unroll
+                for (int m = 0; m < NC; ++m)
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v[m][i] = __uint_as_float(r[m][i]);
+#pragma unroll
+                for (int p = 0; p < PPB; ++p) {
+                    const int ql = blk * PPB + p, q = ch * L.qc + ql;
+                    const bool live = good && ql < L.qc && q < a.nq;
+                    const float w = live ? wf[q] : 0.f;
+                    if constexpr (OP == OP_MASS) {
+                        v[0][p] = w * v[0][p];
+                    } else {
+                        float gh[D][D], G[D][D], S[D][D], e[D][D];
+#pragma unroll
+                        for (int m = 0; m < D; ++m)
+#pragma unroll
+                            for (int k = 0; k < D; ++k) gh[m][k] = v[m][p * KDP + k];
+                        map_grad<D, float>(gh, Jh, G);
+                        float tr = G[0][0];
+#pragma unroll
+                        for (int i = 1; i < D; ++i) tr += G[i][i];
+                        const float smu = w * mu_f, slt = w * lam_f * tr;
+#pragma unroll
+                        for (int i = 0; i < D; ++i) {
+                            S[i][i] = fmaf(2.f * smu, G[i][i], slt);
+#pragma unroll
+                            for (int k = i + 1; k < D; ++k) {
+                                const float s = smu * (G[i][k] + G[k][i]);
+                                S[i][k] = s;
+                                S[k][i] = s;
+                            }
+                        }
+                        pull_back<D, float>(S, Jh, e);
+#pragma unroll
+                        for (int m = 0; m < D; ++m)
+#pragma unroll
+                            for (int k = 0; k < KDP; ++k) v[m][p * KDP + k] = (k < D && live) ? e[m][k] : 0.f;
+                    }
+                }
+#pragma unroll
+                for (int m = 0; m < NC; ++m) {
+                    T16 *A2 = reinterpret_cast<T16 *>(hb + L.a2_off) + (size_t)m * kTcRows * L.N1p;
+                    uint32_t w[8];
+#pragma unroll
+                    for (int h = 0; h < 8; ++h) w[h] = pack2<T16>(v[m][2 * h], v[m][2 * h + 1]);
+                    *reinterpret_cast<uint4 *>(A2 + tc_off(t, blk * 16, L.N1p)) = make_uint4(w[0], w[1], w[2], w[3]);
+                    *reinterpret_cast<uint4 *>(A2 + tc_off(t, blk * 16 + 8, L.N1p)) =
+                        make_uint4(w[4], w[5], w[6], w[7]);
+                }
+            }
+            fence_async_smem();
+            tc_fence_before();
+            half_sync(half);
+            tc_fence_after();
+
+            // ---- quadrature GEMM of chunk ch, accumulated over the chunks
+            if (t == 0) {
+                const uint32_t sboa = (uint32_t)L.N1p * 16u, sbob = (uint32_t)L.K2 * 16u;
+                for (int m = 0; m < NC; ++m)
+                    for (int s = 0; s < L.N1p / 16; ++s) {
+                        const uint64_t da =
+                            tc_smem_desc(a2s + (uint32_t)(m * kTcRows * L.N1p * 2) + (uint32_t)s * 256u, 128u, sboa);
+                        const uint64_t db =
+                            tc_smem_desc(b2s + (uint32_t)((ch * L.N1p / 16 + s) * 256), 128u, sbob);
+                        tc_mma(thalf + (uint32_t)(L.acc1_cols + m * L.N2p), da, db, id2,
+                               (ch > 0 || s > 0) ? 1u : 0u);
+                    }
+            }
+        }
+        if (timed_out) break;
+        if (t == 0) tc_commit(barh);
+        if (!half_all(half, tc_wait(barh, phase))) {
+            tc_wait(barh, phase);
+            timed_out = true;
+            break;
+        }
+        phase ^= 1u;
+        tc_fence_after();
+
+        // ---- scatter-add (FP64): row t of Y_m holds this cell's node contributions
+        for (int blk = 0; blk < L.N2p / 16; ++blk) {
+            uint32_t r[NC][16];
+#pragma unroll
+            for (int m = 0; m < NC; ++m) tc_ld16(tlane + (uint32_t)(L.acc1_cols + m * L.N2p + blk * 16), r[m]);
+            tc_wait_ld();
+            if (good) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int j = blk * 16 + i;
+                    if (j < n) {
+                        const int node = snodes[j * kTcRows + t];
+#pragma unroll
+                        for (int m = 0; m < NC; ++m)
+                            atomicAdd(a.y + (size_t)node * NC + m, f32_to_f64(__uint_as_float(r[m][i])) * scale);
+                    }
+                }
+            }
+        }
+        tc_fence_before();
+        half_sync(half);
+    }
+    if (timed_out && t == 0) set_status(a.status, FE_ERR_TIMEOUT);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"((uint32_t)L.tmem_cols)
+                     : "memory");
+    leave_queue(a.sched);
+}
+
+template <int OP, int D, typename T16>
+cudaError_t launch_tc(const ActionArgs &a, int grid, int block, size_t smem, cudaStream_t s)
+{
+    k_action_tc<OP, D, T16><<<grid, block, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int OP, int D, typename T16>
+Variant make_tc_variant()
+{
+    Variant v;
+    v.form = OP;
+    v.dim = D;
+    v.degree = 0;   // any degree with at most 256 local nodes
+    v.op = 0;
+    v.precision = std::is_same<T16, __nv_bfloat16>::value ? FE_PREC_BF16 : FE_PREC_FP16;
+    v.kernel_id = 2;
+    v.block = kTcRows;
+    v.launch = &launch_tc<OP, D, T16>;
+    v.func = reinterpret_cast<const void *>(&k_action_tc<OP, D, T16>);
+    return v;
+}
+
+}  // namespace fe

@@ -106,3 +106,78 @@ def test_symmetric_tabulation_matches_oracle(fe, dim, q, degree):
     else:                        # both sides round the extended-precision solution once
         assert np.array_equal(pts, p2) and np.array_equal(wts, w2)
     assert np.abs(tab - t2).max() <= 1e-14 * np.abs(t2).max()
+
+
+# ---------------------------------------------------------------- 16-bit rounding of the tables
+def _round_ref(x: float, p: int, emin: int, emax: int) -> float:
+    """Round-to-nearest-even of x to a binary format with p significand bits and
+    normal exponents emin..emax (IEEE 754 definition, exact rational arithmetic)."""
+    from fractions import Fraction
+    import math
+    if math.isnan(x) or math.isinf(x) or x == 0.0:
+        return x
+    fx = Fraction(x)
+    e = math.frexp(abs(x))[1] - 1          # 2^e <= |x| < 2^(e+1)
+    q = Fraction(2) ** (max(e, emin) - (p - 1))   # quantum (subnormal below emin)
+    r = round(fx / q) * q                  # round() on Fraction: ties to even
+    big = (2 - Fraction(2) ** (1 - p)) * Fraction(2) ** emax
+    half_ulp_max = Fraction(2) ** (emax - p)
+    if abs(fx) >= big + half_ulp_max:
+        return math.copysign(math.inf, x)
+    return math.copysign(float(r), x) if r != 0 else math.copysign(0.0, x)
+
+
+def _bits_bf16(v: float) -> int:
+    return int(np.array([v], dtype=np.float32).view(np.uint32)[0] >> 16)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_round16_matches_ieee_definition(fe, prec):
+    """fe_round16 (the plans' table rounding, shared with the kernel's DoF
+    conversion) against round-to-nearest-even written from its definition,
+    on random magnitudes, exact ties, the overflow and subnormal edges."""
+    import ctypes
+    from paper_2506_17471_gb300 import _native as N
+    rng = np.random.default_rng(11)
+    p, emin, emax = (8, -126, 127) if prec == "bf16" else (11, -14, 15)
+    x = list(rng.standard_normal(3000) * 2.0 ** rng.integers(emin - 14, emax + 2, 3000))
+    # exact ties between neighbours and just off them
+    for _ in range(1500):
+        e = int(rng.integers(emin - 8, emax))
+        m = int(rng.integers(2 ** (p - 1), 2 ** p))
+        t = (m + 0.5) * 2.0 ** (e - p + 1)
+        x += [t, -t, np.nextafter(t, 0), np.nextafter(t, np.inf)]
+    big = (2 - 2.0 ** (1 - p)) * 2.0 ** emax
+    x += [0.0, -0.0, np.inf, -np.inf, big, big + 2.0 ** (emax - p), np.nextafter(big + 2.0 ** (emax - p), 0),
+          2.0 ** (emin - p + 1), 2.0 ** (emin - p), np.nextafter(2.0 ** (emin - p), 1), 1e-300, 5e-324]
+    x = np.asarray(x, dtype=np.float64)
+    bits = np.zeros(len(x), dtype=np.uint16)
+    code = N.FE_PREC_BF16 if prec == "bf16" else N.FE_PREC_FP16
+    assert N.lib.fe_round16(ctypes.c_void_p(x.ctypes.data), len(x), code,
+                            ctypes.c_void_p(bits.ctypes.data)) == 0
+    for xi, b in zip(x, bits):
+        r = _round_ref(float(xi), p, emin, emax)
+        if prec == "bf16":
+            assert b == _bits_bf16(r), (xi, hex(b), r)
+        else:
+            assert b == int(np.array([r], dtype=np.float16).view(np.uint16)[0]), (xi, hex(b), r)
+    # NaN stays NaN
+    nan = np.array([np.nan], dtype=np.float64)
+    assert N.lib.fe_round16(ctypes.c_void_p(nan.ctypes.data), 1, code, ctypes.c_void_p(bits.ctypes.data)) == 0
+    mask = (0x7F80, 0x7F) if prec == "bf16" else (0x7C00, 0x3FF)
+    assert (bits[0] & mask[0]) == mask[0] and (bits[0] & mask[1])
+
+
+def test_round16_agrees_with_numpy_half(fe):
+    """numpy's binary64 -> binary16 conversion is an independent implementation."""
+    import ctypes
+    from paper_2506_17471_gb300 import _native as N
+    rng = np.random.default_rng(12)
+    x = rng.standard_normal(200_000) * 2.0 ** rng.integers(-30, 18, 200_000)
+    bits = np.zeros(len(x), dtype=np.uint16)
+    assert N.lib.fe_round16(ctypes.c_void_p(x.ctypes.data), len(x), N.FE_PREC_FP16,
+                            ctypes.c_void_p(bits.ctypes.data)) == 0
+    with np.errstate(over="ignore"):
+        ref = x.astype(np.float16).view(np.uint16)
+    assert np.array_equal(bits, ref)
+    assert N.lib.fe_round16(ctypes.c_void_p(x.ctypes.data), 1, N.FE_PREC_FP64, ctypes.c_void_p(bits.ctypes.data)) != 0

@@ -1,0 +1,196 @@
+"""GPU parity of the tensor-core kernel (16-bit contractions, FP32 accumulate)
+against the FP64 oracle.
+
+Stated bound.  The kernel rounds three things to the 16-bit type: the
+tabulation (once, in the plan), each cell's DoFs after scaling by a power of two,
+and the pointwise values E' after scaling; products accumulate in FP32 and the
+geometry, output scaling and scatter are FP64.  Each rounding is a relative
+perturbation of at most the unit roundoff u16 (bfloat16: 2^-8 = 3.9e-3,
+binary16: 2^-11 = 4.9e-4); through the two contractions they add up to about
+3 u16 of the sum of absolute terms, which for the random fields below is close
+to the result itself (a numpy emulation of the kernel measured 0.6-1.2 u16).
+The parity tolerance is TOL16 = 4 u16 norm-wise, relative to ||y_ref||_inf.
+A lower bound (> 1e-7) checks that the work really ran in 16 bits.
+"""
+
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from feinputs import structured_mesh, uniform_field
+
+pytestmark = pytest.mark.gpu
+U16 = {"bf16": 2.0 ** -8, "fp16": 2.0 ** -11}
+TOL16 = {k: 4 * v for k, v in U16.items()}
+
+
+@pytest.fixture(scope="module")
+def fe():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2506_17471_gb300 as fe
+    return fe
+
+
+def rel(a, b):
+    a = a.detach().cpu().numpy() if torch.is_tensor(a) else a
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def cuda(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def make(fe, dim, N, p, seed, scale=1.0):
+    m = structured_mesh(dim, N, p, jitter=0.2 if dim == 2 else 0.15, seed=seed)
+    if scale != 1.0:
+        m.coords = m.coords * scale
+    return m, fe.Mesh(dim, p, m.coords, m.cell2vertex, m.cell2node, m.n_nodes)
+
+
+# (kind, dim, N, p, q, scheme): every case spans several 128-cell tiles with a ragged tail
+CASES = [
+    ("mass", 2, 13, 1, 2, "conical"), ("mass", 2, 13, 3, 6, "symmetric"), ("mass", 2, 13, 6, 12, "conical"),
+    ("mass", 3, 5, 2, 4, "conical"), ("mass", 3, 5, 4, 8, "conical"),
+    ("elasticity", 2, 13, 2, 2, "symmetric"), ("elasticity", 2, 13, 4, 6, "symmetric"),
+    ("elasticity", 2, 13, 6, 10, "conical"), ("elasticity", 3, 5, 1, 0, "conical"),
+    ("elasticity", 3, 5, 2, 2, "symmetric"), ("elasticity", 3, 5, 2, 2, "conical"),
+    ("elasticity", 3, 5, 4, 6, "conical"),
+]
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+@pytest.mark.parametrize("kind,dim,N,p,q,scheme", CASES)
+def test_tc_parity(fe, kind, dim, N, p, q, scheme, prec):
+    m, M = make(fe, dim, N, p, 300 + 10 * dim + p)
+    assert m.n_cells > 256 and m.n_cells % 128 != 0
+    o = oracle.Oracle.from_mesh(m, q, scheme=scheme)
+    nc = 1 if kind == "mass" else dim
+    u = uniform_field(m.n_nodes * nc, 7 + p)
+    if kind == "mass":
+        plan = fe.Plan(M, fe.MASS, q, precision=prec, quad_scheme=scheme)
+        ref = o.mass(u)
+    else:
+        plan = fe.Plan(M, fe.ELASTICITY, q, lam=1.25, mu=1.0, precision=prec, quad_scheme=scheme)
+        ref = o.elasticity(u, 1.25, 1.0)
+    assert plan.info.kernel == 2
+    y = plan.apply(cuda(u))
+    err = rel(y, ref)
+    assert 1e-7 < err <= TOL16[prec], err
+    assert plan.status() == 0
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_tc_scale_invariance(fe, prec):
+    """Per-cell power-of-two scaling: A(2^k u) = 2^k A(u) up to the order of the
+    FP64 atomics, for magnitudes far outside binary16's range."""
+    m, M = make(fe, 3, 5, 2, 41)
+    plan = fe.Plan(M, fe.ELASTICITY, 2, lam=1.25, mu=1.0, precision=prec, quad_scheme="symmetric")
+    u = uniform_field(m.n_nodes * 3, 9)
+    y1 = plan.apply(cuda(u)).cpu().numpy()
+    for k in (-700, -60, 40, 700):
+        yk = plan.apply(cuda(u * 2.0 ** k)).cpu().numpy()
+        assert np.abs(yk * 2.0 ** -k - y1).max() <= 1e-13 * np.abs(y1).max(), k
+    assert plan.status() == 0
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_tc_tiny_and_huge_cells(fe, prec):
+    """Mesh scaled by 2^-24 and 2^+24: J^{-1} is scaled per cell by a power of
+    two, so the pointwise values stay in range and the bound still holds."""
+    for s in (2.0 ** -24, 2.0 ** 24):
+        m, M = make(fe, 2, 13, 4, 42, scale=s)
+        o = oracle.Oracle.from_mesh(m, 6, scheme="symmetric")
+        u = uniform_field(m.n_nodes * 2, 10)
+        plan = fe.Plan(M, fe.ELASTICITY, 6, lam=1.25, mu=1.0, precision=prec, quad_scheme="symmetric")
+        assert rel(plan.apply(cuda(u)), o.elasticity(u, 1.25, 1.0)) <= TOL16[prec]
+        assert plan.status() == 0
+
+
+def test_tc_edge_cases(fe):
+    # empty mesh: y = 0, nothing launched
+    m, _ = make(fe, 2, 4, 3, 43)
+    M0 = fe.Mesh(2, 3, m.coords, m.cell2vertex[:0], m.cell2node[:0], m.n_nodes)
+    plan = fe.Plan(M0, fe.MASS, 6, precision="bf16")
+    y = plan.apply(cuda(np.ones(m.n_nodes)))
+    assert float(y.abs().max()) == 0.0
+    # a single cell (one partial tile)
+    M1 = fe.Mesh(2, 3, m.coords, m.cell2vertex[:1], m.cell2node[:1], m.n_nodes)
+    o1 = oracle.Oracle(2, 3, 6, m.coords, m.cell2vertex[:1], m.cell2node[:1], m.n_nodes)
+    u = uniform_field(m.n_nodes, 3)
+    assert rel(fe.Plan(M1, fe.MASS, 6, precision="fp16").apply(cuda(u)), o1.mass(u)) <= TOL16["fp16"]
+    # accumulate: y += A u
+    m, M = make(fe, 2, 13, 3, 44)
+    o = oracle.Oracle.from_mesh(m, 6)
+    u = uniform_field(m.n_nodes, 4)
+    y0 = uniform_field(m.n_nodes, 5)
+    acc = fe.Plan(M, fe.MASS, 6, precision="fp16", accumulate=True)
+    y = acc.apply(cuda(u), cuda(y0.copy()))
+    ref = y0 + o.mass(u)
+    assert np.abs(y.cpu().numpy() - ref).max() <= TOL16["fp16"] * np.abs(o.mass(u)).max()
+    # forms without a tensor-core variant are refused
+    with pytest.raises(Exception):
+        fe.Plan(M, fe.NH_RESIDUAL, 6, mu=1.0, lam=1.0, precision="bf16")
+
+
+def test_tc_bad_index_sets_status(fe):
+    """An out-of-range node index skips its cell and reports FE_ERR_INDEX; the
+    other cells are still applied."""
+    from paper_2506_17471_gb300 import _native as N
+    m, _ = make(fe, 2, 13, 3, 45)
+    c2n = m.cell2node.copy()
+    c2n[200, 4] = m.n_nodes + 7
+    M = fe.Mesh(2, 3, m.coords, m.cell2vertex, c2n, m.n_nodes)
+    plan = fe.Plan(M, fe.MASS, 6, precision="bf16")
+    u = uniform_field(m.n_nodes, 6)
+    y = plan.apply(cuda(u)).cpu().numpy()
+    assert plan.status() == N.FE_ERR_INDEX
+    keep = np.ones(m.n_cells, dtype=bool)
+    keep[200] = False
+    o = oracle.Oracle(2, 3, 6, m.coords, m.cell2vertex[keep], m.cell2node[keep], m.n_nodes)
+    assert rel(y, o.mass(u)) <= TOL16["bf16"]
+    assert plan.status() == 0
+
+
+def test_tc_conversions_match_hardware(fe):
+    """The kernel converts binary64 DoFs to 16 bits with integer operations; they
+    must agree bit for bit with CUDA's __double2bfloat16 / __double2half."""
+    from paper_2506_17471_gb300 import _native as N
+    rng = np.random.default_rng(1)
+    vals = [rng.standard_normal(300_000) * 2.0 ** rng.integers(-150, 140, 300_000),
+            rng.uniform(-1, 1, 100_000),
+            np.array([0.0, -0.0, np.inf, -np.inf, np.nan, 65504.0, 65520.0, 65519.99, 6e-8, 2.0 ** -25,
+                      2.0 ** -25 * 1.0000001, 3.3895313892515355e38, 3.39e38, 1e-300, 5e-324])]
+    h = rng.standard_normal(100_000).astype(np.float16)
+    hn = np.nextafter(h, np.float16(np.inf))
+    vals.append((h.astype(np.float64) + hn.astype(np.float64)) / 2)   # binary16 ties
+    x = cuda(np.concatenate(vals))
+    count = torch.zeros(2, dtype=torch.int64, device="cuda")
+    assert N.lib.fe_selftest_conversions16(ctypes.c_void_p(x.data_ptr()), x.numel(),
+                                           ctypes.c_void_p(count.data_ptr()), None) == 0
+    assert count.tolist() == [0, 0]
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_tc_full_mass_p3_2d(fe, prec):
+    """hp-sweep size: mass P3 on 2 x 667^2 triangles (4,008,004 DoFs), all outputs."""
+    m, M = make(fe, 2, 667, 3, 20250620)
+    o = oracle.Oracle.from_mesh(m, 6, scheme="symmetric")
+    u = uniform_field(m.n_nodes, 21)
+    plan = fe.Plan(M, fe.MASS, 6, precision=prec, quad_scheme="symmetric")
+    assert rel(plan.apply(cuda(u)), o.mass(u, threads=16)) <= TOL16[prec]
+    assert plan.status() == 0
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_tc_full_elasticity_p4_3d(fe, prec):
+    """hp-sweep size: elasticity P4 on 6 x 27^3 tetrahedra (3,885,087 DoFs), all outputs."""
+    m, M = make(fe, 3, 27, 4, 20250622)
+    o = oracle.Oracle.from_mesh(m, 6)
+    u = uniform_field(m.n_nodes * 3, 22)
+    plan = fe.Plan(M, fe.ELASTICITY, 6, lam=1.25, mu=1.0, precision=prec)
+    assert rel(plan.apply(cuda(u)), o.elasticity(u, 1.25, 1.0, threads=16)) <= TOL16[prec]
+    assert plan.status() == 0
