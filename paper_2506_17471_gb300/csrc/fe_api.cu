@@ -62,21 +62,24 @@ int coop_cells_for(int n, int nq, int dim, int ncomp, int fields, size_t esz, si
     return best;
 }
 
-// Tensor-core tile shape: two 128-cell pipelines per CTA if their tables,
-// operands and accumulators fit (256 TMEM columns each), else one; the fewest
-// quadrature-point chunks that fit.  Returns false if nothing fits.
-bool tc_choose(int n, int nq, int ncomp, int kd, int fields, size_t smem_cap, TcLayout *out)
+// Tensor-core tile shape: the most 128-cell pipelines per CTA (4, 2, 1, or the
+// count force_pipes asks for) whose staged tables, operands and accumulators
+// fit the SM's shared memory and 512 TMEM columns, with the fewest
+// quadrature-point chunks.  Returns false if nothing fits.
+bool tc_choose(int n, int nq, int ncomp, int kd, int fields, size_t smem_cap, int force_pipes, TcLayout *out)
 {
     if (n > 256 || nq < 1) return false;
-    for (int halves = 2; halves >= 1; --halves)
+    for (int pipes = kTcMaxPipes; pipes >= 1; pipes /= 2) {
+        if (force_pipes && pipes != force_pipes) continue;
         for (int nch = 1; nch <= nq; ++nch) {
             const int qc = (nq + nch - 1) / nch;
-            const TcLayout L = tc_layout(n, nq, ncomp, kd, fields, qc, halves);
+            const TcLayout L = tc_layout(n, nq, ncomp, kd, fields, qc, pipes);
             if (L.N1p > 256 || L.N2p > 256 || L.tmem_cols > 512) continue;
             if (L.total > smem_cap || L.staged_bytes >= (1u << 20)) continue;
             *out = L;
             return true;
         }
+    }
     return false;
 }
 
@@ -247,8 +250,14 @@ static int plan_create_tc(const fe_form &f, const fe_mesh &m, const Variant &v, 
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
         return FE_ERR_CUDA;
     const int kd = f.kind == FE_FORM_MASS ? 1 : m.dim;
+    // tiles copy their cell2node block with 16-byte loads
+    if (reinterpret_cast<uintptr_t>(m.cell2node) % 16 != 0) return FE_ERR_INVALID_ARG;
+    // tile_cells selects the pipelines per CTA (128 cells each): 128, 256, 512, or 0 automatic
+    if (f.tile_cells != 0 && f.tile_cells != kTcRows && f.tile_cells != 2 * kTcRows &&
+        f.tile_cells != 4 * kTcRows)
+        return FE_ERR_UNSUPPORTED;
     TcLayout L;
-    if (!tc_choose(n, nq, ncomp, kd, 1, (size_t)optin - 256, &L)) return FE_ERR_UNSUPPORTED;
+    if (!tc_choose(n, nq, ncomp, kd, 1, (size_t)optin - 256, f.tile_cells / kTcRows, &L)) return FE_ERR_UNSUPPORTED;
     std::vector<unsigned char> blk;
     if (f.precision == FE_PREC_BF16)
         tc_fill_block<__nv_bfloat16>(L, f.kind, wts, tab, blk);
@@ -264,12 +273,12 @@ static int plan_create_tc(const fe_form &f, const fe_mesh &m, const Variant &v, 
     p->ncomp = ncomp;
     p->tab_doubles = (int)(L.staged_bytes / sizeof(double));
     p->var = v;
-    p->var.block = kTcRows * L.halves;
+    p->var.block = kTcRows * L.pipes;
     p->adj = Variant{};
     p->smem_bytes = L.total;
     p->device = dev;
     p->tc_qc = L.qc;
-    p->tc_halves = L.halves;
+    p->tc_pipes = L.pipes;
     if (cudaMalloc(&p->d_tab, L.staged_bytes) != cudaSuccess ||
         cudaMalloc(&p->d_status, 8 * sizeof(int32_t)) != cudaSuccess) {
         cudaFree(p->d_tab);
@@ -283,16 +292,10 @@ static int plan_create_tc(const fe_form &f, const fe_mesh &m, const Variant &v, 
         fe_plan_destroy(p);
         return FE_ERR_CUDA;
     }
-    // resident CTAs per SM: shared memory and registers, and the 512 TMEM
-    // columns (a CTA whose allocation does not fit would wait for another to exit)
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, v.func, p->var.block, L.total) != cudaSuccess ||
-        per_sm < 1)
-        per_sm = 1;
-    per_sm = std::min(per_sm, 512 / L.tmem_cols);
+    // one CTA per SM (a kernel that uses tensor memory is resident alone on its SM)
     const long long tiles = ((long long)m.n_cells + kTcRows - 1) / kTcRows;
-    const long long want = (tiles + L.halves - 1) / L.halves;
-    p->grid_blocks = (int)std::max(1LL, std::min(want, (long long)per_sm * num_sms()));
+    const long long want = (tiles + L.pipes - 1) / L.pipes;
+    p->grid_blocks = (int)std::max(1LL, std::min(want, (long long)num_sms()));
     p->flops_per_cell = algorithmic_flops(f.kind, m.dim, n, nq);
     const double dofs = (double)m.n_nodes * ncomp;
     p->bytes_min = 2.0 * dofs * 8.0 + (double)m.n_vertices * m.dim * 8.0 + (double)m.n_cells * (n + m.dim + 1) * 4.0;
@@ -480,7 +483,7 @@ static ActionArgs make_args(const fe_plan *p, const double *u, double *y)
     a.tab_b = p->d_tab_b;
     a.tab_c = p->d_tab_c;
     a.tc_qc = p->tc_qc;
-    a.tc_halves = p->tc_halves;
+    a.tc_pipes = p->tc_pipes;
     return a;
 }
 

@@ -39,7 +39,7 @@ struct ActionArgs {
     const void *tab_b;        // cooperative kernel, large tables: [1+D][N][nq] in global memory
     const void *tab_c;        // cooperative kernel, large tables: [nq][1+D][N] in global memory
     int32_t tc_qc;            // tensor-core kernel: quadrature points per chunk
-    int32_t tc_halves;        // tensor-core kernel: 128-cell pipelines per CTA (1 or 2)
+    int32_t tc_pipes;         // tensor-core kernel: 128-cell pipelines per CTA (1, 2 or 4)
 };
 
 // Launch function of one compiled kernel variant.
@@ -102,7 +102,7 @@ struct fe_plan {
     size_t smem_bytes;
     int coop_cells;       // cells per CTA batch (cooperative kernel), else 0
     int tc_qc;            // tensor-core kernel: quadrature points per chunk, else 0
-    int tc_halves;        // tensor-core kernel: 128-cell pipelines per CTA, else 0
+    int tc_pipes;         // tensor-core kernel: 128-cell pipelines per CTA, else 0
     int device;
     double flops_per_cell;
     double bytes_min;

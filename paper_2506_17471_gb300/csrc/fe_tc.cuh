@@ -20,16 +20,22 @@
 // core-matrix layout and staged once per CTA by one bulk copy.  Quadrature
 // points are processed in chunks of qc points so the evaluation accumulators of
 // a chunk and the quadrature accumulators of the whole tile fit in TMEM; the
-// quadrature GEMM accumulates over the chunks.  A CTA runs one or two
-// independent 128-cell pipelines ("halves", 128 threads each) that share the
-// staged tables and synchronise with named barriers.
+// quadrature GEMM accumulates over the chunks.  A CTA runs one to four
+// independent 128-cell pipelines (128 threads each) that share the staged
+// tables, split the SM's 512 TMEM columns and synchronise with named barriers:
+// a CTA that uses tensor memory is resident alone on its SM, so the pipelines
+// are what hides one another's gather, MMA and scatter latency.
 //
-// Precision: the DoFs are scaled per cell by a power of two s_u >= max |u|
+// Precision: the DoFs are scaled per cell by a power of two s_u > max |u|
 // and rounded to 16 bits; for elasticity J^{-1} is scaled by a power of two
-// s_J >= max |J^{-1}_ik|.  The pointwise values then stay O(1) whatever the
-// mesh size and field magnitude (FP16 neither overflows nor goes subnormal),
-// and the output factor |det J| s_u s_J^2 is applied in FP64 at the scatter.
-// Geometry is FP64, the linear stress FP32, the scatter-add FP64.
+// s_J > max |J^{-1}_ik|.  The pointwise values then stay O(1) whatever the
+// mesh size and field magnitude (FP16 neither overflows nor goes subnormal).
+// The output factor |det J| s_u s_J^2 is applied as an FP32 multiply by the
+// significand of |det J| (relative error 2^-24, far below the 16-bit
+// rounding) and an exponent add on the widened FP64 value.  All power-of-two
+// scalings are exponent arithmetic on the bit patterns: on this part FP64
+// instructions issue at about 1/64 of the FP32 rate, and the only ones left are
+// the FP64 geometry (det J, J^{-1}) and the FP64 scatter-add.
 //
 // Operand layout (K-major, no swizzle): 8x8 core matrices of 16-bit elements
 // (128 bytes), ordered [row group][K group][row][col]; LBO = 128 B between
@@ -45,7 +51,8 @@
 
 namespace fe {
 
-constexpr int kTcRows = 128;   // cells (threads, TMEM lanes) per half
+constexpr int kTcRows = 128;   // cells (threads, TMEM lanes) per pipeline
+constexpr int kTcMaxPipes = 4; // pipelines per CTA (a CTA that uses TMEM has an SM to itself)
 
 __host__ __device__ inline int tc_round_up(int x, int m) { return (x + m - 1) / m * m; }
 __host__ __device__ inline size_t tc_round_up_sz(size_t x, size_t m) { return (x + m - 1) / m * m; }
@@ -56,16 +63,16 @@ struct TcLayout {
     int qc, nch;                 // points per chunk, chunks
     int N1p, K1p;                // evaluation GEMM: N (chunk columns), K (n padded to 16)
     int N2p, K2;                 // quadrature GEMM: N (n padded to 16), K (nch * N1p)
-    int halves;
+    int pipes;
     size_t b1_off, b2_off, wd_off, wf_off, staged_bytes;   // staged block
-    size_t a1_off, a2_off, nodes_off, half_bytes;          // per-half scratch (from its base)
+    size_t a1_off, a2_off, nodes_off, pipe_bytes;          // per-pipeline scratch (from its base)
     size_t total;                                          // dynamic shared memory
-    int acc1_cols, acc2_cols, half_cols, tmem_cols;
+    int acc1_cols, acc2_cols, pipe_cols, tmem_cols;
 };
 
 __host__ __device__ inline int tc_kdp(int kd) { return kd == 1 ? 1 : (kd == 2 ? 2 : 4); }
 
-__host__ __device__ inline TcLayout tc_layout(int n, int nq, int NC, int KD, int F, int qc, int halves)
+__host__ __device__ inline TcLayout tc_layout(int n, int nq, int NC, int KD, int F, int qc, int pipes)
 {
     TcLayout L;
     L.n = n;
@@ -80,7 +87,7 @@ __host__ __device__ inline TcLayout tc_layout(int n, int nq, int NC, int KD, int
     L.K1p = tc_round_up(n, 16);
     L.N2p = tc_round_up(n, 16);
     L.K2 = L.nch * L.N1p;
-    L.halves = halves;
+    L.pipes = pipes;
     L.b1_off = 0;
     L.b2_off = (size_t)L.nch * L.N1p * L.K1p * 2;
     L.wd_off = L.b2_off + (size_t)L.N2p * L.K2 * 2;
@@ -89,14 +96,14 @@ __host__ __device__ inline TcLayout tc_layout(int n, int nq, int NC, int KD, int
     L.a1_off = 0;
     L.a2_off = L.a1_off + (size_t)F * NC * kTcRows * L.K1p * 2;
     L.nodes_off = L.a2_off + (size_t)NC * kTcRows * L.N1p * 2;
-    L.half_bytes = tc_round_up_sz(L.nodes_off + (size_t)n * kTcRows * 4, 128);
-    L.total = L.staged_bytes + (size_t)halves * L.half_bytes;
+    L.pipe_bytes = tc_round_up_sz(L.nodes_off + (size_t)(n | 1) * kTcRows * 4, 128);   // nodes [128][n | 1]
+    L.total = L.staged_bytes + (size_t)pipes * L.pipe_bytes;
     L.acc1_cols = F * NC * L.N1p;
     L.acc2_cols = NC * L.N2p;
-    L.half_cols = L.acc1_cols + L.acc2_cols;
-    // each half owns tmem_cols / halves columns (a power of two >= 32 in total)
+    L.pipe_cols = L.acc1_cols + L.acc2_cols;
+    // each pipeline owns tmem_cols / pipes columns (a power of two >= 32 in total)
     int t = 32;
-    while (t / halves < L.half_cols) t <<= 1;
+    while (t / pipes < L.pipe_cols) t <<= 1;
     L.tmem_cols = t;
     return L;
 }
@@ -107,13 +114,14 @@ __host__ __device__ inline size_t tc_off(int r, int k, int Kp)
     return (size_t)(r >> 3) * (Kp >> 3) * 64 + (size_t)(k >> 3) * 64 + (r & 7) * 8 + (k & 7);
 }
 
-// Round-to-nearest-even conversion of an IEEE binary64 value to a binary16-
-// family format with EB exponent and MB fraction bits (binary16: 5, 10;
-// bfloat16: 8, 7), done on the integer bit pattern (no FP64-pipe conversion).
-// NaN maps to a quiet NaN, overflow to infinity, results below half the
-// smallest subnormal to signed zero.
+// Round-to-nearest-even conversion of x * 2^-k (x an IEEE binary64 value) to
+// a binary16-family format with EB exponent and MB fraction bits (binary16:
+// 5, 10; bfloat16: 8, 7), done on the integer bit pattern (no FP64-pipe
+// operation; the power-of-two scaling is an exponent offset).  NaN maps to a
+// quiet NaN, overflow to infinity, results below half the smallest subnormal
+// to signed zero.
 template <int EB, int MB>
-__host__ __device__ __forceinline__ uint16_t f64_to_small_rn(double x)
+__host__ __device__ __forceinline__ uint16_t f64_to_small_rn(double x, int k = 0)
 {
     uint64_t b;
 #ifdef __CUDA_ARCH__
@@ -127,7 +135,7 @@ __host__ __device__ __forceinline__ uint16_t f64_to_small_rn(double x)
     const uint64_t frac = b & 0xFFFFFFFFFFFFFull;
     const int e = (int)((b >> 52) & 0x7FF);
     if (e == 0x7FF) return (uint16_t)(sign | kInf | (frac ? (1u << (MB - 1)) : 0u));
-    const int te = e - 1023 + kBias;   // biased exponent in the target format
+    const int te = (e ? e : 1) - 1023 + kBias - k;   // biased exponent in the target format
     uint64_t m;
     int shift;
     if (te >= 1) {
@@ -138,6 +146,9 @@ __host__ __device__ __forceinline__ uint16_t f64_to_small_rn(double x)
         shift = 52 - MB + 1 - te;
         if (shift > 62) return (uint16_t)sign;
     }
+    if (te > 2 * kBias + 1) {
+        return (uint16_t)(sign | kInf);   // far above the largest finite value
+    }
     uint64_t r = m >> shift;
     const uint64_t rem = m & ((1ull << shift) - 1ull), halfway = 1ull << (shift - 1);
     if (rem > halfway || (rem == halfway && (r & 1ull))) ++r;
@@ -146,11 +157,62 @@ __host__ __device__ __forceinline__ uint16_t f64_to_small_rn(double x)
 }
 
 template <typename T16>
-__host__ __device__ __forceinline__ uint16_t to16_bits(double x);
+__host__ __device__ __forceinline__ uint16_t to16_bits(double x, int k = 0);
 template <>
-__host__ __device__ __forceinline__ uint16_t to16_bits<__nv_bfloat16>(double x) { return f64_to_small_rn<8, 7>(x); }
+__host__ __device__ __forceinline__ uint16_t to16_bits<__nv_bfloat16>(double x, int k)
+{
+    return f64_to_small_rn<8, 7>(x, k);
+}
 template <>
-__host__ __device__ __forceinline__ uint16_t to16_bits<__half>(double x) { return f64_to_small_rn<5, 10>(x); }
+__host__ __device__ __forceinline__ uint16_t to16_bits<__half>(double x, int k)
+{
+    return f64_to_small_rn<5, 10>(x, k);
+}
+
+// Biased binary64 exponent field of x (0: zero or subnormal, 2047: inf or NaN).
+__device__ __forceinline__ int exp_field(double x) { return (int)(((unsigned)__double2hiint(x) >> 20) & 0x7FFu); }
+
+// binary32 v times 2^k, widened to binary64 exactly, with integer operations
+// only (no FP64-pipe instruction on any path).  Zero and binary32 subnormals
+// give signed zero (they are below 2^-126 of an O(1) accumulator), inf and NaN
+// stay inf and NaN, a result outside binary64's normal range gives zero or inf.
+__device__ __forceinline__ double widen_pow2(float v, int k)
+{
+    const unsigned b = __float_as_uint(v);
+    const unsigned sign = b & 0x80000000u, mant = b & 0x7FFFFFu;
+    const int e = (int)((b >> 23) & 0xFFu);
+    const int E = e - 127 + 1023 + k;
+    unsigned hi, lo;
+    if (e == 0 || E < 1) {
+        hi = sign;
+        lo = 0u;
+    } else if (e == 255 || E > 2046) {
+        hi = sign | 0x7FF00000u | (e == 255 ? (mant >> 3) | (mant ? 0x80000u : 0u) : 0u);
+        lo = 0u;
+    } else {
+        hi = sign | ((unsigned)E << 20) | (mant >> 3);
+        lo = mant << 29;
+    }
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+// binary64 x times 2^-k rounded to binary32 (nearest even) with integer
+// operations only; results below 2^-126 flush to signed zero, overflow gives
+// inf, NaN stays NaN.
+__device__ __forceinline__ float narrow_pow2_ftz(double x, int k)
+{
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const unsigned sign = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7FFu);
+    if (e == 0x7FF) return __uint_as_float(sign | 0x7F800000u | ((hi & 0xFFFFFu) | lo ? 0x400000u : 0u));
+    const int fe = e - 1023 + 127 - k;   // binary32 biased exponent
+    if (e == 0 || fe < 1) return __uint_as_float(sign);
+    if (fe > 254) return __uint_as_float(sign | 0x7F800000u);
+    const unsigned bits = sign | ((unsigned)fe << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+    const unsigned rest = lo & 0x1FFFFFFFu;
+    const unsigned up = (rest > 0x10000000u) || (rest == 0x10000000u && (bits & 1u));
+    return __uint_as_float(bits + up);   // a carry may round up to the next binade or inf
+}
 
 // Two FP32 values to a packed pair of 16-bit values (round to nearest even);
 // the first value lands at the lower address.
@@ -213,24 +275,39 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// Barrier over the 128 threads of one half (named barrier 1 + half).
-__device__ __forceinline__ void half_sync(int half)
+// Barrier over the 128 threads of one pipeline (named barrier 1 + pipe).
+// The barrier ids are immediates, so the kernel reserves only the barriers it
+// uses.
+__device__ __forceinline__ void pipe_sync(int pipe)
 {
-    asm volatile("bar.sync %0, %1;" ::"r"(1 + half), "r"(kTcRows) : "memory");
+    switch (pipe) {
+    case 0: asm volatile("bar.sync 1, 128;" ::: "memory"); break;
+    case 1: asm volatile("bar.sync 2, 128;" ::: "memory"); break;
+    case 2: asm volatile("bar.sync 3, 128;" ::: "memory"); break;
+    default: asm volatile("bar.sync 4, 128;" ::: "memory"); break;
+    }
 }
 
-// Barrier over one half that also returns whether pred held on all its threads.
-__device__ __forceinline__ bool half_all(int half, bool pred)
+#define FE_TC_BAR_RED_AND(ID)                                                        \
+    asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"                \
+                 "bar.red.and.pred q, " #ID ", 128, p;\n\tselp.u32 %0, 1, 0, q;\n\t}" \
+                 : "=r"(r)                                                            \
+                 : "r"((uint32_t)pred)                                                \
+                 : "memory")
+
+// Barrier over one pipeline that also returns whether pred held on all its threads.
+__device__ __forceinline__ bool pipe_all(int pipe, bool pred)
 {
     uint32_t r;
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
-        "bar.red.and.pred q, %2, %3, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
-        : "=r"(r)
-        : "r"((uint32_t)pred), "r"(1 + half), "r"(kTcRows)
-        : "memory");
+    switch (pipe) {
+    case 0: FE_TC_BAR_RED_AND(1); break;
+    case 1: FE_TC_BAR_RED_AND(2); break;
+    case 2: FE_TC_BAR_RED_AND(3); break;
+    default: FE_TC_BAR_RED_AND(4); break;
+    }
     return r != 0;
 }
+#undef FE_TC_BAR_RED_AND
 
 // Bounded wait on an mbarrier phase; true if it completed.
 __device__ __forceinline__ bool tc_wait(uint32_t sbar, uint32_t parity)
@@ -249,22 +326,8 @@ __device__ __forceinline__ bool tc_wait(uint32_t sbar, uint32_t parity)
     return false;
 }
 
-// Power of two s = 2^e with 2^(e-1) <= x < 2^e for finite x > 0, else 1.
-__device__ __forceinline__ void pow2_above(double x, double &s, double &inv_s)
-{
-    if (!(x > 0.0) || !isfinite(x)) {
-        s = 1.0;
-        inv_s = 1.0;
-        return;
-    }
-    int e = 0;
-    frexp(x, &e);
-    s = ldexp(1.0, e);
-    inv_s = ldexp(1.0, -e);
-}
-
 template <int OP, int D, typename T16>
-__global__ void __launch_bounds__(2 * kTcRows, 1) k_action_tc(const ActionArgs a)
+__global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const ActionArgs a)
 {
     constexpr int NC = OpTraits<OP, D>::NC;
     constexpr int KD = (OP == OP_MASS) ? 1 : D;
@@ -273,18 +336,18 @@ __global__ void __launch_bounds__(2 * kTcRows, 1) k_action_tc(const ActionArgs a
     constexpr int PPB = 16 / KDP;   // quadrature points per 16 accumulator columns
     constexpr int FMT = std::is_same<T16, __nv_bfloat16>::value ? 1 : 0;
     extern __shared__ __align__(128) unsigned char tc_smem[];
-    __shared__ __align__(8) uint64_t bars[3];   // table copy; one MMA barrier per half
+    __shared__ __align__(8) uint64_t bars[1 + kTcMaxPipes];   // table copy; one MMA barrier per pipeline
     __shared__ uint32_t s_tmem;
-    __shared__ int s_tile[2];
+    __shared__ int s_tile[kTcMaxPipes];
 
-    const TcLayout L = tc_layout(a.coop_n, a.nq, NC, KD, F, a.tc_qc, a.tc_halves);
-    const int tid = threadIdx.x, half = tid >> 7, t = tid & (kTcRows - 1), warp = tid >> 5;
+    const TcLayout L = tc_layout(a.coop_n, a.nq, NC, KD, F, a.tc_qc, a.tc_pipes);
+    const int tid = threadIdx.x, pipe = tid >> 7, t = tid & (kTcRows - 1), warp = tid >> 5;
     const int n = L.n;
     const uint32_t bar0 = (uint32_t)__cvta_generic_to_shared(&bars[0]);
-    const uint32_t barh = (uint32_t)__cvta_generic_to_shared(&bars[1 + half]);
+    const uint32_t barp = (uint32_t)__cvta_generic_to_shared(&bars[1 + pipe]);
 
     if (tid == 0) {
-        for (int i = 0; i < 3; ++i) {
+        for (int i = 0; i <= L.pipes; ++i) {
             const uint32_t b = (uint32_t)__cvta_generic_to_shared(&bars[i]);
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
         }
@@ -314,33 +377,59 @@ __global__ void __launch_bounds__(2 * kTcRows, 1) k_action_tc(const ActionArgs a
     if (!ok) tc_wait(bar0, 0);   // let a late copy land before the CTA exits
 
     const unsigned char *staged = tc_smem;
-    unsigned char *hb = tc_smem + L.staged_bytes + (size_t)half * L.half_bytes;
+    unsigned char *hb = tc_smem + L.staged_bytes + (size_t)pipe * L.pipe_bytes;
     const float *wf = reinterpret_cast<const float *>(staged + L.wf_off);
-    int *snodes = reinterpret_cast<int *>(hb + L.nodes_off);   // [n][128]
+    int *snodes = reinterpret_cast<int *>(hb + L.nodes_off);   // [128][P]
+    const int P = n | 1;
     const uint32_t b1s = (uint32_t)__cvta_generic_to_shared(staged + L.b1_off);
     const uint32_t b2s = (uint32_t)__cvta_generic_to_shared(staged + L.b2_off);
     const uint32_t a1s = (uint32_t)__cvta_generic_to_shared(hb + L.a1_off);
     const uint32_t a2s = (uint32_t)__cvta_generic_to_shared(hb + L.a2_off);
-    const uint32_t thalf = tbase + (uint32_t)(half * (L.tmem_cols / L.halves));
-    const uint32_t tlane = thalf + ((uint32_t)((warp & 3) * 32) << 16);   // this warp's TMEM lanes
+    const uint32_t tpipe = tbase + (uint32_t)(pipe * (L.tmem_cols / L.pipes));
+    const uint32_t tlane = tpipe + ((uint32_t)((warp & 3) * 32) << 16);   // this warp's TMEM lanes
     const int n_tiles = (a.n_cells + kTcRows - 1) / kTcRows;
-    [[maybe_unused]] const float lam_f = f64_to_f32_rn(a.lam), mu_f = f64_to_f32_rn(a.mu);
+    [[maybe_unused]] const float lam_f = narrow_pow2_ftz(a.lam, 0), mu_f = narrow_pow2_ftz(a.mu, 0);
     uint32_t phase = 0;
     bool timed_out = false;
 
     while (ok) {
-        if (t == 0) s_tile[half] = atomicAdd(a.sched, 1);
-        half_sync(half);
-        const int tile = s_tile[half];
+        if (t == 0) s_tile[pipe] = atomicAdd(a.sched, 1);
+        pipe_sync(pipe);
+        const int tile = s_tile[pipe];
         if (tile >= n_tiles) break;
-        const int cell = tile * kTcRows + t;
 
-        // ---- gather (Algorithm 2): vertices, geometry in FP64, nodes, scaled DoFs
-        double scale = 0.0;   // output factor; 0 marks a cell that is skipped
+        // ---- gather (Algorithm 2).  The tile's cell2node rows are contiguous:
+        // copy them with coalesced 16-byte loads into snodes (odd row pitch P, so
+        // the per-thread row reads below are free of bank conflicts).
+        const int nb = min(kTcRows, a.n_cells - tile * kTcRows);
+        {
+            const int total = nb * n;
+            const int32_t *src = a.c2n + (size_t)tile * kTcRows * n;
+            const int n4 = total >> 2;
+            for (int i4 = t; i4 < n4; i4 += kTcRows) {
+                const int4 v = __ldg(reinterpret_cast<const int4 *>(src) + i4);
+                const int vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int s = 0; s < 4; ++s) {
+                    const int e = 4 * i4 + s, c = e / n, j = e - c * n;
+                    snodes[c * P + j] = (unsigned)vv[s] < (unsigned)a.n_nodes ? vv[s] : -1;
+                }
+            }
+            for (int e = 4 * n4 + t; e < total; e += kTcRows) {
+                const int v = __ldg(src + e), c = e / n, j = e - c * n;
+                snodes[c * P + j] = (unsigned)v < (unsigned)a.n_nodes ? v : -1;
+            }
+        }
+        pipe_sync(pipe);
+
+        // geometry in FP64 (this thread's cell), then the DoFs' largest exponent
+        int K = 0;              // output factor 2^K (with mdet below)
+        float mdet = 0.f;       // |det J| / 2^(its exponent), in [1, 2)
+        int ku = 0;             // DoFs are rounded as u * 2^-ku
         [[maybe_unused]] float Jh[D][D];
-        double inv_su = 1.0;
-        bool good = cell < a.n_cells;
+        bool good = t < nb;
         if (good) {
+            const int cell = tile * kTcRows + t;
             double X[D + 1][D];
 #pragma unroll
             for (int m = 0; m <= D; ++m) {
@@ -352,16 +441,22 @@ __global__ void __launch_bounds__(2 * kTcRows, 1) k_action_tc(const ActionArgs a
             }
             double Jinv[D][D];
             const double det = cell_geometry<D>(X, Jinv);
-            double umax = 0.0;
+            int emax = 0;
             bool nodes_ok = true;
-            for (int j = 0; j < n; ++j) {
-                const int node = __ldg(a.c2n + (size_t)cell * n + j);
-                const bool in = (unsigned)node < (unsigned)a.n_nodes;
-                nodes_ok &= in;
-                snodes[j * kTcRows + t] = in ? node : -1;
-                if (in) {
+            for (int j0 = 0; j0 < n; j0 += 8) {
+                int nd[8];
 #pragma unroll
-                    for (int m = 0; m < NC; ++m) umax = fmax(umax, fabs(__ldg(a.u + (size_t)node * NC + m)));
+                for (int s = 0; s < 8; ++s) nd[s] = j0 + s < n ? snodes[t * P + j0 + s] : -2;
+                double v[8][NC];
+#pragma unroll
+                for (int s = 0; s < 8; ++s)
+#pragma unroll
+                    for (int m = 0; m < NC; ++m) v[s][m] = nd[s] >= 0 ? __ldg(a.u + (size_t)nd[s] * NC + m) : 0.0;
+#pragma unroll
+                for (int s = 0; s < 8; ++s) {
+                    nodes_ok &= nd[s] != -1;
+#pragma unroll
+                    for (int m = 0; m < NC; ++m) emax = max(emax, exp_field(v[s][m]));
                 }
             }
             if (!good || !nodes_ok) {
@@ -372,55 +467,52 @@ __global__ void __launch_bounds__(2 * kTcRows, 1) k_action_tc(const ActionArgs a
                 good = false;
             }
             if (good) {
-                double su;
-                pow2_above(umax, su, inv_su);
-                scale = fabs(det) * su;
+                // s_u = 2^ku > max |u| >= 2^(ku-1) (no scaling for all-zero or non-finite DoFs)
+                ku = (emax == 0 || emax == 0x7FF) ? 0 : emax - 1022;
+                const int ed = exp_field(det) - 1023;
+                const double m64 = __hiloint2double((__double2hiint(det) & 0x000FFFFF) | (1023 << 20),
+                                                    __double2loint(det));
+                mdet = narrow_pow2_ftz(m64, 0);
+                K = ed + ku;
                 if constexpr (OP == OP_ELASTICITY) {
-                    double jmax = 0.0;
+                    int ej = 0;
 #pragma unroll
                     for (int i = 0; i < D; ++i)
 #pragma unroll
-                        for (int k = 0; k < D; ++k) jmax = fmax(jmax, fabs(Jinv[i][k]));
-                    double sj, inv_sj;
-                    pow2_above(jmax, sj, inv_sj);
-                    scale *= sj * sj;
+                        for (int k = 0; k < D; ++k) ej = max(ej, exp_field(Jinv[i][k]));
+                    const int kj = ej - 1022;   // s_J = 2^kj > max |J^{-1}_ik|
+                    K += 2 * kj;
 #pragma unroll
                     for (int i = 0; i < D; ++i)
 #pragma unroll
-                        for (int k = 0; k < D; ++k) Jh[i][k] = f64_to_f32_rn(Jinv[i][k] * inv_sj);
+                        for (int k = 0; k < D; ++k) Jh[i][k] = narrow_pow2_ftz(Jinv[i][k], kj);
                 }
             }
         }
-        if (!good) {
-            for (int j = 0; j < n; ++j) snodes[j * kTcRows + t] = -1;
-        }
         // A operand of the evaluation GEMM: row t = this cell, K = local node j
+        for (int j0 = 0; j0 < L.K1p; j0 += 8) {
+            int nd[8];
 #pragma unroll
-        for (int m = 0; m < NC; ++m) {
-            T16 *A1 = reinterpret_cast<T16 *>(hb + L.a1_off) + (size_t)m * kTcRows * L.K1p;
-            for (int j8 = 0; j8 < L.K1p; j8 += 8) {
+            for (int s = 0; s < 8; ++s) nd[s] = (good && j0 + s < n) ? snodes[t * P + j0 + s] : -1;
+            double v[8][NC];
+#pragma unroll
+            for (int s = 0; s < 8; ++s)
+#pragma unroll
+                for (int m = 0; m < NC; ++m) v[s][m] = nd[s] >= 0 ? __ldg(a.u + (size_t)nd[s] * NC + m) : 0.0;
+#pragma unroll
+            for (int m = 0; m < NC; ++m) {
                 uint32_t w[4];
 #pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    uint32_t pair = 0;
-#pragma unroll
-                    for (int s = 0; s < 2; ++s) {
-                        const int j = j8 + 2 * h + s;
-                        double v = 0.0;
-                        if (good && j < n) {
-                            const int node = snodes[j * kTcRows + t];
-                            v = __ldg(a.u + (size_t)node * NC + m) * inv_su;
-                        }
-                        pair |= (uint32_t)to16_bits<T16>(v) << (16 * s);
-                    }
-                    w[h] = pair;
-                }
-                *reinterpret_cast<uint4 *>(A1 + tc_off(t, j8, L.K1p)) = make_uint4(w[0], w[1], w[2], w[3]);
+                for (int h = 0; h < 4; ++h)
+                    w[h] = (uint32_t)to16_bits<T16>(v[2 * h][m], ku) |
+                           ((uint32_t)to16_bits<T16>(v[2 * h + 1][m], ku) << 16);
+                T16 *A1 = reinterpret_cast<T16 *>(hb + L.a1_off) + (size_t)m * kTcRows * L.K1p;
+                *reinterpret_cast<uint4 *>(A1 + tc_off(t, j0, L.K1p)) = make_uint4(w[0], w[1], w[2], w[3]);
             }
         }
         fence_async_smem();
         tc_fence_before();
-        half_sync(half);
+        pipe_sync(pipe);
         tc_fence_after();
 
         const uint32_t id1 = tc_idesc(FMT, kTcRows, L.N1p), id2 = tc_idesc(FMT, kTcRows, L.N2p);
@@ -434,12 +526,12 @@ __global__ void __launch_bounds__(2 * kTcRows, 1) k_action_tc(const ActionArgs a
                             tc_smem_desc(a1s + (uint32_t)(m * kTcRows * L.K1p * 2) + (uint32_t)s * 256u, 128u, sbo);
                         const uint64_t db =
                             tc_smem_desc(b1s + (uint32_t)(ch * L.N1p * L.K1p * 2) + (uint32_t)s * 256u, 128u, sbo);
-                        tc_mma(thalf + (uint32_t)(m * L.N1p), da, db, id1, s > 0 ? 1u : 0u);
+                        tc_mma(tpipe + (uint32_t)(m * L.N1p), da, db, id1, s > 0 ? 1u : 0u);
                     }
-                tc_commit(barh);
+                tc_commit(barp);
             }
-            if (!half_all(half, tc_wait(barh, phase))) {
-                tc_wait(barh, phase);
+            if (!pipe_all(pipe, tc_wait(barp, phase))) {
+                tc_wait(barp, phase);
                 timed_out = true;
                 break;
             }
@@ -505,7 +597,7 @@ __global__ void __launch_bounds__(2 * kTcRows, 1) k_action_tc(const ActionArgs a
             }
             fence_async_smem();
             tc_fence_before();
-            half_sync(half);
+            pipe_sync(pipe);
             tc_fence_after();
 
             // ---- quadrature GEMM of chunk ch, accumulated over the chunks
@@ -517,15 +609,15 @@ __global__ void __launch_bounds__(2 * kTcRows, 1) k_action_tc(const ActionArgs a
                             tc_smem_desc(a2s + (uint32_t)(m * kTcRows * L.N1p * 2) + (uint32_t)s * 256u, 128u, sboa);
                         const uint64_t db =
                             tc_smem_desc(b2s + (uint32_t)((ch * L.N1p / 16 + s) * 256), 128u, sbob);
-                        tc_mma(thalf + (uint32_t)(L.acc1_cols + m * L.N2p), da, db, id2,
+                        tc_mma(tpipe + (uint32_t)(L.acc1_cols + m * L.N2p), da, db, id2,
                                (ch > 0 || s > 0) ? 1u : 0u);
                     }
             }
         }
         if (timed_out) break;
-        if (t == 0) tc_commit(barh);
-        if (!half_all(half, tc_wait(barh, phase))) {
-            tc_wait(barh, phase);
+        if (t == 0) tc_commit(barp);
+        if (!pipe_all(pipe, tc_wait(barp, phase))) {
+            tc_wait(barp, phase);
             timed_out = true;
             break;
         }
@@ -543,16 +635,19 @@ __global__ void __launch_bounds__(2 * kTcRows, 1) k_action_tc(const ActionArgs a
                 for (int i = 0; i < 16; ++i) {
                     const int j = blk * 16 + i;
                     if (j < n) {
-                        const int node = snodes[j * kTcRows + t];
+                        const int node = snodes[t * P + j];
 #pragma unroll
-                        for (int m = 0; m < NC; ++m)
-                            atomicAdd(a.y + (size_t)node * NC + m, f32_to_f64(__uint_as_float(r[m][i])) * scale);
+                        for (int m = 0; m < NC; ++m) {
+                            // y += acc |det J| 2^K: FP32 multiply by the mantissa of |det J|,
+                            // exact widening, exponent add
+                            atomicAdd(a.y + (size_t)node * NC + m, widen_pow2(__uint_as_float(r[m][i]) * mdet, K));
+                        }
                     }
                 }
             }
         }
         tc_fence_before();
-        half_sync(half);
+        pipe_sync(pipe);
     }
     if (timed_out && t == 0) set_status(a.status, FE_ERR_TIMEOUT);
     tc_fence_before();
