@@ -217,7 +217,7 @@ extern "C" const char *fe_status_string(int status)
 // FP32.
 template <typename T16>
 static void tc_fill_block(const TcLayout &L, int kind, const std::vector<double> &wts,
-                          const std::vector<double> &tab, std::vector<unsigned char> &blk)
+                          const std::vector<double> &tab, int wshift, std::vector<unsigned char> &blk)
 {
     blk.assign(L.staged_bytes, 0);
     uint16_t *B1 = reinterpret_cast<uint16_t *>(blk.data() + L.b1_off);
@@ -237,8 +237,9 @@ static void tc_fill_block(const TcLayout &L, int kind, const std::vector<double>
             }
         }
     for (int q = 0; q < L.nq; ++q) {
-        reinterpret_cast<double *>(blk.data() + L.wd_off)[q] = wts[q];
-        reinterpret_cast<float *>(blk.data() + L.wf_off)[q] = (float)wts[q];
+        const double w = std::ldexp(wts[q], wshift);   // exact
+        reinterpret_cast<double *>(blk.data() + L.wd_off)[q] = w;
+        reinterpret_cast<float *>(blk.data() + L.wf_off)[q] = (float)w;
     }
 }
 
@@ -257,12 +258,20 @@ static int plan_create_tc(const fe_form &f, const fe_mesh &m, const Variant &v, 
         f.tile_cells != 4 * kTcRows)
         return FE_ERR_UNSUPPORTED;
     TcLayout L;
-    if (!tc_choose(n, nq, ncomp, kd, 1, (size_t)optin - 256, f.tile_cells / kTcRows, &L)) return FE_ERR_UNSUPPORTED;
+    const int fields = f.kind == FE_FORM_NH_JACOBIAN ? 2 : 1;
+    if (!tc_choose(n, nq, ncomp, kd, fields, (size_t)optin - 256, f.tile_cells / kTcRows, &L)) return FE_ERR_UNSUPPORTED;
+    // weights scaled by 2^wshift into [1/2, 1) at their largest, so w_q E' stays
+    // in binary16's normal range for rules with very small weights
+    double wmax = 0.0;
+    for (double w : wts) wmax = std::max(wmax, w);
+    int we = 0;
+    std::frexp(wmax > 0.0 ? wmax : 1.0, &we);
+    const int wshift = -we;
     std::vector<unsigned char> blk;
     if (f.precision == FE_PREC_BF16)
-        tc_fill_block<__nv_bfloat16>(L, f.kind, wts, tab, blk);
+        tc_fill_block<__nv_bfloat16>(L, f.kind, wts, tab, wshift, blk);
     else
-        tc_fill_block<__half>(L, f.kind, wts, tab, blk);
+        tc_fill_block<__half>(L, f.kind, wts, tab, wshift, blk);
 
     fe_plan *p = new (std::nothrow) fe_plan();
     if (!p) return FE_ERR_NO_MEMORY;
@@ -279,6 +288,7 @@ static int plan_create_tc(const fe_form &f, const fe_mesh &m, const Variant &v, 
     p->device = dev;
     p->tc_qc = L.qc;
     p->tc_pipes = L.pipes;
+    p->tc_wshift = wshift;
     if (cudaMalloc(&p->d_tab, L.staged_bytes) != cudaSuccess ||
         cudaMalloc(&p->d_status, 8 * sizeof(int32_t)) != cudaSuccess) {
         cudaFree(p->d_tab);
@@ -299,6 +309,8 @@ static int plan_create_tc(const fe_form &f, const fe_mesh &m, const Variant &v, 
     p->flops_per_cell = algorithmic_flops(f.kind, m.dim, n, nq);
     const double dofs = (double)m.n_nodes * ncomp;
     p->bytes_min = 2.0 * dofs * 8.0 + (double)m.n_vertices * m.dim * 8.0 + (double)m.n_cells * (n + m.dim + 1) * 4.0;
+    if (f.kind == FE_FORM_NH_JACOBIAN)
+        p->bytes_min += dofs * 8.0 + (f.mu_cell ? 8.0 * m.n_cells : 0.0) + (f.lambda_cell ? 8.0 * m.n_cells : 0.0);
     *out = p;
     return FE_OK;
 }
@@ -317,7 +329,7 @@ extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan 
     if (f.kind < FE_FORM_MASS || f.kind > FE_FORM_NH_JACOBIAN) return FE_ERR_INVALID_ARG;
     if (f.precision < FE_PREC_FP64 || f.precision > FE_PREC_FP16) return FE_ERR_UNSUPPORTED;
     const bool tc = f.precision == FE_PREC_BF16 || f.precision == FE_PREC_FP16;
-    if (tc && f.kind != FE_FORM_MASS && f.kind != FE_FORM_ELASTICITY) return FE_ERR_UNSUPPORTED;
+    if (tc && f.kind == FE_FORM_NH_RESIDUAL) return FE_ERR_UNSUPPORTED;
     if (f.quad_degree < 0 || f.quad_degree > 40) return FE_ERR_INVALID_ARG;
     if (f.kind == FE_FORM_NH_JACOBIAN && !f.u_lin) return FE_ERR_INVALID_ARG;
     if (f.tile_cells < 0 || f.tile_cells > 4096) return FE_ERR_INVALID_ARG;
@@ -484,6 +496,7 @@ static ActionArgs make_args(const fe_plan *p, const double *u, double *y)
     a.tab_c = p->d_tab_c;
     a.tc_qc = p->tc_qc;
     a.tc_pipes = p->tc_pipes;
+    a.tc_wshift = p->tc_wshift;
     return a;
 }
 

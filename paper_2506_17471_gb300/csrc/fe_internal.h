@@ -40,6 +40,7 @@ struct ActionArgs {
     const void *tab_c;        // cooperative kernel, large tables: [nq][1+D][N] in global memory
     int32_t tc_qc;            // tensor-core kernel: quadrature points per chunk
     int32_t tc_pipes;         // tensor-core kernel: 128-cell pipelines per CTA (1, 2 or 4)
+    int32_t tc_wshift;        // tensor-core kernel: staged weights are w_q 2^tc_wshift
 };
 
 // Launch function of one compiled kernel variant.
@@ -103,6 +104,7 @@ struct fe_plan {
     int coop_cells;       // cells per CTA batch (cooperative kernel), else 0
     int tc_qc;            // tensor-core kernel: quadrature points per chunk, else 0
     int tc_pipes;         // tensor-core kernel: 128-cell pipelines per CTA, else 0
+    int tc_wshift;        // tensor-core kernel: staged weights are w_q 2^tc_wshift
     int device;
     double flops_per_cell;
     double bytes_min;

@@ -26,8 +26,13 @@
 // a CTA that uses tensor memory is resident alone on its SM, so the pipelines
 // are what hides one another's gather, MMA and scatter latency.
 //
-// Precision: the DoFs are scaled per cell by a power of two s_u > max |u|
-// and rounded to 16 bits; for elasticity J^{-1} is scaled by a power of two
+// Precision: for the gradient-only forms (elasticity, Neo-Hookean) each
+// cell's DoFs are first shifted by a per-cell constant c (the midrange of each
+// component, FP64): the basis gradients sum to zero, so grad u = grad (u - c)
+// exactly, and the 16-bit operands carry only the cell-local variation of the
+// field (a smooth field no longer loses its gradient to cancellation).  The
+// shifted DoFs (mass: the DoFs) are scaled per cell by a power of two
+// s_u > max |u - c| and rounded to 16 bits; J^{-1} is scaled by a power of two
 // s_J > max |J^{-1}_ik|.  The pointwise values then stay O(1) whatever the
 // mesh size and field magnitude (FP16 neither overflows nor goes subnormal).
 // The output factor |det J| s_u s_J^2 is applied as an FP32 multiply by the
@@ -42,6 +47,7 @@
 // K-adjacent core matrices, SBO = (Kp/8) * 128 B between row groups.
 #pragma once
 
+#include <climits>
 #include <cstring>
 
 #include <cuda_bf16.h>
@@ -169,8 +175,28 @@ __host__ __device__ __forceinline__ uint16_t to16_bits<__half>(double x, int k)
     return f64_to_small_rn<5, 10>(x, k);
 }
 
+// Monotone map of binary64 values to signed integers (integer order = value
+// order, -0 just below +0) and its inverse: min/max without FP64 compares.
+__device__ __forceinline__ long long ordered_key(double x)
+{
+    const long long b = __double_as_longlong(x);
+    return b >= 0 ? b : (b ^ 0x7FFFFFFFFFFFFFFFll);
+}
+__device__ __forceinline__ double from_ordered_key(long long k)
+{
+    return __longlong_as_double(k >= 0 ? k : (k ^ 0x7FFFFFFFFFFFFFFFll));
+}
+
 // Biased binary64 exponent field of x (0: zero or subnormal, 2047: inf or NaN).
 __device__ __forceinline__ int exp_field(double x) { return (int)(((unsigned)__double2hiint(x) >> 20) & 0x7FFu); }
+
+// Exponent k of a power of two 2^k > max(|x|, |y|) (0 if both are zero or
+// either is not finite), from the exponent fields alone.
+__device__ __forceinline__ int mat_shift(double x, double y)
+{
+    const int e = max(exp_field(x), exp_field(y));
+    return (e == 0 || e == 0x7FF) ? 0 : e - 1022;
+}
 
 // binary32 v times 2^k, widened to binary64 exactly, with integer operations
 // only (no FP64-pipe instruction on any path).  Zero and binary32 subnormals
@@ -270,6 +296,14 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&r)[16])
         : "r"(taddr));
 }
 
+// 8 consecutive accumulator columns of this warp's 32 lanes (no wait).
+__device__ __forceinline__ void tc_ld8(uint32_t taddr, uint32_t (&r)[8])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+}
+
 __device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -326,13 +360,115 @@ __device__ __forceinline__ bool tc_wait(uint32_t sbar, uint32_t parity)
     return false;
 }
 
+// Neo-Hookean Jacobian pointwise phase for one chunk, for this thread's cell
+// at the chunk's points.  The du and u_lin reference gradients come from the
+// evaluation accumulators (8 columns at a time).  The kinematic contractions
+// with J^{-1} (F = I + grad u_lin, u_lin's per-cell scaling undone exactly by a
+// power of two; H = grad du with J^{-1} 2^-kj) and the pull-back run in FP32,
+// far below the 16-bit rounding of their inputs and output; the law itself
+// (det F, F^{-T}, log det F and the tangent dP/dF applied to H, the same
+// algebra as the FP64 kernel) is FP64.  E' = w_q e is rounded to 16 bits.
+// Returns false if det F <= 0 at a live point.
+template <int D, typename T16>
+__device__ __forceinline__ bool tc_pointwise_nh_jacobian(const TcLayout &L, uint32_t tlane, unsigned char *hb,
+                                                         const double *wd, int t, int ch, int nq, bool good, int ku_lin,
+                                                         const float (&Jf)[D][D], const float (&Jh)[D][D],
+                                                         double mu, double lam)
+{
+    constexpr int NC = D, KDP = (D == 2) ? 2 : 4, PPB = 8 / KDP;
+    // 2^ku_lin as a binary32 value (the u_lin gradient is O(h) in reference
+    // coordinates, so the product stays in range)
+    const float s_lin = __uint_as_float((unsigned)min(max(ku_lin + 127, 1), 254) << 23);
+    bool ok = true;
+    for (int blk = 0; blk < L.N1p / 8; ++blk) {
+        uint32_t r[2 * NC][8];
+#pragma unroll
+        for (int fm = 0; fm < 2 * NC; ++fm) tc_ld8(tlane + (uint32_t)(fm * L.N1p + blk * 8), r[fm]);
+        tc_wait_ld();
+        float out[NC][8];
+#pragma unroll
+        for (int p = 0; p < PPB; ++p) {
+            const int ql = blk * PPB + p, q = ch * L.qc + ql;
+            const bool live = good && ql < L.qc && q < nq;
+            float gd[D][D], gl[D][D], Ff[D][D], Hf[D][D], Sf[D][D], ef[D][D];
+#pragma unroll
+            for (int m = 0; m < D; ++m)
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    gd[m][k] = __uint_as_float(r[m][p * KDP + k]);
+                    gl[m][k] = __uint_as_float(r[NC + m][p * KDP + k]) * s_lin;
+                }
+            map_grad<D, float>(gl, Jf, Ff);
+            map_grad<D, float>(gd, Jh, Hf);
+            double F[D][D], H[D][D], C[D][D], Fit[D][D], A[D][D];
+#pragma unroll
+            for (int i = 0; i < D; ++i)
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    F[i][k] = widen_pow2(Ff[i][k], 0) + (i == k ? 1.0 : 0.0);
+                    H[i][k] = widen_pow2(Hf[i][k], 0);
+                }
+            const double Jd = det_cof<D>(F, C);
+            ok &= !live || (Jd > 0.0);
+            const double Jd_safe = live && Jd > 0.0 ? Jd : 1.0;
+            const double rJ = 1.0 / Jd_safe;
+            const double lnJ = log(Jd_safe);
+            double tr = 0.0;   // F^{-T} : H
+#pragma unroll
+            for (int i = 0; i < D; ++i)
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    Fit[i][k] = C[i][k] * rJ;
+                    tr = fma(Fit[i][k], H[i][k], tr);
+                }
+#pragma unroll
+            for (int i = 0; i < D; ++i)
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    double s = Fit[i][0] * H[k][0];
+#pragma unroll
+                    for (int mm = 1; mm < D; ++mm) s = fma(Fit[i][mm], H[k][mm], s);
+                    A[i][k] = s;
+                }
+            const double w = live ? wd[q] : 0.0;
+            const double smu = w * mu, sm2 = w * fma(-lam, lnJ, mu), str = w * lam * tr;
+#pragma unroll
+            for (int i = 0; i < D; ++i)
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    double mk = A[i][0] * Fit[0][k];
+#pragma unroll
+                    for (int mm = 1; mm < D; ++mm) mk = fma(A[i][mm], Fit[mm][k], mk);
+                    Sf[i][k] = narrow_pow2_ftz(fma(smu, H[i][k], fma(sm2, mk, str * Fit[i][k])), 0);
+                }
+            pull_back<D, float>(Sf, Jh, ef);
+#pragma unroll
+            for (int m = 0; m < NC; ++m)
+#pragma unroll
+                for (int k = 0; k < KDP; ++k) out[m][p * KDP + k] = (k < D && live) ? ef[m][k] : 0.f;
+        }
+#pragma unroll
+        for (int m = 0; m < NC; ++m) {
+            T16 *A2 = reinterpret_cast<T16 *>(hb + L.a2_off) + (size_t)m * kTcRows * L.N1p;
+            uint32_t w[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) w[h] = pack2<T16>(out[m][2 * h], out[m][2 * h + 1]);
+            *reinterpret_cast<uint4 *>(A2 + tc_off(t, blk * 8, L.N1p)) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    }
+    return ok;
+}
+
 template <int OP, int D, typename T16>
 __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const ActionArgs a)
 {
     constexpr int NC = OpTraits<OP, D>::NC;
     constexpr int KD = (OP == OP_MASS) ? 1 : D;
     constexpr int KDP = (KD == 1) ? 1 : (KD == 2 ? 2 : 4);
-    constexpr int F = 1;
+    constexpr int F = (OP == OP_NH_JACOBIAN) ? 2 : 1;   // fields: du (or u), then u_lin
+    // gradient-only forms round u - c (c a per-cell constant): the basis
+    // gradients sum to zero, so the constant drops out of every gradient
+    constexpr bool kOffset = OP != OP_MASS;
     constexpr int PPB = 16 / KDP;   // quadrature points per 16 accumulator columns
     constexpr int FMT = std::is_same<T16, __nv_bfloat16>::value ? 1 : 0;
     extern __shared__ __align__(128) unsigned char tc_smem[];
@@ -388,9 +524,14 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
     const uint32_t tpipe = tbase + (uint32_t)(pipe * (L.tmem_cols / L.pipes));
     const uint32_t tlane = tpipe + ((uint32_t)((warp & 3) * 32) << 16);   // this warp's TMEM lanes
     const int n_tiles = (a.n_cells + kTcRows - 1) / kTcRows;
-    [[maybe_unused]] const float lam_f = narrow_pow2_ftz(a.lam, 0), mu_f = narrow_pow2_ftz(a.mu, 0);
+    // elasticity: lambda, mu scaled by a power of two 2^km > max(|lambda|, |mu|)
+    // (E' stays O(1) for any material); the factor returns in the output exponent
+    [[maybe_unused]] const int km_el = mat_shift(a.lam, a.mu);
+    [[maybe_unused]] const float lam_f = narrow_pow2_ftz(a.lam, km_el), mu_f = narrow_pow2_ftz(a.mu, km_el);
     uint32_t phase = 0;
     bool timed_out = false;
+    bool nh_ok = true;
+    const double *wd = reinterpret_cast<const double *>(staged + L.wd_off);
 
     while (ok) {
         if (t == 0) s_tile[pipe] = atomicAdd(a.sched, 1);
@@ -425,8 +566,11 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
         // geometry in FP64 (this thread's cell), then the DoFs' largest exponent
         int K = 0;              // output factor 2^K (with mdet below)
         float mdet = 0.f;       // |det J| / 2^(its exponent), in [1, 2)
-        int ku = 0;             // DoFs are rounded as u * 2^-ku
+        int ku[F] = {};         // field f is rounded as (u_f - off_f) * 2^-ku[f]
+        double off[F][NC] = {}; // per-cell offsets (gradient forms; zero for mass)
         [[maybe_unused]] float Jh[D][D];
+        [[maybe_unused]] float Jf[D][D];   // Neo-Hookean: J^{-1} in binary32
+        [[maybe_unused]] double mu_c = a.mu, lam_c = a.lam;
         bool good = t < nb;
         if (good) {
             const int cell = tile * kTcRows + t;
@@ -441,23 +585,51 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
             }
             double Jinv[D][D];
             const double det = cell_geometry<D>(X, Jinv);
-            int emax = 0;
+            if constexpr (OP == OP_NH_JACOBIAN) {
+                if (a.mu_cell) mu_c = __ldg(a.mu_cell + cell);
+                if (a.lam_cell) lam_c = __ldg(a.lam_cell + cell);
+            }
+            // mass: largest exponent of |u|; gradient forms: range [min, max] of each
+            // component (ordered integer keys, no FP64 compare)
+            int emax[F] = {};
+            [[maybe_unused]] long long kmin[F][NC], kmax[F][NC];
+#pragma unroll
+            for (int f = 0; f < F; ++f)
+#pragma unroll
+                for (int m = 0; m < NC; ++m) {
+                    kmin[f][m] = LLONG_MAX;
+                    kmax[f][m] = LLONG_MIN;
+                }
             bool nodes_ok = true;
             for (int j0 = 0; j0 < n; j0 += 8) {
                 int nd[8];
 #pragma unroll
                 for (int s = 0; s < 8; ++s) nd[s] = j0 + s < n ? snodes[t * P + j0 + s] : -2;
-                double v[8][NC];
 #pragma unroll
-                for (int s = 0; s < 8; ++s)
+                for (int f = 0; f < F; ++f) {
+                    const double *uf = f == 0 ? a.u : a.u_lin;
+                    double v[8][NC];
 #pragma unroll
-                    for (int m = 0; m < NC; ++m) v[s][m] = nd[s] >= 0 ? __ldg(a.u + (size_t)nd[s] * NC + m) : 0.0;
+                    for (int s = 0; s < 8; ++s)
 #pragma unroll
-                for (int s = 0; s < 8; ++s) {
-                    nodes_ok &= nd[s] != -1;
+                        for (int m = 0; m < NC; ++m) v[s][m] = nd[s] >= 0 ? __ldg(uf + (size_t)nd[s] * NC + m) : 0.0;
 #pragma unroll
-                    for (int m = 0; m < NC; ++m) emax = max(emax, exp_field(v[s][m]));
+                    for (int s = 0; s < 8; ++s)
+#pragma unroll
+                        for (int m = 0; m < NC; ++m) {
+                            if constexpr (kOffset) {
+                                if (nd[s] >= 0) {
+                                    const long long key = ordered_key(v[s][m]);
+                                    kmin[f][m] = min(kmin[f][m], key);
+                                    kmax[f][m] = max(kmax[f][m], key);
+                                }
+                            } else {
+                                emax[f] = max(emax[f], exp_field(v[s][m]));
+                            }
+                        }
                 }
+#pragma unroll
+                for (int s = 0; s < 8; ++s) nodes_ok &= nd[s] != -1;
             }
             if (!good || !nodes_ok) {
                 set_status(a.status, FE_ERR_INDEX);
@@ -467,14 +639,33 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
                 good = false;
             }
             if (good) {
-                // s_u = 2^ku > max |u| >= 2^(ku-1) (no scaling for all-zero or non-finite DoFs)
-                ku = (emax == 0 || emax == 0x7FF) ? 0 : emax - 1022;
+                if constexpr (kOffset) {
+                    // offset c = midrange of each component; the half-range bounds |u - c|
+#pragma unroll
+                    for (int f = 0; f < F; ++f)
+#pragma unroll
+                        for (int m = 0; m < NC; ++m) {
+                            const double lo = from_ordered_key(kmin[f][m]), hi = from_ordered_key(kmax[f][m]);
+                            off[f][m] = 0.5 * (lo + hi);
+                            emax[f] = max(emax[f], exp_field(hi - off[f][m]));
+                        }
+                }
+                // s_u = 2^ku > max |u - c| >= 2^(ku-1) (no scaling for zero or non-finite ranges)
+#pragma unroll
+                for (int f = 0; f < F; ++f) ku[f] = (emax[f] == 0 || emax[f] == 0x7FF) ? 0 : emax[f] - 1022;
                 const int ed = exp_field(det) - 1023;
                 const double m64 = __hiloint2double((__double2hiint(det) & 0x000FFFFF) | (1023 << 20),
                                                     __double2loint(det));
                 mdet = narrow_pow2_ftz(m64, 0);
-                K = ed + ku;
-                if constexpr (OP == OP_ELASTICITY) {
+                K = ed + ku[0] - a.tc_wshift;
+                if constexpr (OP == OP_ELASTICITY) K += km_el;
+                if constexpr (OP == OP_NH_JACOBIAN) {
+                    const int km = mat_shift(lam_c, mu_c);
+                    K += km;
+                    mu_c = ldexp(mu_c, -km);
+                    lam_c = ldexp(lam_c, -km);
+                }
+                if constexpr (OP == OP_ELASTICITY || OP == OP_NH_JACOBIAN) {
                     int ej = 0;
 #pragma unroll
                     for (int i = 0; i < D; ++i)
@@ -485,29 +676,38 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
 #pragma unroll
                     for (int i = 0; i < D; ++i)
 #pragma unroll
-                        for (int k = 0; k < D; ++k) Jh[i][k] = narrow_pow2_ftz(Jinv[i][k], kj);
+                        for (int k = 0; k < D; ++k) {
+                            Jh[i][k] = narrow_pow2_ftz(Jinv[i][k], kj);
+                            if constexpr (OP == OP_NH_JACOBIAN) Jf[i][k] = narrow_pow2_ftz(Jinv[i][k], 0);
+                        }
                 }
             }
         }
-        // A operand of the evaluation GEMM: row t = this cell, K = local node j
+        // A operands of the evaluation GEMM (one per field and component): row t =
+        // this cell, K = local node j
         for (int j0 = 0; j0 < L.K1p; j0 += 8) {
             int nd[8];
 #pragma unroll
             for (int s = 0; s < 8; ++s) nd[s] = (good && j0 + s < n) ? snodes[t * P + j0 + s] : -1;
-            double v[8][NC];
 #pragma unroll
-            for (int s = 0; s < 8; ++s)
+            for (int f = 0; f < F; ++f) {
+                const double *uf = f == 0 ? a.u : a.u_lin;
+                double v[8][NC];
 #pragma unroll
-                for (int m = 0; m < NC; ++m) v[s][m] = nd[s] >= 0 ? __ldg(a.u + (size_t)nd[s] * NC + m) : 0.0;
+                for (int s = 0; s < 8; ++s)
 #pragma unroll
-            for (int m = 0; m < NC; ++m) {
-                uint32_t w[4];
+                    for (int m = 0; m < NC; ++m) v[s][m] = nd[s] >= 0 ? __ldg(uf + (size_t)nd[s] * NC + m) : 0.0;
 #pragma unroll
-                for (int h = 0; h < 4; ++h)
-                    w[h] = (uint32_t)to16_bits<T16>(v[2 * h][m], ku) |
-                           ((uint32_t)to16_bits<T16>(v[2 * h + 1][m], ku) << 16);
-                T16 *A1 = reinterpret_cast<T16 *>(hb + L.a1_off) + (size_t)m * kTcRows * L.K1p;
-                *reinterpret_cast<uint4 *>(A1 + tc_off(t, j0, L.K1p)) = make_uint4(w[0], w[1], w[2], w[3]);
+                for (int m = 0; m < NC; ++m) {
+                    uint32_t w[4];
+#pragma unroll
+                    for (int h = 0; h < 4; ++h)
+                        w[h] = (uint32_t)to16_bits<T16>(nd[2 * h] >= 0 ? v[2 * h][m] - off[f][m] : 0.0, ku[f]) |
+                               ((uint32_t)to16_bits<T16>(nd[2 * h + 1] >= 0 ? v[2 * h + 1][m] - off[f][m] : 0.0, ku[f])
+                                << 16);
+                    T16 *A1 = reinterpret_cast<T16 *>(hb + L.a1_off) + (size_t)(f * NC + m) * kTcRows * L.K1p;
+                    *reinterpret_cast<uint4 *>(A1 + tc_off(t, j0, L.K1p)) = make_uint4(w[0], w[1], w[2], w[3]);
+                }
             }
         }
         fence_async_smem();
@@ -520,7 +720,7 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
             // ---- evaluation GEMM of chunk ch (its commit also covers the previous chunk's quadrature GEMM)
             if (t == 0) {
                 const uint32_t sbo = (uint32_t)L.K1p * 16u;
-                for (int m = 0; m < NC; ++m)
+                for (int m = 0; m < F * NC; ++m)
                     for (int s = 0; s < L.K1p / 16; ++s) {
                         const uint64_t da =
                             tc_smem_desc(a1s + (uint32_t)(m * kTcRows * L.K1p * 2) + (uint32_t)s * 256u, 128u, sbo);
@@ -539,6 +739,10 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
             tc_fence_after();
 
             // ---- pointwise: this thread's cell at the chunk's points, E' into the quadrature A operand
+            if constexpr (OP == OP_NH_JACOBIAN) {
+                nh_ok &= tc_pointwise_nh_jacobian<D, T16>(L, tlane, hb, wd, t, ch, a.nq, good, ku[1], Jf, Jh, mu_c,
+                                                          lam_c);
+            } else
             for (int blk = 0; blk < L.N1p / 16; ++blk) {
                 uint32_t r[NC][16];
 #pragma unroll
@@ -650,6 +854,7 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
         pipe_sync(pipe);
     }
     if (timed_out && t == 0) set_status(a.status, FE_ERR_TIMEOUT);
+    if (!nh_ok) set_status(a.status, FE_ERR_NONFINITE);
     tc_fence_before();
     __syncthreads();
     if (warp == 0)
