@@ -44,7 +44,7 @@ FP64_NOMINAL_GFLOPS = 1250.0
 # DRAM traffic of the benchmark kernel per launch (dram__bytes_read.sum + dram__bytes_write.sum)
 # from the ncu capture summarised in profiles/elasticity_p2_3d_n32_fp64_sym4.md; reported only
 # while the kernel source still hashes to the captured version.
-MEASURED_TRAFFIC = {"source_hash": "dea944c9e368eb2a", "bytes": 25096448}
+MEASURED_TRAFFIC = {"source_hash": "ee53ea7dbd5a758c", "bytes": 25097216}
 QUAD_SCHEME = "symmetric"   # the 4-point fully symmetric degree-2 rule
 WORKLOAD = ("linear elasticity, vector P2 tets, unit cube 32^3 x 6 Kuhn tets (196,608 cells, "
             "823,875 DoFs), jitter 0.15h, lambda=1.25 mu=1, quadrature degree 2 (4-point fully "
@@ -287,6 +287,17 @@ def time_secondary(fe, torch, flush, M_el, u_el, y64_el):
         "ir_s": t_ir, "ir_outer": stir.outer, "ir_inner_iters": stir.iterations,
         "ir_rel_residual_fp64": stir.rel_residual, "speedup": t_cg / t_ir,
         "note": "relative residuals are true FP64 residuals ||M(b - A_64 x)|| / ||M b||"}
+    for prec in ("bf16", "fp16"):
+        plo = fe.Plan(M_el, fe.ELASTICITY, 2, lam=1.25, mu=1.0, precision=prec, quad_scheme=QUAD_SCHEME)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, st = solvers.cg_ir(lambda a, c: p64.apply(a, c), lambda a, c: plo.apply(a, c), b, free,
+                              tol=1e-10, inner_rtol=1e-2)
+        torch.cuda.synchronize()
+        t_lo = time.perf_counter() - t0
+        out["cg_ir_elasticity_p2_3d_n32"][f"{prec}_inner"] = {
+            "ir_s": t_lo, "ir_outer": st.outer, "ir_inner_iters": st.iterations,
+            "ir_rel_residual_fp64": st.rel_residual, "speedup": t_cg / t_lo}
 
     # mass P3 2D at ~4M DoFs (hp sweep point), FP64 vs FP32 contractions
     m = structured_mesh(2, 667, 3, jitter=0.2, seed=20250620)
@@ -321,8 +332,20 @@ def time_secondary(fe, torch, flush, M_el, u_el, y64_el):
         "fp64_cg_s": t_cg, "fp64_cg_iters": st64.iterations, "fp64_cg_rel_residual": st64.rel_residual,
         "ir_s": t_ir, "ir_outer": stir.outer, "ir_inner_iters": stir.iterations,
         "ir_rel_residual_fp64": stir.rel_residual, "speedup": t_cg / t_ir}
+    for prec in ("bf16", "fp16"):
+        plo = fe.Plan(M, fe.MASS, 6, precision=prec)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, st = solvers.cg_ir(lambda a, c: p64.apply(a, c), lambda a, c: plo.apply(a, c), b, tol=1e-10,
+                              inner_rtol=1e-2)
+        torch.cuda.synchronize()
+        t_lo = time.perf_counter() - t0
+        out["cg_ir_mass_p3_2d_n667"][f"{prec}_inner"] = {
+            "ir_s": t_lo, "ir_outer": st.outer, "ir_inner_iters": st.iterations,
+            "ir_rel_residual_fp64": st.rel_residual, "speedup": t_cg / t_lo}
 
-    # hp sweep at ~4M and ~16M DoFs, FP64 and FP32 contractions
+    # hp sweep at ~4M and ~16M DoFs: FP64, FP32 contractions, and BF16 / FP16
+    # tensor-core contractions (kernel 2)
     hp = {}
     for name, dim, p, N, q in (("nh_jacobian_p6_2d", 2, 6, 236, 12), ("nh_jacobian_p6_2d", 2, 6, 471, 12),
                                ("elasticity_p4_3d", 3, 4, 27, 6), ("elasticity_p4_3d", 3, 4, 43, 6),
@@ -343,16 +366,17 @@ def time_secondary(fe, torch, flush, M_el, u_el, y64_el):
         u = torch.from_numpy(uniform_field(m.n_nodes * nc, 4)).cuda()
         row = {"dofs": m.n_nodes * nc, "cells": m.n_cells}
         ys = {}
-        for prec in ("fp64", "fp32"):
+        for prec in ("fp64", "fp32", "bf16", "fp16"):
             plan = fe.Plan(M, kind, q, precision=prec, **extra_kw)
             ys[prec] = torch.empty_like(u)
             t = timed(lambda: plan.apply(u, ys[prec]), reps=5)
             row[prec] = {"ms": t * 1e3, "dofs_per_s": m.n_nodes * nc / t,
                          "gflops": plan.flops() / t / 1e9, "kernel": plan.info.kernel,
                          "nq": plan.info.nq}
+            if prec != "fp64":
+                row[prec]["speedup_vs_fp64"] = row["fp64"]["ms"] / row[prec]["ms"]
+                row[prec]["rel_dev_vs_fp64"] = rel(ys[prec], ys["fp64"])
         row["fp64"]["frac_of_fp64_peak"] = row["fp64"]["gflops"] / FP64_NOMINAL_GFLOPS
-        row["fp32_speedup"] = row["fp64"]["ms"] / row["fp32"]["ms"]
-        row["fp32_rel_dev_vs_fp64"] = rel(ys["fp32"], ys["fp64"])
         hp[f"{name}_n{N}"] = row
     out["hp_sweep"] = hp
     return out
