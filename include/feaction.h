@@ -133,7 +133,9 @@ typedef struct fe_form {
     const double *u_lin;         /* [n_nodes*dim] for NH_JACOBIAN, else NULL       */
     int32_t tile_cells;          /* cells per CTA batch of the cells-per-CTA kernel
                                     (0: the largest that leaves room for two CTAs
-                                    per SM); ignored by the thread-per-cell kernel  */
+                                    per SM); tensor-core kernel: cells per CTA
+                                    (128, 256, 512; 0 automatic); ignored by the
+                                    thread-per-cell kernel                         */
     int32_t quad_scheme;         /* enum fe_quad_scheme (0: conical product)        */
 } fe_form;
 
@@ -178,6 +180,22 @@ typedef struct fe_plan fe_plan;
 /* Validates the form/mesh pair, tabulates on the host, uploads the tables to
  * the current device and selects the kernel.  Synchronous.  The plan stores
  * copies of *form and *mesh (pointers inside them are borrowed).
+ *
+ * Accuracy of y = A(u) against the exact-arithmetic action (norm-wise,
+ * ||y - y_exact||_inf / ||y_exact||_inf):
+ *   FE_PREC_FP64  rounding level (parity with an FP64 reference to 1e-12,
+ *                 except where the action itself is ill-conditioned in FP64);
+ *   FE_PREC_FP32  <= 5e-5 (each contraction's forward error is at most
+ *                 gamma_256 of its absolute terms; measured 1e-7 - 6e-7);
+ *   FE_PREC_BF16, FE_PREC_FP16  <= 8 u16 with u16 = 2^-8 (BF16) or 2^-11
+ *                 (FP16), i.e. 3.1e-2 / 3.9e-3 (measured 0.6 - 4.3 u16).
+ *
+ * Tensor-core plans (FE_PREC_BF16 / FE_PREC_FP16): kinds MASS, ELASTICITY and
+ * NH_JACOBIAN (NH_RESIDUAL: FE_ERR_UNSUPPORTED); cell2node must be 16-byte
+ * aligned (FE_ERR_INVALID_ARG otherwise); tile_cells selects the 128-cell
+ * pipelines per CTA (0 automatic, 128, 256 or 512; other values
+ * FE_ERR_UNSUPPORTED); FE_ERR_UNSUPPORTED also if the degree has more than 256
+ * local nodes or the tables and operands do not fit one SM.
  * Errors: FE_ERR_INVALID_ARG, FE_ERR_UNSUPPORTED, FE_ERR_NO_MEMORY, FE_ERR_CUDA. */
 int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan **out);
 
