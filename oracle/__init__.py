@@ -63,8 +63,14 @@ def _load():
             lib.orc_nh_jacobian.argtypes = common + [P, P, P, P, P, L, L]
             lib.orc_nh_energy.argtypes = common + [P, P, P, P, L, L]
             lib.orc_nh_adjoint.argtypes = common + [P, P, P, P, P, P, P, L, L]
+            lib.orc_laplace.argtypes = common + [P, P, L, L]
+            lib.orc_helmholtz.argtypes = common + [P, P, L, L]
+            lib.orc_svk_residual.argtypes = common + [P, P, P, P, L, L]
+            lib.orc_svk_jacobian.argtypes = common + [P, P, P, P, P, L, L]
+            lib.orc_svk_energy.argtypes = common + [P, P, P, P, L, L]
             for f in (lib.orc_mass, lib.orc_elasticity, lib.orc_nh_residual,
-                      lib.orc_nh_jacobian, lib.orc_nh_energy, lib.orc_nh_adjoint):
+                      lib.orc_nh_jacobian, lib.orc_nh_energy, lib.orc_nh_adjoint, lib.orc_laplace,
+                      lib.orc_helmholtz, lib.orc_svk_residual, lib.orc_svk_jacobian, lib.orc_svk_energy):
                 f.restype = I
             _lib = lib
     return _lib
@@ -209,6 +215,48 @@ class Oracle:
             lambda o: [_ptr(mu), _ptr(lam), _ptr(u), _ptr(w), _ptr(o[0]), _ptr(o[1]), _ptr(o[2])],
             [(self.n_nodes * self.dim,), (self.n_cells,), (self.n_cells,)], threads, cells)
         return jtw, dmu, dlam
+
+    def laplace(self, u, threads=1, cells=None):
+        lib = _load()
+        u = self._vec(u, 1)
+        (y,) = self._run(lib.orc_laplace, lambda o: [_ptr(u), _ptr(o[0])],
+                         [(self.n_nodes,)], threads, cells)
+        return y
+
+    def helmholtz(self, u, threads=1, cells=None):
+        lib = _load()
+        u = self._vec(u, 1)
+        (y,) = self._run(lib.orc_helmholtz, lambda o: [_ptr(u), _ptr(o[0])],
+                         [(self.n_nodes,)], threads, cells)
+        return y
+
+    def svk_residual(self, u, mu_cell, lam_cell, threads=1, cells=None):
+        lib = _load()
+        u = self._vec(u, self.dim)
+        mu, lam = self._cellvec(mu_cell), self._cellvec(lam_cell)
+        (y,) = self._run(lib.orc_svk_residual,
+                         lambda o: [_ptr(mu), _ptr(lam), _ptr(u), _ptr(o[0])],
+                         [(self.n_nodes * self.dim,)], threads, cells)
+        return y
+
+    def svk_jacobian(self, u, du, mu_cell, lam_cell, threads=1, cells=None):
+        lib = _load()
+        u, du = self._vec(u, self.dim), self._vec(du, self.dim)
+        mu, lam = self._cellvec(mu_cell), self._cellvec(lam_cell)
+        (y,) = self._run(lib.orc_svk_jacobian,
+                         lambda o: [_ptr(mu), _ptr(lam), _ptr(u), _ptr(du), _ptr(o[0])],
+                         [(self.n_nodes * self.dim,)], threads, cells)
+        return y
+
+    def svk_energy(self, u, mu_cell, lam_cell, threads=1):
+        """Per-cell St. Venant-Kirchhoff energies; their sum is Pi(u)."""
+        lib = _load()
+        u = self._vec(u, self.dim)
+        mu, lam = self._cellvec(mu_cell), self._cellvec(lam_cell)
+        (e,) = self._run(lib.orc_svk_energy,
+                         lambda o: [_ptr(mu), _ptr(lam), _ptr(u), _ptr(o[0])],
+                         [(self.n_cells,)], threads)
+        return e
 
     # ------------------------------------------------------------------ dense
     def dense(self, apply, n):

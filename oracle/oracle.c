@@ -13,8 +13,9 @@
  * reference derivatives from the tabulation; apply the pointwise form and the
  * geometry mapping; accumulate the quadrature contraction against the test
  * tabulation; scatter-add into the global output.  The forms are those of the
- * paper's Appendix A (Mass, Elasticity), and a compressible Neo-Hookean law in
- * place of the appendix's St. Venant-Kirchhoff law:
+ * paper's Appendix A (Mass, Laplacian, Helmholtz, Elasticity, and the
+ * St. Venant-Kirchhoff hyperelastic law with its linearisation), and a
+ * compressible Neo-Hookean law beside it:
  *     Psi(F) = mu/2 (tr F^T F - d) - mu ln J + lambda/2 (ln J)^2,  J = det F,
  *     P      = dPsi/dF = mu (F - F^{-T}) + lambda ln J F^{-T}.
  *
@@ -455,4 +456,216 @@ int orc_nh_adjoint(int dim, int nloc, int nq, const double *wts, const double *t
     }
     free(K);
     return rc;
+}
+
+/* ---------------------------------------------------------------- Laplacian
+ * a(u, v) = int grad u . grad v dx (Appendix A, Laplacian), scalar u, v.
+ * Per point: the physical gradient g = J^{-T} (reference gradient); the test
+ * side needs grad v . g = sum_k dv/dxhat_k (sum_i g_i Jinv[k][i]). */
+static void scalar_grad(int dim, int nloc, int nq, const double *tab, int q, const double *l,
+                        double Jinv[ORC_MAXD][ORC_MAXD], double g[ORC_MAXD])
+{
+    double gh[ORC_MAXD][ORC_MAXD], G[ORC_MAXD][ORC_MAXD];
+    eval_ref_grad(dim, 1, nloc, nq, tab, q, l, gh);
+    to_physical(dim, 1, gh, Jinv, G);
+    for (int i = 0; i < dim; ++i) g[i] = G[0][i];
+}
+
+static void quad_scalar_grad(int dim, int nloc, int nq, const double *tab, int q, double scale,
+                             const double g[ORC_MAXD], double Jinv[ORC_MAXD][ORC_MAXD], double *out)
+{
+    for (int k = 0; k < dim; ++k) {
+        double e = 0.0;
+        for (int i = 0; i < dim; ++i) e += g[i] * Jinv[k][i];
+        const double *psi = T(tab, nq, nloc, k + 1, q);
+        for (int j = 0; j < nloc; ++j) out[j] += psi[j] * e * scale;
+    }
+}
+
+int orc_laplace(int dim, int nloc, int nq, const double *wts, const double *tab,
+                const int32_t *c2v, const double *coords, const int32_t *c2n,
+                const double *u, double *y, long c0, long c1)
+{
+    if (!check_args(dim, nloc)) return 3;
+    double X[ORC_MAXD + 1][ORC_MAXD], J[ORC_MAXD][ORC_MAXD], Jinv[ORC_MAXD][ORC_MAXD], detJ;
+    double l[ORC_MAXLOC], out[ORC_MAXLOC], g[ORC_MAXD];
+    for (long c = c0; c < c1; ++c) {
+        gather_coords(dim, c, c2v, coords, X);
+        gather_dofs(1, nloc, c, c2n, u, l);
+        if (!geometry(dim, X, J, &detJ, Jinv)) return 1;
+        for (int j = 0; j < nloc; ++j) out[j] = 0.0;
+        for (int q = 0; q < nq; ++q) {
+            scalar_grad(dim, nloc, nq, tab, q, l, Jinv, g);
+            quad_scalar_grad(dim, nloc, nq, tab, q, wts[q] * fabs(detJ), g, Jinv, out);
+        }
+        scatter_dofs(1, nloc, c, c2n, out, y);
+    }
+    return 0;
+}
+
+/* ---------------------------------------------------------------- Helmholtz
+ * a(u, v) = int (grad u . grad v + u v) dx (Appendix A, Helmholtz). */
+int orc_helmholtz(int dim, int nloc, int nq, const double *wts, const double *tab,
+                  const int32_t *c2v, const double *coords, const int32_t *c2n,
+                  const double *u, double *y, long c0, long c1)
+{
+    if (!check_args(dim, nloc)) return 3;
+    double X[ORC_MAXD + 1][ORC_MAXD], J[ORC_MAXD][ORC_MAXD], Jinv[ORC_MAXD][ORC_MAXD], detJ;
+    double l[ORC_MAXLOC], out[ORC_MAXLOC], g[ORC_MAXD];
+    for (long c = c0; c < c1; ++c) {
+        gather_coords(dim, c, c2v, coords, X);
+        gather_dofs(1, nloc, c, c2n, u, l);
+        if (!geometry(dim, X, J, &detJ, Jinv)) return 1;
+        for (int j = 0; j < nloc; ++j) out[j] = 0.0;
+        for (int q = 0; q < nq; ++q) {
+            const double scale = wts[q] * fabs(detJ);
+            const double *phi = T(tab, nq, nloc, 0, q);
+            double uq = 0.0;
+            for (int j = 0; j < nloc; ++j) uq += phi[j] * l[j];
+            for (int j = 0; j < nloc; ++j) out[j] += phi[j] * uq * scale;
+            scalar_grad(dim, nloc, nq, tab, q, l, Jinv, g);
+            quad_scalar_grad(dim, nloc, nq, tab, q, scale, g, Jinv, out);
+        }
+        scatter_dofs(1, nloc, c, c2n, out, y);
+    }
+    return 0;
+}
+
+/* St. Venant-Kirchhoff law (Appendix A, Hyperelasticity): from the physical
+ * displacement gradient G, F = I + G, C = F^T F, E = (C - I)/2,
+ * S = dPsi/dE = lambda tr(E) I + 2 mu E for Psi = lambda/2 (tr E)^2 + mu tr(E^2),
+ * P = F S.  Returns Psi. */
+static double svk_stress(int dim, double G[ORC_MAXD][ORC_MAXD], double mu, double lam,
+                         double F[ORC_MAXD][ORC_MAXD], double S[ORC_MAXD][ORC_MAXD],
+                         double P[ORC_MAXD][ORC_MAXD])
+{
+    double E[ORC_MAXD][ORC_MAXD];
+    for (int a = 0; a < dim; ++a)
+        for (int b = 0; b < dim; ++b) F[a][b] = (a == b ? 1.0 : 0.0) + G[a][b];
+    for (int a = 0; a < dim; ++a)
+        for (int b = 0; b < dim; ++b) {
+            double cab = 0.0;   /* C[a][b] = sum_m F[m][a] F[m][b] */
+            for (int m = 0; m < dim; ++m) cab += F[m][a] * F[m][b];
+            E[a][b] = 0.5 * (cab - (a == b ? 1.0 : 0.0));
+        }
+    double trE = 0.0, trE2 = 0.0;
+    for (int a = 0; a < dim; ++a) trE += E[a][a];
+    for (int a = 0; a < dim; ++a)
+        for (int b = 0; b < dim; ++b) trE2 += E[a][b] * E[b][a];
+    for (int a = 0; a < dim; ++a)
+        for (int b = 0; b < dim; ++b) S[a][b] = 2.0 * mu * E[a][b] + (a == b ? lam * trE : 0.0);
+    for (int a = 0; a < dim; ++a)
+        for (int b = 0; b < dim; ++b) {
+            double p = 0.0;
+            for (int m = 0; m < dim; ++m) p += F[a][m] * S[m][b];
+            P[a][b] = p;
+        }
+    return 0.5 * lam * trE * trE + mu * trE2;
+}
+
+/* ---------------------------------------------------------------- SVK residual
+ * r(u; v) = int P(F) : grad v dx, P = F S (body force zero), per-cell mu, lambda. */
+int orc_svk_residual(int dim, int nloc, int nq, const double *wts, const double *tab,
+                     const int32_t *c2v, const double *coords, const int32_t *c2n,
+                     const double *mu_cell, const double *lam_cell,
+                     const double *u, double *y, long c0, long c1)
+{
+    if (!check_args(dim, nloc)) return 3;
+    double X[ORC_MAXD + 1][ORC_MAXD], J[ORC_MAXD][ORC_MAXD], Jinv[ORC_MAXD][ORC_MAXD], detJ;
+    double l[ORC_MAXLOC * ORC_MAXD], out[ORC_MAXLOC * ORC_MAXD];
+    double gh[ORC_MAXD][ORC_MAXD], G[ORC_MAXD][ORC_MAXD], F[ORC_MAXD][ORC_MAXD], S[ORC_MAXD][ORC_MAXD],
+        P[ORC_MAXD][ORC_MAXD];
+    for (long c = c0; c < c1; ++c) {
+        gather_coords(dim, c, c2v, coords, X);
+        gather_dofs(dim, nloc, c, c2n, u, l);
+        const double mu = mu_cell[c], lam = lam_cell[c];
+        if (!geometry(dim, X, J, &detJ, Jinv)) return 1;
+        for (int j = 0; j < nloc * dim; ++j) out[j] = 0.0;
+        for (int q = 0; q < nq; ++q) {
+            eval_ref_grad(dim, dim, nloc, nq, tab, q, l, gh);
+            to_physical(dim, dim, gh, Jinv, G);
+            svk_stress(dim, G, mu, lam, F, S, P);
+            quad_stress(dim, nloc, nq, tab, q, wts[q] * fabs(detJ), P, Jinv, out);
+        }
+        scatter_dofs(dim, nloc, c, c2n, out, y);
+    }
+    return 0;
+}
+
+/* ---------------------------------------------------------------- SVK Jacobian action
+ * a(du; v) = d/de r(u + e du; v) at e = 0:  dP = H S + F dS, H = grad du,
+ * dE = (H^T F + F^T H)/2, dS = lambda tr(dE) I + 2 mu dE. */
+int orc_svk_jacobian(int dim, int nloc, int nq, const double *wts, const double *tab,
+                     const int32_t *c2v, const double *coords, const int32_t *c2n,
+                     const double *mu_cell, const double *lam_cell,
+                     const double *u, const double *du, double *y, long c0, long c1)
+{
+    if (!check_args(dim, nloc)) return 3;
+    double X[ORC_MAXD + 1][ORC_MAXD], J[ORC_MAXD][ORC_MAXD], Jinv[ORC_MAXD][ORC_MAXD], detJ;
+    double l[ORC_MAXLOC * ORC_MAXD], dl[ORC_MAXLOC * ORC_MAXD], out[ORC_MAXLOC * ORC_MAXD];
+    double gh[ORC_MAXD][ORC_MAXD], G[ORC_MAXD][ORC_MAXD], F[ORC_MAXD][ORC_MAXD], S[ORC_MAXD][ORC_MAXD],
+        P[ORC_MAXD][ORC_MAXD], H[ORC_MAXD][ORC_MAXD], dE[ORC_MAXD][ORC_MAXD], dS[ORC_MAXD][ORC_MAXD],
+        dP[ORC_MAXD][ORC_MAXD];
+    for (long c = c0; c < c1; ++c) {
+        gather_coords(dim, c, c2v, coords, X);
+        gather_dofs(dim, nloc, c, c2n, u, l);
+        gather_dofs(dim, nloc, c, c2n, du, dl);
+        const double mu = mu_cell[c], lam = lam_cell[c];
+        if (!geometry(dim, X, J, &detJ, Jinv)) return 1;
+        for (int j = 0; j < nloc * dim; ++j) out[j] = 0.0;
+        for (int q = 0; q < nq; ++q) {
+            eval_ref_grad(dim, dim, nloc, nq, tab, q, l, gh);
+            to_physical(dim, dim, gh, Jinv, G);
+            eval_ref_grad(dim, dim, nloc, nq, tab, q, dl, gh);
+            to_physical(dim, dim, gh, Jinv, H);
+            svk_stress(dim, G, mu, lam, F, S, P);
+            double trdE = 0.0;
+            for (int a = 0; a < dim; ++a)
+                for (int b = 0; b < dim; ++b) {
+                    double s = 0.0;   /* (H^T F + F^T H)[a][b] / 2 */
+                    for (int m = 0; m < dim; ++m) s += H[m][a] * F[m][b] + F[m][a] * H[m][b];
+                    dE[a][b] = 0.5 * s;
+                }
+            for (int a = 0; a < dim; ++a) trdE += dE[a][a];
+            for (int a = 0; a < dim; ++a)
+                for (int b = 0; b < dim; ++b) dS[a][b] = 2.0 * mu * dE[a][b] + (a == b ? lam * trdE : 0.0);
+            for (int a = 0; a < dim; ++a)
+                for (int b = 0; b < dim; ++b) {
+                    double s = 0.0;
+                    for (int m = 0; m < dim; ++m) s += H[a][m] * S[m][b] + F[a][m] * dS[m][b];
+                    dP[a][b] = s;
+                }
+            quad_stress(dim, nloc, nq, tab, q, wts[q] * fabs(detJ), dP, Jinv, out);
+        }
+        scatter_dofs(dim, nloc, c, c2n, out, y);
+    }
+    return 0;
+}
+
+/* ---------------------------------------------------------------- SVK energy
+ * Pi(u) = sum_c sum_q w_q |det J| Psi(E), per cell into energy[c]. */
+int orc_svk_energy(int dim, int nloc, int nq, const double *wts, const double *tab,
+                   const int32_t *c2v, const double *coords, const int32_t *c2n,
+                   const double *mu_cell, const double *lam_cell,
+                   const double *u, double *energy, long c0, long c1)
+{
+    if (!check_args(dim, nloc)) return 3;
+    double X[ORC_MAXD + 1][ORC_MAXD], J[ORC_MAXD][ORC_MAXD], Jinv[ORC_MAXD][ORC_MAXD], detJ;
+    double l[ORC_MAXLOC * ORC_MAXD];
+    double gh[ORC_MAXD][ORC_MAXD], G[ORC_MAXD][ORC_MAXD], F[ORC_MAXD][ORC_MAXD], S[ORC_MAXD][ORC_MAXD],
+        P[ORC_MAXD][ORC_MAXD];
+    for (long c = c0; c < c1; ++c) {
+        gather_coords(dim, c, c2v, coords, X);
+        gather_dofs(dim, nloc, c, c2n, u, l);
+        const double mu = mu_cell[c], lam = lam_cell[c];
+        if (!geometry(dim, X, J, &detJ, Jinv)) return 1;
+        double e = 0.0;
+        for (int q = 0; q < nq; ++q) {
+            eval_ref_grad(dim, dim, nloc, nq, tab, q, l, gh);
+            to_physical(dim, dim, gh, Jinv, G);
+            e += wts[q] * fabs(detJ) * svk_stress(dim, G, mu, lam, F, S, P);
+        }
+        energy[c] += e;
+    }
+    return 0;
 }

@@ -170,6 +170,17 @@ def element_elasticity(X, degree, lam, mu):
     return K
 
 
+def element_laplace(X, degree):
+    """K[i][j] = int grad phi_i . grad phi_j."""
+    cell = ExactCell(X)
+    d = cell.d
+    B = lagrange_basis(d, degree)
+    G = [cell.grad(b) for b in B]
+    n = len(B)
+    return [[sum(cell.integrate(_mul(G[i][k], G[j][k])) for k in range(d)) for j in range(n)]
+            for i in range(n)]
+
+
 def assemble(cells_X, cell2node, n_nodes, degree, kind, ncomp=1, **kw):
     """Exact global matrix from element matrices (Fractions)."""
     N = n_nodes * ncomp
@@ -177,6 +188,11 @@ def assemble(cells_X, cell2node, n_nodes, degree, kind, ncomp=1, **kw):
     for X, nodes in zip(cells_X, cell2node):
         if kind == "mass":
             Ke = element_mass(X, degree)
+        elif kind == "laplace":
+            Ke = element_laplace(X, degree)
+        elif kind == "helmholtz":
+            Kl, Km = element_laplace(X, degree), element_mass(X, degree)
+            Ke = [[a + b for a, b in zip(ra, rb)] for ra, rb in zip(Kl, Km)]
         else:
             Ke = element_elasticity(X, degree, kw["lam"], kw["mu"])
         dofs = [int(nd) * ncomp + c for nd in nodes for c in range(ncomp)]
