@@ -70,8 +70,16 @@ enum fe_form_kind {
                                                                          (App. A, Elasticity) */
     FE_FORM_NH_RESIDUAL = 2, /* r(u;v) = int P(F):grad v, F = I + grad u,
                                 P = mu (F - F^{-T}) + lambda ln(det F) F^{-T}; nonlinear in u */
-    FE_FORM_NH_JACOBIAN = 3  /* a(du,v) = d/de r(u_lin + e du; v) at e = 0: the linearisation
+    FE_FORM_NH_JACOBIAN = 3, /* a(du,v) = d/de r(u_lin + e du; v) at e = 0: the linearisation
                                 of the residual (App. A, Hyperelasticity's bilinear form)    */
+    FE_FORM_LAPLACE = 4,     /* a(u,v) = int grad u . grad v, scalar     (App. A, Laplacian)  */
+    FE_FORM_HELMHOLTZ = 5,   /* a(u,v) = int (grad u . grad v + u v), scalar (App. A, Helmholtz) */
+    FE_FORM_SVK_RESIDUAL = 6,/* r(u;v) = int P(F):grad v, St. Venant-Kirchhoff: F = I + grad u,
+                                E = (F^T F - I)/2, S = lambda tr(E) I + 2 mu E, P = F S
+                                                                 (App. A, Hyperelasticity)   */
+    FE_FORM_SVK_JACOBIAN = 7 /* a(du,v) = d/de r(u_lin + e du; v) at e = 0 for the
+                                St. Venant-Kirchhoff residual: dP = H S + F dS, H = grad du,
+                                dE = (H^T F + F^T H)/2, dS = lambda tr(dE) I + 2 mu dE       */
 };
 
 enum fe_precision {
@@ -118,10 +126,12 @@ typedef struct fe_mesh {
 } fe_mesh;
 
 /* Form descriptor.  Coefficients: ELASTICITY uses the constants (lambda, mu);
- * the Neo-Hookean kinds use per-cell P0 arrays mu_cell / lambda_cell (device,
- * [n_cells]) when non-NULL, else the constants.  NH_JACOBIAN linearises at
- * u_lin (device, [n_nodes*dim]); the plan keeps the pointer, so the caller may
- * update its contents between calls. */
+ * the hyperelastic kinds (Neo-Hookean and St. Venant-Kirchhoff) use per-cell
+ * P0 arrays mu_cell / lambda_cell (device, [n_cells]) when non-NULL, else the
+ * constants.  NH_JACOBIAN and SVK_JACOBIAN linearise at u_lin (device,
+ * [n_nodes*dim]); the plan keeps the pointer, so the caller may update its
+ * contents between calls.  MASS, LAPLACE and HELMHOLTZ act on scalar fields
+ * (ncomp = 1), the others on vector fields (ncomp = dim). */
 typedef struct fe_form {
     int32_t kind;                /* enum fe_form_kind                              */
     int32_t quad_degree;         /* quadrature exactness degree q >= 0             */
@@ -130,7 +140,8 @@ typedef struct fe_form {
     double lambda, mu;           /* constant Lame parameters                       */
     const double *lambda_cell;   /* [n_cells] or NULL                              */
     const double *mu_cell;       /* [n_cells] or NULL                              */
-    const double *u_lin;         /* [n_nodes*dim] for NH_JACOBIAN, else NULL       */
+    const double *u_lin;         /* [n_nodes*dim] for NH_JACOBIAN / SVK_JACOBIAN,
+                                    else NULL                                      */
     int32_t tile_cells;          /* cells per CTA batch of the cells-per-CTA kernel
                                     (0: the largest that leaves room for two CTAs
                                     per SM); tensor-core kernel: cells per CTA
@@ -204,8 +215,9 @@ int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan **out);
 int fe_plan_destroy(fe_plan *plan);
 
 /* y = A(u) (or y += A(u) with FE_FLAG_ACCUMULATE), enqueued on stream.
- * u, y: device arrays of n_nodes * ncomp doubles (ncomp = 1 for MASS, dim
- * otherwise); u and y must not alias.  For NH_JACOBIAN u is the direction du.
+ * u, y: device arrays of n_nodes * ncomp doubles (ncomp = 1 for MASS, LAPLACE
+ * and HELMHOLTZ, dim otherwise); u and y must not alias.  For the Jacobian kinds
+ * u is the direction du.
  * Errors: FE_ERR_INVALID_ARG before launch, FE_ERR_CUDA on a failed launch. */
 int fe_action(fe_plan *plan, const double *u, double *y, void *stream);
 

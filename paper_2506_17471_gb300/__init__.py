@@ -1,17 +1,20 @@
 """GB300-native matrix-free finite element actions (arXiv 2506.17471's hot path).
 
-y = A(u) for the mass, linear elasticity and compressible Neo-Hookean forms on
-affine simplex meshes, computed by hand-written sm_103a CUDA kernels behind the
+y = A(u) for the mass, Laplacian, Helmholtz, linear elasticity, compressible
+Neo-Hookean and St. Venant-Kirchhoff forms on affine simplex meshes, computed by
+hand-written sm_103a CUDA kernels behind the
 C-ABI declared in include/feaction.h.  Importing the package loads the in-tree
 shared library and raises ImportError if it has not been built.
 """
 
 from ._native import FeError, LIB_PATH, EXPORTS
-from .api import (MASS, ELASTICITY, NH_RESIDUAL, NH_JACOBIAN, FORM_NAMES, PRECISIONS, QUAD_SCHEMES,
+from .api import (MASS, ELASTICITY, NH_RESIDUAL, NH_JACOBIAN, LAPLACE, HELMHOLTZ, SVK_RESIDUAL,
+                  SVK_JACOBIAN, FORM_NAMES, PRECISIONS, QUAD_SCHEMES,
                   Mesh, Plan,
                   PlanInfo,
                   NeoHookeanResidual, Batch, tabulate, measure_fp64_peak)
 
 __all__ = ["FeError", "LIB_PATH", "EXPORTS", "MASS", "ELASTICITY", "NH_RESIDUAL", "NH_JACOBIAN",
+           "LAPLACE", "HELMHOLTZ", "SVK_RESIDUAL", "SVK_JACOBIAN",
            "FORM_NAMES", "PRECISIONS", "QUAD_SCHEMES", "Mesh", "Plan", "PlanInfo", "NeoHookeanResidual", "Batch", "tabulate",
            "measure_fp64_peak"]

@@ -23,6 +23,10 @@ FE_FORM_MASS = 0
 FE_FORM_ELASTICITY = 1
 FE_FORM_NH_RESIDUAL = 2
 FE_FORM_NH_JACOBIAN = 3
+FE_FORM_LAPLACE = 4
+FE_FORM_HELMHOLTZ = 5
+FE_FORM_SVK_RESIDUAL = 6
+FE_FORM_SVK_JACOBIAN = 7
 FE_PREC_FP64 = 0
 FE_PREC_FP32 = 1
 FE_PREC_BF16 = 2

@@ -18,8 +18,14 @@ MASS = N.FE_FORM_MASS
 ELASTICITY = N.FE_FORM_ELASTICITY
 NH_RESIDUAL = N.FE_FORM_NH_RESIDUAL
 NH_JACOBIAN = N.FE_FORM_NH_JACOBIAN
+LAPLACE = N.FE_FORM_LAPLACE
+HELMHOLTZ = N.FE_FORM_HELMHOLTZ
+SVK_RESIDUAL = N.FE_FORM_SVK_RESIDUAL
+SVK_JACOBIAN = N.FE_FORM_SVK_JACOBIAN
 FORM_NAMES = {MASS: "mass", ELASTICITY: "elasticity", NH_RESIDUAL: "nh_residual",
-              NH_JACOBIAN: "nh_jacobian"}
+              NH_JACOBIAN: "nh_jacobian", LAPLACE: "laplace", HELMHOLTZ: "helmholtz",
+              SVK_RESIDUAL: "svk_residual", SVK_JACOBIAN: "svk_jacobian"}
+SCALAR_FORMS = (MASS, LAPLACE, HELMHOLTZ)
 # contraction precision of a plan (include/feaction.h, enum fe_precision)
 PRECISIONS = {"fp64": N.FE_PREC_FP64, "fp32": N.FE_PREC_FP32, "bf16": N.FE_PREC_BF16,
               "fp16": N.FE_PREC_FP16}
@@ -99,7 +105,8 @@ class PlanInfo:
 class Plan:
     """A form bound to a mesh: tables uploaded once, kernel selected once.
 
-    kind: MASS, ELASTICITY, NH_RESIDUAL or NH_JACOBIAN.  Neo-Hookean kinds take
+    kind: MASS, ELASTICITY, NH_RESIDUAL, NH_JACOBIAN, LAPLACE, HELMHOLTZ, SVK_RESIDUAL
+    or SVK_JACOBIAN.  Hyperelastic (Neo-Hookean, St. Venant-Kirchhoff) kinds take
     per-cell ``mu_cell``/``lam_cell`` (copied into plan-owned device buffers that
     :meth:`set_lame` can overwrite) or the constants ``mu``/``lam``; NH_JACOBIAN
     takes the linearisation point ``u_lin`` (plan-owned copy, see
@@ -111,7 +118,7 @@ class Plan:
                  tile_cells: int = 0, tables_global: bool = False, quad_scheme: str = "conical"):
         self.mesh = mesh
         self.kind = int(kind)
-        self.ncomp = 1 if kind == MASS else mesh.dim
+        self.ncomp = 1 if kind in SCALAR_FORMS else mesh.dim
         dev = mesh.device
         self.mu_cell = None if mu_cell is None else torch.as_tensor(
             mu_cell, dtype=torch.float64, device=dev).clone().contiguous()
@@ -263,7 +270,7 @@ class Batch:
         for i, pb in enumerate(problems):
             mesh = pb["mesh"]
             kind = int(pb["kind"])
-            nc = 1 if kind == MASS else mesh.dim
+            nc = 1 if kind in SCALAR_FORMS else mesh.dim
             u = pb["u"]
             if u.dtype != torch.float64 or not u.is_cuda or u.numel() != mesh.n_nodes * nc:
                 raise ValueError(f"problem {i}: u must be a float64 CUDA tensor of {mesh.n_nodes * nc}")

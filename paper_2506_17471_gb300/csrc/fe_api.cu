@@ -15,7 +15,7 @@
 namespace fe {
 namespace {
 
-constexpr int kMaxVariants = 128;
+constexpr int kMaxVariants = 256;
 Variant g_variants[kMaxVariants];
 int g_nvariants = 0;
 std::once_flag g_once;
@@ -28,6 +28,8 @@ void init_registry()
     n += register_variants_3d(g_variants + n, kMaxVariants - n);
     n += register_variants_coop(g_variants + n, kMaxVariants - n);
     n += register_variants_tc(g_variants + n, kMaxVariants - n);
+    n += register_variants_forms(g_variants + n, kMaxVariants - n);
+    n += register_variants_coop_forms(g_variants + n, kMaxVariants - n);
     g_nvariants = n;
 }
 
@@ -118,6 +120,26 @@ double algorithmic_flops(int op, int d, int n, int nq)
         pw = d == 2 ? 131.0 : 401.0;
         quad = 2.0 * d2 * n;
         break;
+    case 5:  // Laplacian: map (2 d^2), scale (d), pull back (2 d^2)
+        eval = 2.0 * d * n;
+        pw = 4.0 * d2 + d + 1.0;
+        quad = 2.0 * d * n;
+        break;
+    case 6:  // Helmholtz: Laplacian plus the value term
+        eval = 2.0 * (d + 1) * n;
+        pw = 4.0 * d2 + d + 2.0;
+        quad = 2.0 * (d + 1) * n;
+        break;
+    case 7:  // St. Venant-Kirchhoff residual: map, E, S, P = F S, pull back
+        eval = 2.0 * d2 * n;
+        pw = d == 2 ? 66.0 : 202.0;
+        quad = 2.0 * d2 * n;
+        break;
+    case 8:  // St. Venant-Kirchhoff Jacobian action: two maps, E, S, dE, dS, dP, pull back
+        eval = 4.0 * d2 * n;
+        pw = d == 2 ? 129.0 : 395.0;
+        quad = 2.0 * d2 * n;
+        break;
     }
     return geo + nq * (eval + pw + quad);
 }
@@ -160,7 +182,22 @@ cudaError_t launch_zero(double *y, long long n, cudaStream_t s)
     return cudaGetLastError();
 }
 
-int ncomp_of(int kind, int dim) { return kind == FE_FORM_MASS ? 1 : dim; }
+int ncomp_of(int kind, int dim)
+{
+    return (kind == FE_FORM_MASS || kind == FE_FORM_LAPLACE || kind == FE_FORM_HELMHOLTZ) ? 1 : dim;
+}
+
+// Internal operation of a public form kind (adjoint: see find_variant's op).
+int op_of(int kind)
+{
+    switch (kind) {
+    case FE_FORM_LAPLACE: return OP_LAPLACE;
+    case FE_FORM_HELMHOLTZ: return OP_HELMHOLTZ;
+    case FE_FORM_SVK_RESIDUAL: return OP_SVK_RESIDUAL;
+    case FE_FORM_SVK_JACOBIAN: return OP_SVK_JACOBIAN;
+    default: return kind;
+    }
+}
 
 int grid_for(const Variant &v, size_t smem, int n_cells, int cells_per_cta)
 {
@@ -306,7 +343,7 @@ static int plan_create_tc(const fe_form &f, const fe_mesh &m, const Variant &v, 
     const long long tiles = ((long long)m.n_cells + kTcRows - 1) / kTcRows;
     const long long want = (tiles + L.pipes - 1) / L.pipes;
     p->grid_blocks = (int)std::max(1LL, std::min(want, (long long)num_sms()));
-    p->flops_per_cell = algorithmic_flops(f.kind, m.dim, n, nq);
+    p->flops_per_cell = algorithmic_flops(op_of(f.kind), m.dim, n, nq);
     const double dofs = (double)m.n_nodes * ncomp;
     p->bytes_min = 2.0 * dofs * 8.0 + (double)m.n_vertices * m.dim * 8.0 + (double)m.n_cells * (n + m.dim + 1) * 4.0;
     if (f.kind == FE_FORM_NH_JACOBIAN)
@@ -326,12 +363,14 @@ extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan 
     if (m.n_cells > 0 && (!m.coords || !m.cell2vertex || !m.cell2node)) return FE_ERR_INVALID_ARG;
     // 2D vertex coordinates are gathered as one 16-byte load per vertex
     if (m.dim == 2 && reinterpret_cast<uintptr_t>(m.coords) % 16 != 0) return FE_ERR_INVALID_ARG;
-    if (f.kind < FE_FORM_MASS || f.kind > FE_FORM_NH_JACOBIAN) return FE_ERR_INVALID_ARG;
+    if (f.kind < FE_FORM_MASS || f.kind > FE_FORM_SVK_JACOBIAN) return FE_ERR_INVALID_ARG;
     if (f.precision < FE_PREC_FP64 || f.precision > FE_PREC_FP16) return FE_ERR_UNSUPPORTED;
     const bool tc = f.precision == FE_PREC_BF16 || f.precision == FE_PREC_FP16;
-    if (tc && f.kind == FE_FORM_NH_RESIDUAL) return FE_ERR_UNSUPPORTED;
+    if (tc && f.kind != FE_FORM_MASS && f.kind != FE_FORM_ELASTICITY && f.kind != FE_FORM_NH_JACOBIAN &&
+        f.kind != FE_FORM_LAPLACE && f.kind != FE_FORM_HELMHOLTZ)
+        return FE_ERR_UNSUPPORTED;
     if (f.quad_degree < 0 || f.quad_degree > 40) return FE_ERR_INVALID_ARG;
-    if (f.kind == FE_FORM_NH_JACOBIAN && !f.u_lin) return FE_ERR_INVALID_ARG;
+    if ((f.kind == FE_FORM_NH_JACOBIAN || f.kind == FE_FORM_SVK_JACOBIAN) && !f.u_lin) return FE_ERR_INVALID_ARG;
     if (f.tile_cells < 0 || f.tile_cells > 4096) return FE_ERR_INVALID_ARG;
     const int ncomp = ncomp_of(f.kind, m.dim);
     if ((long long)m.n_nodes * ncomp >= (1ll << 31)) return FE_ERR_INVALID_ARG;
@@ -361,7 +400,8 @@ extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan 
     if (tc) return plan_create_tc(f, m, *v, nq, n, ncomp, wts, tab, out);
     const size_t esz = f.precision == FE_PREC_FP32 ? sizeof(float) : sizeof(double);
     const bool coop = v->kernel_id == 1;
-    const int fields_max = (f.kind == FE_FORM_NH_JACOBIAN || (adj != nullptr)) ? 2 : 1;
+    const int fields_max =
+        (f.kind == FE_FORM_NH_JACOBIAN || f.kind == FE_FORM_SVK_JACOBIAN || (adj != nullptr)) ? 2 : 1;
     int coop_cells = 0;
     bool global_tab = false;
     size_t rs = (size_t)(1 + m.dim) * n, woff, smem, block_bytes;
@@ -447,13 +487,14 @@ extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan 
     }
     p->grid_blocks = grid_for(*v, smem, m.n_cells, coop ? coop_cells : v->block);
     p->adj_grid_blocks = adj ? grid_for(*adj, smem, m.n_cells, coop ? coop_cells : adj->block) : 0;
-    p->flops_per_cell = algorithmic_flops(f.kind, m.dim, n, nq);
+    p->flops_per_cell = algorithmic_flops(op_of(f.kind), m.dim, n, nq);
     const double dofs = (double)m.n_nodes * ncomp;
     double bytes = 2.0 * dofs * 8.0 + (double)m.n_vertices * m.dim * 8.0 +
                    (double)m.n_cells * (n + m.dim + 1) * 4.0;
-    if (f.kind >= FE_FORM_NH_RESIDUAL)
-        bytes += (f.mu_cell ? 8.0 * m.n_cells : 0.0) + (f.lambda_cell ? 8.0 * m.n_cells : 0.0);
-    if (f.kind == FE_FORM_NH_JACOBIAN) bytes += dofs * 8.0;
+    const bool hyper = f.kind == FE_FORM_NH_RESIDUAL || f.kind == FE_FORM_NH_JACOBIAN ||
+                       f.kind == FE_FORM_SVK_RESIDUAL || f.kind == FE_FORM_SVK_JACOBIAN;
+    if (hyper) bytes += (f.mu_cell ? 8.0 * m.n_cells : 0.0) + (f.lambda_cell ? 8.0 * m.n_cells : 0.0);
+    if (f.kind == FE_FORM_NH_JACOBIAN || f.kind == FE_FORM_SVK_JACOBIAN) bytes += dofs * 8.0;
     p->bytes_min = bytes;
     *out = p;
     return FE_OK;

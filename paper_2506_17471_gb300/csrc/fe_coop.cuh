@@ -63,7 +63,7 @@ __host__ __device__ inline CoopLayout coop_layout(int n, int nq, int D, int NC, 
     L.fields = fields;
     L.rs = ((1 + D) * n) | 1;
     L.ls = (fields * n * NC) | 1;
-    L.es = (D * NC) | 1;
+    L.es = ((D * NC > 1 + D) ? D * NC : 1 + D) | 1;   // gradient terms, or value + gradient
     L.global_tab = global_tab ? 1 : 0;
     L.tab_bytes = L.global_tab ? 0 : (size_t)nq * L.rs * sizeof(R);
     L.wts_off = (L.tab_bytes + 7) & ~(size_t)7;
@@ -221,7 +221,49 @@ __device__ __forceinline__ void coop_batch(const ActionArgs &a, const CoopLayout
                         for (int k = 0; k < D; ++k) gh[f][m][k] = fma(t[k], lv, gh[f][m][k]);
                     }
             }
-            if constexpr (OP == OP_ELASTICITY) {
+            if constexpr (OP == OP_LAPLACE || OP == OP_HELMHOLTZ) {
+                // e = w |det J| J^{-1} J^{-T} grad_ref u  (+ the value term for Helmholtz)
+                R Jr[D][D], g[D];
+                convert<D, D>(Jinv, Jr);
+                const R wdet_r = wts_r[q] * cvt<R>(absdet);
+                constexpr int kV = (OP == OP_HELMHOLTZ) ? 1 : 0;
+#pragma unroll
+                for (int ii = 0; ii < D; ++ii) {
+                    R sg = R(0);
+#pragma unroll
+                    for (int k = 0; k < D; ++k) sg = fma(gh[0][0][k], Jr[k][ii], sg);
+                    g[ii] = sg * wdet_r;
+                }
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    R sk = R(0);
+#pragma unroll
+                    for (int ii = 0; ii < D; ++ii) sk = fma(g[ii], Jr[k][ii], sk);
+                    e[kV + k] = sk;
+                }
+                if constexpr (OP == OP_HELMHOLTZ) {
+                    R uq = R(0);
+                    for (int j = 0; j < n; ++j)
+                        uq = fma(gtab ? __ldg(TB + (size_t)j * nq) : T[j], cvt<R>(lc[j]), uq);
+                    e[0] = uq * wdet_r;
+                }
+            } else if constexpr (OP == OP_SVK_RESIDUAL || OP == OP_SVK_JACOBIAN) {
+                // St. Venant-Kirchhoff law in FP64; the linearisation point is the last field
+                const double wdet = wts[q] * absdet;
+                double ghd[D][D], G[D][D], H[D][D], P[D][D], ed[D][D];
+                convert<D, D>(gh[FIELDS - 1], ghd);
+                map_grad<D, double>(ghd, Jinv, G);
+                if constexpr (OP == OP_SVK_JACOBIAN) {
+                    convert<D, D>(gh[0], ghd);
+                    map_grad<D, double>(ghd, Jinv, H);
+                }
+                svk_stress<D, OP == OP_SVK_JACOBIAN>(G, H, mu, lam, wdet, P);
+                pull_back<D, double>(P, Jinv, ed);
+#pragma unroll
+                for (int m = 0; m < NC; ++m)
+#pragma unroll
+                    for (int k = 0; k < D; ++k) e[m * D + k] = cvt<R>(ed[m][k]);
+            } else if constexpr (OP == OP_ELASTICITY) {
                 R Jr[D][D], G[D][D], S[D][D], er[D][D];
                 convert<D, D>(Jinv, Jr);
                 map_grad<D, R>(gh[0], Jr, G);
@@ -337,6 +379,12 @@ __device__ __forceinline__ void coop_batch(const ActionArgs &a, const CoopLayout
             const R *e = ec + (size_t)q * L.es;
             if constexpr (OP == OP_MASS) {
                 out[0] = fma(gtab ? __ldg(T + j) : T[j], e[0], out[0]);
+            } else if constexpr (OP == OP_HELMHOLTZ) {
+                R o = fma(gtab ? __ldg(T + j) : T[j], e[0], out[0]);
+#pragma unroll
+                for (int k = 0; k < D; ++k)
+                    o = fma(gtab ? __ldg(T + (k + 1) * n + j) : T[(k + 1) * n + j], e[1 + k], o);
+                out[0] = o;
             } else {
 #pragma unroll
                 for (int k = 0; k < D; ++k) {
@@ -395,7 +443,7 @@ template <int OP, int D, typename R = double>
 Variant make_coop_variant()
 {
     Variant v;
-    v.form = OP == OP_NH_ADJOINT ? OP_NH_RESIDUAL : OP;
+    v.form = form_of(OP);
     v.dim = D;
     v.degree = 0;   // any degree
     v.op = OP == OP_NH_ADJOINT ? 1 : 0;

@@ -265,14 +265,114 @@ __device__ __forceinline__ void convert(const T (&x)[A][B], U (&y)[A][B])
 }
 
 // Internal operation ids (forms of the public API plus the Neo-Hookean adjoint).
-enum Op { OP_MASS = 0, OP_ELASTICITY = 1, OP_NH_RESIDUAL = 2, OP_NH_JACOBIAN = 3, OP_NH_ADJOINT = 4 };
+enum Op {
+    OP_MASS = 0,
+    OP_ELASTICITY = 1,
+    OP_NH_RESIDUAL = 2,
+    OP_NH_JACOBIAN = 3,
+    OP_NH_ADJOINT = 4,
+    OP_LAPLACE = 5,
+    OP_HELMHOLTZ = 6,
+    OP_SVK_RESIDUAL = 7,
+    OP_SVK_JACOBIAN = 8
+};
+
+// Public form kind (enum fe_form_kind) of an operation; the adjoint belongs to
+// the Neo-Hookean residual.
+__host__ __device__ constexpr int form_of(int op)
+{
+    return op == OP_NH_ADJOINT     ? FE_FORM_NH_RESIDUAL
+           : op == OP_LAPLACE      ? FE_FORM_LAPLACE
+           : op == OP_HELMHOLTZ    ? FE_FORM_HELMHOLTZ
+           : op == OP_SVK_RESIDUAL ? FE_FORM_SVK_RESIDUAL
+           : op == OP_SVK_JACOBIAN ? FE_FORM_SVK_JACOBIAN
+                                   : op;
+}
 
 template <int OP, int D>
 struct OpTraits {
-    static constexpr int NC = (OP == OP_MASS) ? 1 : D;
-    static constexpr bool kTwoFields = (OP == OP_NH_JACOBIAN || OP == OP_NH_ADJOINT);
-    static constexpr bool kCellCoeff = (OP >= OP_NH_RESIDUAL);
+    static constexpr bool kScalar = (OP == OP_MASS || OP == OP_LAPLACE || OP == OP_HELMHOLTZ);
+    static constexpr int NC = kScalar ? 1 : D;
+    static constexpr bool kTwoFields = (OP == OP_NH_JACOBIAN || OP == OP_NH_ADJOINT || OP == OP_SVK_JACOBIAN);
+    static constexpr bool kCellCoeff = (OP == OP_NH_RESIDUAL || OP == OP_NH_JACOBIAN || OP == OP_NH_ADJOINT ||
+                                        OP == OP_SVK_RESIDUAL || OP == OP_SVK_JACOBIAN);
+    // the law needs FP64 pointwise evaluation (hyperelastic forms)
+    static constexpr bool kNonlinear = kCellCoeff;
 };
+
+// St. Venant-Kirchhoff law (Appendix A, Hyperelasticity) at one point, FP64:
+// F = I + G, E = (F^T F - I)/2, S = lambda tr(E) I + 2 mu E.  For the Jacobian
+// action, with H = grad du: dE = (H^T F + F^T H)/2, dS = lambda tr(dE) I +
+// 2 mu dE and dP = H S + F dS; for the residual P = F S.  Writes P (or dP),
+// already multiplied by scale.
+template <int D, bool kTangent>
+__device__ __forceinline__ void svk_stress(const double (&G)[D][D], const double (&H)[D][D], double mu,
+                                           double lam, double scale, double (&P)[D][D])
+{
+    double F[D][D], E[D][D], S[D][D];
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int k = 0; k < D; ++k) F[i][k] = G[i][k] + (i == k ? 1.0 : 0.0);
+    double trE = 0.0;
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int k = i; k < D; ++k) {
+            double c = F[0][i] * F[0][k];
+#pragma unroll
+            for (int m = 1; m < D; ++m) c = fma(F[m][i], F[m][k], c);
+            E[i][k] = 0.5 * (c - (i == k ? 1.0 : 0.0));
+            E[k][i] = E[i][k];
+        }
+#pragma unroll
+    for (int i = 0; i < D; ++i) trE += E[i][i];
+    const double m2 = 2.0 * mu * scale, lt = lam * trE * scale;
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int k = 0; k < D; ++k) S[i][k] = fma(m2, E[i][k], i == k ? lt : 0.0);
+    if constexpr (!kTangent) {
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                double p = F[i][0] * S[0][k];
+#pragma unroll
+                for (int m = 1; m < D; ++m) p = fma(F[i][m], S[m][k], p);
+                P[i][k] = p;
+            }
+    } else {
+        double dE[D][D], dS[D][D];
+        double trdE = 0.0;
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int k = i; k < D; ++k) {
+                double c = fma(H[0][i], F[0][k], F[0][i] * H[0][k]);
+#pragma unroll
+                for (int m = 1; m < D; ++m) c = fma(H[m][i], F[m][k], fma(F[m][i], H[m][k], c));
+                dE[i][k] = 0.5 * c;
+                dE[k][i] = dE[i][k];
+            }
+#pragma unroll
+        for (int i = 0; i < D; ++i) trdE += dE[i][i];
+        const double ldt = lam * trdE * scale;
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int k = 0; k < D; ++k) dS[i][k] = fma(m2, dE[i][k], i == k ? ldt : 0.0);
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                double p = fma(H[i][0], S[0][k], F[i][0] * dS[0][k]);
+#pragma unroll
+                for (int m = 1; m < D; ++m) p = fma(H[i][m], S[m][k], fma(F[i][m], dS[m][k], p));
+                P[i][k] = p;
+            }
+    }
+}
 
 template <int D, int N, int NC>
 __device__ __forceinline__ bool gather_nodes(const int32_t *__restrict__ c2n, int cell, int n_nodes,
@@ -398,6 +498,66 @@ __device__ __forceinline__ void action_cell(const ActionArgs &a, const R *__rest
             const R e = uq * wdet_r;
 #pragma unroll
             for (int j = 0; j < N; ++j) out[j][0] = fma(T[j], e, out[j][0]);
+        } else if constexpr (OP == OP_LAPLACE || OP == OP_HELMHOLTZ) {
+            // grad u . grad v (+ u v): scalar gradient mapped with J^{-1}, pulled back
+            R gs[D];
+#pragma unroll
+            for (int k = 0; k < D; ++k) gs[k] = R(0);
+#pragma unroll
+            for (int j = 0; j < N; ++j)
+#pragma unroll
+                for (int k = 0; k < D; ++k) gs[k] = fma(T[(k + 1) * N + j], l[j][0], gs[k]);
+            R g[D], e[D];
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                R s = R(0);
+#pragma unroll
+                for (int k = 0; k < D; ++k) s = fma(gs[k], kMixed ? Jinv_r[k][i] : R(Jinv[k][i]), s);
+                g[i] = s * wdet_r;
+            }
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                R s = R(0);
+#pragma unroll
+                for (int i = 0; i < D; ++i) s = fma(g[i], kMixed ? Jinv_r[k][i] : R(Jinv[k][i]), s);
+                e[k] = s;
+            }
+            [[maybe_unused]] R ev = R(0);
+            if constexpr (OP == OP_HELMHOLTZ) {
+                R uq = R(0);
+#pragma unroll
+                for (int j = 0; j < N; ++j) uq = fma(T[j], l[j][0], uq);
+                ev = uq * wdet_r;
+            }
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                R o = out[j][0];
+                if constexpr (OP == OP_HELMHOLTZ) o = fma(T[j], ev, o);
+#pragma unroll
+                for (int k = 0; k < D; ++k) o = fma(T[(k + 1) * N + j], e[k], o);
+                out[j][0] = o;
+            }
+        } else if constexpr (OP == OP_SVK_RESIDUAL || OP == OP_SVK_JACOBIAN) {
+            // St. Venant-Kirchhoff law in FP64 (contractions in R)
+            const double wdet = wts[q] * absdet;
+            R ghr[D][D], er[D][D];
+            double gh[D][D], G[D][D], H[D][D], Pk[D][D], e[D][D];
+            if constexpr (OP == OP_SVK_JACOBIAN) {
+                eval_grad<D, N, D, R>(T, l0, ghr);   // linearisation point
+                convert<D, D>(ghr, gh);
+                map_grad<D, double>(gh, Jinv, G);
+                eval_grad<D, N, D, R>(T, l, ghr);    // direction du
+                convert<D, D>(ghr, gh);
+                map_grad<D, double>(gh, Jinv, H);
+            } else {
+                eval_grad<D, N, D, R>(T, l, ghr);
+                convert<D, D>(ghr, gh);
+                map_grad<D, double>(gh, Jinv, G);
+            }
+            svk_stress<D, OP == OP_SVK_JACOBIAN>(G, H, mu, lam, wdet, Pk);
+            pull_back<D, double>(Pk, Jinv, e);
+            convert<D, D>(e, er);
+            quad_grad<D, N, D, R>(T, er, out);
         } else if constexpr (OP == OP_ELASTICITY) {
             // linear stress: evaluated in the contraction type
             R gh[D][D], G[D][D], S[D][D], e[D][D];
@@ -577,7 +737,7 @@ template <int OP, int D, int P, typename R = double>
 Variant make_tpc_variant()
 {
     Variant v;
-    v.form = OP == OP_NH_ADJOINT ? OP_NH_RESIDUAL : OP;
+    v.form = form_of(OP);
     v.dim = D;
     v.degree = P;
     v.op = OP == OP_NH_ADJOINT ? 1 : 0;

@@ -874,7 +874,7 @@ template <int OP, int D, typename T16>
 Variant make_tc_variant()
 {
     Variant v;
-    v.form = OP;
+    v.form = form_of(OP);
     v.dim = D;
     v.degree = 0;   // any degree with at most 256 local nodes
     v.op = 0;
