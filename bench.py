@@ -379,6 +379,42 @@ def time_secondary(fe, torch, flush, M_el, u_el, y64_el):
         row["fp64"]["frac_of_fp64_peak"] = row["fp64"]["gflops"] / FP64_NOMINAL_GFLOPS
         hp[f"{name}_n{N}"] = row
     out["hp_sweep"] = hp
+
+    # the paper's other forms (Appendix A): Laplacian, Helmholtz (the paper's P4 rows),
+    # St. Venant-Kirchhoff residual and Jacobian action
+    forms = {}
+    for name, kind, dim, p, N, q, scheme, precs in (
+            ("laplace_p2_3d", fe.LAPLACE, 3, 2, 32, 2, "symmetric", ("fp64", "fp32", "bf16", "fp16")),
+            ("helmholtz_p4_2d", fe.HELMHOLTZ, 2, 4, 256, 8, "symmetric", ("fp64", "fp32", "bf16", "fp16")),
+            ("helmholtz_p4_3d", fe.HELMHOLTZ, 3, 4, 24, 8, "conical", ("fp64", "fp32", "bf16", "fp16")),
+            ("svk_residual_p4_2d", fe.SVK_RESIDUAL, 2, 4, 256, 8, "symmetric", ("fp64", "fp32")),
+            ("svk_jacobian_p4_2d", fe.SVK_JACOBIAN, 2, 4, 256, 8, "symmetric", ("fp64", "fp32"))):
+        m = structured_mesh(dim, N, p, jitter=0.2 if dim == 2 else 0.15, seed=20250630 + N)
+        M = fe.Mesh(dim, p, m.coords, m.cell2vertex, m.cell2node, m.n_nodes)
+        nc = 1 if kind in (fe.LAPLACE, fe.HELMHOLTZ) else dim
+        kw = {}
+        if kind in (fe.SVK_RESIDUAL, fe.SVK_JACOBIAN):
+            mu, lam = lame_fields(m.n_cells, 8)
+            kw = dict(mu_cell=mu, lam_cell=lam)
+            if kind == fe.SVK_JACOBIAN:
+                kw["u_lin"] = torch.from_numpy(sinusoid_displacement(m, 9)).cuda()
+        u = (torch.from_numpy(sinusoid_displacement(m, 9)).cuda() if kind == fe.SVK_RESIDUAL
+             else torch.from_numpy(uniform_field(m.n_nodes * nc, 10)).cuda())
+        row = {"dofs": m.n_nodes * nc, "cells": m.n_cells}
+        ys = {}
+        for prec in precs:
+            plan = fe.Plan(M, kind, q, precision=prec, quad_scheme=scheme, **kw)
+            ys[prec] = torch.empty_like(u)
+            t = timed(lambda: plan.apply(u, ys[prec]), reps=5)
+            row[prec] = {"ms": t * 1e3, "dofs_per_s": m.n_nodes * nc / t, "gflops": plan.flops() / t / 1e9,
+                         "kernel": plan.info.kernel, "nq": plan.info.nq}
+            if prec == "fp64":
+                row[prec]["frac_of_fp64_peak"] = row[prec]["gflops"] / FP64_NOMINAL_GFLOPS
+            else:
+                row[prec]["speedup_vs_fp64"] = row["fp64"]["ms"] / row[prec]["ms"]
+                row[prec]["rel_dev_vs_fp64"] = rel(ys[prec], ys["fp64"])
+        forms[f"{name}_n{N}"] = row
+    out["other_forms"] = forms
     return out
 
 

@@ -265,7 +265,8 @@ static void tc_fill_block(const TcLayout &L, int kind, const std::vector<double>
             if (q >= L.nq) break;
             for (int k = 0; k < L.KD; ++k) {
                 const int row = ch * L.N1p + ql * L.KDP + k;
-                const int kt = kind == FE_FORM_MASS ? 0 : 1 + k;
+                // value row first for the forms that use values, then the derivatives
+                const int kt = (kind == FE_FORM_MASS || kind == FE_FORM_HELMHOLTZ) ? k : 1 + k;
                 for (int j = 0; j < L.n; ++j) {
                     const uint16_t bits = to16_bits<T16>(tab[((size_t)kt * L.nq + q) * L.n + j]);
                     B1[tc_off(row, j, L.K1p)] = bits;
@@ -287,7 +288,7 @@ static int plan_create_tc(const fe_form &f, const fe_mesh &m, const Variant &v, 
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
         return FE_ERR_CUDA;
-    const int kd = f.kind == FE_FORM_MASS ? 1 : m.dim;
+    const int kd = f.kind == FE_FORM_MASS ? 1 : (f.kind == FE_FORM_HELMHOLTZ ? 1 + m.dim : m.dim);
     // tiles copy their cell2node block with 16-byte loads
     if (reinterpret_cast<uintptr_t>(m.cell2node) % 16 != 0) return FE_ERR_INVALID_ARG;
     // tile_cells selects the pipelines per CTA (128 cells each): 128, 256, 512, or 0 automatic

@@ -1,6 +1,6 @@
-// Tensor-core variants (16-bit contractions): mass, linear elasticity and the
-// Neo-Hookean Jacobian action in 2D and 3D, BF16 and FP16; degree and rule are
-// runtime values.
+// Tensor-core variants (16-bit contractions): mass, Laplacian, Helmholtz, linear
+// elasticity and the Neo-Hookean Jacobian action in 2D and 3D, BF16 and FP16;
+// degree and rule are runtime values.
 #include "fe_tc.cuh"
 
 namespace fe {
@@ -14,6 +14,10 @@ int register_variants_tc(Variant *out, int cap)
         make_tc_variant<OP_ELASTICITY, 2, __half>(),        make_tc_variant<OP_ELASTICITY, 3, __half>(),
         make_tc_variant<OP_NH_JACOBIAN, 2, __nv_bfloat16>(), make_tc_variant<OP_NH_JACOBIAN, 3, __nv_bfloat16>(),
         make_tc_variant<OP_NH_JACOBIAN, 2, __half>(),       make_tc_variant<OP_NH_JACOBIAN, 3, __half>(),
+        make_tc_variant<OP_LAPLACE, 2, __nv_bfloat16>(),    make_tc_variant<OP_LAPLACE, 3, __nv_bfloat16>(),
+        make_tc_variant<OP_LAPLACE, 2, __half>(),           make_tc_variant<OP_LAPLACE, 3, __half>(),
+        make_tc_variant<OP_HELMHOLTZ, 2, __nv_bfloat16>(),  make_tc_variant<OP_HELMHOLTZ, 3, __nv_bfloat16>(),
+        make_tc_variant<OP_HELMHOLTZ, 2, __half>(),         make_tc_variant<OP_HELMHOLTZ, 3, __half>(),
     };
     int n = 0;
     for (const Variant &x : v)

@@ -175,6 +175,13 @@ __host__ __device__ __forceinline__ uint16_t to16_bits<__half>(double x, int k)
     return f64_to_small_rn<5, 10>(x, k);
 }
 
+// 2^e as a binary32 value for e <= 127; 0 below the normal range (the terms it
+// scales are then negligible against the other term of the sum).
+__device__ __forceinline__ float exp2_float(int e)
+{
+    return e < -126 ? 0.f : __uint_as_float((unsigned)min(e + 127, 254) << 23);
+}
+
 // Monotone map of binary64 values to signed integers (integer order = value
 // order, -0 just below +0) and its inverse: min/max without FP64 compares.
 __device__ __forceinline__ long long ordered_key(double x)
@@ -463,12 +470,13 @@ template <int OP, int D, typename T16>
 __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const ActionArgs a)
 {
     constexpr int NC = OpTraits<OP, D>::NC;
-    constexpr int KD = (OP == OP_MASS) ? 1 : D;
+    // derivative terms per point: value (mass), value + gradient (Helmholtz), gradient
+    constexpr int KD = (OP == OP_MASS) ? 1 : (OP == OP_HELMHOLTZ ? 1 + D : D);
     constexpr int KDP = (KD == 1) ? 1 : (KD == 2 ? 2 : 4);
     constexpr int F = (OP == OP_NH_JACOBIAN) ? 2 : 1;   // fields: du (or u), then u_lin
     // gradient-only forms round u - c (c a per-cell constant): the basis
     // gradients sum to zero, so the constant drops out of every gradient
-    constexpr bool kOffset = OP != OP_MASS;
+    constexpr bool kOffset = OP != OP_MASS && OP != OP_HELMHOLTZ;
     constexpr int PPB = 16 / KDP;   // quadrature points per 16 accumulator columns
     constexpr int FMT = std::is_same<T16, __nv_bfloat16>::value ? 1 : 0;
     extern __shared__ __align__(128) unsigned char tc_smem[];
@@ -569,6 +577,7 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
         int ku[F] = {};         // field f is rounded as (u_f - off_f) * 2^-ku[f]
         double off[F][NC] = {}; // per-cell offsets (gradient forms; zero for mass)
         [[maybe_unused]] float Jh[D][D];
+        [[maybe_unused]] float s_val = 1.f, s_grad = 1.f;   // Helmholtz: value / gradient term factors
         [[maybe_unused]] float Jf[D][D];   // Neo-Hookean: J^{-1} in binary32
         [[maybe_unused]] double mu_c = a.mu, lam_c = a.lam;
         bool good = t < nb;
@@ -665,14 +674,23 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
                     mu_c = ldexp(mu_c, -km);
                     lam_c = ldexp(lam_c, -km);
                 }
-                if constexpr (OP == OP_ELASTICITY || OP == OP_NH_JACOBIAN) {
+                if constexpr (OP != OP_MASS) {
                     int ej = 0;
 #pragma unroll
                     for (int i = 0; i < D; ++i)
 #pragma unroll
                         for (int k = 0; k < D; ++k) ej = max(ej, exp_field(Jinv[i][k]));
                     const int kj = ej - 1022;   // s_J = 2^kj > max |J^{-1}_ik|
-                    K += 2 * kj;
+                    if constexpr (OP == OP_HELMHOLTZ) {
+                        // value term ~ |det J| u, gradient term ~ |det J| 2^2kj (O(1) each
+                        // before these factors): the common scale follows the larger one
+                        const int sig = max(2 * kj, 0);
+                        K += sig;
+                        s_val = exp2_float(-sig);
+                        s_grad = exp2_float(2 * kj - sig);
+                    } else {
+                        K += 2 * kj;
+                    }
 #pragma unroll
                     for (int i = 0; i < D; ++i)
 #pragma unroll
@@ -760,6 +778,28 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
                     const float w = live ? wf[q] : 0.f;
                     if constexpr (OP == OP_MASS) {
                         v[0][p] = w * v[0][p];
+                    } else if constexpr (OP == OP_LAPLACE || OP == OP_HELMHOLTZ) {
+                        // e = w J^{-1} J^{-T} grad_ref u (scaled by 2^-2kj), value term w u / 2^2kj
+                        constexpr int kV = (OP == OP_HELMHOLTZ) ? 1 : 0;
+                        float g[D];
+#pragma unroll
+                        for (int i = 0; i < D; ++i) {
+                            float sg = 0.f;
+#pragma unroll
+                            for (int k = 0; k < D; ++k) sg = fmaf(v[0][p * KDP + kV + k], Jh[k][i], sg);
+                            g[i] = sg * w;
+                        }
+                        float ek[D];
+#pragma unroll
+                        for (int k = 0; k < D; ++k) {
+                            float sk = 0.f;
+#pragma unroll
+                            for (int i = 0; i < D; ++i) sk = fmaf(g[i], Jh[k][i], sk);
+                            ek[k] = OP == OP_HELMHOLTZ ? sk * s_grad : sk;
+                        }
+                        if constexpr (OP == OP_HELMHOLTZ) v[0][p * KDP] = live ? w * s_val * v[0][p * KDP] : 0.f;
+#pragma unroll
+                        for (int k = 0; k < KDP - kV; ++k) v[0][p * KDP + kV + k] = (k < D && live) ? ek[k] : 0.f;
                     } else {
                         float gh[D][D], G[D][D], S[D][D], e[D][D];
 #pragma unroll
@@ -879,7 +919,7 @@ Variant make_tc_variant()
     v.degree = 0;   // any degree with at most 256 local nodes
     v.op = 0;
     v.precision = std::is_same<T16, __nv_bfloat16>::value ? FE_PREC_BF16 : FE_PREC_FP16;
-    v.kernel_id = 2;
+    v.kernel_id = 2;   // 128-cell tensor-core tiles
     v.block = kTcRows;
     v.launch = &launch_tc<OP, D, T16>;
     v.func = reinterpret_cast<const void *>(&k_action_tc<OP, D, T16>);

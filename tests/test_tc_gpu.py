@@ -252,3 +252,34 @@ def test_tc_material_scaling(fe, prec):
         plan = fe.Plan(M, fe.ELASTICITY, 4, lam=lam, mu=mu, precision=prec)
         assert rel(plan.apply(cuda(u)), o.elasticity(u, lam, mu)) <= TOL16[prec]
         assert plan.status() == 0
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+@pytest.mark.parametrize("kind,dim,N,p,q", [("laplace", 2, 13, 2, 2), ("laplace", 2, 13, 4, 6),
+                                            ("laplace", 3, 5, 3, 4), ("helmholtz", 2, 13, 4, 8),
+                                            ("helmholtz", 3, 5, 2, 4), ("helmholtz", 3, 5, 4, 8)])
+def test_tc_laplace_helmholtz(fe, kind, dim, N, p, q, prec):
+    """Scalar gradient forms on the tensor cores: the Laplacian with the per-cell
+    shift, Helmholtz with its value row (no shift: values need the constant)."""
+    m, M = make(fe, dim, N, p, 600 + 10 * dim + p)
+    assert m.n_cells % 128 != 0
+    o = oracle.Oracle.from_mesh(m, q)
+    u = uniform_field(m.n_nodes, 12 + p)
+    plan = fe.Plan(M, getattr(fe, kind.upper()), q, precision=prec)
+    assert plan.info.kernel == 2
+    err = rel(plan.apply(cuda(u)), getattr(o, kind)(u))
+    assert 1e-7 < err <= TOL16[prec], err
+    assert plan.status() == 0
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_tc_helmholtz_cell_scale(fe, prec):
+    """Helmholtz mixes a value term (scale h^d) and a gradient term (h^(d-2)); both
+    share the per-cell output factor, on meshes scaled by 2^-20 and 2^+20."""
+    for s in (2.0 ** -20, 2.0 ** 20):
+        m, M = make(fe, 2, 13, 3, 47, scale=s)
+        o = oracle.Oracle.from_mesh(m, 6)
+        u = uniform_field(m.n_nodes, 13)
+        plan = fe.Plan(M, fe.HELMHOLTZ, 6, precision=prec)
+        assert rel(plan.apply(cuda(u)), o.helmholtz(u)) <= TOL16[prec]
+        assert plan.status() == 0
