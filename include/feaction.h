@@ -241,6 +241,23 @@ int fe_action_adjoint(fe_plan *plan, const double *u, const double *w, double *j
 int fe_action_host(fe_plan *plan, const double *u_host, double *y_host, double *u_dev,
                    double *y_dev, void *stream);
 
+/* End-to-end over a sequence of n_steps independent inputs (for example the
+ * right-hand sides of successive solves): y_host[i] = A(u_host[i]), i < n_steps,
+ * each u_host[i] / y_host[i] a host array of n_dofs doubles (pinned for the
+ * copies to be asynchronous).  The steps are pipelined through two device
+ * buffer pairs u_dev[0..1], y_dev[0..1] (caller-owned, n_dofs doubles each,
+ * all four distinct): the host-to-device copy of step i+1 and the
+ * device-to-host copy of step i-1 run on two plan-owned copy streams while the
+ * action of step i runs on `stream`, ordered by events, so the per-step time is
+ * the largest of the three instead of their sum.  Every step still copies its
+ * input in and its result out.  Returns after the last result has reached
+ * y_host[n_steps-1] (synchronises `stream`).  The plan creates its two copy
+ * streams and six events on first use and frees them in fe_plan_destroy.
+ * Errors: FE_ERR_INVALID_ARG (NULL arrays, aliasing device buffers, n_steps <
+ * 0), FE_ERR_CUDA. */
+int fe_action_host_pipelined(fe_plan *plan, int n_steps, const double *const *u_host, double *const *y_host,
+                             double *const *u_dev, double *const *y_dev, void *stream);
+
 /* Reads and clears the plan's device status word (synchronises the device).
  * *device_status receives FE_OK or the first device-detected error; it is
  * FE_ERR_CUDA if a launch left the plan's work-queue counters inconsistent.

@@ -44,7 +44,8 @@ EXPORTS = ("fe_status_string", "fe_tabulate", "fe_tabulate_scheme", "fe_plan_cre
            "fe_measure_fp64_peak", "fe_action_noalloc", "fe_cg_start", "fe_cg_direction",
            "fe_cg_update", "fe_cg_new_direction", "fe_vec_axpy", "fe_vec_dot",
            "fe_selftest_conversions", "fe_batch_create", "fe_batch_run", "fe_batch_status",
-           "fe_batch_get_info", "fe_batch_destroy", "fe_selftest_conversions16", "fe_round16")
+           "fe_batch_get_info", "fe_batch_destroy", "fe_selftest_conversions16", "fe_round16",
+           "fe_action_host_pipelined")
 FE_CG_PARTIALS = 1024
 FE_CG_WORKSPACE_DOUBLES = FE_CG_PARTIALS + 16
 
@@ -106,6 +107,7 @@ def _load() -> ctypes.CDLL:
     lib.fe_action.argtypes = [P, P, P, P]
     lib.fe_action_adjoint.argtypes = [P, P, P, P, P, P, P]
     lib.fe_action_host.argtypes = [P, P, P, P, P, P]
+    lib.fe_action_host_pipelined.argtypes = [P, I, P, P, P, P, P]
     lib.fe_plan_status.argtypes = [P, ctypes.POINTER(I)]
     lib.fe_plan_get_info.argtypes = [P, ctypes.POINTER(FePlanInfo)]
     lib.fe_measure_fp64_peak.argtypes = [P, Z, ctypes.POINTER(D)]

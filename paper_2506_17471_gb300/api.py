@@ -200,6 +200,30 @@ class Plan:
                                      _dptr(y_dev), _stream_ptr(stream)), "fe_action_host")
         return y_host
 
+    def apply_host_pipelined(self, u_hosts, y_hosts=None, stream=None):
+        """End to end over several host inputs through ``fe_action_host_pipelined``:
+        copies in, actions and copies out overlap across steps (two device buffer
+        pairs).  Returns the list of host results."""
+        u_hosts = [u.contiguous() for u in u_hosts]
+        if y_hosts is None:
+            y_hosts = [torch.empty_like(u) for u in u_hosts]
+        for t in list(u_hosts) + list(y_hosts):
+            if t.is_cuda or t.dtype != torch.float64 or t.numel() != self.n_dofs:
+                raise ValueError(f"expected host float64 tensors of {self.n_dofs} values")
+        dev = self.mesh.device
+        if getattr(self, "_pipe_bufs", None) is None:
+            self._pipe_bufs = [torch.empty(self.n_dofs, dtype=torch.float64, device=dev) for _ in range(4)]
+        ub, yb = self._pipe_bufs[:2], self._pipe_bufs[2:]
+        n = len(u_hosts)
+        P = ctypes.c_void_p
+        up = (P * n)(*[t.data_ptr() for t in u_hosts])
+        yp = (P * n)(*[t.data_ptr() for t in y_hosts])
+        ud = (P * 2)(*[t.data_ptr() for t in ub])
+        yd = (P * 2)(*[t.data_ptr() for t in yb])
+        N.check(N.lib.fe_action_host_pipelined(self._h, n, up, yp, ud, yd, _stream_ptr(stream)),
+                "fe_action_host_pipelined")
+        return y_hosts
+
     def adjoint(self, u: torch.Tensor, w: torch.Tensor, stream=None):
         """(J(u)^T w, dmu [n_cells], dlambda [n_cells]) of the Neo-Hookean residual."""
         self._check_vec(u, "u")

@@ -507,6 +507,11 @@ extern "C" int fe_plan_destroy(fe_plan *plan)
     cudaDeviceSynchronize();
     cudaFree(plan->d_tab);
     cudaFree(plan->d_status);
+    if (plan->pipe_ready) {
+        for (cudaEvent_t e : plan->pipe_ev) cudaEventDestroy(e);
+        cudaStreamDestroy(plan->pipe_h2d);
+        cudaStreamDestroy(plan->pipe_d2h);
+    }
     delete plan;
     return FE_OK;
 }
@@ -597,6 +602,61 @@ extern "C" int fe_action_host(fe_plan *plan, const double *u_host, double *y_hos
     if (rc != FE_OK) return rc;
     if (cudaMemcpyAsync(y_host, y_dev, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return FE_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return FE_ERR_CUDA;
+    return FE_OK;
+}
+
+extern "C" int fe_action_host_pipelined(fe_plan *plan, int n_steps, const double *const *u_host,
+                                        double *const *y_host, double *const *u_dev, double *const *y_dev,
+                                        void *stream)
+{
+    if (!plan || n_steps < 0) return FE_ERR_INVALID_ARG;
+    if (n_steps == 0) return FE_OK;
+    if (!u_host || !y_host || !u_dev || !y_dev || !u_dev[0] || !u_dev[1] || !y_dev[0] || !y_dev[1])
+        return FE_ERR_INVALID_ARG;
+    const double *bufs[4] = {u_dev[0], u_dev[1], y_dev[0], y_dev[1]};
+    for (int i = 0; i < 4; ++i)
+        for (int k = i + 1; k < 4; ++k)
+            if (bufs[i] == bufs[k]) return FE_ERR_INVALID_ARG;
+    for (int i = 0; i < n_steps; ++i)
+        if (!u_host[i] || !y_host[i]) return FE_ERR_INVALID_ARG;
+    if (!plan->pipe_ready) {
+        if (cudaStreamCreateWithFlags(&plan->pipe_h2d, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&plan->pipe_d2h, cudaStreamNonBlocking) != cudaSuccess)
+            return FE_ERR_CUDA;
+        for (cudaEvent_t &e : plan->pipe_ev)
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return FE_ERR_CUDA;
+        plan->pipe_ready = true;
+    }
+    cudaStream_t sc = static_cast<cudaStream_t>(stream);
+    const size_t bytes = (size_t)plan->mesh.n_nodes * plan->ncomp * sizeof(double);
+    cudaEvent_t *ev = plan->pipe_ev;   // [b*3 + 0] h2d done, [b*3 + 1] action done, [b*3 + 2] d2h done
+    // the copy streams start after everything the caller queued on `stream`
+    if (cudaEventRecord(ev[1], sc) != cudaSuccess || cudaEventRecord(ev[4], sc) != cudaSuccess ||
+        cudaEventRecord(ev[2], sc) != cudaSuccess || cudaEventRecord(ev[5], sc) != cudaSuccess)
+        return FE_ERR_CUDA;
+    for (int i = 0; i < n_steps; ++i) {
+        const int b = i & 1;
+        cudaEvent_t h2d = ev[3 * b], act = ev[3 * b + 1], d2h = ev[3 * b + 2];
+        // input copy: after the action that last read u_dev[b]
+        if (cudaStreamWaitEvent(plan->pipe_h2d, act, 0) != cudaSuccess ||
+            cudaMemcpyAsync(u_dev[b], u_host[i], bytes, cudaMemcpyHostToDevice, plan->pipe_h2d) != cudaSuccess ||
+            cudaEventRecord(h2d, plan->pipe_h2d) != cudaSuccess)
+            return FE_ERR_CUDA;
+        // action: after its input arrived and after the copy that last read y_dev[b]
+        if (cudaStreamWaitEvent(sc, h2d, 0) != cudaSuccess || cudaStreamWaitEvent(sc, d2h, 0) != cudaSuccess)
+            return FE_ERR_CUDA;
+        const int rc = fe_action(plan, u_dev[b], y_dev[b], stream);
+        if (rc != FE_OK) return rc;
+        if (cudaEventRecord(act, sc) != cudaSuccess) return FE_ERR_CUDA;
+        // result copy
+        if (cudaStreamWaitEvent(plan->pipe_d2h, act, 0) != cudaSuccess ||
+            cudaMemcpyAsync(y_host[i], y_dev[b], bytes, cudaMemcpyDeviceToHost, plan->pipe_d2h) != cudaSuccess ||
+            cudaEventRecord(d2h, plan->pipe_d2h) != cudaSuccess)
+            return FE_ERR_CUDA;
+    }
+    // the caller's stream ends after the last result copy
+    if (cudaStreamWaitEvent(sc, ev[3 * ((n_steps - 1) & 1) + 2], 0) != cudaSuccess) return FE_ERR_CUDA;
+    if (cudaStreamSynchronize(sc) != cudaSuccess) return FE_ERR_CUDA;
     return FE_OK;
 }
 

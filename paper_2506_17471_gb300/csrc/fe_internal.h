@@ -110,4 +110,9 @@ struct fe_plan {
     int device;
     double flops_per_cell;
     double bytes_min;
+    // fe_action_host_pipelined: two copy streams and, per buffer pair b, the
+    // events h2d done, action done, d2h done (created on first use)
+    cudaStream_t pipe_h2d = nullptr, pipe_d2h = nullptr;
+    cudaEvent_t pipe_ev[6] = {};
+    bool pipe_ready = false;
 };
