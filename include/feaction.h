@@ -90,7 +90,7 @@ enum fe_precision {
                                 Neo-Hookean kinematics, log det F and stress, and the
                                 scatter-add stay FP64.  The linear elasticity stress is
                                 evaluated in single.  Error: see fe_plan_create.        */
-    FE_PREC_BF16 = 2,        /* tensor-core kernel (mass, elasticity): both contractions on
+    FE_PREC_BF16 = 2,        /* tensor-core kernel (forms: see fe_plan_create): both contractions on
                                 tcgen05 tensor cores with bfloat16 operands (tables, DoFs
                                 scaled per cell by a power of two, pointwise results) and
                                 FP32 accumulation in tensor memory; geometry FP64, linear
@@ -201,8 +201,9 @@ typedef struct fe_plan fe_plan;
  *   FE_PREC_BF16, FE_PREC_FP16  <= 8 u16 with u16 = 2^-8 (BF16) or 2^-11
  *                 (FP16), i.e. 3.1e-2 / 3.9e-3 (measured 0.6 - 4.3 u16).
  *
- * Tensor-core plans (FE_PREC_BF16 / FE_PREC_FP16): kinds MASS, ELASTICITY and
- * NH_JACOBIAN (NH_RESIDUAL: FE_ERR_UNSUPPORTED); cell2node must be 16-byte
+ * Tensor-core plans (FE_PREC_BF16 / FE_PREC_FP16): kinds MASS, ELASTICITY,
+ * LAPLACE, HELMHOLTZ, NH_JACOBIAN and SVK_JACOBIAN (the residual kinds:
+ * FE_ERR_UNSUPPORTED); cell2node must be 16-byte
  * aligned (FE_ERR_INVALID_ARG otherwise); tile_cells selects the 128-cell
  * pipelines per CTA (0 automatic, 128, 256 or 512; other values
  * FE_ERR_UNSUPPORTED); FE_ERR_UNSUPPORTED also if the degree has more than 256

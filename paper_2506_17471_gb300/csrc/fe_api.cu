@@ -296,7 +296,7 @@ static int plan_create_tc(const fe_form &f, const fe_mesh &m, const Variant &v, 
         f.tile_cells != 4 * kTcRows)
         return FE_ERR_UNSUPPORTED;
     TcLayout L;
-    const int fields = f.kind == FE_FORM_NH_JACOBIAN ? 2 : 1;
+    const int fields = (f.kind == FE_FORM_NH_JACOBIAN || f.kind == FE_FORM_SVK_JACOBIAN) ? 2 : 1;
     if (!tc_choose(n, nq, ncomp, kd, fields, (size_t)optin - 256, f.tile_cells / kTcRows, &L)) return FE_ERR_UNSUPPORTED;
     // weights scaled by 2^wshift into [1/2, 1) at their largest, so w_q E' stays
     // in binary16's normal range for rules with very small weights
@@ -367,9 +367,7 @@ extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan 
     if (f.kind < FE_FORM_MASS || f.kind > FE_FORM_SVK_JACOBIAN) return FE_ERR_INVALID_ARG;
     if (f.precision < FE_PREC_FP64 || f.precision > FE_PREC_FP16) return FE_ERR_UNSUPPORTED;
     const bool tc = f.precision == FE_PREC_BF16 || f.precision == FE_PREC_FP16;
-    if (tc && f.kind != FE_FORM_MASS && f.kind != FE_FORM_ELASTICITY && f.kind != FE_FORM_NH_JACOBIAN &&
-        f.kind != FE_FORM_LAPLACE && f.kind != FE_FORM_HELMHOLTZ)
-        return FE_ERR_UNSUPPORTED;
+    if (tc && (f.kind == FE_FORM_NH_RESIDUAL || f.kind == FE_FORM_SVK_RESIDUAL)) return FE_ERR_UNSUPPORTED;
     if (f.quad_degree < 0 || f.quad_degree > 40) return FE_ERR_INVALID_ARG;
     if ((f.kind == FE_FORM_NH_JACOBIAN || f.kind == FE_FORM_SVK_JACOBIAN) && !f.u_lin) return FE_ERR_INVALID_ARG;
     if (f.tile_cells < 0 || f.tile_cells > 4096) return FE_ERR_INVALID_ARG;

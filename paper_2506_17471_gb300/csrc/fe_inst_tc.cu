@@ -1,6 +1,6 @@
 // Tensor-core variants (16-bit contractions): mass, Laplacian, Helmholtz, linear
-// elasticity and the Neo-Hookean Jacobian action in 2D and 3D, BF16 and FP16;
-// degree and rule are runtime values.
+// elasticity and the Neo-Hookean and St. Venant-Kirchhoff Jacobian actions in 2D
+// and 3D, BF16 and FP16; degree and rule are runtime values.
 #include "fe_tc.cuh"
 
 namespace fe {
@@ -18,6 +18,8 @@ int register_variants_tc(Variant *out, int cap)
         make_tc_variant<OP_LAPLACE, 2, __half>(),           make_tc_variant<OP_LAPLACE, 3, __half>(),
         make_tc_variant<OP_HELMHOLTZ, 2, __nv_bfloat16>(),  make_tc_variant<OP_HELMHOLTZ, 3, __nv_bfloat16>(),
         make_tc_variant<OP_HELMHOLTZ, 2, __half>(),         make_tc_variant<OP_HELMHOLTZ, 3, __half>(),
+        make_tc_variant<OP_SVK_JACOBIAN, 2, __nv_bfloat16>(), make_tc_variant<OP_SVK_JACOBIAN, 3, __nv_bfloat16>(),
+        make_tc_variant<OP_SVK_JACOBIAN, 2, __half>(),      make_tc_variant<OP_SVK_JACOBIAN, 3, __half>(),
     };
     int n = 0;
     for (const Variant &x : v)

@@ -367,20 +367,21 @@ __device__ __forceinline__ bool tc_wait(uint32_t sbar, uint32_t parity)
     return false;
 }
 
-// Neo-Hookean Jacobian pointwise phase for one chunk, for this thread's cell
-// at the chunk's points.  The du and u_lin reference gradients come from the
-// evaluation accumulators (8 columns at a time).  The kinematic contractions
-// with J^{-1} (F = I + grad u_lin, u_lin's per-cell scaling undone exactly by a
-// power of two; H = grad du with J^{-1} 2^-kj) and the pull-back run in FP32,
-// far below the 16-bit rounding of their inputs and output; the law itself
-// (det F, F^{-T}, log det F and the tangent dP/dF applied to H, the same
-// algebra as the FP64 kernel) is FP64.  E' = w_q e is rounded to 16 bits.
-// Returns false if det F <= 0 at a live point.
-template <int D, typename T16>
-__device__ __forceinline__ bool tc_pointwise_nh_jacobian(const TcLayout &L, uint32_t tlane, unsigned char *hb,
-                                                         const double *wd, int t, int ch, int nq, bool good, int ku_lin,
-                                                         const float (&Jf)[D][D], const float (&Jh)[D][D],
-                                                         double mu, double lam)
+// Hyperelastic Jacobian pointwise phase (Neo-Hookean or St. Venant-Kirchhoff)
+// for one chunk, for this thread's cell at the chunk's points.  The du and
+// u_lin reference gradients come from the evaluation accumulators (8 columns at
+// a time).  The kinematic contractions with J^{-1} (F = I + grad u_lin,
+// u_lin's per-cell scaling undone exactly by a power of two; H = grad du with
+// J^{-1} 2^-kj) and the pull-back run in FP32, far below the 16-bit rounding of
+// their inputs and output; the law itself is FP64 (Neo-Hookean: det F, F^{-T},
+// log det F and the tangent applied to H; St. Venant-Kirchhoff: E, S, dE, dS,
+// dP = H S + F dS — the same algebra as the FP64 kernels).  E' = w_q e is
+// rounded to 16 bits.  Returns false if det F <= 0 at a live Neo-Hookean point.
+template <int OP, int D, typename T16>
+__device__ __forceinline__ bool tc_pointwise_hyper_jacobian(const TcLayout &L, uint32_t tlane, unsigned char *hb,
+                                                            const double *wd, int t, int ch, int nq, bool good,
+                                                            int ku_lin, const float (&Jf)[D][D],
+                                                            const float (&Jh)[D][D], double mu, double lam)
 {
     constexpr int NC = D, KDP = (D == 2) ? 2 : 4, PPB = 8 / KDP;
     // 2^ku_lin as a binary32 value (the u_lin gradient is O(h) in reference
@@ -405,49 +406,66 @@ __device__ __forceinline__ bool tc_pointwise_nh_jacobian(const TcLayout &L, uint
                     gd[m][k] = __uint_as_float(r[m][p * KDP + k]);
                     gl[m][k] = __uint_as_float(r[NC + m][p * KDP + k]) * s_lin;
                 }
-            map_grad<D, float>(gl, Jf, Ff);
-            map_grad<D, float>(gd, Jh, Hf);
-            double F[D][D], H[D][D], C[D][D], Fit[D][D], A[D][D];
-#pragma unroll
-            for (int i = 0; i < D; ++i)
-#pragma unroll
-                for (int k = 0; k < D; ++k) {
-                    F[i][k] = widen_pow2(Ff[i][k], 0) + (i == k ? 1.0 : 0.0);
-                    H[i][k] = widen_pow2(Hf[i][k], 0);
-                }
-            const double Jd = det_cof<D>(F, C);
-            ok &= !live || (Jd > 0.0);
-            const double Jd_safe = live && Jd > 0.0 ? Jd : 1.0;
-            const double rJ = 1.0 / Jd_safe;
-            const double lnJ = log(Jd_safe);
-            double tr = 0.0;   // F^{-T} : H
-#pragma unroll
-            for (int i = 0; i < D; ++i)
-#pragma unroll
-                for (int k = 0; k < D; ++k) {
-                    Fit[i][k] = C[i][k] * rJ;
-                    tr = fma(Fit[i][k], H[i][k], tr);
-                }
-#pragma unroll
-            for (int i = 0; i < D; ++i)
-#pragma unroll
-                for (int k = 0; k < D; ++k) {
-                    double s = Fit[i][0] * H[k][0];
-#pragma unroll
-                    for (int mm = 1; mm < D; ++mm) s = fma(Fit[i][mm], H[k][mm], s);
-                    A[i][k] = s;
-                }
+            map_grad<D, float>(gl, Jf, Ff);   // grad u_lin (physical), F = I + Ff
+            map_grad<D, float>(gd, Jh, Hf);   // grad du with J^{-1} 2^-kj
             const double w = live ? wd[q] : 0.0;
-            const double smu = w * mu, sm2 = w * fma(-lam, lnJ, mu), str = w * lam * tr;
+            if constexpr (OP == OP_SVK_JACOBIAN) {
+                // St. Venant-Kirchhoff tangent dP = H S + F dS in FP64 (no det F condition)
+                double G[D][D], H[D][D], Pd[D][D];
 #pragma unroll
-            for (int i = 0; i < D; ++i)
+                for (int i = 0; i < D; ++i)
 #pragma unroll
-                for (int k = 0; k < D; ++k) {
-                    double mk = A[i][0] * Fit[0][k];
+                    for (int k = 0; k < D; ++k) {
+                        G[i][k] = widen_pow2(Ff[i][k], 0);
+                        H[i][k] = widen_pow2(Hf[i][k], 0);
+                    }
+                svk_stress<D, true>(G, H, mu, lam, w, Pd);
 #pragma unroll
-                    for (int mm = 1; mm < D; ++mm) mk = fma(A[i][mm], Fit[mm][k], mk);
-                    Sf[i][k] = narrow_pow2_ftz(fma(smu, H[i][k], fma(sm2, mk, str * Fit[i][k])), 0);
-                }
+                for (int i = 0; i < D; ++i)
+#pragma unroll
+                    for (int k = 0; k < D; ++k) Sf[i][k] = narrow_pow2_ftz(Pd[i][k], 0);
+            } else {
+                double F[D][D], H[D][D], C[D][D], Fit[D][D], A[D][D];
+#pragma unroll
+                for (int i = 0; i < D; ++i)
+#pragma unroll
+                    for (int k = 0; k < D; ++k) {
+                        F[i][k] = widen_pow2(Ff[i][k], 0) + (i == k ? 1.0 : 0.0);
+                        H[i][k] = widen_pow2(Hf[i][k], 0);
+                    }
+                const double Jd = det_cof<D>(F, C);
+                ok &= !live || (Jd > 0.0);
+                const double Jd_safe = live && Jd > 0.0 ? Jd : 1.0;
+                const double rJ = 1.0 / Jd_safe;
+                const double lnJ = log(Jd_safe);
+                double tr = 0.0;   // F^{-T} : H
+#pragma unroll
+                for (int i = 0; i < D; ++i)
+#pragma unroll
+                    for (int k = 0; k < D; ++k) {
+                        Fit[i][k] = C[i][k] * rJ;
+                        tr = fma(Fit[i][k], H[i][k], tr);
+                    }
+#pragma unroll
+                for (int i = 0; i < D; ++i)
+#pragma unroll
+                    for (int k = 0; k < D; ++k) {
+                        double s = Fit[i][0] * H[k][0];
+#pragma unroll
+                        for (int mm = 1; mm < D; ++mm) s = fma(Fit[i][mm], H[k][mm], s);
+                        A[i][k] = s;
+                    }
+                const double smu = w * mu, sm2 = w * fma(-lam, lnJ, mu), str = w * lam * tr;
+#pragma unroll
+                for (int i = 0; i < D; ++i)
+#pragma unroll
+                    for (int k = 0; k < D; ++k) {
+                        double mk = A[i][0] * Fit[0][k];
+#pragma unroll
+                        for (int mm = 1; mm < D; ++mm) mk = fma(A[i][mm], Fit[mm][k], mk);
+                        Sf[i][k] = narrow_pow2_ftz(fma(smu, H[i][k], fma(sm2, mk, str * Fit[i][k])), 0);
+                    }
+            }
             pull_back<D, float>(Sf, Jh, ef);
 #pragma unroll
             for (int m = 0; m < NC; ++m)
@@ -473,7 +491,9 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
     // derivative terms per point: value (mass), value + gradient (Helmholtz), gradient
     constexpr int KD = (OP == OP_MASS) ? 1 : (OP == OP_HELMHOLTZ ? 1 + D : D);
     constexpr int KDP = (KD == 1) ? 1 : (KD == 2 ? 2 : 4);
-    constexpr int F = (OP == OP_NH_JACOBIAN) ? 2 : 1;   // fields: du (or u), then u_lin
+    // hyperelastic Jacobian actions gather two fields: du, then the linearisation point
+    constexpr bool kHyperJac = (OP == OP_NH_JACOBIAN || OP == OP_SVK_JACOBIAN);
+    constexpr int F = kHyperJac ? 2 : 1;
     // gradient-only forms round u - c (c a per-cell constant): the basis
     // gradients sum to zero, so the constant drops out of every gradient
     constexpr bool kOffset = OP != OP_MASS && OP != OP_HELMHOLTZ;
@@ -594,7 +614,7 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
             }
             double Jinv[D][D];
             const double det = cell_geometry<D>(X, Jinv);
-            if constexpr (OP == OP_NH_JACOBIAN) {
+            if constexpr (kHyperJac) {
                 if (a.mu_cell) mu_c = __ldg(a.mu_cell + cell);
                 if (a.lam_cell) lam_c = __ldg(a.lam_cell + cell);
             }
@@ -668,7 +688,7 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
                 mdet = narrow_pow2_ftz(m64, 0);
                 K = ed + ku[0] - a.tc_wshift;
                 if constexpr (OP == OP_ELASTICITY) K += km_el;
-                if constexpr (OP == OP_NH_JACOBIAN) {
+                if constexpr (kHyperJac) {
                     const int km = mat_shift(lam_c, mu_c);
                     K += km;
                     mu_c = ldexp(mu_c, -km);
@@ -696,7 +716,7 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
 #pragma unroll
                         for (int k = 0; k < D; ++k) {
                             Jh[i][k] = narrow_pow2_ftz(Jinv[i][k], kj);
-                            if constexpr (OP == OP_NH_JACOBIAN) Jf[i][k] = narrow_pow2_ftz(Jinv[i][k], 0);
+                            if constexpr (kHyperJac) Jf[i][k] = narrow_pow2_ftz(Jinv[i][k], 0);
                         }
                 }
             }
@@ -757,8 +777,8 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
             tc_fence_after();
 
             // ---- pointwise: this thread's cell at the chunk's points, E' into the quadrature A operand
-            if constexpr (OP == OP_NH_JACOBIAN) {
-                nh_ok &= tc_pointwise_nh_jacobian<D, T16>(L, tlane, hb, wd, t, ch, a.nq, good, ku[1], Jf, Jh, mu_c,
+            if constexpr (kHyperJac) {
+                nh_ok &= tc_pointwise_hyper_jacobian<OP, D, T16>(L, tlane, hb, wd, t, ch, a.nq, good, ku[1], Jf, Jh, mu_c,
                                                           lam_c);
             } else
             for (int blk = 0; blk < L.N1p / 16; ++blk) {

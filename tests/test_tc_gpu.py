@@ -138,6 +138,8 @@ def test_tc_edge_cases(fe):
     # forms without a tensor-core variant are refused
     with pytest.raises(Exception):
         fe.Plan(M, fe.NH_RESIDUAL, 6, mu=1.0, lam=1.0, precision="bf16")
+    with pytest.raises(Exception):
+        fe.Plan(M, fe.SVK_RESIDUAL, 6, mu=1.0, lam=1.0, precision="fp16")
 
 
 def test_tc_bad_index_sets_status(fe):
@@ -283,3 +285,22 @@ def test_tc_helmholtz_cell_scale(fe, prec):
         plan = fe.Plan(M, fe.HELMHOLTZ, 6, precision=prec)
         assert rel(plan.apply(cuda(u)), o.helmholtz(u)) <= TOL16[prec]
         assert plan.status() == 0
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+@pytest.mark.parametrize("dim,N,p,q", [(2, 13, 2, 4), (2, 13, 4, 8), (3, 5, 2, 4)])
+def test_tc_svk_jacobian(fe, dim, N, p, q, prec):
+    """St. Venant-Kirchhoff Jacobian action (the paper's hyperelastic law) on the
+    tensor cores: two 16-bit fields, FP64 law."""
+    from feinputs import lame_fields
+    from feinputs.fields import sinusoid_displacement
+    m, M = make(fe, dim, N, p, 800 + 10 * dim + p)
+    o = oracle.Oracle.from_mesh(m, q)
+    mu, lam = lame_fields(m.n_cells, 3)
+    ul = sinusoid_displacement(m, 4)
+    du = uniform_field(m.n_nodes * dim, 5)
+    plan = fe.Plan(M, fe.SVK_JACOBIAN, q, mu_cell=mu, lam_cell=lam, u_lin=cuda(ul), precision=prec)
+    assert plan.info.kernel == 2
+    err = rel(plan.apply(cuda(du)), o.svk_jacobian(ul, du, mu, lam))
+    assert 1e-7 < err <= TOL16[prec], err
+    assert plan.status() == 0
