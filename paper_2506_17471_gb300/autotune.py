@@ -72,7 +72,7 @@ def _coop_total_bytes(n, nq, dim, ncomp, C, fields, esz=8, tables_global=None):
         tables_global = nq * (1 + dim) * n * esz > SMEM_TABLE_MAX
     rs = ((1 + dim) * n) | 1
     ls = (fields * n * ncomp) | 1
-    es = (dim * ncomp) | 1
+    es = max(dim * ncomp, 1 + dim) | 1   # gradient terms, or value + gradient
     tab = 0 if tables_global else nq * rs * esz
     woff = (tab + 7) & ~7
     block = (woff + nq * 8 + nq * esz + 15) & ~15
@@ -89,10 +89,21 @@ def eta_simd(items: int, threads: int = COOP_BLOCK) -> float:
     return items / (threads * math.ceil(items / threads))
 
 
+# highest degree with a thread-per-cell variant, per (form, dimension)
+_TPC_MAX_DEGREE = {
+    (N.FE_FORM_MASS, 2): 6, (N.FE_FORM_MASS, 3): 4,
+    (N.FE_FORM_ELASTICITY, 2): 4, (N.FE_FORM_ELASTICITY, 3): 2,
+    (N.FE_FORM_NH_RESIDUAL, 2): 4, (N.FE_FORM_NH_RESIDUAL, 3): 2,
+    (N.FE_FORM_NH_JACOBIAN, 2): 4, (N.FE_FORM_NH_JACOBIAN, 3): 2,
+    (N.FE_FORM_LAPLACE, 2): 4, (N.FE_FORM_LAPLACE, 3): 2,
+    (N.FE_FORM_HELMHOLTZ, 2): 4, (N.FE_FORM_HELMHOLTZ, 3): 2,
+    (N.FE_FORM_SVK_RESIDUAL, 2): 3, (N.FE_FORM_SVK_RESIDUAL, 3): 2,
+    (N.FE_FORM_SVK_JACOBIAN, 2): 3, (N.FE_FORM_SVK_JACOBIAN, 3): 1,
+}
+
+
 def tpc_available(kind: int, dim: int, degree: int) -> bool:
-    if dim == 2:
-        return (kind == N.FE_FORM_MASS and degree <= 6) or degree <= 4
-    return (kind == N.FE_FORM_MASS and degree <= 4) or degree <= 2
+    return 1 <= degree <= _TPC_MAX_DEGREE.get((kind, dim), 0)
 
 
 def candidates(kind, dim, degree, nq, n_loc, ncomp, fields=1, eta_min=0.3, max_tiles=6):
@@ -184,7 +195,7 @@ def _save_cache(cache):
     os.replace(tmp, _CACHE_PATH)
 
 
-def tune(make_plan, u, key: str, kind, dim, degree, top_b: int = 3, reps: int = 5, use_cache=True,
+def tune(make_plan, u, key: str, kind, dim, degree, top_b: int = 9, reps: int = 5, use_cache=True,
          time_all: bool = False):
     """Pick the fastest launch configuration for one problem.
 
