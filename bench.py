@@ -386,10 +386,12 @@ def time_secondary(fe, torch, flush, M_el, u_el, y64_el):
         hp[f"{name}_n{N}"] = row
     out["hp_sweep"] = hp
 
+    # elasticity P1 3D at the paper's H200 problem size (~1e6 tets, its low-order case), and
     # the paper's other forms (Appendix A): Laplacian, Helmholtz (the paper's P4 rows),
     # St. Venant-Kirchhoff residual and Jacobian action
     forms = {}
     for name, kind, dim, p, N, q, scheme, precs in (
+            ("elasticity_p1_3d", fe.ELASTICITY, 3, 1, 55, 0, "conical", ("fp64", "fp32", "bf16")),
             ("laplace_p2_3d", fe.LAPLACE, 3, 2, 32, 2, "symmetric", ("fp64", "fp32", "bf16", "fp16")),
             ("helmholtz_p4_2d", fe.HELMHOLTZ, 2, 4, 256, 8, "symmetric", ("fp64", "fp32", "bf16", "fp16")),
             ("helmholtz_p4_3d", fe.HELMHOLTZ, 3, 4, 24, 8, "conical", ("fp64", "fp32", "bf16", "fp16")),
@@ -399,6 +401,8 @@ def time_secondary(fe, torch, flush, M_el, u_el, y64_el):
         M = fe.Mesh(dim, p, m.coords, m.cell2vertex, m.cell2node, m.n_nodes)
         nc = 1 if kind in (fe.LAPLACE, fe.HELMHOLTZ) else dim
         kw = {}
+        if kind == fe.ELASTICITY:
+            kw = dict(lam=1.25, mu=1.0)
         if kind in (fe.SVK_RESIDUAL, fe.SVK_JACOBIAN):
             mu, lam = lame_fields(m.n_cells, 8)
             kw = dict(mu_cell=mu, lam_cell=lam)

@@ -128,3 +128,15 @@ def test_forms_edge_cases(fe):
     u, y0 = uniform_field(m.n_nodes, 1), uniform_field(m.n_nodes, 2)
     y = fe.Plan(M, fe.LAPLACE, 2, accumulate=True).apply(cuda(u), cuda(y0.copy()))
     assert rel(y, y0 + o.laplace(u)) <= TOL
+
+
+def test_elasticity_p1_3d_paper_size(fe):
+    """Elasticity P1 on ~1e6 tetrahedra (the paper's H200 3D problem size, and the
+    case of its low-order traffic analysis): every output against the oracle."""
+    m, M = make(fe, 3, 55, 1, 55)
+    assert m.n_cells == 998250
+    o = oracle.Oracle.from_mesh(m, 0)
+    u = uniform_field(m.n_nodes * 3, 56)
+    plan = fe.Plan(M, fe.ELASTICITY, 0, lam=1.25, mu=1.0)
+    assert rel(plan.apply(cuda(u)), o.elasticity(u, 1.25, 1.0, threads=16)) <= TOL
+    assert plan.status() == 0
