@@ -295,13 +295,19 @@ int fe_plan_get_info(const fe_plan *plan, fe_plan_info *info);
  * degree, else cells-per-CTA), 0 thread-per-cell (tiles of 128 cells), 1
  * cells-per-CTA with tile_cells cells per tile (0: 16).
  * fe_batch_create validates, tabulates every problem, uploads the tables and
- * the cost-ordered work list, and allocates the batch's device memory
- * (synchronous).  Pointers inside the problems are borrowed and must outlive
- * the batch.  fe_batch_run enqueues two kernels on stream: one that zeroes
- * every y, and the persistent kernel whose CTAs pull tiles from the work list
- * (a CTA restages a problem's table only when the problem changes).  Runs of
- * one batch must not overlap in time.  fe_batch_status reads and clears the
- * batch's device status word (synchronises).
+ * the cost-ordered work lists (one per device code), and allocates the
+ * batch's device memory, a side stream and two events (synchronous).  Pointers
+ * inside the problems are borrowed and must outlive the batch.  fe_batch_run
+ * enqueues on stream a kernel that zeroes every y, then two persistent kernels
+ * whose CTAs pull tiles from their work lists (a CTA restages a problem's table
+ * only when the problem changes): one for the thread-per-cell problems (128
+ * threads per CTA), one for the cells-per-CTA problems (256 threads) on the
+ * batch's side stream, forked from and joined back to stream with events, so
+ * the two run concurrently and the whole run can be captured in a CUDA graph
+ * on stream.  Runs of one batch must not overlap in time.  fe_batch_status
+ * reads and clears the batch's device status word (synchronises).
+ * fe_batch_info: grid_blocks is the sum of the two grids, smem_bytes the
+ * larger of their dynamic shared memories.
  * Errors: FE_ERR_INVALID_ARG, FE_ERR_UNSUPPORTED, FE_ERR_NO_MEMORY, FE_ERR_CUDA. */
 typedef struct fe_batch_problem {
     fe_form form;

@@ -1,17 +1,19 @@
 // Batched persistent action: many independent meshes of uneven size, degree and
-// form in one launch.
+// form in one persistent launch per device code.
 //
-// The host builds a work list of items (problem, first cell), each a tile of
-// cells (one CTA's worth: 128 cells for the thread-per-cell code, C cells for
-// the cooperative code), sorted so that the most expensive problems' items come
-// first.  A persistent grid of CTAs pulls items from a global counter.  A CTA
-// stages a problem's table block into shared memory only when the problem
-// changes (one bulk async copy completing on an mbarrier whose phase it tracks;
-// waits are bounded), then runs the item with the device code chosen for that
-// problem: the thread-per-cell code instantiated for its (form, dimension,
-// degree), or the cooperative batch code (any degree).  All outputs are zeroed
-// by one multi-array kernel before the persistent launch; the pair can be
-// captured in a CUDA graph.
+// The host builds two work lists of items (problem, first cell), one per
+// device code: tiles of 128 cells for the problems run by the thread-per-cell
+// code, tiles of C cells for those run by the cooperative code, each list
+// sorted so that the most expensive problems' items come first.  Each list is
+// served by its own persistent kernel (128 threads per CTA and the registers of
+// the thread-per-cell paths; 256 threads and the registers of the cooperative
+// paths), so neither code runs with the other's occupancy.  A CTA pulls items
+// from its list's counter and stages a problem's table block into shared memory
+// only when the problem changes (one bulk async copy completing on an mbarrier
+// whose phase it tracks; waits are bounded).  All outputs are zeroed by one
+// multi-array kernel first; the two persistent kernels then run concurrently
+// (the second on a batch-owned stream forked from and joined back to the
+// caller's stream with events), and the whole can be captured in a CUDA graph.
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -21,7 +23,8 @@
 
 namespace fe {
 
-constexpr int kBatchBlock = 128;
+constexpr int kBatchBlock = 128;       // thread-per-cell code: one cell per thread
+constexpr int kBatchCoopBlock = 256;   // cooperative code: the per-problem kernel's block
 
 struct BatchProblemDev {
     ActionArgs a;        // pointers and sizes; a.tab points into the batch's table buffer
@@ -85,9 +88,11 @@ __device__ __forceinline__ void run_coop(const BatchProblemDev &P, unsigned char
     coop_batch<OP, D, double>(P.a, L, S, cell0, min(P.coop_cells, P.a.n_cells - cell0));
 }
 
-__global__ void __launch_bounds__(kBatchBlock) k_action_batched(const BatchProblemDev *__restrict__ probs,
-                                                                const BatchItem *__restrict__ items, int n_items,
-                                                                int32_t *sched, int32_t *status)
+// CODE 0: items of thread-per-cell problems; CODE 1: items of cooperative problems.
+template <int CODE>
+__global__ void __launch_bounds__(CODE == 0 ? kBatchBlock : kBatchCoopBlock)
+    k_action_batched(const BatchProblemDev *__restrict__ probs, const BatchItem *__restrict__ items, int n_items,
+                     int32_t *sched, int32_t *status)
 {
     extern __shared__ __align__(128) double smem[];
     __shared__ __align__(8) uint64_t bar;
@@ -131,7 +136,7 @@ __global__ void __launch_bounds__(kBatchBlock) k_action_batched(const BatchProbl
             staged = item.problem;
         }
         unsigned char *base = reinterpret_cast<unsigned char *>(smem);
-        if (P.kind == 0) {
+        if constexpr (CODE == 0) {
             const int cell = item.cell0 + (int)threadIdx.x;
             if (cell < P.a.n_cells) {
                 const double *tab = smem;
@@ -192,8 +197,13 @@ struct fe_batch {
     fe::BatchItem *d_items = nullptr;
     fe::ZeroSpan *d_spans = nullptr;
     double *d_tables = nullptr;
-    int32_t *d_words = nullptr;  // status [0], queue counters [4..5]
+    int32_t *d_words = nullptr;  // status [0]; queue counters: thread-per-cell [4..5], cooperative [6..7]
     int n_items = 0;
+    int n_items_code[2] = {0, 0};   // items per device code (thread-per-cell first in d_items)
+    int grid_code[2] = {0, 0};
+    size_t smem_code[2] = {0, 0};
+    cudaStream_t side = nullptr;    // the cooperative kernel's stream (forked from the caller's)
+    cudaEvent_t fork = nullptr, join = nullptr;
     int grid = 0;
     size_t smem = 0;
     long long max_dofs = 0;
@@ -212,6 +222,9 @@ void batch_free(fe_batch *b)
     cudaFree(b->d_spans);
     cudaFree(b->d_tables);
     cudaFree(b->d_words);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->join) cudaEventDestroy(b->join);
+    if (b->side) cudaStreamDestroy(b->side);
     delete b;
 }
 
@@ -283,6 +296,7 @@ extern "C" int fe_batch_create(const fe_batch_problem *problems, int count, fe_b
             return FE_ERR_UNSUPPORTED;
         }
         smem = std::max(smem, need);
+        b->smem_code[kind] = std::max(b->smem_code[kind], need);
         // staged block (table rows unless kept in global memory, then the weights
         // twice), followed for global-table problems by the phase-B [1+d][n][nq]
         // and phase-C [nq][1+d][n] tables; every piece an even number of doubles
@@ -346,15 +360,19 @@ extern "C" int fe_batch_create(const fe_batch_problem *problems, int count, fe_b
         b->dofs += spans[i].n;
         b->max_dofs = std::max(b->max_dofs, spans[i].n);
     }
-    // items: problems in decreasing cost, each problem's tiles in order
+    // items: per device code, problems in decreasing cost, each problem's tiles in
+    // order; the thread-per-cell list first, then the cooperative list
     std::vector<int> order(count);
     for (int i = 0; i < count; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
     std::vector<BatchItem> items;
-    for (int i : order) {
-        const int tile = probs[i].kind == 0 ? kBatchBlock : probs[i].coop_cells;
-        for (int c0 = 0; c0 < probs[i].a.n_cells; c0 += tile) items.push_back(BatchItem{i, c0});
-    }
+    for (int code = 0; code < 2; ++code)
+        for (int i : order) {
+            if (probs[i].kind != code) continue;
+            const int tile = code == 0 ? kBatchBlock : probs[i].coop_cells;
+            for (int c0 = 0; c0 < probs[i].a.n_cells; c0 += tile) items.push_back(BatchItem{i, c0});
+            b->n_items_code[code] += (probs[i].a.n_cells + tile - 1) / tile;
+        }
     b->n_items = (int)items.size();
     b->smem = smem;
     if (cudaMalloc(&b->d_tables, std::max<size_t>(table_doubles, 2) * 8) != cudaSuccess ||
@@ -385,17 +403,30 @@ extern "C" int fe_batch_create(const fe_batch_problem *problems, int count, fe_b
                                       cudaMemcpyHostToDevice) != cudaSuccess) ||
         cudaMemcpy(b->d_spans, spans.data(), sizeof(ZeroSpan) * count, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(b->d_words, 0, 8 * sizeof(int32_t)) != cudaSuccess ||
-        allow_max_dynamic_smem(reinterpret_cast<const void *>(k_action_batched)) != cudaSuccess) {
+        allow_max_dynamic_smem(reinterpret_cast<const void *>(k_action_batched<0>)) != cudaSuccess ||
+        allow_max_dynamic_smem(reinterpret_cast<const void *>(k_action_batched<1>)) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming) != cudaSuccess) {
         batch_free(b);
         return FE_ERR_CUDA;
     }
-    int per_sm = 0, sms = 0, dev = 0;
+    int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_action_batched, kBatchBlock, smem) != cudaSuccess ||
-        per_sm < 1)
-        per_sm = 1;
-    b->grid = std::max(1, std::min(per_sm * std::max(sms, 1), b->n_items));
+    const void *fn[2] = {reinterpret_cast<const void *>(k_action_batched<0>),
+                         reinterpret_cast<const void *>(k_action_batched<1>)};
+    const int block[2] = {kBatchBlock, kBatchCoopBlock};
+    b->grid = 0;
+    for (int code = 0; code < 2; ++code) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn[code], block[code], b->smem_code[code]) !=
+                cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
+        b->grid_code[code] = std::max(0, std::min(per_sm * std::max(sms, 1), b->n_items_code[code]));
+        b->grid += b->grid_code[code];
+    }
     *out = b;
     return FE_OK;
 }
@@ -409,10 +440,24 @@ extern "C" int fe_batch_run(fe_batch *b, void *stream)
     gx = std::max(1ll, std::min(gx, 256ll));
     k_zero_many<<<dim3((unsigned)gx, (unsigned)b->count), 256, 0, s>>>(b->d_spans);
     if (cudaGetLastError() != cudaSuccess) return FE_ERR_CUDA;
-    if (b->n_items == 0) return FE_OK;
-    k_action_batched<<<b->grid, kBatchBlock, b->smem, s>>>(b->d_probs, b->d_items, b->n_items, b->d_words + 4,
-                                                          b->d_words);
-    return cudaGetLastError() == cudaSuccess ? FE_OK : FE_ERR_CUDA;
+    const int n0 = b->n_items_code[0], n1 = b->n_items_code[1];
+    const bool both = n0 > 0 && n1 > 0;
+    // the cooperative kernel runs on the side stream, forked after the zero kernel
+    if (both && (cudaEventRecord(b->fork, s) != cudaSuccess || cudaStreamWaitEvent(b->side, b->fork, 0) != cudaSuccess))
+        return FE_ERR_CUDA;
+    if (n1 > 0) {
+        k_action_batched<1><<<b->grid_code[1], kBatchCoopBlock, b->smem_code[1], both ? b->side : s>>>(
+            b->d_probs, b->d_items + n0, n1, b->d_words + 6, b->d_words);
+        if (cudaGetLastError() != cudaSuccess) return FE_ERR_CUDA;
+    }
+    if (n0 > 0) {
+        k_action_batched<0><<<b->grid_code[0], kBatchBlock, b->smem_code[0], s>>>(b->d_probs, b->d_items, n0,
+                                                                                  b->d_words + 4, b->d_words);
+        if (cudaGetLastError() != cudaSuccess) return FE_ERR_CUDA;
+    }
+    if (both && (cudaEventRecord(b->join, b->side) != cudaSuccess || cudaStreamWaitEvent(s, b->join, 0) != cudaSuccess))
+        return FE_ERR_CUDA;
+    return FE_OK;
 }
 
 extern "C" int fe_batch_status(fe_batch *b, int *device_status)
@@ -422,7 +467,7 @@ extern "C" int fe_batch_status(fe_batch *b, int *device_status)
     if (cudaDeviceSynchronize() != cudaSuccess) return FE_ERR_CUDA;
     if (cudaMemcpy(w, b->d_words, sizeof(w), cudaMemcpyDeviceToHost) != cudaSuccess) return FE_ERR_CUDA;
     int32_t st = w[0];
-    if ((w[4] || w[5]) && st == FE_OK) st = FE_ERR_CUDA;
+    if ((w[4] || w[5] || w[6] || w[7]) && st == FE_OK) st = FE_ERR_CUDA;
     if (cudaMemset(b->d_words, 0, sizeof(w)) != cudaSuccess) return FE_ERR_CUDA;
     *device_status = st;
     return FE_OK;
