@@ -425,6 +425,61 @@ def time_secondary(fe, torch, flush, M_el, u_el, y64_el):
                 row[prec]["rel_dev_vs_fp64"] = rel(ys[prec], ys["fp64"])
         forms[f"{name}_n{N}"] = row
     out["other_forms"] = forms
+
+    # the paper's work-group study for the single-cell-per-work-item kernel, on
+    # its three representative forms (which are configs 1-3 here): threads per
+    # block of the thread-per-cell kernel
+    sweep = {}
+    for name, kind, dim, p, N, q, scheme, kw in (
+            ("mass_p2_2d_n64", fe.MASS, 2, 2, 64, 4, "conical", {}),
+            ("nh_residual_p4_2d_n256", fe.NH_RESIDUAL, 2, 4, 256, 8, "conical", "nh"),
+            ("elasticity_p2_3d_n32", fe.ELASTICITY, 3, 2, 32, 2, QUAD_SCHEME, dict(lam=1.25, mu=1.0))):
+        m = structured_mesh(dim, N, p, jitter=0.2 if dim == 2 else 0.15, seed=20250640 + N)
+        M = fe.Mesh(dim, p, m.coords, m.cell2vertex, m.cell2node, m.n_nodes)
+        if kw == "nh":
+            mu, lam = lame_fields(m.n_cells, 11)
+            kw = dict(mu_cell=mu, lam_cell=lam)
+            u = torch.from_numpy(sinusoid_displacement(m, 12)).cuda()
+        else:
+            u = torch.from_numpy(uniform_field(m.n_nodes * (1 if kind == fe.MASS else dim), 13)).cuda()
+        y = torch.empty_like(u)
+        row = {}
+        for block in (32, 64, 96, 128):
+            plan = fe.Plan(M, kind, q, tile_cells=block, quad_scheme=scheme, **kw)
+            row[f"block{block}_ms"] = timed(lambda: plan.apply(u, y)) * 1e3
+        best = min(row.values())
+        row["slowest_over_fastest"] = max(row.values()) / best
+        sweep[name] = row
+    out["tpc_block_sweep"] = sweep
+
+    # parameter sensitivity of the hp forms (the paper's Mass P3 2D, Hyper P6 2D,
+    # Elast P4 3D study): every candidate of the autotuner's space, timed
+    from paper_2506_17471_gb300 import autotune
+    sens = {}
+    for name, kind, dim, p, N, q in (("mass_p3_2d_n667", fe.MASS, 2, 3, 667, 6),
+                                     ("nh_jacobian_p6_2d_n236", fe.NH_JACOBIAN, 2, 6, 236, 12),
+                                     ("elasticity_p4_3d_n27", fe.ELASTICITY, 3, 4, 27, 6)):
+        m = structured_mesh(dim, N, p, jitter=0.2 if dim == 2 else 0.15, seed=20250620 + N)
+        M = fe.Mesh(dim, p, m.coords, m.cell2vertex, m.cell2node, m.n_nodes)
+        if kind == fe.NH_JACOBIAN:
+            mu, lam = lame_fields(m.n_cells, 2)
+            kw = dict(mu_cell=mu, lam_cell=lam, u_lin=torch.from_numpy(sinusoid_displacement(m, 3)).cuda())
+        elif kind == fe.ELASTICITY:
+            kw = dict(lam=1.25, mu=1.0)
+        else:
+            kw = {}
+        u = torch.from_numpy(uniform_field(m.n_nodes * (1 if kind == fe.MASS else dim), 4)).cuda()
+
+        def make_plan(c, M=M, kind=kind, q=q, kw=kw):
+            return fe.Plan(M, kind, q, cooperative=c.kernel == 1, tile_cells=c.tile_cells,
+                           tables_global=c.tables_global, **kw)
+
+        best, rep = autotune.tune(make_plan, u, "", kind, dim, p, use_cache=False, time_all=True, reps=3)
+        ms = rep["measured_s"]
+        sens[name] = {"candidates_ms": {k: v * 1e3 for k, v in ms.items()}, "best": rep["best"],
+                      "slowest_over_fastest": max(ms.values()) / min(ms.values()),
+                      "spearman": rep.get("spearman")}
+    out["param_sensitivity"] = sens
     return out
 
 

@@ -145,8 +145,9 @@ typedef struct fe_form {
     int32_t tile_cells;          /* cells per CTA batch of the cells-per-CTA kernel
                                     (0: the largest that leaves room for two CTAs
                                     per SM); tensor-core kernel: cells per CTA
-                                    (128, 256, 512; 0 automatic); ignored by the
-                                    thread-per-cell kernel                         */
+                                    (128, 256, 512; 0 automatic); thread-per-cell
+                                    kernel: threads (= cells) per block, 32, 64,
+                                    96 or 128 (0: 128; others FE_ERR_UNSUPPORTED) */
     int32_t quad_scheme;         /* enum fe_quad_scheme (0: conical product)        */
 } fe_form;
 

@@ -462,6 +462,15 @@ extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan 
     p->tab_doubles = tab_doubles;
     p->var = *v;
     p->adj = adj ? *adj : Variant{};
+    if (!coop && f.tile_cells > 0) {
+        // thread-per-cell: tile_cells is the block size (the paper's work-group size)
+        if (f.tile_cells % 32 != 0 || f.tile_cells > kTpcBlock) {
+            delete p;
+            return FE_ERR_UNSUPPORTED;
+        }
+        p->var.block = f.tile_cells;
+        if (adj) p->adj.block = f.tile_cells;
+    }
     p->smem_bytes = smem;
     cudaGetDevice(&p->device);
     p->coop_cells = coop_cells;
@@ -484,8 +493,8 @@ extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan 
         fe_plan_destroy(p);
         return FE_ERR_CUDA;
     }
-    p->grid_blocks = grid_for(*v, smem, m.n_cells, coop ? coop_cells : v->block);
-    p->adj_grid_blocks = adj ? grid_for(*adj, smem, m.n_cells, coop ? coop_cells : adj->block) : 0;
+    p->grid_blocks = grid_for(p->var, smem, m.n_cells, coop ? coop_cells : p->var.block);
+    p->adj_grid_blocks = adj ? grid_for(p->adj, smem, m.n_cells, coop ? coop_cells : p->adj.block) : 0;
     p->flops_per_cell = algorithmic_flops(op_of(f.kind), m.dim, n, nq);
     const double dofs = (double)m.n_nodes * ncomp;
     double bytes = 2.0 * dofs * 8.0 + (double)m.n_vertices * m.dim * 8.0 +

@@ -344,3 +344,20 @@ def test_full_elasticity_p2_3d_n32_symmetric_rule(fe):
     assert plan.info.nq == 4
     assert rel(plan.apply(cuda(u)), o.elasticity(u, 1.25, 1.0, threads=16)) <= TOL
     assert plan.status() == 0
+
+
+@pytest.mark.parametrize("block", [32, 64, 96, 128])
+def test_tpc_block_sizes(fe, block):
+    """Threads per block of the thread-per-cell kernel (the paper's work-group
+    size): every size gives the same action; other sizes are refused."""
+    m = structured_mesh(2, 20, 3, jitter=0.2, seed=61)
+    M = fe.Mesh(2, 3, m.coords, m.cell2vertex, m.cell2node, m.n_nodes)
+    o = oracle.Oracle.from_mesh(m, 4)
+    u = uniform_field(m.n_nodes * 2, 62)
+    plan = fe.Plan(M, fe.ELASTICITY, 4, lam=1.25, mu=1.0, tile_cells=block)
+    assert plan.info.kernel == 0 and plan.info.threads_per_block == block
+    y = plan.apply(torch.from_numpy(u).cuda()).cpu().numpy()
+    assert np.abs(y - o.elasticity(u, 1.25, 1.0)).max() <= 1e-12 * np.abs(y).max()
+    assert plan.status() == 0
+    with pytest.raises(Exception):
+        fe.Plan(M, fe.ELASTICITY, 4, lam=1.25, mu=1.0, tile_cells=48)
