@@ -34,6 +34,7 @@ FE_PREC_FP16 = 3
 FE_FLAG_ACCUMULATE = 1
 FE_FLAG_COOPERATIVE = 2
 FE_FLAG_TABLES_GLOBAL = 4
+FE_FLAG_GATHER_SCATTER = 8
 
 # every symbol declared in include/feaction.h
 FE_QUAD_CONICAL = 0

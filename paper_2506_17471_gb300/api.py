@@ -115,7 +115,8 @@ class Plan:
     def __init__(self, mesh: Mesh, kind: int, quad_degree: int, *, lam: float = 0.0,
                  mu: float = 0.0, mu_cell=None, lam_cell=None, u_lin=None,
                  accumulate: bool = False, precision: str = "fp64", cooperative: bool = False,
-                 tile_cells: int = 0, tables_global: bool = False, quad_scheme: str = "conical"):
+                 tile_cells: int = 0, tables_global: bool = False, quad_scheme: str = "conical",
+                 gather_scatter: bool = False):
         self.mesh = mesh
         self.kind = int(kind)
         self.ncomp = 1 if kind in SCALAR_FORMS else mesh.dim
@@ -127,7 +128,8 @@ class Plan:
         self.u_lin = None if u_lin is None else torch.as_tensor(
             u_lin, dtype=torch.float64, device=dev).clone().contiguous()
         flags = ((N.FE_FLAG_ACCUMULATE if accumulate else 0) | (N.FE_FLAG_COOPERATIVE if cooperative else 0)
-                 | (N.FE_FLAG_TABLES_GLOBAL if tables_global else 0))
+                 | (N.FE_FLAG_TABLES_GLOBAL if tables_global else 0)
+                 | (N.FE_FLAG_GATHER_SCATTER if gather_scatter else 0))
         if precision not in PRECISIONS:
             raise ValueError(f"precision must be one of {sorted(PRECISIONS)}")
         self.precision = precision

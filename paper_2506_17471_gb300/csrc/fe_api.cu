@@ -226,6 +226,82 @@ __global__ void k_dfma(double *out, int iters, double b, double c)
     out[tid] = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
 }
 
+// Node-gather scatter: y[node] (+)= the node's incident cell outputs, summed in
+// the fixed order of the incidence list (T: the stored type; float sums in
+// float, then widens exactly).
+template <typename T, int NC>
+__global__ void k_gather_nodes(const int32_t *__restrict__ ptr, const int32_t *__restrict__ inc,
+                               const T *__restrict__ cell_out, double *__restrict__ y, int n_nodes, int accumulate)
+{
+    for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < n_nodes; node += gridDim.x * blockDim.x) {
+        T s[NC];
+#pragma unroll
+        for (int m = 0; m < NC; ++m) s[m] = T(0);
+        const int e = __ldg(ptr + node + 1);
+        for (int k = __ldg(ptr + node); k < e; ++k) {
+            const T *v = cell_out + (size_t)__ldg(inc + k) * NC;
+#pragma unroll
+            for (int m = 0; m < NC; ++m) s[m] += __ldg(v + m);
+        }
+#pragma unroll
+        for (int m = 0; m < NC; ++m) {
+            const double sm = cvt<double>(s[m]);
+            double *dst = y + (size_t)node * NC + m;
+            *dst = accumulate ? *dst + sm : sm;
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_gather(const fe_plan *p, double *y, cudaStream_t st)
+{
+    const int n = p->mesh.n_nodes;
+    if (n <= 0) return cudaSuccess;
+    const int block = 256;
+    const int grid = std::max(1, std::min((n + block - 1) / block, num_sms() * 16));
+    const int acc = (p->form.flags & FE_FLAG_ACCUMULATE) ? 1 : 0;
+    const T *co = static_cast<const T *>(p->d_cell_out);
+    switch (p->ncomp) {
+    case 1: k_gather_nodes<T, 1><<<grid, block, 0, st>>>(p->d_node_ptr, p->d_node_inc, co, y, n, acc); break;
+    case 2: k_gather_nodes<T, 2><<<grid, block, 0, st>>>(p->d_node_ptr, p->d_node_inc, co, y, n, acc); break;
+    default: k_gather_nodes<T, 3><<<grid, block, 0, st>>>(p->d_node_ptr, p->d_node_inc, co, y, n, acc); break;
+    }
+    return cudaGetLastError();
+}
+
+// FE_FLAG_GATHER_SCATTER: node -> (cell * n_loc + j) incidences from a host
+// snapshot of cell2node (cells in increasing order: the summation order), and
+// the per-cell output buffer.
+int build_gather(fe_plan *p)
+{
+    const long long nc = p->mesh.n_cells, n = p->n_loc, nn = p->mesh.n_nodes;
+    if (nc * n >= (1ll << 31)) return FE_ERR_UNSUPPORTED;
+    std::vector<int32_t> c2n((size_t)(nc * n));
+    if (nc > 0 && cudaMemcpy(c2n.data(), p->mesh.cell2node, c2n.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return FE_ERR_CUDA;
+    std::vector<int32_t> ptr((size_t)nn + 1, 0);
+    for (int32_t v : c2n)
+        if (v >= 0 && v < nn) ++ptr[(size_t)v + 1];
+    for (long long i = 0; i < nn; ++i) ptr[i + 1] += ptr[i];
+    std::vector<int32_t> inc((size_t)ptr[nn] + 1), pos(ptr.begin(), ptr.end() - 1);
+    for (long long k = 0; k < nc * n; ++k) {
+        const int32_t v = c2n[k];
+        if (v >= 0 && v < nn) inc[pos[v]++] = (int32_t)k;
+    }
+    p->cell_out_f32 = p->form.precision == FE_PREC_FP32;
+    const size_t esz = p->cell_out_f32 ? sizeof(float) : sizeof(double);
+    if (cudaMalloc(&p->d_cell_out, std::max<size_t>((size_t)(nc * n) * p->ncomp * esz, 16)) != cudaSuccess ||
+        cudaMalloc(&p->d_node_ptr, ptr.size() * 4) != cudaSuccess ||
+        cudaMalloc(&p->d_node_inc, inc.size() * 4) != cudaSuccess) {
+        cudaGetLastError();
+        return FE_ERR_NO_MEMORY;
+    }
+    if (cudaMemcpy(p->d_node_ptr, ptr.data(), ptr.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(p->d_node_inc, inc.data(), inc.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+        return FE_ERR_CUDA;
+    return FE_OK;
+}
+
 }  // namespace
 }  // namespace fe
 
@@ -349,6 +425,13 @@ static int plan_create_tc(const fe_form &f, const fe_mesh &m, const Variant &v, 
     p->bytes_min = 2.0 * dofs * 8.0 + (double)m.n_vertices * m.dim * 8.0 + (double)m.n_cells * (n + m.dim + 1) * 4.0;
     if (f.kind == FE_FORM_NH_JACOBIAN)
         p->bytes_min += dofs * 8.0 + (f.mu_cell ? 8.0 * m.n_cells : 0.0) + (f.lambda_cell ? 8.0 * m.n_cells : 0.0);
+    if (f.flags & FE_FLAG_GATHER_SCATTER) {
+        const int rc = build_gather(p);
+        if (rc != FE_OK) {
+            fe_plan_destroy(p);
+            return rc;
+        }
+    }
     *out = p;
     return FE_OK;
 }
@@ -504,6 +587,13 @@ extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan 
     if (hyper) bytes += (f.mu_cell ? 8.0 * m.n_cells : 0.0) + (f.lambda_cell ? 8.0 * m.n_cells : 0.0);
     if (f.kind == FE_FORM_NH_JACOBIAN || f.kind == FE_FORM_SVK_JACOBIAN) bytes += dofs * 8.0;
     p->bytes_min = bytes;
+    if (f.flags & FE_FLAG_GATHER_SCATTER) {
+        const int rc = build_gather(p);
+        if (rc != FE_OK) {
+            fe_plan_destroy(p);
+            return rc;
+        }
+    }
     *out = p;
     return FE_OK;
 }
@@ -514,6 +604,9 @@ extern "C" int fe_plan_destroy(fe_plan *plan)
     cudaDeviceSynchronize();
     cudaFree(plan->d_tab);
     cudaFree(plan->d_status);
+    cudaFree(plan->d_cell_out);
+    cudaFree(plan->d_node_ptr);
+    cudaFree(plan->d_node_inc);
     if (plan->pipe_ready) {
         for (cudaEvent_t e : plan->pipe_ev) cudaEventDestroy(e);
         cudaStreamDestroy(plan->pipe_h2d);
@@ -551,6 +644,7 @@ static ActionArgs make_args(const fe_plan *p, const double *u, double *y)
     a.tc_qc = p->tc_qc;
     a.tc_pipes = p->tc_pipes;
     a.tc_wshift = p->tc_wshift;
+    a.cell_out = p->d_cell_out;
     return a;
 }
 
@@ -564,13 +658,18 @@ extern "C" int fe_action(fe_plan *plan, const double *u, double *y, void *stream
                              (plan->form.u_lin && reinterpret_cast<uintptr_t>(plan->form.u_lin) % 16 != 0)))
         return FE_ERR_INVALID_ARG;  // vector gathers of 2-component nodes load 16 B at once
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (!(plan->form.flags & FE_FLAG_ACCUMULATE)) {
+    const bool gather = plan->d_cell_out != nullptr;
+    if (!(plan->form.flags & FE_FLAG_ACCUMULATE) && !gather) {
         if (launch_zero(y, n, s) != cudaSuccess) return FE_ERR_CUDA;
     }
-    if (plan->mesh.n_cells == 0) return FE_OK;
     ActionArgs a = make_args(plan, u, y);
-    if (plan->var.launch(a, plan->grid_blocks, plan->var.block, plan->smem_bytes, s) != cudaSuccess)
+    if (plan->mesh.n_cells > 0 &&
+        plan->var.launch(a, plan->grid_blocks, plan->var.block, plan->smem_bytes, s) != cudaSuccess)
         return FE_ERR_CUDA;
+    if (gather) {
+        const cudaError_t e = plan->cell_out_f32 ? launch_gather<float>(plan, y, s) : launch_gather<double>(plan, y, s);
+        if (e != cudaSuccess) return FE_ERR_CUDA;
+    }
     return FE_OK;
 }
 
@@ -589,6 +688,7 @@ extern "C" int fe_action_adjoint(fe_plan *plan, const double *u, const double *w
     }
     if (plan->mesh.n_cells == 0) return FE_OK;
     ActionArgs a = make_args(plan, w, jtw);
+    a.cell_out = nullptr;   // the adjoint adds into jtw atomically
     a.u_lin = u;
     a.sched = plan->d_sched + 2;
     a.dmu = dmu;

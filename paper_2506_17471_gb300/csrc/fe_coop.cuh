@@ -365,10 +365,18 @@ __device__ __forceinline__ void coop_batch(const ActionArgs &a, const CoopLayout
     __syncthreads();
 
     // ---- C: quadrature contraction + scatter per (cell, node)
+    const bool store = OP != OP_NH_ADJOINT && a.cell_out;   // node-gather scatter
     for (int i = threadIdx.x; i < nb * n; i += blockDim.x) {
         const int c = i / n, j = i - c * n;
         const int node = snodes[c * n + j];
-        if (node < 0 || sgeo[c * 16 + D * D + 3] == 0.0) continue;
+        if (node < 0 || sgeo[c * 16 + D * D + 3] == 0.0) {
+            if (store) {
+                R *o = static_cast<R *>(a.cell_out) + ((size_t)(cell0 + c) * n + j) * NC;
+#pragma unroll
+                for (int m = 0; m < NC; ++m) o[m] = R(0);
+            }
+            continue;
+        }
         R out[NC];
 #pragma unroll
         for (int m = 0; m < NC; ++m) out[m] = R(0);
@@ -394,8 +402,14 @@ __device__ __forceinline__ void coop_batch(const ActionArgs &a, const CoopLayout
                 }
             }
         }
+        if (store) {
+            R *o = static_cast<R *>(a.cell_out) + ((size_t)(cell0 + c) * n + j) * NC;
 #pragma unroll
-        for (int m = 0; m < NC; ++m) atomicAdd(a.y + (size_t)node * NC + m, cvt<double>(out[m]));
+            for (int m = 0; m < NC; ++m) o[m] = out[m];
+        } else {
+#pragma unroll
+            for (int m = 0; m < NC; ++m) atomicAdd(a.y + (size_t)node * NC + m, cvt<double>(out[m]));
+        }
     }
     if constexpr (OP == OP_NH_ADJOINT) {
         for (int c = threadIdx.x; c < nb; c += blockDim.x) {

@@ -41,6 +41,10 @@ struct ActionArgs {
     int32_t tc_qc;            // tensor-core kernel: quadrature points per chunk
     int32_t tc_pipes;         // tensor-core kernel: 128-cell pipelines per CTA (1, 2 or 4)
     int32_t tc_wshift;        // tensor-core kernel: staged weights are w_q 2^tc_wshift
+    // Node-gather scatter (FE_FLAG_GATHER_SCATTER): when non-null the action stores
+    // each cell's outputs to cell_out[cell][j][comp] (float for FP32 contractions,
+    // double otherwise) instead of adding them into y; skipped cells store zeros.
+    void *cell_out;
 };
 
 // Launch function of one compiled kernel variant.
@@ -112,6 +116,11 @@ struct fe_plan {
     double bytes_min;
     // fe_action_host_pipelined: two copy streams and, per buffer pair b, the
     // events h2d done, action done, d2h done (created on first use)
+    // FE_FLAG_GATHER_SCATTER: per-cell outputs and the node -> (cell*n + j) incidences
+    void *d_cell_out = nullptr;
+    int32_t *d_node_ptr = nullptr;   // [n_nodes + 1]
+    int32_t *d_node_inc = nullptr;   // [incidences]
+    int cell_out_f32 = 0;
     cudaStream_t pipe_h2d = nullptr, pipe_d2h = nullptr;
     cudaEvent_t pipe_ev[6] = {};
     bool pipe_ready = false;

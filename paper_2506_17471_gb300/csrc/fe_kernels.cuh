@@ -417,6 +417,17 @@ __host__ __device__ constexpr size_t table_weights_offset_bytes(int nq, int d, i
     return ((size_t)nq * (d + 1) * n * sizeof(R) + 7) & ~(size_t)7;
 }
 
+// Node-gather scatter: a skipped cell's outputs are zeros, so that the gather
+// does not sum values of an earlier call.
+template <int N, int NC, typename R>
+__device__ __forceinline__ void store_zero_cell(const ActionArgs &a, int cell)
+{
+    if (!a.cell_out) return;
+    R *o = static_cast<R *>(a.cell_out) + (size_t)cell * N * NC;
+#pragma unroll
+    for (int i = 0; i < N * NC; ++i) o[i] = R(0);
+}
+
 // One cell of Algorithm 2 for operation OP, contractions in R.  Geometry, the
 // quadrature weights, the Neo-Hookean kinematics/stress and the scatter are
 // always FP64.
@@ -441,6 +452,7 @@ __device__ __forceinline__ void action_cell(const ActionArgs &a, const R *__rest
     ok &= gather_nodes<D, N, NC>(a.c2n, cell, a.n_nodes, nodes);
     if (!ok) {
         set_status(a.status, FE_ERR_INDEX);
+        store_zero_cell<N, NC, R>(a, cell);
         return;
     }
     double X[D + 1][D];
@@ -460,6 +472,7 @@ __device__ __forceinline__ void action_cell(const ActionArgs &a, const R *__rest
     const double det = cell_geometry<D>(X, Jinv);
     if (!(det != 0.0) || !isfinite(det)) {
         set_status(a.status, FE_ERR_BAD_MESH);
+        store_zero_cell<N, NC, R>(a, cell);
         return;
     }
     const double absdet = fabs(det);
@@ -671,11 +684,20 @@ __device__ __forceinline__ void action_cell(const ActionArgs &a, const R *__rest
     }
     if (!nh_ok) set_status(a.status, FE_ERR_NONFINITE);
 
-    // scatter-add in FP64 (Algorithm 2 scatter; cross-cell races resolved with atomics)
+    // scatter (Algorithm 2): FP64 atomics into y, or the cell's outputs stored for
+    // the node-gather scatter (the adjoint always adds into its output)
+    if (OP != OP_NH_ADJOINT && a.cell_out) {
+        R *o = static_cast<R *>(a.cell_out) + (size_t)cell * N * NC;
 #pragma unroll
-    for (int j = 0; j < N; ++j)
+        for (int j = 0; j < N; ++j)
 #pragma unroll
-        for (int c = 0; c < NC; ++c) atomicAdd(a.y + (size_t)nodes[j] * NC + c, cvt<double>(out[j][c]));
+            for (int c = 0; c < NC; ++c) o[j * NC + c] = out[j][c];
+    } else {
+#pragma unroll
+        for (int j = 0; j < N; ++j)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) atomicAdd(a.y + (size_t)nodes[j] * NC + c, cvt<double>(out[j][c]));
+    }
     if constexpr (OP == OP_NH_ADJOINT) {
         a.dmu[cell] = acc_mu;   // one thread per cell: plain stores, no reduction
         a.dlam[cell] = acc_lam;

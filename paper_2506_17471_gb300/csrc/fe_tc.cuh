@@ -894,7 +894,19 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
 #pragma unroll
             for (int m = 0; m < NC; ++m) tc_ld16(tlane + (uint32_t)(L.acc1_cols + m * L.N2p + blk * 16), r[m]);
             tc_wait_ld();
-            if (good) {
+            if (a.cell_out && t < nb) {
+                // node-gather scatter: store this cell's outputs (zeros for a skipped cell)
+                double *o = static_cast<double *>(a.cell_out) + (size_t)(tile * kTcRows + t) * n * NC;
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int j = blk * 16 + i;
+                    if (j < n) {
+#pragma unroll
+                        for (int m = 0; m < NC; ++m)
+                            o[j * NC + m] = good ? widen_pow2(__uint_as_float(r[m][i]) * mdet, K) : 0.0;
+                    }
+                }
+            } else if (good && !a.cell_out) {
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
                     const int j = blk * 16 + i;
