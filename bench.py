@@ -293,12 +293,12 @@ def time_secondary(fe, torch, flush, M_el, u_el, y64_el):
         "ir_s": t_ir, "ir_outer": stir.outer, "ir_inner_iters": stir.iterations,
         "ir_rel_residual_fp64": stir.rel_residual, "speedup": t_cg / t_ir,
         "note": "relative residuals are true FP64 residuals ||M(b - A_64 x)|| / ||M b||"}
-    for prec in ("bf16", "fp16"):
+    for prec in ("bf16", "fp16", "fp16x2"):
         plo = fe.Plan(M_el, fe.ELASTICITY, 2, lam=1.25, mu=1.0, precision=prec, quad_scheme=QUAD_SCHEME)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         _, st = solvers.cg_ir(lambda a, c: p64.apply(a, c), lambda a, c: plo.apply(a, c), b, free,
-                              tol=1e-10, inner_rtol=1e-2)
+                              tol=1e-10, inner_rtol=1e-5 if prec == "fp16x2" else 1e-2)
         torch.cuda.synchronize()
         t_lo = time.perf_counter() - t0
         out["cg_ir_elasticity_p2_3d_n32"][f"{prec}_inner"] = {
@@ -338,20 +338,20 @@ def time_secondary(fe, torch, flush, M_el, u_el, y64_el):
         "fp64_cg_s": t_cg, "fp64_cg_iters": st64.iterations, "fp64_cg_rel_residual": st64.rel_residual,
         "ir_s": t_ir, "ir_outer": stir.outer, "ir_inner_iters": stir.iterations,
         "ir_rel_residual_fp64": stir.rel_residual, "speedup": t_cg / t_ir}
-    for prec in ("bf16", "fp16"):
+    for prec in ("bf16", "fp16", "fp16x2"):
         plo = fe.Plan(M, fe.MASS, 6, precision=prec)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         _, st = solvers.cg_ir(lambda a, c: p64.apply(a, c), lambda a, c: plo.apply(a, c), b, tol=1e-10,
-                              inner_rtol=1e-2)
+                              inner_rtol=1e-5 if prec == "fp16x2" else 1e-2)
         torch.cuda.synchronize()
         t_lo = time.perf_counter() - t0
         out["cg_ir_mass_p3_2d_n667"][f"{prec}_inner"] = {
             "ir_s": t_lo, "ir_outer": st.outer, "ir_inner_iters": st.iterations,
             "ir_rel_residual_fp64": st.rel_residual, "speedup": t_cg / t_lo}
 
-    # hp sweep at ~4M and ~16M DoFs: FP64, FP32 contractions, and BF16 / FP16
-    # tensor-core contractions (kernel 2)
+    # hp sweep at ~4M and ~16M DoFs: FP64, FP32 contractions, and BF16 / FP16 / split
+    # FP16 (hi + lo) tensor-core contractions (kernel 2)
     hp = {}
     for name, dim, p, N, q in (("nh_jacobian_p6_2d", 2, 6, 236, 12), ("nh_jacobian_p6_2d", 2, 6, 471, 12),
                                ("elasticity_p4_3d", 3, 4, 27, 6), ("elasticity_p4_3d", 3, 4, 43, 6),
@@ -372,7 +372,7 @@ def time_secondary(fe, torch, flush, M_el, u_el, y64_el):
         u = torch.from_numpy(uniform_field(m.n_nodes * nc, 4)).cuda()
         row = {"dofs": m.n_nodes * nc, "cells": m.n_cells}
         ys = {}
-        for prec in ("fp64", "fp32", "bf16", "fp16"):
+        for prec in ("fp64", "fp32", "bf16", "fp16", "fp16x2"):
             plan = fe.Plan(M, kind, q, precision=prec, **extra_kw)
             ys[prec] = torch.empty_like(u)
             t = timed(lambda: plan.apply(u, ys[prec]), reps=5)
@@ -392,8 +392,9 @@ def time_secondary(fe, torch, flush, M_el, u_el, y64_el):
     forms = {}
     for name, kind, dim, p, N, q, scheme, precs in (
             ("elasticity_p1_3d", fe.ELASTICITY, 3, 1, 55, 0, "conical", ("fp64", "fp32", "bf16")),
-            ("laplace_p2_3d", fe.LAPLACE, 3, 2, 32, 2, "symmetric", ("fp64", "fp32", "bf16", "fp16")),
-            ("helmholtz_p4_2d", fe.HELMHOLTZ, 2, 4, 256, 8, "symmetric", ("fp64", "fp32", "bf16", "fp16")),
+            ("laplace_p2_3d", fe.LAPLACE, 3, 2, 32, 2, "symmetric", ("fp64", "fp32", "bf16", "fp16", "fp16x2")),
+            ("helmholtz_p4_2d", fe.HELMHOLTZ, 2, 4, 256, 8, "symmetric",
+             ("fp64", "fp32", "bf16", "fp16", "fp16x2")),
             ("helmholtz_p4_3d", fe.HELMHOLTZ, 3, 4, 24, 8, "conical", ("fp64", "fp32", "bf16", "fp16")),
             ("svk_residual_p4_2d", fe.SVK_RESIDUAL, 2, 4, 256, 8, "symmetric", ("fp64", "fp32")),
             ("svk_jacobian_p4_2d", fe.SVK_JACOBIAN, 2, 4, 256, 8, "symmetric", ("fp64", "fp32"))):

@@ -96,9 +96,14 @@ enum fe_precision {
                                 FP32 accumulation in tensor memory; geometry FP64, linear
                                 stress FP32, scatter-add FP64.  Any degree with at most
                                 256 local nodes.  Error: see fe_plan_create.            */
-    FE_PREC_FP16 = 3         /* as FE_PREC_BF16 with IEEE binary16 operands (3 more
+    FE_PREC_FP16 = 3,        /* as FE_PREC_BF16 with IEEE binary16 operands (3 more
                                 significand bits, smaller range; the per-cell power-of-two
                                 scaling keeps the operands O(1))                        */
+    FE_PREC_FP16X2 = 4       /* tensor-core kernel with every operand split into a pair of
+                                binary16 values (hi + the rounding of the remainder, ~22
+                                significand bits) and three products per term (hi*hi,
+                                hi*lo, lo*hi): error of the same class as FE_PREC_FP32 at
+                                tensor-core speed                                       */
 };
 
 /* Flags for fe_form.flags */
@@ -214,15 +219,17 @@ typedef struct fe_plan fe_plan;
  *   FE_PREC_FP32  <= 5e-5 (each contraction's forward error is at most
  *                 gamma_256 of its absolute terms; measured 1e-7 - 6e-7);
  *   FE_PREC_BF16, FE_PREC_FP16  <= 8 u16 with u16 = 2^-8 (BF16) or 2^-11
- *                 (FP16), i.e. 3.1e-2 / 3.9e-3 (measured 0.6 - 4.3 u16).
+ *                 (FP16), i.e. 3.1e-2 / 3.9e-3 (measured 0.6 - 4.3 u16);
+ *   FE_PREC_FP16X2 <= 5e-5 (the FP32 bound).
  *
- * Tensor-core plans (FE_PREC_BF16 / FE_PREC_FP16): kinds MASS, ELASTICITY,
+ * Tensor-core plans (FE_PREC_BF16 / FE_PREC_FP16 / FE_PREC_FP16X2): kinds MASS, ELASTICITY,
  * LAPLACE, HELMHOLTZ, NH_JACOBIAN and SVK_JACOBIAN (the residual kinds:
  * FE_ERR_UNSUPPORTED); cell2node must be 16-byte
  * aligned (FE_ERR_INVALID_ARG otherwise); tile_cells selects the 128-cell
  * pipelines per CTA (0 automatic, 128, 256 or 512; other values
  * FE_ERR_UNSUPPORTED); FE_ERR_UNSUPPORTED also if the degree has more than 256
- * local nodes or the tables and operands do not fit one SM.
+ * local nodes or the tables and operands do not fit one SM (FE_PREC_FP16X2
+ * doubles both).
  * Errors: FE_ERR_INVALID_ARG, FE_ERR_UNSUPPORTED, FE_ERR_NO_MEMORY, FE_ERR_CUDA. */
 int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan **out);
 

@@ -31,6 +31,7 @@ FE_PREC_FP64 = 0
 FE_PREC_FP32 = 1
 FE_PREC_BF16 = 2
 FE_PREC_FP16 = 3
+FE_PREC_FP16X2 = 4
 FE_FLAG_ACCUMULATE = 1
 FE_FLAG_COOPERATIVE = 2
 FE_FLAG_TABLES_GLOBAL = 4

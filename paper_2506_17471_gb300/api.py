@@ -28,7 +28,7 @@ FORM_NAMES = {MASS: "mass", ELASTICITY: "elasticity", NH_RESIDUAL: "nh_residual"
 SCALAR_FORMS = (MASS, LAPLACE, HELMHOLTZ)
 # contraction precision of a plan (include/feaction.h, enum fe_precision)
 PRECISIONS = {"fp64": N.FE_PREC_FP64, "fp32": N.FE_PREC_FP32, "bf16": N.FE_PREC_BF16,
-              "fp16": N.FE_PREC_FP16}
+              "fp16": N.FE_PREC_FP16, "fp16x2": N.FE_PREC_FP16X2}
 
 
 def _stream_ptr(stream=None) -> ctypes.c_void_p:

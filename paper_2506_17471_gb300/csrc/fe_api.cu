@@ -28,6 +28,7 @@ void init_registry()
     n += register_variants_3d(g_variants + n, kMaxVariants - n);
     n += register_variants_coop(g_variants + n, kMaxVariants - n);
     n += register_variants_tc(g_variants + n, kMaxVariants - n);
+    n += register_variants_tc2(g_variants + n, kMaxVariants - n);
     n += register_variants_forms(g_variants + n, kMaxVariants - n);
     n += register_variants_coop_forms(g_variants + n, kMaxVariants - n);
     g_nvariants = n;
@@ -35,7 +36,7 @@ void init_registry()
 
 // The thread-per-cell variant compiled for exactly this degree, else (or when
 // forced) the cooperative variant, which serves every degree.
-// The 16-bit precisions have only the tensor-core kernel (any degree).
+// The 16-bit precisions (single or split) have only the tensor-core kernel (any degree).
 const Variant *find_variant(int form, int dim, int degree, int op, int precision, bool force_coop)
 {
     std::call_once(g_once, init_registry);
@@ -68,14 +69,15 @@ int coop_cells_for(int n, int nq, int dim, int ncomp, int fields, size_t esz, si
 // count force_pipes asks for) whose staged tables, operands and accumulators
 // fit the SM's shared memory and 512 TMEM columns, with the fewest
 // quadrature-point chunks.  Returns false if nothing fits.
-bool tc_choose(int n, int nq, int ncomp, int kd, int fields, size_t smem_cap, int force_pipes, TcLayout *out)
+bool tc_choose(int n, int nq, int ncomp, int kd, int fields, size_t smem_cap, int force_pipes, int terms,
+               TcLayout *out)
 {
     if (n > 256 || nq < 1) return false;
     for (int pipes = kTcMaxPipes; pipes >= 1; pipes /= 2) {
         if (force_pipes && pipes != force_pipes) continue;
         for (int nch = 1; nch <= nq; ++nch) {
             const int qc = (nq + nch - 1) / nch;
-            const TcLayout L = tc_layout(n, nq, ncomp, kd, fields, qc, pipes);
+            const TcLayout L = tc_layout(n, nq, ncomp, kd, fields, qc, pipes, terms);
             if (L.N1p > 256 || L.N2p > 256 || L.tmem_cols > 512) continue;
             if (L.total > smem_cap || L.staged_bytes >= (1u << 20)) continue;
             *out = L;
@@ -323,6 +325,21 @@ extern "C" const char *fe_status_string(int status)
     }
 }
 
+// Value of a binary16 / bfloat16 bit pattern (exact), on the host.
+template <typename T16>
+static double small_to_double(uint16_t b)
+{
+    constexpr int EB = std::is_same<T16, __nv_bfloat16>::value ? 8 : 5;
+    constexpr int MB = 15 - EB;
+    constexpr int bias = (1 << (EB - 1)) - 1;
+    const int e = (b >> MB) & ((1 << EB) - 1);
+    const int mant = b & ((1 << MB) - 1);
+    const double sgn = (b >> 15) ? -1.0 : 1.0;
+    if (e == (1 << EB) - 1) return mant ? NAN : sgn * INFINITY;
+    if (e == 0) return sgn * std::ldexp((double)mant, 1 - bias - MB);
+    return sgn * std::ldexp((double)(mant | (1 << MB)), e - bias - MB);
+}
+
 // Plan of the tensor-core kernel: the staged block holds Phi (evaluation GEMM
 // B operand, rows = chunk columns (q, k), K = node j) and Phi^T (quadrature
 // GEMM B operand, rows = node j, K = (q, k) over all chunks) rounded to the
@@ -335,6 +352,7 @@ static void tc_fill_block(const TcLayout &L, int kind, const std::vector<double>
     blk.assign(L.staged_bytes, 0);
     uint16_t *B1 = reinterpret_cast<uint16_t *>(blk.data() + L.b1_off);
     uint16_t *B2 = reinterpret_cast<uint16_t *>(blk.data() + L.b2_off);
+    const size_t b1_region = (size_t)L.nch * L.N1p * L.K1p, b2_region = (size_t)L.N2p * L.K2;
     for (int ch = 0; ch < L.nch; ++ch)
         for (int ql = 0; ql < L.qc; ++ql) {
             const int q = ch * L.qc + ql;
@@ -344,9 +362,16 @@ static void tc_fill_block(const TcLayout &L, int kind, const std::vector<double>
                 // value row first for the forms that use values, then the derivatives
                 const int kt = (kind == FE_FORM_MASS || kind == FE_FORM_HELMHOLTZ) ? k : 1 + k;
                 for (int j = 0; j < L.n; ++j) {
-                    const uint16_t bits = to16_bits<T16>(tab[((size_t)kt * L.nq + q) * L.n + j]);
+                    const double tv = tab[((size_t)kt * L.nq + q) * L.n + j];
+                    const uint16_t bits = to16_bits<T16>(tv);
                     B1[tc_off(row, j, L.K1p)] = bits;
                     B2[tc_off(j, row, L.K2)] = bits;
+                    if (L.terms == 2) {
+                        // lo term: the rounding of the remainder
+                        const uint16_t lo = to16_bits<T16>(tv - small_to_double<T16>(bits));
+                        B1[b1_region + tc_off(row, j, L.K1p)] = lo;
+                        B2[b2_region + tc_off(j, row, L.K2)] = lo;
+                    }
                 }
             }
         }
@@ -373,7 +398,9 @@ static int plan_create_tc(const fe_form &f, const fe_mesh &m, const Variant &v, 
         return FE_ERR_UNSUPPORTED;
     TcLayout L;
     const int fields = (f.kind == FE_FORM_NH_JACOBIAN || f.kind == FE_FORM_SVK_JACOBIAN) ? 2 : 1;
-    if (!tc_choose(n, nq, ncomp, kd, fields, (size_t)optin - 256, f.tile_cells / kTcRows, &L)) return FE_ERR_UNSUPPORTED;
+    const int terms = f.precision == FE_PREC_FP16X2 ? 2 : 1;
+    if (!tc_choose(n, nq, ncomp, kd, fields, (size_t)optin - 256, f.tile_cells / kTcRows, terms, &L))
+        return FE_ERR_UNSUPPORTED;
     // weights scaled by 2^wshift into [1/2, 1) at their largest, so w_q E' stays
     // in binary16's normal range for rules with very small weights
     double wmax = 0.0;
@@ -385,7 +412,7 @@ static int plan_create_tc(const fe_form &f, const fe_mesh &m, const Variant &v, 
     if (f.precision == FE_PREC_BF16)
         tc_fill_block<__nv_bfloat16>(L, f.kind, wts, tab, wshift, blk);
     else
-        tc_fill_block<__half>(L, f.kind, wts, tab, wshift, blk);
+        tc_fill_block<__half>(L, f.kind, wts, tab, wshift, blk);   // binary16, single or split
 
     fe_plan *p = new (std::nothrow) fe_plan();
     if (!p) return FE_ERR_NO_MEMORY;
@@ -448,8 +475,8 @@ extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan 
     // 2D vertex coordinates are gathered as one 16-byte load per vertex
     if (m.dim == 2 && reinterpret_cast<uintptr_t>(m.coords) % 16 != 0) return FE_ERR_INVALID_ARG;
     if (f.kind < FE_FORM_MASS || f.kind > FE_FORM_SVK_JACOBIAN) return FE_ERR_INVALID_ARG;
-    if (f.precision < FE_PREC_FP64 || f.precision > FE_PREC_FP16) return FE_ERR_UNSUPPORTED;
-    const bool tc = f.precision == FE_PREC_BF16 || f.precision == FE_PREC_FP16;
+    if (f.precision < FE_PREC_FP64 || f.precision > FE_PREC_FP16X2) return FE_ERR_UNSUPPORTED;
+    const bool tc = f.precision == FE_PREC_BF16 || f.precision == FE_PREC_FP16 || f.precision == FE_PREC_FP16X2;
     if (tc && (f.kind == FE_FORM_NH_RESIDUAL || f.kind == FE_FORM_SVK_RESIDUAL)) return FE_ERR_UNSUPPORTED;
     if (f.quad_degree < 0 || f.quad_degree > 40) return FE_ERR_INVALID_ARG;
     if ((f.kind == FE_FORM_NH_JACOBIAN || f.kind == FE_FORM_SVK_JACOBIAN) && !f.u_lin) return FE_ERR_INVALID_ARG;

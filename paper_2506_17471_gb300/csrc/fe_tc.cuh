@@ -70,6 +70,7 @@ struct TcLayout {
     int N1p, K1p;                // evaluation GEMM: N (chunk columns), K (n padded to 16)
     int N2p, K2;                 // quadrature GEMM: N (n padded to 16), K (nch * N1p)
     int pipes;
+    int terms;                   // 16-bit terms per operand: 1, or 2 (hi + lo binary16 pairs)
     size_t b1_off, b2_off, wd_off, wf_off, staged_bytes;   // staged block
     size_t a1_off, a2_off, nodes_off, pipe_bytes;          // per-pipeline scratch (from its base)
     size_t total;                                          // dynamic shared memory
@@ -78,7 +79,8 @@ struct TcLayout {
 
 __host__ __device__ inline int tc_kdp(int kd) { return kd == 1 ? 1 : (kd == 2 ? 2 : 4); }
 
-__host__ __device__ inline TcLayout tc_layout(int n, int nq, int NC, int KD, int F, int qc, int pipes)
+__host__ __device__ inline TcLayout tc_layout(int n, int nq, int NC, int KD, int F, int qc, int pipes,
+                                              int terms = 1)
 {
     TcLayout L;
     L.n = n;
@@ -94,14 +96,16 @@ __host__ __device__ inline TcLayout tc_layout(int n, int nq, int NC, int KD, int
     L.N2p = tc_round_up(n, 16);
     L.K2 = L.nch * L.N1p;
     L.pipes = pipes;
+    L.terms = terms;
+    // every operand region is repeated per term (term 0 = hi, term 1 = lo)
     L.b1_off = 0;
-    L.b2_off = (size_t)L.nch * L.N1p * L.K1p * 2;
-    L.wd_off = L.b2_off + (size_t)L.N2p * L.K2 * 2;
+    L.b2_off = (size_t)terms * L.nch * L.N1p * L.K1p * 2;
+    L.wd_off = L.b2_off + (size_t)terms * L.N2p * L.K2 * 2;
     L.wf_off = L.wd_off + (size_t)nq * 8;
     L.staged_bytes = tc_round_up_sz(L.wf_off + (size_t)nq * 4, 128);
     L.a1_off = 0;
-    L.a2_off = L.a1_off + (size_t)F * NC * kTcRows * L.K1p * 2;
-    L.nodes_off = L.a2_off + (size_t)NC * kTcRows * L.N1p * 2;
+    L.a2_off = L.a1_off + (size_t)terms * F * NC * kTcRows * L.K1p * 2;
+    L.nodes_off = L.a2_off + (size_t)terms * NC * kTcRows * L.N1p * 2;
     L.pipe_bytes = tc_round_up_sz(L.nodes_off + (size_t)(n | 1) * kTcRows * 4, 128);   // nodes [128][n | 1]
     L.total = L.staged_bytes + (size_t)pipes * L.pipe_bytes;
     L.acc1_cols = F * NC * L.N1p;
@@ -264,6 +268,42 @@ __device__ __forceinline__ uint32_t pack2<__half>(float lo, float hi)
     return *reinterpret_cast<const uint32_t *>(&v);
 }
 
+// The two 16-bit values of a packed pair back in binary32.
+template <typename T16>
+__device__ __forceinline__ float2 unpack2(uint32_t w);
+template <>
+__device__ __forceinline__ float2 unpack2<__nv_bfloat16>(uint32_t w)
+{
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w));
+}
+template <>
+__device__ __forceinline__ float2 unpack2<__half>(uint32_t w)
+{
+    return __half22float2(*reinterpret_cast<const __half2 *>(&w));
+}
+
+// Stores 8 consecutive K entries (16 bytes) of one operand row: term 0 is the
+// 16-bit rounding of v; with TERMS == 2 term 1, region_elems further on, holds
+// the 16-bit rounding of the remainder v - term0 (a hi + lo pair, ~2 x the
+// significand bits).
+template <typename T16, int TERMS>
+__device__ __forceinline__ void store8(T16 *p, size_t region_elems, const float (&v)[8])
+{
+    uint32_t w[4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) w[h] = pack2<T16>(v[2 * h], v[2 * h + 1]);
+    *reinterpret_cast<uint4 *>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+    if constexpr (TERMS == 2) {
+        uint32_t r[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const float2 hi = unpack2<T16>(w[h]);
+            r[h] = pack2<T16>(v[2 * h] - hi.x, v[2 * h + 1] - hi.y);
+        }
+        *reinterpret_cast<uint4 *>(p + region_elems) = make_uint4(r[0], r[1], r[2], r[3]);
+    }
+}
+
 __device__ __forceinline__ uint64_t tc_smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
 {
     return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)((lbo & 0x3FFFF) >> 4) << 16) |
@@ -377,7 +417,7 @@ __device__ __forceinline__ bool tc_wait(uint32_t sbar, uint32_t parity)
 // log det F and the tangent applied to H; St. Venant-Kirchhoff: E, S, dE, dS,
 // dP = H S + F dS — the same algebra as the FP64 kernels).  E' = w_q e is
 // rounded to 16 bits.  Returns false if det F <= 0 at a live Neo-Hookean point.
-template <int OP, int D, typename T16>
+template <int OP, int D, typename T16, int TERMS>
 __device__ __forceinline__ bool tc_pointwise_hyper_jacobian(const TcLayout &L, uint32_t tlane, unsigned char *hb,
                                                             const double *wd, int t, int ch, int nq, bool good,
                                                             int ku_lin, const float (&Jf)[D][D],
@@ -474,17 +514,15 @@ __device__ __forceinline__ bool tc_pointwise_hyper_jacobian(const TcLayout &L, u
         }
 #pragma unroll
         for (int m = 0; m < NC; ++m) {
-            T16 *A2 = reinterpret_cast<T16 *>(hb + L.a2_off) + (size_t)m * kTcRows * L.N1p;
-            uint32_t w[4];
-#pragma unroll
-            for (int h = 0; h < 4; ++h) w[h] = pack2<T16>(out[m][2 * h], out[m][2 * h + 1]);
-            *reinterpret_cast<uint4 *>(A2 + tc_off(t, blk * 8, L.N1p)) = make_uint4(w[0], w[1], w[2], w[3]);
+            const size_t region = (size_t)kTcRows * L.N1p;
+            T16 *A2 = reinterpret_cast<T16 *>(hb + L.a2_off) + (size_t)m * TERMS * region;
+            store8<T16, TERMS>(A2 + tc_off(t, blk * 8, L.N1p), region, out[m]);
         }
     }
     return ok;
 }
 
-template <int OP, int D, typename T16>
+template <int OP, int D, typename T16, int TERMS>
 __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const ActionArgs a)
 {
     constexpr int NC = OpTraits<OP, D>::NC;
@@ -504,7 +542,7 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
     __shared__ uint32_t s_tmem;
     __shared__ int s_tile[kTcMaxPipes];
 
-    const TcLayout L = tc_layout(a.coop_n, a.nq, NC, KD, F, a.tc_qc, a.tc_pipes);
+    const TcLayout L = tc_layout(a.coop_n, a.nq, NC, KD, F, a.tc_qc, a.tc_pipes, TERMS);
     const int tid = threadIdx.x, pipe = tid >> 7, t = tid & (kTcRows - 1), warp = tid >> 5;
     const int n = L.n;
     const uint32_t bar0 = (uint32_t)__cvta_generic_to_shared(&bars[0]);
@@ -737,14 +775,26 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
                     for (int m = 0; m < NC; ++m) v[s][m] = nd[s] >= 0 ? __ldg(uf + (size_t)nd[s] * NC + m) : 0.0;
 #pragma unroll
                 for (int m = 0; m < NC; ++m) {
-                    uint32_t w[4];
+                    const size_t region = (size_t)kTcRows * L.K1p;
+                    T16 *A1 = reinterpret_cast<T16 *>(hb + L.a1_off) + (size_t)(f * NC + m) * TERMS * region;
+                    if constexpr (TERMS == 1) {
+                        // one term: binary64 rounded to 16 bits directly
+                        uint32_t w[4];
 #pragma unroll
-                    for (int h = 0; h < 4; ++h)
-                        w[h] = (uint32_t)to16_bits<T16>(nd[2 * h] >= 0 ? v[2 * h][m] - off[f][m] : 0.0, ku[f]) |
-                               ((uint32_t)to16_bits<T16>(nd[2 * h + 1] >= 0 ? v[2 * h + 1][m] - off[f][m] : 0.0, ku[f])
-                                << 16);
-                    T16 *A1 = reinterpret_cast<T16 *>(hb + L.a1_off) + (size_t)(f * NC + m) * kTcRows * L.K1p;
-                    *reinterpret_cast<uint4 *>(A1 + tc_off(t, j0, L.K1p)) = make_uint4(w[0], w[1], w[2], w[3]);
+                        for (int h = 0; h < 4; ++h)
+                            w[h] = (uint32_t)to16_bits<T16>(nd[2 * h] >= 0 ? v[2 * h][m] - off[f][m] : 0.0, ku[f]) |
+                                   ((uint32_t)to16_bits<T16>(nd[2 * h + 1] >= 0 ? v[2 * h + 1][m] - off[f][m] : 0.0,
+                                                             ku[f])
+                                    << 16);
+                        *reinterpret_cast<uint4 *>(A1 + tc_off(t, j0, L.K1p)) = make_uint4(w[0], w[1], w[2], w[3]);
+                    } else {
+                        // hi + lo pair from the scaled value in binary32
+                        float xs[8];
+#pragma unroll
+                        for (int s = 0; s < 8; ++s)
+                            xs[s] = nd[s] >= 0 ? narrow_pow2_ftz(v[s][m] - off[f][m], ku[f]) : 0.f;
+                        store8<T16, TERMS>(A1 + tc_off(t, j0, L.K1p), region, xs);
+                    }
                 }
             }
         }
@@ -758,14 +808,18 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
             // ---- evaluation GEMM of chunk ch (its commit also covers the previous chunk's quadrature GEMM)
             if (t == 0) {
                 const uint32_t sbo = (uint32_t)L.K1p * 16u;
+                const uint32_t a_region = (uint32_t)(kTcRows * L.K1p * 2), b_region = (uint32_t)(L.nch * L.N1p * L.K1p * 2);
                 for (int m = 0; m < F * NC; ++m)
-                    for (int s = 0; s < L.K1p / 16; ++s) {
-                        const uint64_t da =
-                            tc_smem_desc(a1s + (uint32_t)(m * kTcRows * L.K1p * 2) + (uint32_t)s * 256u, 128u, sbo);
-                        const uint64_t db =
-                            tc_smem_desc(b1s + (uint32_t)(ch * L.N1p * L.K1p * 2) + (uint32_t)s * 256u, 128u, sbo);
-                        tc_mma(tpipe + (uint32_t)(m * L.N1p), da, db, id1, s > 0 ? 1u : 0u);
-                    }
+                    for (int s = 0; s < L.K1p / 16; ++s)
+                        // one product, or hi*hi + hi*lo + lo*hi for split operands
+                        for (int pr = 0; pr < (TERMS == 2 ? 3 : 1); ++pr) {
+                            const uint32_t ta = pr == 2 ? 1u : 0u, tb = pr == 1 ? 1u : 0u;
+                            const uint64_t da = tc_smem_desc(
+                                a1s + ((uint32_t)m * TERMS + ta) * a_region + (uint32_t)s * 256u, 128u, sbo);
+                            const uint64_t db = tc_smem_desc(
+                                b1s + tb * b_region + (uint32_t)(ch * L.N1p * L.K1p * 2) + (uint32_t)s * 256u, 128u, sbo);
+                            tc_mma(tpipe + (uint32_t)(m * L.N1p), da, db, id1, (s > 0 || pr > 0) ? 1u : 0u);
+                        }
                 tc_commit(barp);
             }
             if (!pipe_all(pipe, tc_wait(barp, phase))) {
@@ -778,7 +832,7 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
 
             // ---- pointwise: this thread's cell at the chunk's points, E' into the quadrature A operand
             if constexpr (kHyperJac) {
-                nh_ok &= tc_pointwise_hyper_jacobian<OP, D, T16>(L, tlane, hb, wd, t, ch, a.nq, good, ku[1], Jf, Jh, mu_c,
+                nh_ok &= tc_pointwise_hyper_jacobian<OP, D, T16, TERMS>(L, tlane, hb, wd, t, ch, a.nq, good, ku[1], Jf, Jh, mu_c,
                                                           lam_c);
             } else
             for (int blk = 0; blk < L.N1p / 16; ++blk) {
@@ -850,13 +904,16 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
                 }
 #pragma unroll
                 for (int m = 0; m < NC; ++m) {
-                    T16 *A2 = reinterpret_cast<T16 *>(hb + L.a2_off) + (size_t)m * kTcRows * L.N1p;
-                    uint32_t w[8];
+                    const size_t region = (size_t)kTcRows * L.N1p;
+                    T16 *A2 = reinterpret_cast<T16 *>(hb + L.a2_off) + (size_t)m * TERMS * region;
+                    float first[8], second[8];
 #pragma unroll
-                    for (int h = 0; h < 8; ++h) w[h] = pack2<T16>(v[m][2 * h], v[m][2 * h + 1]);
-                    *reinterpret_cast<uint4 *>(A2 + tc_off(t, blk * 16, L.N1p)) = make_uint4(w[0], w[1], w[2], w[3]);
-                    *reinterpret_cast<uint4 *>(A2 + tc_off(t, blk * 16 + 8, L.N1p)) =
-                        make_uint4(w[4], w[5], w[6], w[7]);
+                    for (int i = 0; i < 8; ++i) {
+                        first[i] = v[m][i];
+                        second[i] = v[m][8 + i];
+                    }
+                    store8<T16, TERMS>(A2 + tc_off(t, blk * 16, L.N1p), region, first);
+                    store8<T16, TERMS>(A2 + tc_off(t, blk * 16 + 8, L.N1p), region, second);
                 }
             }
             fence_async_smem();
@@ -867,15 +924,18 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
             // ---- quadrature GEMM of chunk ch, accumulated over the chunks
             if (t == 0) {
                 const uint32_t sboa = (uint32_t)L.N1p * 16u, sbob = (uint32_t)L.K2 * 16u;
+                const uint32_t a_region = (uint32_t)(kTcRows * L.N1p * 2), b_region = (uint32_t)(L.N2p * L.K2 * 2);
                 for (int m = 0; m < NC; ++m)
-                    for (int s = 0; s < L.N1p / 16; ++s) {
-                        const uint64_t da =
-                            tc_smem_desc(a2s + (uint32_t)(m * kTcRows * L.N1p * 2) + (uint32_t)s * 256u, 128u, sboa);
-                        const uint64_t db =
-                            tc_smem_desc(b2s + (uint32_t)((ch * L.N1p / 16 + s) * 256), 128u, sbob);
-                        tc_mma(tpipe + (uint32_t)(L.acc1_cols + m * L.N2p), da, db, id2,
-                               (ch > 0 || s > 0) ? 1u : 0u);
-                    }
+                    for (int s = 0; s < L.N1p / 16; ++s)
+                        for (int pr = 0; pr < (TERMS == 2 ? 3 : 1); ++pr) {
+                            const uint32_t ta = pr == 2 ? 1u : 0u, tb = pr == 1 ? 1u : 0u;
+                            const uint64_t da = tc_smem_desc(
+                                a2s + ((uint32_t)m * TERMS + ta) * a_region + (uint32_t)s * 256u, 128u, sboa);
+                            const uint64_t db = tc_smem_desc(
+                                b2s + tb * b_region + (uint32_t)((ch * L.N1p / 16 + s) * 256), 128u, sbob);
+                            tc_mma(tpipe + (uint32_t)(L.acc1_cols + m * L.N2p), da, db, id2,
+                                   (ch > 0 || s > 0 || pr > 0) ? 1u : 0u);
+                        }
             }
         }
         if (timed_out) break;
@@ -935,14 +995,15 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
     leave_queue(a.sched);
 }
 
-template <int OP, int D, typename T16>
+template <int OP, int D, typename T16, int TERMS>
 cudaError_t launch_tc(const ActionArgs &a, int grid, int block, size_t smem, cudaStream_t s)
 {
-    k_action_tc<OP, D, T16><<<grid, block, smem, s>>>(a);
+    k_action_tc<OP, D, T16, TERMS><<<grid, block, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-template <int OP, int D, typename T16>
+// TERMS == 2 (binary16 hi + lo pairs) is the FE_PREC_FP16X2 precision.
+template <int OP, int D, typename T16, int TERMS = 1>
 Variant make_tc_variant()
 {
     Variant v;
@@ -950,11 +1011,11 @@ Variant make_tc_variant()
     v.dim = D;
     v.degree = 0;   // any degree with at most 256 local nodes
     v.op = 0;
-    v.precision = std::is_same<T16, __nv_bfloat16>::value ? FE_PREC_BF16 : FE_PREC_FP16;
+    v.precision = TERMS == 2 ? FE_PREC_FP16X2 : (std::is_same<T16, __nv_bfloat16>::value ? FE_PREC_BF16 : FE_PREC_FP16);
     v.kernel_id = 2;   // 128-cell tensor-core tiles
     v.block = kTcRows;
-    v.launch = &launch_tc<OP, D, T16>;
-    v.func = reinterpret_cast<const void *>(&k_action_tc<OP, D, T16>);
+    v.launch = &launch_tc<OP, D, T16, TERMS>;
+    v.func = reinterpret_cast<const void *>(&k_action_tc<OP, D, T16, TERMS>);
     return v;
 }
 

@@ -304,3 +304,48 @@ def test_tc_svk_jacobian(fe, dim, N, p, q, prec):
     err = rel(plan.apply(cuda(du)), o.svk_jacobian(ul, du, mu, lam))
     assert 1e-7 < err <= TOL16[prec], err
     assert plan.status() == 0
+
+
+TOL_X2 = 5e-5   # split binary16 operands: the FP32 bound
+
+
+@pytest.mark.parametrize("kind,dim,N,p,q", [("mass", 2, 13, 3, 6), ("elasticity", 3, 5, 2, 2),
+                                            ("elasticity", 3, 5, 4, 6), ("laplace", 2, 13, 4, 6),
+                                            ("helmholtz", 3, 5, 3, 6), ("elasticity", 2, 13, 6, 10)])
+def test_tc_fp16x2(fe, kind, dim, N, p, q):
+    """Split binary16 operands (hi + lo) with three tensor-core products per term:
+    error of the FP32 class, far below the single 16-bit rounding."""
+    m, M = make(fe, dim, N, p, 900 + 10 * dim + p)
+    o = oracle.Oracle.from_mesh(m, q)
+    nc = 1 if kind in ("mass", "laplace", "helmholtz") else dim
+    u = uniform_field(m.n_nodes * nc, 14 + p)
+    kw = dict(lam=1.25, mu=1.0) if kind == "elasticity" else {}
+    plan = fe.Plan(M, getattr(fe, kind.upper()), q, precision="fp16x2", **kw)
+    assert plan.info.kernel == 2
+    ref = o.elasticity(u, 1.25, 1.0) if kind == "elasticity" else getattr(o, kind)(u)
+    err = rel(plan.apply(cuda(u)), ref)
+    assert 1e-10 < err <= TOL_X2, err
+    assert plan.status() == 0
+
+
+def test_tc_fp16x2_nh_jacobian(fe):
+    from feinputs import lame_fields
+    from feinputs.fields import sinusoid_displacement
+    m, M = make(fe, 2, 13, 4, 950)
+    o = oracle.Oracle.from_mesh(m, 8)
+    mu, lam = lame_fields(m.n_cells, 3)
+    ul = sinusoid_displacement(m, 4)
+    du = uniform_field(m.n_nodes * 2, 5)
+    plan = fe.Plan(M, fe.NH_JACOBIAN, 8, mu_cell=mu, lam_cell=lam, u_lin=cuda(ul), precision="fp16x2")
+    assert rel(plan.apply(cuda(du)), o.nh_jacobian(ul, du, mu, lam)) <= TOL_X2
+    assert plan.status() == 0
+
+
+def test_tc_fp16x2_tables_too_large(fe):
+    """The split operands double the staged basis tables; Helmholtz P4 3D with 125
+    quadrature points then exceeds shared memory and the plan is refused cleanly."""
+    m, M = make(fe, 3, 3, 4, 960)
+    with pytest.raises(fe.FeError) as e:
+        fe.Plan(M, fe.HELMHOLTZ, 8, precision="fp16x2")
+    assert e.value.code == 2
+    assert fe.Plan(M, fe.HELMHOLTZ, 8, precision="fp16").info.kernel == 2
