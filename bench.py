@@ -271,6 +271,14 @@ def time_secondary(fe, torch, flush, M_el, u_el, y64_el):
     out["elasticity_p2_3d_n32_fp32"] = {
         "ms": t32 * 1e3, "dofs_per_s": nd / t32, "speedup_vs_fp64": t64 / t32,
         "rel_dev_vs_fp64": rel(y32, y64_el)}
+    # the same workload with TF32 tensor-core contractions (FP32 accumulate, FP64
+    # geometry and scatter)
+    ptf = fe.Plan(M_el, fe.ELASTICITY, 2, lam=1.25, mu=1.0, precision="tf32", quad_scheme=QUAD_SCHEME)
+    ytf = torch.empty_like(u_el)
+    ttf = timed(lambda: ptf.apply(u_el, ytf))
+    out["elasticity_p2_3d_n32_tf32"] = {
+        "ms": ttf * 1e3, "dofs_per_s": nd / ttf, "speedup_vs_fp64": t64 / ttf,
+        "rel_dev_vs_fp64": rel(ytf, y64_el), "kernel": ptf.info.kernel}
 
     # CG with FP64 iterative refinement, clamped boundary, b = M A_64 x*
     free = torch.from_numpy(np.repeat(~_BOUNDARY[0], 3).astype(np.uint8)).cuda()
@@ -351,7 +359,7 @@ def time_secondary(fe, torch, flush, M_el, u_el, y64_el):
             "ir_rel_residual_fp64": st.rel_residual, "speedup": t_cg / t_lo}
 
     # hp sweep at ~4M and ~16M DoFs: FP64, FP32 contractions, and BF16 / FP16 / split
-    # FP16 (hi + lo) tensor-core contractions (kernel 2)
+    # FP16 (hi + lo) / TF32 tensor-core contractions (kernel 2)
     hp = {}
     for name, dim, p, N, q in (("nh_jacobian_p6_2d", 2, 6, 236, 12), ("nh_jacobian_p6_2d", 2, 6, 471, 12),
                                ("elasticity_p4_3d", 3, 4, 27, 6), ("elasticity_p4_3d", 3, 4, 43, 6),
@@ -372,7 +380,7 @@ def time_secondary(fe, torch, flush, M_el, u_el, y64_el):
         u = torch.from_numpy(uniform_field(m.n_nodes * nc, 4)).cuda()
         row = {"dofs": m.n_nodes * nc, "cells": m.n_cells}
         ys = {}
-        for prec in ("fp64", "fp32", "bf16", "fp16", "fp16x2"):
+        for prec in ("fp64", "fp32", "bf16", "fp16", "fp16x2", "tf32"):
             plan = fe.Plan(M, kind, q, precision=prec, **extra_kw)
             ys[prec] = torch.empty_like(u)
             t = timed(lambda: plan.apply(u, ys[prec]), reps=5)

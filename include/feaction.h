@@ -99,11 +99,16 @@ enum fe_precision {
     FE_PREC_FP16 = 3,        /* as FE_PREC_BF16 with IEEE binary16 operands (3 more
                                 significand bits, smaller range; the per-cell power-of-two
                                 scaling keeps the operands O(1))                        */
-    FE_PREC_FP16X2 = 4       /* tensor-core kernel with every operand split into a pair of
+    FE_PREC_FP16X2 = 4,      /* tensor-core kernel with every operand split into a pair of
                                 binary16 values (hi + the rounding of the remainder, ~22
                                 significand bits) and three products per term (hi*hi,
                                 hi*lo, lo*hi): error of the same class as FE_PREC_FP32 at
                                 tensor-core speed                                       */
+    FE_PREC_TF32 = 5         /* as FE_PREC_BF16 with TF32 operands (tcgen05 kind::tf32:
+                                binary32 containers rounded to nearest even to 10
+                                fraction bits, 8 exponent bits; 4 bytes per operand, so
+                                the staged tables and operands take twice the shared
+                                memory of the 16-bit types)                             */
 };
 
 /* Flags for fe_form.flags */
@@ -218,18 +223,18 @@ typedef struct fe_plan fe_plan;
  *                 except where the action itself is ill-conditioned in FP64);
  *   FE_PREC_FP32  <= 5e-5 (each contraction's forward error is at most
  *                 gamma_256 of its absolute terms; measured 1e-7 - 6e-7);
- *   FE_PREC_BF16, FE_PREC_FP16  <= 8 u16 with u16 = 2^-8 (BF16) or 2^-11
- *                 (FP16), i.e. 3.1e-2 / 3.9e-3 (measured 0.6 - 4.3 u16);
+ *   FE_PREC_BF16, FE_PREC_FP16, FE_PREC_TF32  <= 8 u16 with u16 = 2^-8 (BF16)
+ *                 or 2^-11 (FP16, TF32), i.e. 3.1e-2 / 3.9e-3 (measured 0.6 - 4.3 u16);
  *   FE_PREC_FP16X2 <= 5e-5 (the FP32 bound).
  *
- * Tensor-core plans (FE_PREC_BF16 / FE_PREC_FP16 / FE_PREC_FP16X2): kinds MASS, ELASTICITY,
+ * Tensor-core plans (FE_PREC_BF16 / FE_PREC_FP16 / FE_PREC_FP16X2 / FE_PREC_TF32): kinds MASS, ELASTICITY,
  * LAPLACE, HELMHOLTZ, NH_JACOBIAN and SVK_JACOBIAN (the residual kinds:
  * FE_ERR_UNSUPPORTED); cell2node must be 16-byte
  * aligned (FE_ERR_INVALID_ARG otherwise); tile_cells selects the 128-cell
  * pipelines per CTA (0 automatic, 128, 256 or 512; other values
  * FE_ERR_UNSUPPORTED); FE_ERR_UNSUPPORTED also if the degree has more than 256
  * local nodes or the tables and operands do not fit one SM (FE_PREC_FP16X2
- * doubles both).
+ * and FE_PREC_TF32 double both).
  * Errors: FE_ERR_INVALID_ARG, FE_ERR_UNSUPPORTED, FE_ERR_NO_MEMORY, FE_ERR_CUDA. */
 int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan **out);
 
@@ -453,6 +458,15 @@ int fe_selftest_conversions16(const double *x, long long n, unsigned long long *
  * the bit patterns.  Errors: FE_ERR_INVALID_ARG (NULL with n > 0),
  * FE_ERR_UNSUPPORTED (another precision). */
 int fe_round16(const double *x, size_t n, int precision, uint16_t *bits);
+
+/* Host function.  Rounds x[n] (host) to TF32 to nearest even, as a TF32 plan
+ * rounds its operands: from_binary32 = 0 rounds the binary64 value directly
+ * (the tables and the DoFs), from_binary32 != 0 first rounds it to binary32
+ * and then to TF32 (the pointwise results, which the kernel holds in
+ * binary32).  bits[n] (host, caller-owned) receives the binary32 container bit
+ * patterns (13 low fraction bits zero).  Errors: FE_ERR_INVALID_ARG (NULL with
+ * n > 0). */
+int fe_round_tf32(const double *x, size_t n, int from_binary32, uint32_t *bits);
 
 #ifdef __cplusplus
 }

@@ -12,9 +12,10 @@ from .api import (MASS, ELASTICITY, NH_RESIDUAL, NH_JACOBIAN, LAPLACE, HELMHOLTZ
                   SVK_JACOBIAN, FORM_NAMES, PRECISIONS, QUAD_SCHEMES,
                   Mesh, Plan,
                   PlanInfo,
-                  NeoHookeanResidual, Batch, tabulate, measure_fp64_peak)
+                  NeoHookeanResidual, Batch, tabulate, measure_fp64_peak, action)
+from .solvers import cg, cg_ir
 
 __all__ = ["FeError", "LIB_PATH", "EXPORTS", "MASS", "ELASTICITY", "NH_RESIDUAL", "NH_JACOBIAN",
            "LAPLACE", "HELMHOLTZ", "SVK_RESIDUAL", "SVK_JACOBIAN",
            "FORM_NAMES", "PRECISIONS", "QUAD_SCHEMES", "Mesh", "Plan", "PlanInfo", "NeoHookeanResidual", "Batch", "tabulate",
-           "measure_fp64_peak"]
+           "measure_fp64_peak", "action", "cg", "cg_ir"]

@@ -28,7 +28,7 @@ FORM_NAMES = {MASS: "mass", ELASTICITY: "elasticity", NH_RESIDUAL: "nh_residual"
 SCALAR_FORMS = (MASS, LAPLACE, HELMHOLTZ)
 # contraction precision of a plan (include/feaction.h, enum fe_precision)
 PRECISIONS = {"fp64": N.FE_PREC_FP64, "fp32": N.FE_PREC_FP32, "bf16": N.FE_PREC_BF16,
-              "fp16": N.FE_PREC_FP16, "fp16x2": N.FE_PREC_FP16X2}
+              "fp16": N.FE_PREC_FP16, "fp16x2": N.FE_PREC_FP16X2, "tf32": N.FE_PREC_TF32}
 
 
 def _stream_ptr(stream=None) -> ctypes.c_void_p:
@@ -245,6 +245,35 @@ class Plan:
 
     def flops(self) -> float:
         return self.info.flops_per_cell * self.mesh.n_cells
+
+
+_FIELD_KW = ("mu_cell", "lam_cell", "u_lin")
+
+
+def action(mesh: Mesh, kind: int, u: torch.Tensor, quad_degree: int, y: torch.Tensor | None = None,
+           *, stream=None, **plan_kw) -> torch.Tensor:
+    """One-call y = A(u) (the action of Algorithm 2 for form ``kind`` on ``mesh``).
+
+    The plan for (kind, quad_degree, options) is built on first use and kept on the
+    mesh, so repeated calls pay only the kernel launch.  ``plan_kw`` are
+    :class:`Plan`'s keyword options; the per-call fields ``mu_cell``, ``lam_cell``
+    and ``u_lin`` are copied into the cached plan's buffers on every call that
+    passes them.  A host ``u`` is copied to the device and the result back."""
+    fields = {k: plan_kw.pop(k) for k in _FIELD_KW if plan_kw.get(k) is not None}
+    plan_kw = {k: v for k, v in plan_kw.items() if k not in _FIELD_KW}
+    key = (int(kind), int(quad_degree), tuple(sorted(plan_kw.items())), tuple(sorted(fields)))
+    cache = mesh.__dict__.setdefault("_action_plans", {})
+    plan = cache.get(key)
+    if plan is None:
+        plan = cache[key] = Plan(mesh, kind, quad_degree, **fields, **plan_kw)
+    else:
+        if "mu_cell" in fields or "lam_cell" in fields:
+            plan.set_lame(fields.get("mu_cell"), fields.get("lam_cell"))
+        if "u_lin" in fields:
+            plan.set_linearisation(fields["u_lin"])
+    if not u.is_cuda:
+        return plan.apply_host(u, y)
+    return plan.apply(u, y, stream)
 
 
 def measure_fp64_peak() -> float:

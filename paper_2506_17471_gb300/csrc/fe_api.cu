@@ -29,6 +29,7 @@ void init_registry()
     n += register_variants_coop(g_variants + n, kMaxVariants - n);
     n += register_variants_tc(g_variants + n, kMaxVariants - n);
     n += register_variants_tc2(g_variants + n, kMaxVariants - n);
+    n += register_variants_tc3(g_variants + n, kMaxVariants - n);
     n += register_variants_forms(g_variants + n, kMaxVariants - n);
     n += register_variants_coop_forms(g_variants + n, kMaxVariants - n);
     g_nvariants = n;
@@ -70,14 +71,14 @@ int coop_cells_for(int n, int nq, int dim, int ncomp, int fields, size_t esz, si
 // fit the SM's shared memory and 512 TMEM columns, with the fewest
 // quadrature-point chunks.  Returns false if nothing fits.
 bool tc_choose(int n, int nq, int ncomp, int kd, int fields, size_t smem_cap, int force_pipes, int terms,
-               TcLayout *out)
+               int esz, TcLayout *out)
 {
     if (n > 256 || nq < 1) return false;
     for (int pipes = kTcMaxPipes; pipes >= 1; pipes /= 2) {
         if (force_pipes && pipes != force_pipes) continue;
         for (int nch = 1; nch <= nq; ++nch) {
             const int qc = (nq + nch - 1) / nch;
-            const TcLayout L = tc_layout(n, nq, ncomp, kd, fields, qc, pipes, terms);
+            const TcLayout L = tc_layout(n, nq, ncomp, kd, fields, qc, pipes, terms, esz);
             if (L.N1p > 256 || L.N2p > 256 || L.tmem_cols > 512) continue;
             if (L.total > smem_cap || L.staged_bytes >= (1u << 20)) continue;
             *out = L;
@@ -343,15 +344,17 @@ static double small_to_double(uint16_t b)
 // Plan of the tensor-core kernel: the staged block holds Phi (evaluation GEMM
 // B operand, rows = chunk columns (q, k), K = node j) and Phi^T (quadrature
 // GEMM B operand, rows = node j, K = (q, k) over all chunks) rounded to the
-// 16-bit type, in the K-major core-matrix layout, then the weights in FP64 and
-// FP32.
-template <typename T16>
+// operand type, in the K-major core-matrix layout, then the weights in FP64
+// and FP32.
+template <typename TE>
 static void tc_fill_block(const TcLayout &L, int kind, const std::vector<double> &wts,
                           const std::vector<double> &tab, int wshift, std::vector<unsigned char> &blk)
 {
+    constexpr int esz = TcElem<TE>::kBytes;
+    using Bits = typename std::conditional<esz == 4, uint32_t, uint16_t>::type;
     blk.assign(L.staged_bytes, 0);
-    uint16_t *B1 = reinterpret_cast<uint16_t *>(blk.data() + L.b1_off);
-    uint16_t *B2 = reinterpret_cast<uint16_t *>(blk.data() + L.b2_off);
+    Bits *B1 = reinterpret_cast<Bits *>(blk.data() + L.b1_off);
+    Bits *B2 = reinterpret_cast<Bits *>(blk.data() + L.b2_off);
     const size_t b1_region = (size_t)L.nch * L.N1p * L.K1p, b2_region = (size_t)L.N2p * L.K2;
     for (int ch = 0; ch < L.nch; ++ch)
         for (int ql = 0; ql < L.qc; ++ql) {
@@ -363,14 +366,20 @@ static void tc_fill_block(const TcLayout &L, int kind, const std::vector<double>
                 const int kt = (kind == FE_FORM_MASS || kind == FE_FORM_HELMHOLTZ) ? k : 1 + k;
                 for (int j = 0; j < L.n; ++j) {
                     const double tv = tab[((size_t)kt * L.nq + q) * L.n + j];
-                    const uint16_t bits = to16_bits<T16>(tv);
-                    B1[tc_off(row, j, L.K1p)] = bits;
-                    B2[tc_off(j, row, L.K2)] = bits;
-                    if (L.terms == 2) {
-                        // lo term: the rounding of the remainder
-                        const uint16_t lo = to16_bits<T16>(tv - small_to_double<T16>(bits));
-                        B1[b1_region + tc_off(row, j, L.K1p)] = lo;
-                        B2[b2_region + tc_off(j, row, L.K2)] = lo;
+                    if constexpr (esz == 4) {
+                        const uint32_t bits = to_tf32_bits(tv);
+                        B1[tc_off(row, j, L.K1p, esz)] = bits;
+                        B2[tc_off(j, row, L.K2, esz)] = bits;
+                    } else {
+                        const uint16_t bits = to16_bits<TE>(tv);
+                        B1[tc_off(row, j, L.K1p)] = bits;
+                        B2[tc_off(j, row, L.K2)] = bits;
+                        if (L.terms == 2) {
+                            // lo term: the rounding of the remainder
+                            const uint16_t lo = to16_bits<TE>(tv - small_to_double<TE>(bits));
+                            B1[b1_region + tc_off(row, j, L.K1p)] = lo;
+                            B2[b2_region + tc_off(j, row, L.K2)] = lo;
+                        }
                     }
                 }
             }
@@ -399,7 +408,8 @@ static int plan_create_tc(const fe_form &f, const fe_mesh &m, const Variant &v, 
     TcLayout L;
     const int fields = (f.kind == FE_FORM_NH_JACOBIAN || f.kind == FE_FORM_SVK_JACOBIAN) ? 2 : 1;
     const int terms = f.precision == FE_PREC_FP16X2 ? 2 : 1;
-    if (!tc_choose(n, nq, ncomp, kd, fields, (size_t)optin - 256, f.tile_cells / kTcRows, terms, &L))
+    const int esz = f.precision == FE_PREC_TF32 ? 4 : 2;
+    if (!tc_choose(n, nq, ncomp, kd, fields, (size_t)optin - 256, f.tile_cells / kTcRows, terms, esz, &L))
         return FE_ERR_UNSUPPORTED;
     // weights scaled by 2^wshift into [1/2, 1) at their largest, so w_q E' stays
     // in binary16's normal range for rules with very small weights
@@ -411,6 +421,8 @@ static int plan_create_tc(const fe_form &f, const fe_mesh &m, const Variant &v, 
     std::vector<unsigned char> blk;
     if (f.precision == FE_PREC_BF16)
         tc_fill_block<__nv_bfloat16>(L, f.kind, wts, tab, wshift, blk);
+    else if (f.precision == FE_PREC_TF32)
+        tc_fill_block<tf32_t>(L, f.kind, wts, tab, wshift, blk);
     else
         tc_fill_block<__half>(L, f.kind, wts, tab, wshift, blk);   // binary16, single or split
 
@@ -475,8 +487,8 @@ extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan 
     // 2D vertex coordinates are gathered as one 16-byte load per vertex
     if (m.dim == 2 && reinterpret_cast<uintptr_t>(m.coords) % 16 != 0) return FE_ERR_INVALID_ARG;
     if (f.kind < FE_FORM_MASS || f.kind > FE_FORM_SVK_JACOBIAN) return FE_ERR_INVALID_ARG;
-    if (f.precision < FE_PREC_FP64 || f.precision > FE_PREC_FP16X2) return FE_ERR_UNSUPPORTED;
-    const bool tc = f.precision == FE_PREC_BF16 || f.precision == FE_PREC_FP16 || f.precision == FE_PREC_FP16X2;
+    if (f.precision < FE_PREC_FP64 || f.precision > FE_PREC_TF32) return FE_ERR_UNSUPPORTED;
+    const bool tc = f.precision >= FE_PREC_BF16;   // BF16, FP16, FP16X2, TF32: tensor-core kernel
     if (tc && (f.kind == FE_FORM_NH_RESIDUAL || f.kind == FE_FORM_SVK_RESIDUAL)) return FE_ERR_UNSUPPORTED;
     if (f.quad_degree < 0 || f.quad_degree > 40) return FE_ERR_INVALID_ARG;
     if ((f.kind == FE_FORM_NH_JACOBIAN || f.kind == FE_FORM_SVK_JACOBIAN) && !f.u_lin) return FE_ERR_INVALID_ARG;
@@ -911,6 +923,22 @@ extern "C" int fe_round16(const double *x, size_t n, int precision, uint16_t *bi
     if (precision != FE_PREC_BF16 && precision != FE_PREC_FP16) return FE_ERR_UNSUPPORTED;
     for (size_t i = 0; i < n; ++i)
         bits[i] = precision == FE_PREC_BF16 ? to16_bits<__nv_bfloat16>(x[i]) : to16_bits<__half>(x[i]);
+    return FE_OK;
+}
+
+extern "C" int fe_round_tf32(const double *x, size_t n, int from_binary32, uint32_t *bits)
+{
+    if ((n > 0 && (!x || !bits))) return FE_ERR_INVALID_ARG;
+    for (size_t i = 0; i < n; ++i) {
+        if (from_binary32) {
+            const float v = (float)x[i];   // IEEE round to nearest even
+            uint32_t b;
+            std::memcpy(&b, &v, 4);
+            bits[i] = f32_bits_to_tf32(b);
+        } else {
+            bits[i] = to_tf32_bits(x[i]);
+        }
+    }
     return FE_OK;
 }
 

@@ -86,6 +86,7 @@ int register_variants_3d(Variant *out, int cap);
 int register_variants_coop(Variant *out, int cap);
 int register_variants_tc(Variant *out, int cap);
 int register_variants_tc2(Variant *out, int cap);
+int register_variants_tc3(Variant *out, int cap);
 int register_variants_forms(Variant *out, int cap);
 int register_variants_coop_forms(Variant *out, int cap);
 

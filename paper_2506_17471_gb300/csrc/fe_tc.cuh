@@ -70,7 +70,8 @@ struct TcLayout {
     int N1p, K1p;                // evaluation GEMM: N (chunk columns), K (n padded to 16)
     int N2p, K2;                 // quadrature GEMM: N (n padded to 16), K (nch * N1p)
     int pipes;
-    int terms;                   // 16-bit terms per operand: 1, or 2 (hi + lo binary16 pairs)
+    int terms;                   // terms per operand: 1, or 2 (hi + lo binary16 pairs)
+    int esz;                     // operand element bytes: 2 (BF16, FP16) or 4 (TF32)
     size_t b1_off, b2_off, wd_off, wf_off, staged_bytes;   // staged block
     size_t a1_off, a2_off, nodes_off, pipe_bytes;          // per-pipeline scratch (from its base)
     size_t total;                                          // dynamic shared memory
@@ -80,7 +81,7 @@ struct TcLayout {
 __host__ __device__ inline int tc_kdp(int kd) { return kd == 1 ? 1 : (kd == 2 ? 2 : 4); }
 
 __host__ __device__ inline TcLayout tc_layout(int n, int nq, int NC, int KD, int F, int qc, int pipes,
-                                              int terms = 1)
+                                              int terms = 1, int esz = 2)
 {
     TcLayout L;
     L.n = n;
@@ -97,15 +98,16 @@ __host__ __device__ inline TcLayout tc_layout(int n, int nq, int NC, int KD, int
     L.K2 = L.nch * L.N1p;
     L.pipes = pipes;
     L.terms = terms;
+    L.esz = esz;
     // every operand region is repeated per term (term 0 = hi, term 1 = lo)
     L.b1_off = 0;
-    L.b2_off = (size_t)terms * L.nch * L.N1p * L.K1p * 2;
-    L.wd_off = L.b2_off + (size_t)terms * L.N2p * L.K2 * 2;
+    L.b2_off = (size_t)terms * L.nch * L.N1p * L.K1p * esz;
+    L.wd_off = L.b2_off + (size_t)terms * L.N2p * L.K2 * esz;
     L.wf_off = L.wd_off + (size_t)nq * 8;
     L.staged_bytes = tc_round_up_sz(L.wf_off + (size_t)nq * 4, 128);
     L.a1_off = 0;
-    L.a2_off = L.a1_off + (size_t)terms * F * NC * kTcRows * L.K1p * 2;
-    L.nodes_off = L.a2_off + (size_t)terms * NC * kTcRows * L.N1p * 2;
+    L.a2_off = L.a1_off + (size_t)terms * F * NC * kTcRows * L.K1p * esz;
+    L.nodes_off = L.a2_off + (size_t)terms * NC * kTcRows * L.N1p * esz;
     L.pipe_bytes = tc_round_up_sz(L.nodes_off + (size_t)(n | 1) * kTcRows * 4, 128);   // nodes [128][n | 1]
     L.total = L.staged_bytes + (size_t)pipes * L.pipe_bytes;
     L.acc1_cols = F * NC * L.N1p;
@@ -118,20 +120,23 @@ __host__ __device__ inline TcLayout tc_layout(int n, int nq, int NC, int KD, int
     return L;
 }
 
-// Element offset of (row r, k) in a K-major no-swizzle operand with Kp columns.
-__host__ __device__ inline size_t tc_off(int r, int k, int Kp)
+// Element offset of (row r, k) in a K-major no-swizzle operand with Kp columns
+// of esz-byte elements: core matrices of 8 rows x 16 bytes (ce = 16 / esz
+// elements), ordered [row group][K group][row][element].
+__host__ __device__ inline size_t tc_off(int r, int k, int Kp, int esz = 2)
 {
-    return (size_t)(r >> 3) * (Kp >> 3) * 64 + (size_t)(k >> 3) * 64 + (r & 7) * 8 + (k & 7);
+    const int ce = 16 / esz;
+    return (size_t)(r >> 3) * (Kp / ce) * (8 * ce) + (size_t)(k / ce) * (8 * ce) + (r & 7) * ce + (k % ce);
 }
 
 // Round-to-nearest-even conversion of x * 2^-k (x an IEEE binary64 value) to
-// a binary16-family format with EB exponent and MB fraction bits (binary16:
-// 5, 10; bfloat16: 8, 7), done on the integer bit pattern (no FP64-pipe
-// operation; the power-of-two scaling is an exponent offset).  NaN maps to a
-// quiet NaN, overflow to infinity, results below half the smallest subnormal
-// to signed zero.
+// a small format with EB exponent and MB fraction bits (binary16: 5, 10;
+// bfloat16: 8, 7; TF32: 8, 10), done on the integer bit pattern (no FP64-pipe
+// operation; the power-of-two scaling is an exponent offset).  Returns the
+// 1 + EB + MB bit pattern.  NaN maps to a quiet NaN, overflow to infinity,
+// results below half the smallest subnormal to signed zero.
 template <int EB, int MB>
-__host__ __device__ __forceinline__ uint16_t f64_to_small_rn(double x, int k = 0)
+__host__ __device__ __forceinline__ uint32_t f64_to_small_rn(double x, int k = 0)
 {
     uint64_t b;
 #ifdef __CUDA_ARCH__
@@ -144,7 +149,7 @@ __host__ __device__ __forceinline__ uint16_t f64_to_small_rn(double x, int k = 0
     const uint32_t sign = (uint32_t)(b >> 63) << (EB + MB);
     const uint64_t frac = b & 0xFFFFFFFFFFFFFull;
     const int e = (int)((b >> 52) & 0x7FF);
-    if (e == 0x7FF) return (uint16_t)(sign | kInf | (frac ? (1u << (MB - 1)) : 0u));
+    if (e == 0x7FF) return sign | kInf | (frac ? (1u << (MB - 1)) : 0u);
     const int te = (e ? e : 1) - 1023 + kBias - k;   // biased exponent in the target format
     uint64_t m;
     int shift;
@@ -154,30 +159,69 @@ __host__ __device__ __forceinline__ uint16_t f64_to_small_rn(double x, int k = 0
     } else {
         m = frac | (e ? (1ull << 52) : 0ull);
         shift = 52 - MB + 1 - te;
-        if (shift > 62) return (uint16_t)sign;
+        if (shift > 62) return sign;
     }
     if (te > 2 * kBias + 1) {
-        return (uint16_t)(sign | kInf);   // far above the largest finite value
+        return sign | kInf;   // far above the largest finite value
     }
     uint64_t r = m >> shift;
     const uint64_t rem = m & ((1ull << shift) - 1ull), halfway = 1ull << (shift - 1);
     if (rem > halfway || (rem == halfway && (r & 1ull))) ++r;
-    if (r >= kInf) return (uint16_t)(sign | kInf);
-    return (uint16_t)(sign | (uint32_t)r);
+    if (r >= kInf) return sign | kInf;
+    return sign | (uint32_t)r;
 }
 
-template <typename T16>
+template <typename TE>
 __host__ __device__ __forceinline__ uint16_t to16_bits(double x, int k = 0);
 template <>
 __host__ __device__ __forceinline__ uint16_t to16_bits<__nv_bfloat16>(double x, int k)
 {
-    return f64_to_small_rn<8, 7>(x, k);
+    return (uint16_t)f64_to_small_rn<8, 7>(x, k);
 }
 template <>
 __host__ __device__ __forceinline__ uint16_t to16_bits<__half>(double x, int k)
 {
-    return f64_to_small_rn<5, 10>(x, k);
+    return (uint16_t)f64_to_small_rn<5, 10>(x, k);
 }
+
+// TF32 operand: a binary32 container whose 13 low fraction bits are zero (the
+// tensor cores read sign, 8 exponent and 10 fraction bits).
+struct tf32_t {
+    uint32_t bits;
+};
+
+// x * 2^-k rounded to nearest even TF32, as its binary32 container bits.
+__host__ __device__ __forceinline__ uint32_t to_tf32_bits(double x, int k = 0)
+{
+    return f64_to_small_rn<8, 10>(x, k) << 13;
+}
+
+// binary32 v rounded to nearest even TF32 (integer arithmetic: a carry out of
+// the kept fraction rounds into the exponent, up to infinity); inf stays inf,
+// NaN stays a quiet NaN.
+__host__ __device__ __forceinline__ uint32_t f32_bits_to_tf32(uint32_t b)
+{
+    if ((b & 0x7F800000u) == 0x7F800000u) return (b & 0xFFFFE000u) | ((b & 0x7FFFFFu) ? 0x400000u : 0u);
+    return (b + 0xFFFu + ((b >> 13) & 1u)) & 0xFFFFE000u;
+}
+
+// Operand element traits: bytes, the instruction descriptor's A/B format
+// (kind::f16: 0 = F16, 1 = BF16; kind::tf32: 2) and the MMA K per instruction
+// (32 bytes of K: 16 elements of 2 bytes, 8 of 4).
+template <typename T>
+struct TcElem;
+template <>
+struct TcElem<__half> {
+    static constexpr int kBytes = 2, kFmt = 0, kK = 16;
+};
+template <>
+struct TcElem<__nv_bfloat16> {
+    static constexpr int kBytes = 2, kFmt = 1, kK = 16;
+};
+template <>
+struct TcElem<tf32_t> {
+    static constexpr int kBytes = 4, kFmt = 2, kK = 8;
+};
 
 // 2^e as a binary32 value for e <= 127; 0 below the normal range (the terms it
 // scales are then negligible against the other term of the sum).
@@ -253,7 +297,7 @@ __device__ __forceinline__ float narrow_pow2_ftz(double x, int k)
 
 // Two FP32 values to a packed pair of 16-bit values (round to nearest even);
 // the first value lands at the lower address.
-template <typename T16>
+template <typename TE>
 __device__ __forceinline__ uint32_t pack2(float lo, float hi);
 template <>
 __device__ __forceinline__ uint32_t pack2<__nv_bfloat16>(float lo, float hi)
@@ -269,7 +313,7 @@ __device__ __forceinline__ uint32_t pack2<__half>(float lo, float hi)
 }
 
 // The two 16-bit values of a packed pair back in binary32.
-template <typename T16>
+template <typename TE>
 __device__ __forceinline__ float2 unpack2(uint32_t w);
 template <>
 __device__ __forceinline__ float2 unpack2<__nv_bfloat16>(uint32_t w)
@@ -282,25 +326,36 @@ __device__ __forceinline__ float2 unpack2<__half>(uint32_t w)
     return __half22float2(*reinterpret_cast<const __half2 *>(&w));
 }
 
-// Stores 8 consecutive K entries (16 bytes) of one operand row: term 0 is the
-// 16-bit rounding of v; with TERMS == 2 term 1, region_elems further on, holds
-// the 16-bit rounding of the remainder v - term0 (a hi + lo pair, ~2 x the
-// significand bits).
-template <typename T16, int TERMS>
-__device__ __forceinline__ void store8(T16 *p, size_t region_elems, const float (&v)[8])
+// Stores 8 consecutive K entries of one operand row, p at the first: for the
+// 16-bit types one 16-byte core-matrix row, for TF32 the 4-element rows of two
+// K-adjacent core matrices (32 elements apart).  Term 0 is the rounding of v;
+// with TERMS == 2 term 1, region_elems further on, holds the rounding of the
+// remainder v - term0 (a binary16 hi + lo pair, ~2 x the significand bits).
+template <typename TE, int TERMS>
+__device__ __forceinline__ void store8(TE *p, size_t region_elems, const float (&v)[8])
 {
+    if constexpr (TcElem<TE>::kBytes == 4) {
+        static_assert(TERMS == 1, "TF32 operands are single-term");
+        uint32_t w[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) w[i] = f32_bits_to_tf32(__float_as_uint(v[i]));
+        *reinterpret_cast<uint4 *>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+        *reinterpret_cast<uint4 *>(p + 32) = make_uint4(w[4], w[5], w[6], w[7]);
+        return;
+    } else {
     uint32_t w[4];
 #pragma unroll
-    for (int h = 0; h < 4; ++h) w[h] = pack2<T16>(v[2 * h], v[2 * h + 1]);
+    for (int h = 0; h < 4; ++h) w[h] = pack2<TE>(v[2 * h], v[2 * h + 1]);
     *reinterpret_cast<uint4 *>(p) = make_uint4(w[0], w[1], w[2], w[3]);
     if constexpr (TERMS == 2) {
         uint32_t r[4];
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
-            const float2 hi = unpack2<T16>(w[h]);
-            r[h] = pack2<T16>(v[2 * h] - hi.x, v[2 * h + 1] - hi.y);
+            const float2 hi = unpack2<TE>(w[h]);
+            r[h] = pack2<TE>(v[2 * h] - hi.x, v[2 * h + 1] - hi.y);
         }
         *reinterpret_cast<uint4 *>(p + region_elems) = make_uint4(r[0], r[1], r[2], r[3]);
+    }
     }
 }
 
@@ -310,21 +365,30 @@ __device__ __forceinline__ uint64_t tc_smem_desc(uint32_t addr, uint32_t lbo, ui
            ((uint64_t)((sbo & 0x3FFFF) >> 4) << 32) | ((uint64_t)1 << 46);
 }
 
-// Instruction descriptor of tcgen05.mma kind::f16: FP32 accumulator, A and B of
-// the same 16-bit type (fmt 0 = F16, 1 = BF16), both K-major.
+// Instruction descriptor of tcgen05.mma kind::f16 / kind::tf32: FP32
+// accumulator, A and B of the same type (fmt 0 = F16, 1 = BF16, 2 = TF32),
+// both K-major.
 __host__ __device__ constexpr uint32_t tc_idesc(int fmt, int M, int N)
 {
     return (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | ((uint32_t)(N >> 3) << 17) |
            ((uint32_t)(M >> 4) << 24);
 }
 
+template <bool kTf32>
 __device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc)
 {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-        "l"(da), "l"(db), "r"(idesc), "r"(acc)
-        : "memory");
+    if constexpr (kTf32)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+            "l"(da), "l"(db), "r"(idesc), "r"(acc)
+            : "memory");
+    else
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+            "l"(da), "l"(db), "r"(idesc), "r"(acc)
+            : "memory");
 }
 
 __device__ __forceinline__ void tc_commit(uint32_t sbar)
@@ -417,7 +481,7 @@ __device__ __forceinline__ bool tc_wait(uint32_t sbar, uint32_t parity)
 // log det F and the tangent applied to H; St. Venant-Kirchhoff: E, S, dE, dS,
 // dP = H S + F dS — the same algebra as the FP64 kernels).  E' = w_q e is
 // rounded to 16 bits.  Returns false if det F <= 0 at a live Neo-Hookean point.
-template <int OP, int D, typename T16, int TERMS>
+template <int OP, int D, typename TE, int TERMS>
 __device__ __forceinline__ bool tc_pointwise_hyper_jacobian(const TcLayout &L, uint32_t tlane, unsigned char *hb,
                                                             const double *wd, int t, int ch, int nq, bool good,
                                                             int ku_lin, const float (&Jf)[D][D],
@@ -515,14 +579,14 @@ __device__ __forceinline__ bool tc_pointwise_hyper_jacobian(const TcLayout &L, u
 #pragma unroll
         for (int m = 0; m < NC; ++m) {
             const size_t region = (size_t)kTcRows * L.N1p;
-            T16 *A2 = reinterpret_cast<T16 *>(hb + L.a2_off) + (size_t)m * TERMS * region;
-            store8<T16, TERMS>(A2 + tc_off(t, blk * 8, L.N1p), region, out[m]);
+            TE *A2 = reinterpret_cast<TE *>(hb + L.a2_off) + (size_t)m * TERMS * region;
+            store8<TE, TERMS>(A2 + tc_off(t, blk * 8, L.N1p, TcElem<TE>::kBytes), region, out[m]);
         }
     }
     return ok;
 }
 
-template <int OP, int D, typename T16, int TERMS>
+template <int OP, int D, typename TE, int TERMS>
 __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const ActionArgs a)
 {
     constexpr int NC = OpTraits<OP, D>::NC;
@@ -536,13 +600,14 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
     // gradients sum to zero, so the constant drops out of every gradient
     constexpr bool kOffset = OP != OP_MASS && OP != OP_HELMHOLTZ;
     constexpr int PPB = 16 / KDP;   // quadrature points per 16 accumulator columns
-    constexpr int FMT = std::is_same<T16, __nv_bfloat16>::value ? 1 : 0;
+    constexpr int FMT = TcElem<TE>::kFmt, ESZ = TcElem<TE>::kBytes, KK = TcElem<TE>::kK;
+    constexpr bool kTf32 = ESZ == 4;
     extern __shared__ __align__(128) unsigned char tc_smem[];
     __shared__ __align__(8) uint64_t bars[1 + kTcMaxPipes];   // table copy; one MMA barrier per pipeline
     __shared__ uint32_t s_tmem;
     __shared__ int s_tile[kTcMaxPipes];
 
-    const TcLayout L = tc_layout(a.coop_n, a.nq, NC, KD, F, a.tc_qc, a.tc_pipes, TERMS);
+    const TcLayout L = tc_layout(a.coop_n, a.nq, NC, KD, F, a.tc_qc, a.tc_pipes, TERMS, ESZ);
     const int tid = threadIdx.x, pipe = tid >> 7, t = tid & (kTcRows - 1), warp = tid >> 5;
     const int n = L.n;
     const uint32_t bar0 = (uint32_t)__cvta_generic_to_shared(&bars[0]);
@@ -776,24 +841,33 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
 #pragma unroll
                 for (int m = 0; m < NC; ++m) {
                     const size_t region = (size_t)kTcRows * L.K1p;
-                    T16 *A1 = reinterpret_cast<T16 *>(hb + L.a1_off) + (size_t)(f * NC + m) * TERMS * region;
-                    if constexpr (TERMS == 1) {
+                    TE *A1 = reinterpret_cast<TE *>(hb + L.a1_off) + (size_t)(f * NC + m) * TERMS * region;
+                    if constexpr (kTf32) {
+                        // binary64 rounded to TF32 directly (two K-adjacent core matrices)
+                        uint32_t w[8];
+#pragma unroll
+                        for (int s = 0; s < 8; ++s)
+                            w[s] = to_tf32_bits(nd[s] >= 0 ? v[s][m] - off[f][m] : 0.0, ku[f]);
+                        TE *q = A1 + tc_off(t, j0, L.K1p, ESZ);
+                        *reinterpret_cast<uint4 *>(q) = make_uint4(w[0], w[1], w[2], w[3]);
+                        *reinterpret_cast<uint4 *>(q + 32) = make_uint4(w[4], w[5], w[6], w[7]);
+                    } else if constexpr (TERMS == 1) {
                         // one term: binary64 rounded to 16 bits directly
                         uint32_t w[4];
 #pragma unroll
                         for (int h = 0; h < 4; ++h)
-                            w[h] = (uint32_t)to16_bits<T16>(nd[2 * h] >= 0 ? v[2 * h][m] - off[f][m] : 0.0, ku[f]) |
-                                   ((uint32_t)to16_bits<T16>(nd[2 * h + 1] >= 0 ? v[2 * h + 1][m] - off[f][m] : 0.0,
+                            w[h] = (uint32_t)to16_bits<TE>(nd[2 * h] >= 0 ? v[2 * h][m] - off[f][m] : 0.0, ku[f]) |
+                                   ((uint32_t)to16_bits<TE>(nd[2 * h + 1] >= 0 ? v[2 * h + 1][m] - off[f][m] : 0.0,
                                                              ku[f])
                                     << 16);
-                        *reinterpret_cast<uint4 *>(A1 + tc_off(t, j0, L.K1p)) = make_uint4(w[0], w[1], w[2], w[3]);
+                        *reinterpret_cast<uint4 *>(A1 + tc_off(t, j0, L.K1p, ESZ)) = make_uint4(w[0], w[1], w[2], w[3]);
                     } else {
                         // hi + lo pair from the scaled value in binary32
                         float xs[8];
 #pragma unroll
                         for (int s = 0; s < 8; ++s)
                             xs[s] = nd[s] >= 0 ? narrow_pow2_ftz(v[s][m] - off[f][m], ku[f]) : 0.f;
-                        store8<T16, TERMS>(A1 + tc_off(t, j0, L.K1p), region, xs);
+                        store8<TE, TERMS>(A1 + tc_off(t, j0, L.K1p, ESZ), region, xs);
                     }
                 }
             }
@@ -807,18 +881,20 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
         for (int ch = 0; ch < L.nch; ++ch) {
             // ---- evaluation GEMM of chunk ch (its commit also covers the previous chunk's quadrature GEMM)
             if (t == 0) {
-                const uint32_t sbo = (uint32_t)L.K1p * 16u;
-                const uint32_t a_region = (uint32_t)(kTcRows * L.K1p * 2), b_region = (uint32_t)(L.nch * L.N1p * L.K1p * 2);
+                // K steps of KK elements (32 bytes: two core matrices) at 256 B each
+                const uint32_t sbo = (uint32_t)L.K1p * 8u * ESZ;
+                const uint32_t a_region = (uint32_t)(kTcRows * L.K1p * ESZ),
+                               b_region = (uint32_t)(L.nch * L.N1p * L.K1p * ESZ);
                 for (int m = 0; m < F * NC; ++m)
-                    for (int s = 0; s < L.K1p / 16; ++s)
+                    for (int s = 0; s < L.K1p / KK; ++s)
                         // one product, or hi*hi + hi*lo + lo*hi for split operands
                         for (int pr = 0; pr < (TERMS == 2 ? 3 : 1); ++pr) {
                             const uint32_t ta = pr == 2 ? 1u : 0u, tb = pr == 1 ? 1u : 0u;
                             const uint64_t da = tc_smem_desc(
                                 a1s + ((uint32_t)m * TERMS + ta) * a_region + (uint32_t)s * 256u, 128u, sbo);
                             const uint64_t db = tc_smem_desc(
-                                b1s + tb * b_region + (uint32_t)(ch * L.N1p * L.K1p * 2) + (uint32_t)s * 256u, 128u, sbo);
-                            tc_mma(tpipe + (uint32_t)(m * L.N1p), da, db, id1, (s > 0 || pr > 0) ? 1u : 0u);
+                                b1s + tb * b_region + (uint32_t)(ch * L.N1p * L.K1p * ESZ) + (uint32_t)s * 256u, 128u, sbo);
+                            tc_mma<kTf32>(tpipe + (uint32_t)(m * L.N1p), da, db, id1, (s > 0 || pr > 0) ? 1u : 0u);
                         }
                 tc_commit(barp);
             }
@@ -832,7 +908,7 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
 
             // ---- pointwise: this thread's cell at the chunk's points, E' into the quadrature A operand
             if constexpr (kHyperJac) {
-                nh_ok &= tc_pointwise_hyper_jacobian<OP, D, T16, TERMS>(L, tlane, hb, wd, t, ch, a.nq, good, ku[1], Jf, Jh, mu_c,
+                nh_ok &= tc_pointwise_hyper_jacobian<OP, D, TE, TERMS>(L, tlane, hb, wd, t, ch, a.nq, good, ku[1], Jf, Jh, mu_c,
                                                           lam_c);
             } else
             for (int blk = 0; blk < L.N1p / 16; ++blk) {
@@ -905,15 +981,15 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
 #pragma unroll
                 for (int m = 0; m < NC; ++m) {
                     const size_t region = (size_t)kTcRows * L.N1p;
-                    T16 *A2 = reinterpret_cast<T16 *>(hb + L.a2_off) + (size_t)m * TERMS * region;
+                    TE *A2 = reinterpret_cast<TE *>(hb + L.a2_off) + (size_t)m * TERMS * region;
                     float first[8], second[8];
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
                         first[i] = v[m][i];
                         second[i] = v[m][8 + i];
                     }
-                    store8<T16, TERMS>(A2 + tc_off(t, blk * 16, L.N1p), region, first);
-                    store8<T16, TERMS>(A2 + tc_off(t, blk * 16 + 8, L.N1p), region, second);
+                    store8<TE, TERMS>(A2 + tc_off(t, blk * 16, L.N1p, ESZ), region, first);
+                    store8<TE, TERMS>(A2 + tc_off(t, blk * 16 + 8, L.N1p, ESZ), region, second);
                 }
             }
             fence_async_smem();
@@ -923,17 +999,17 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
 
             // ---- quadrature GEMM of chunk ch, accumulated over the chunks
             if (t == 0) {
-                const uint32_t sboa = (uint32_t)L.N1p * 16u, sbob = (uint32_t)L.K2 * 16u;
-                const uint32_t a_region = (uint32_t)(kTcRows * L.N1p * 2), b_region = (uint32_t)(L.N2p * L.K2 * 2);
+                const uint32_t sboa = (uint32_t)L.N1p * 8u * ESZ, sbob = (uint32_t)L.K2 * 8u * ESZ;
+                const uint32_t a_region = (uint32_t)(kTcRows * L.N1p * ESZ), b_region = (uint32_t)(L.N2p * L.K2 * ESZ);
                 for (int m = 0; m < NC; ++m)
-                    for (int s = 0; s < L.N1p / 16; ++s)
+                    for (int s = 0; s < L.N1p / KK; ++s)
                         for (int pr = 0; pr < (TERMS == 2 ? 3 : 1); ++pr) {
                             const uint32_t ta = pr == 2 ? 1u : 0u, tb = pr == 1 ? 1u : 0u;
                             const uint64_t da = tc_smem_desc(
                                 a2s + ((uint32_t)m * TERMS + ta) * a_region + (uint32_t)s * 256u, 128u, sboa);
                             const uint64_t db = tc_smem_desc(
-                                b2s + tb * b_region + (uint32_t)((ch * L.N1p / 16 + s) * 256), 128u, sbob);
-                            tc_mma(tpipe + (uint32_t)(L.acc1_cols + m * L.N2p), da, db, id2,
+                                b2s + tb * b_region + (uint32_t)((ch * L.N1p / KK + s) * 256), 128u, sbob);
+                            tc_mma<kTf32>(tpipe + (uint32_t)(L.acc1_cols + m * L.N2p), da, db, id2,
                                    (ch > 0 || s > 0 || pr > 0) ? 1u : 0u);
                         }
             }
@@ -995,15 +1071,16 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
     leave_queue(a.sched);
 }
 
-template <int OP, int D, typename T16, int TERMS>
+template <int OP, int D, typename TE, int TERMS>
 cudaError_t launch_tc(const ActionArgs &a, int grid, int block, size_t smem, cudaStream_t s)
 {
-    k_action_tc<OP, D, T16, TERMS><<<grid, block, smem, s>>>(a);
+    k_action_tc<OP, D, TE, TERMS><<<grid, block, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-// TERMS == 2 (binary16 hi + lo pairs) is the FE_PREC_FP16X2 precision.
-template <int OP, int D, typename T16, int TERMS = 1>
+// TERMS == 2 (binary16 hi + lo pairs) is the FE_PREC_FP16X2 precision; tf32_t
+// operands are FE_PREC_TF32.
+template <int OP, int D, typename TE, int TERMS = 1>
 Variant make_tc_variant()
 {
     Variant v;
@@ -1011,11 +1088,14 @@ Variant make_tc_variant()
     v.dim = D;
     v.degree = 0;   // any degree with at most 256 local nodes
     v.op = 0;
-    v.precision = TERMS == 2 ? FE_PREC_FP16X2 : (std::is_same<T16, __nv_bfloat16>::value ? FE_PREC_BF16 : FE_PREC_FP16);
+    v.precision = TERMS == 2                                      ? FE_PREC_FP16X2
+                  : std::is_same<TE, tf32_t>::value              ? FE_PREC_TF32
+                  : std::is_same<TE, __nv_bfloat16>::value       ? FE_PREC_BF16
+                                                                  : FE_PREC_FP16;
     v.kernel_id = 2;   // 128-cell tensor-core tiles
     v.block = kTcRows;
-    v.launch = &launch_tc<OP, D, T16, TERMS>;
-    v.func = reinterpret_cast<const void *>(&k_action_tc<OP, D, T16, TERMS>);
+    v.launch = &launch_tc<OP, D, TE, TERMS>;
+    v.func = reinterpret_cast<const void *>(&k_action_tc<OP, D, TE, TERMS>);
     return v;
 }
 

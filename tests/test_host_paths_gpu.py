@@ -57,3 +57,30 @@ def test_pipelined_reused_buffers_and_edge_cases(setup):
     same = (P * 2)(d.data_ptr(), d.data_ptr())
     assert N.lib.fe_action_host_pipelined(plan._h, 1, up, yp, same, same, None) == N.FE_ERR_INVALID_ARG
     assert N.lib.fe_action_host_pipelined(plan._h, -1, up, yp, same, same, None) == N.FE_ERR_INVALID_ARG
+
+
+def test_one_call_action_caches_plans(setup):
+    """fe.action builds each (form, options) plan once, keeps it on the mesh and
+    copies per-call fields into it; results equal an explicit plan's."""
+    import oracle
+    from feinputs import lame_fields
+    from feinputs.fields import sinusoid_displacement
+    fe, m, plan = setup
+    M = plan.mesh
+    u = torch.from_numpy(uniform_field(m.n_nodes * 3, 5)).cuda()
+    y = fe.action(M, fe.ELASTICITY, u, 2, lam=1.25, mu=1.0)
+    assert torch.equal(y, plan.apply(u)) or float((y - plan.apply(u)).abs().max() / y.abs().max()) < 1e-14
+    fe.action(M, fe.ELASTICITY, u, 2, lam=1.25, mu=1.0)
+    assert len(M._action_plans) == 1
+    # per-cell fields: a second set of coefficients reuses the cached plan
+    o = oracle.Oracle.from_mesh(m, 4)
+    ul = sinusoid_displacement(m, 3)
+    for seed in (1, 2):
+        mu, lam = lame_fields(m.n_cells, seed)
+        r = fe.action(M, fe.NH_RESIDUAL, torch.from_numpy(ul).cuda(), 4, mu_cell=mu, lam_cell=lam)
+        ref = o.nh_residual(ul, mu, lam)
+        assert np.abs(r.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
+    assert len(M._action_plans) == 2
+    # a host input goes through the end-to-end path
+    yh = fe.action(M, fe.ELASTICITY, u.cpu(), 2, lam=1.25, mu=1.0)
+    assert not yh.is_cuda and float((yh - y.cpu()).abs().max() / y.abs().max()) < 1e-14

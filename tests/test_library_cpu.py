@@ -181,3 +181,38 @@ def test_round16_agrees_with_numpy_half(fe):
         ref = x.astype(np.float16).view(np.uint16)
     assert np.array_equal(bits, ref)
     assert N.lib.fe_round16(ctypes.c_void_p(x.ctypes.data), 1, N.FE_PREC_FP64, ctypes.c_void_p(bits.ctypes.data)) != 0
+
+
+@pytest.mark.parametrize("from_binary32", [0, 1])
+def test_round_tf32_matches_ieee_definition(fe, from_binary32):
+    """fe_round_tf32 (the TF32 plans' rounding of tables and DoFs, and of the
+    binary32 pointwise results) against round-to-nearest-even to 11 significand
+    bits with binary32's exponent range, written from its definition."""
+    import ctypes
+    from paper_2506_17471_gb300 import _native as N
+    rng = np.random.default_rng(13)
+    p, emin, emax = 11, -126, 127
+    x = list(rng.standard_normal(3000) * 2.0 ** rng.integers(emin - 14, emax + 2, 3000))
+    for _ in range(1500):
+        e = int(rng.integers(emin - 8, emax))
+        m = int(rng.integers(2 ** (p - 1), 2 ** p))
+        t = (m + 0.5) * 2.0 ** (e - p + 1)
+        x += [t, -t, np.nextafter(t, 0), np.nextafter(t, np.inf)]
+    big = (2 - 2.0 ** (1 - p)) * 2.0 ** emax
+    x += [0.0, -0.0, np.inf, -np.inf, big, big + 2.0 ** (emax - p), np.nextafter(big + 2.0 ** (emax - p), 0),
+          2.0 ** (emin - p + 1), 2.0 ** (emin - p), np.nextafter(2.0 ** (emin - p), 1), 1e-300, 5e-324]
+    x = np.asarray(x, dtype=np.float64)
+    bits = np.zeros(len(x), dtype=np.uint32)
+    assert N.lib.fe_round_tf32(ctypes.c_void_p(x.ctypes.data), len(x), from_binary32,
+                               ctypes.c_void_p(bits.ctypes.data)) == 0
+    with np.errstate(over="ignore"):
+        src = x.astype(np.float32).astype(np.float64) if from_binary32 else x
+    for xi, si, b in zip(x, src, bits):
+        r = _round_ref(float(si), p, emin, emax)
+        want = int(np.array([r], dtype=np.float32).view(np.uint32)[0])
+        assert b == want, (xi, from_binary32, hex(int(b)), r)
+        assert b & 0x1FFF == 0
+    nan = np.array([np.nan], dtype=np.float64)
+    assert N.lib.fe_round_tf32(ctypes.c_void_p(nan.ctypes.data), 1, from_binary32,
+                               ctypes.c_void_p(bits.ctypes.data)) == 0
+    assert (bits[0] & 0x7F800000) == 0x7F800000 and (bits[0] & 0x7FE000)

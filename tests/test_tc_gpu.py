@@ -1,5 +1,5 @@
-"""GPU parity of the tensor-core kernel (16-bit contractions, FP32 accumulate)
-against the FP64 oracle.
+"""GPU parity of the tensor-core kernel (16-bit or TF32 contractions, FP32
+accumulate) against the FP64 oracle.
 
 Stated bound.  The kernel rounds three things to the 16-bit type: the
 tabulation (once, in the plan), each cell's DoFs (for gradient forms after
@@ -7,8 +7,8 @@ removing a per-cell constant) scaled by a power of two, and the pointwise
 values E' after scaling; products accumulate in FP32, and geometry, the
 Neo-Hookean law, the output scaling and the scatter are FP64 (the kinematic
 contractions with J^{-1} FP32).  Each rounding is a relative perturbation of
-at most the unit roundoff u16 (bfloat16: 2^-8 = 3.9e-3, binary16: 2^-11 =
-4.9e-4); through the two contractions they are amplified by the ratio of the
+at most the unit roundoff u16 (bfloat16: 2^-8 = 3.9e-3, binary16 and TF32:
+2^-11 = 4.9e-4); through the two contractions they are amplified by the ratio of the
 absolute terms to the result.  Measured: mass and elasticity 0.6-1.2 u16 up to
 P6; the Neo-Hookean Jacobian 1-4.3 u16, largest at P6 where the linearisation
 point's gradient (a smooth field) is evaluated from 16-bit data.  The stated
@@ -27,7 +27,7 @@ import oracle
 from feinputs import structured_mesh, uniform_field
 
 pytestmark = pytest.mark.gpu
-U16 = {"bf16": 2.0 ** -8, "fp16": 2.0 ** -11}
+U16 = {"bf16": 2.0 ** -8, "fp16": 2.0 ** -11, "tf32": 2.0 ** -11}
 TOL16 = {k: 8 * v for k, v in U16.items()}
 
 
@@ -66,7 +66,7 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+@pytest.mark.parametrize("prec", ["bf16", "fp16", "tf32"])
 @pytest.mark.parametrize("kind,dim,N,p,q,scheme", CASES)
 def test_tc_parity(fe, kind, dim, N, p, q, scheme, prec):
     m, M = make(fe, dim, N, p, 300 + 10 * dim + p)
@@ -87,7 +87,7 @@ def test_tc_parity(fe, kind, dim, N, p, q, scheme, prec):
     assert plan.status() == 0
 
 
-@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+@pytest.mark.parametrize("prec", ["bf16", "fp16", "tf32"])
 def test_tc_scale_invariance(fe, prec):
     """Per-cell power-of-two scaling: A(2^k u) = 2^k A(u) up to the order of the
     FP64 atomics, for magnitudes far outside binary16's range."""
@@ -101,7 +101,7 @@ def test_tc_scale_invariance(fe, prec):
     assert plan.status() == 0
 
 
-@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+@pytest.mark.parametrize("prec", ["bf16", "fp16", "tf32"])
 def test_tc_tiny_and_huge_cells(fe, prec):
     """Mesh scaled by 2^-24 and 2^+24: J^{-1} is scaled per cell by a power of
     two, so the pointwise values stay in range and the bound still holds."""
@@ -191,7 +191,7 @@ def test_tc_full_mass_p3_2d(fe, prec):
     assert plan.status() == 0
 
 
-@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+@pytest.mark.parametrize("prec", ["bf16", "fp16", "tf32"])
 def test_tc_full_elasticity_p4_3d(fe, prec):
     """hp-sweep size: elasticity P4 on 6 x 27^3 tetrahedra (3,885,087 DoFs), all outputs."""
     m, M = make(fe, 3, 27, 4, 20250622)
@@ -205,7 +205,7 @@ def test_tc_full_elasticity_p4_3d(fe, prec):
 NH_CASES = [(2, 13, 2, 4), (2, 13, 4, 8), (2, 13, 6, 12), (3, 5, 2, 4)]
 
 
-@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+@pytest.mark.parametrize("prec", ["bf16", "fp16", "tf32"])
 @pytest.mark.parametrize("dim,N,p,q", NH_CASES)
 def test_tc_nh_jacobian(fe, dim, N, p, q, prec):
     """Neo-Hookean Jacobian action: u_lin and du both in 16 bits (each scaled per
@@ -242,7 +242,7 @@ def test_tc_full_nh_jacobian_p6_2d(fe, prec):
     assert plan.status() == 0
 
 
-@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+@pytest.mark.parametrize("prec", ["bf16", "fp16", "tf32"])
 def test_tc_material_scaling(fe, prec):
     """Lame parameters far from O(1) (and conical rules with very small weights):
     E' is scaled per plan / per cell by powers of two, so binary16 neither
@@ -267,6 +267,12 @@ def test_tc_laplace_helmholtz(fe, kind, dim, N, p, q, prec):
     assert m.n_cells % 128 != 0
     o = oracle.Oracle.from_mesh(m, q)
     u = uniform_field(m.n_nodes, 12 + p)
+    if prec == "tf32" and (kind, dim, p, q) == ("helmholtz", 3, 4, 8):
+        # 4-byte operands: the 125-point tables exceed shared memory, refused cleanly
+        with pytest.raises(fe.FeError) as e:
+            fe.Plan(M, fe.HELMHOLTZ, q, precision=prec)
+        assert e.value.code == 2
+        return
     plan = fe.Plan(M, getattr(fe, kind.upper()), q, precision=prec)
     assert plan.info.kernel == 2
     err = rel(plan.apply(cuda(u)), getattr(o, kind)(u))
@@ -274,7 +280,7 @@ def test_tc_laplace_helmholtz(fe, kind, dim, N, p, q, prec):
     assert plan.status() == 0
 
 
-@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+@pytest.mark.parametrize("prec", ["bf16", "fp16", "tf32"])
 def test_tc_helmholtz_cell_scale(fe, prec):
     """Helmholtz mixes a value term (scale h^d) and a gradient term (h^(d-2)); both
     share the per-cell output factor, on meshes scaled by 2^-20 and 2^+20."""
@@ -287,7 +293,7 @@ def test_tc_helmholtz_cell_scale(fe, prec):
         assert plan.status() == 0
 
 
-@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+@pytest.mark.parametrize("prec", ["bf16", "fp16", "tf32"])
 @pytest.mark.parametrize("dim,N,p,q", [(2, 13, 2, 4), (2, 13, 4, 8), (3, 5, 2, 4)])
 def test_tc_svk_jacobian(fe, dim, N, p, q, prec):
     """St. Venant-Kirchhoff Jacobian action (the paper's hyperelastic law) on the
