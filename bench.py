@@ -23,6 +23,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -107,9 +108,35 @@ def cpu_oracle_rate(m, u, budget_cpu_s=12.0, threads=None):
         if el * threads >= budget_cpu_s or el > budget_cpu_s:
             break
     dofs = m.n_nodes * 3
+    # the same action on one core (about 3 s)
+    reps1, t0 = 0, time.perf_counter()
+    while True:
+        o.elasticity(u, 1.25, 1.0, threads=1)
+        reps1 += 1
+        el1 = time.perf_counter() - t0
+        if el1 >= 3.0:
+            break
     return {"value": dofs * reps / el, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{reps} full-mesh oracle actions ({m.n_cells} cells) in {el:.2f} s wall "
-                      f"on {threads} threads"}
+                      f"on {threads} threads; single core: {reps1} in {el1:.2f} s",
+            "single_core_value": dofs * reps1 / el1, "cpu_model": cpu_model()}
+
+
+def cpu_model() -> str:
+    """Host CPU name from /proc/cpuinfo (x86: model name; Arm: implementer/part ids)."""
+    fields = {}
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k, _, v = line.partition(":")
+                fields.setdefault(k.strip(), v.strip())
+    except OSError:
+        pass
+    if fields.get("model name"):
+        return fields["model name"]
+    parts = {"0xd4f": "Neoverse-V2", "0xd40": "Neoverse-V1", "0xd0c": "Neoverse-N1", "0xd49": "Neoverse-N2"}
+    part = fields.get("CPU part", "")
+    return f"{platform.machine()} {parts.get(part, 'CPU part ' + part)}".strip()
 
 
 def run_reference(args):
@@ -137,7 +164,8 @@ def run_reference(args):
             "data": "synthetic", "config": {"workload": WORKLOAD, "parallelism": "host threads"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": f"each step: oracle action over cells [0, {c1}) of "
-                                       f"{m.n_cells}, scaled to the full mesh"},
+                                       f"{m.n_cells}, scaled to the full mesh",
+                             "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
