@@ -408,7 +408,7 @@ __device__ __forceinline__ void coop_batch(const ActionArgs &a, const CoopLayout
             for (int m = 0; m < NC; ++m) o[m] = out[m];
         } else {
 #pragma unroll
-            for (int m = 0; m < NC; ++m) atomicAdd(a.y + (size_t)node * NC + m, cvt<double>(out[m]));
+            for (int m = 0; m < NC; ++m) red_add(a.y + (size_t)node * NC + m, cvt<double>(out[m]));
         }
     }
     if constexpr (OP == OP_NH_ADJOINT) {

@@ -35,6 +35,13 @@ namespace fe {
 constexpr int kTpcBlock = 128;
 constexpr int kWaitLimit = 1 << 21;   // bounded mbarrier polls (~0.1-0.3 s with backoff)
 
+// *p += v as a global reduction that returns nothing (the scatter-add never
+// reads the old value, so no register waits on the reply).
+__device__ __forceinline__ void red_add(double *p, double v)
+{
+    asm volatile("red.global.add.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+
 __device__ __forceinline__ void set_status(int32_t *status, int32_t code)
 {
     if (status) atomicCAS(status, 0, code);
@@ -696,7 +703,7 @@ __device__ __forceinline__ void action_cell(const ActionArgs &a, const R *__rest
 #pragma unroll
         for (int j = 0; j < N; ++j)
 #pragma unroll
-            for (int c = 0; c < NC; ++c) atomicAdd(a.y + (size_t)nodes[j] * NC + c, cvt<double>(out[j][c]));
+            for (int c = 0; c < NC; ++c) red_add(a.y + (size_t)nodes[j] * NC + c, cvt<double>(out[j][c]));
     }
     if constexpr (OP == OP_NH_ADJOINT) {
         a.dmu[cell] = acc_mu;   // one thread per cell: plain stores, no reduction

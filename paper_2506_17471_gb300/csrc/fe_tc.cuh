@@ -1052,7 +1052,7 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
                         for (int m = 0; m < NC; ++m) {
                             // y += acc |det J| 2^K: FP32 multiply by the mantissa of |det J|,
                             // exact widening, exponent add
-                            atomicAdd(a.y + (size_t)node * NC + m, widen_pow2(__uint_as_float(r[m][i]) * mdet, K));
+                            red_add(a.y + (size_t)node * NC + m, widen_pow2(__uint_as_float(r[m][i]) * mdet, K));
                         }
                     }
                 }
