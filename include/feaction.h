@@ -231,8 +231,11 @@ typedef struct fe_plan fe_plan;
  * LAPLACE, HELMHOLTZ, NH_JACOBIAN and SVK_JACOBIAN (the residual kinds:
  * FE_ERR_UNSUPPORTED); cell2node must be 16-byte
  * aligned (FE_ERR_INVALID_ARG otherwise); tile_cells selects the 128-cell
- * pipelines per CTA (0 automatic, 128, 256 or 512; other values
- * FE_ERR_UNSUPPORTED); FE_ERR_UNSUPPORTED also if the degree has more than 256
+ * pipelines per CTA (128, 256 or 512, one thread per cell; other values
+ * FE_ERR_UNSUPPORTED); 0 lets the plan take the most pipelines that fit and,
+ * when fewer than four fit, 2 or 4 threads per cell (fe_plan_info reports
+ * threads_per_block = 128 x pipelines x threads per cell);
+ * FE_ERR_UNSUPPORTED also if the degree has more than 256
  * local nodes or the tables and operands do not fit one SM (FE_PREC_FP16X2
  * and FE_PREC_TF32 double both).
  * Errors: FE_ERR_INVALID_ARG, FE_ERR_UNSUPPORTED, FE_ERR_NO_MEMORY, FE_ERR_CUDA. */

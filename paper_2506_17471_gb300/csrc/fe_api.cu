@@ -435,7 +435,18 @@ static int plan_create_tc(const fe_form &f, const fe_mesh &m, const Variant &v, 
     p->ncomp = ncomp;
     p->tab_doubles = (int)(L.staged_bytes / sizeof(double));
     p->var = v;
-    p->var.block = kTcRows * L.pipes;
+    // threads per cell: with fewer than four pipelines, 2 or 4 threads share each
+    // tile row (more warps to hide the gather and scatter latency, same TMEM); a
+    // forced tile_cells keeps one.  The cell's threads combine their partial
+    // DoF ranges through the quadrature A-operand region, which must hold them.
+    int tpc = 1;
+    if (f.tile_cells == 0) {
+        const bool offset = f.kind != FE_FORM_MASS && f.kind != FE_FORM_HELMHOLTZ;
+        const size_t slot = 8 * (size_t)(offset ? 2 * fields * ncomp + 1 : fields + 1);
+        const size_t a2_bytes = L.nodes_off - L.a2_off;
+        while (L.pipes * tpc * 2 <= kTcMaxPipes && (size_t)kTcRows * tpc * 2 * slot <= a2_bytes) tpc *= 2;
+    }
+    p->var.block = kTcRows * L.pipes * tpc;
     p->adj = Variant{};
     p->smem_bytes = L.total;
     p->device = dev;

@@ -49,6 +49,7 @@
 
 #include <climits>
 #include <cstring>
+#include <type_traits>
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -420,35 +421,55 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// Barrier over the 128 threads of one pipeline (named barrier 1 + pipe).
-// The barrier ids are immediates, so the kernel reserves only the barriers it
-// uses.
-__device__ __forceinline__ void pipe_sync(int pipe)
+// Barrier over the 128 x tpc threads of one pipeline (named barrier 1 + pipe;
+// pipes x tpc <= 4).  Ids and counts are immediates, so the kernel reserves
+// only the barriers it uses.
+#define FE_TC_BAR(ID, CNT) asm volatile("bar.sync " #ID ", " #CNT ";" ::: "memory")
+__device__ __forceinline__ void pipe_sync(int pipe, int tpc)
 {
-    switch (pipe) {
-    case 0: asm volatile("bar.sync 1, 128;" ::: "memory"); break;
-    case 1: asm volatile("bar.sync 2, 128;" ::: "memory"); break;
-    case 2: asm volatile("bar.sync 3, 128;" ::: "memory"); break;
-    default: asm volatile("bar.sync 4, 128;" ::: "memory"); break;
+    if (tpc == 1) {
+        switch (pipe) {
+        case 0: FE_TC_BAR(1, 128); break;
+        case 1: FE_TC_BAR(2, 128); break;
+        case 2: FE_TC_BAR(3, 128); break;
+        default: FE_TC_BAR(4, 128); break;
+        }
+    } else if (tpc == 2) {
+        if (pipe == 0)
+            FE_TC_BAR(1, 256);
+        else
+            FE_TC_BAR(2, 256);
+    } else {
+        FE_TC_BAR(1, 512);
     }
 }
+#undef FE_TC_BAR
 
-#define FE_TC_BAR_RED_AND(ID)                                                        \
-    asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"                \
-                 "bar.red.and.pred q, " #ID ", 128, p;\n\tselp.u32 %0, 1, 0, q;\n\t}" \
-                 : "=r"(r)                                                            \
-                 : "r"((uint32_t)pred)                                                \
+#define FE_TC_BAR_RED_AND(ID, CNT)                                                         \
+    asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"                      \
+                 "bar.red.and.pred q, " #ID ", " #CNT ", p;\n\tselp.u32 %0, 1, 0, q;\n\t}"    \
+                 : "=r"(r)                                                                  \
+                 : "r"((uint32_t)pred)                                                      \
                  : "memory")
 
 // Barrier over one pipeline that also returns whether pred held on all its threads.
-__device__ __forceinline__ bool pipe_all(int pipe, bool pred)
+__device__ __forceinline__ bool pipe_all(int pipe, int tpc, bool pred)
 {
     uint32_t r;
-    switch (pipe) {
-    case 0: FE_TC_BAR_RED_AND(1); break;
-    case 1: FE_TC_BAR_RED_AND(2); break;
-    case 2: FE_TC_BAR_RED_AND(3); break;
-    default: FE_TC_BAR_RED_AND(4); break;
+    if (tpc == 1) {
+        switch (pipe) {
+        case 0: FE_TC_BAR_RED_AND(1, 128); break;
+        case 1: FE_TC_BAR_RED_AND(2, 128); break;
+        case 2: FE_TC_BAR_RED_AND(3, 128); break;
+        default: FE_TC_BAR_RED_AND(4, 128); break;
+        }
+    } else if (tpc == 2) {
+        if (pipe == 0)
+            FE_TC_BAR_RED_AND(1, 256);
+        else
+            FE_TC_BAR_RED_AND(2, 256);
+    } else {
+        FE_TC_BAR_RED_AND(1, 512);
     }
     return r != 0;
 }
@@ -483,7 +504,7 @@ __device__ __forceinline__ bool tc_wait(uint32_t sbar, uint32_t parity)
 // rounded to 16 bits.  Returns false if det F <= 0 at a live Neo-Hookean point.
 template <int OP, int D, typename TE, int TERMS>
 __device__ __forceinline__ bool tc_pointwise_hyper_jacobian(const TcLayout &L, uint32_t tlane, unsigned char *hb,
-                                                            const double *wd, int t, int ch, int nq, bool good,
+                                                            const double *wd, int t, int h, int tpc, int ch, int nq, bool good,
                                                             int ku_lin, const float (&Jf)[D][D],
                                                             const float (&Jh)[D][D], double mu, double lam)
 {
@@ -492,7 +513,7 @@ __device__ __forceinline__ bool tc_pointwise_hyper_jacobian(const TcLayout &L, u
     // coordinates, so the product stays in range)
     const float s_lin = __uint_as_float((unsigned)min(max(ku_lin + 127, 1), 254) << 23);
     bool ok = true;
-    for (int blk = 0; blk < L.N1p / 8; ++blk) {
+    for (int blk = h; blk < L.N1p / 8; blk += tpc) {   // the cell's tpc threads split the columns
         uint32_t r[2 * NC][8];
 #pragma unroll
         for (int fm = 0; fm < 2 * NC; ++fm) tc_ld8(tlane + (uint32_t)(fm * L.N1p + blk * 8), r[fm]);
@@ -608,7 +629,11 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
     __shared__ int s_tile[kTcMaxPipes];
 
     const TcLayout L = tc_layout(a.coop_n, a.nq, NC, KD, F, a.tc_qc, a.tc_pipes, TERMS, ESZ);
-    const int tid = threadIdx.x, pipe = tid >> 7, t = tid & (kTcRows - 1), warp = tid >> 5;
+    // tpc threads per cell (tile row): thread (h, t) of a pipeline works on row t
+    // and takes every tpc-th node batch, column block and output group
+    const int tpc = (int)blockDim.x / (kTcRows * L.pipes);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int pipe = tid / (kTcRows * tpc), pt = tid % (kTcRows * tpc), t = pt & (kTcRows - 1), h = pt >> 7;
     const int n = L.n;
     const uint32_t bar0 = (uint32_t)__cvta_generic_to_shared(&bars[0]);
     const uint32_t barp = (uint32_t)__cvta_generic_to_shared(&bars[1 + pipe]);
@@ -665,8 +690,8 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
     const double *wd = reinterpret_cast<const double *>(staged + L.wd_off);
 
     while (ok) {
-        if (t == 0) s_tile[pipe] = atomicAdd(a.sched, 1);
-        pipe_sync(pipe);
+        if (pt == 0) s_tile[pipe] = atomicAdd(a.sched, 1);
+        pipe_sync(pipe, tpc);
         const int tile = s_tile[pipe];
         if (tile >= n_tiles) break;
 
@@ -678,7 +703,7 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
             const int total = nb * n;
             const int32_t *src = a.c2n + (size_t)tile * kTcRows * n;
             const int n4 = total >> 2;
-            for (int i4 = t; i4 < n4; i4 += kTcRows) {
+            for (int i4 = pt; i4 < n4; i4 += kTcRows * tpc) {
                 const int4 v = __ldg(reinterpret_cast<const int4 *>(src) + i4);
                 const int vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
@@ -687,12 +712,12 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
                     snodes[c * P + j] = (unsigned)vv[s] < (unsigned)a.n_nodes ? vv[s] : -1;
                 }
             }
-            for (int e = 4 * n4 + t; e < total; e += kTcRows) {
+            for (int e = 4 * n4 + pt; e < total; e += kTcRows * tpc) {
                 const int v = __ldg(src + e), c = e / n, j = e - c * n;
                 snodes[c * P + j] = (unsigned)v < (unsigned)a.n_nodes ? v : -1;
             }
         }
-        pipe_sync(pipe);
+        pipe_sync(pipe, tpc);
 
         // geometry in FP64 (this thread's cell), then the DoFs' largest exponent
         int K = 0;              // output factor 2^K (with mdet below)
@@ -704,6 +729,20 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
         [[maybe_unused]] float Jf[D][D];   // Neo-Hookean: J^{-1} in binary32
         [[maybe_unused]] double mu_c = a.mu, lam_c = a.lam;
         bool good = t < nb;
+        // mass: largest exponent of |u|; gradient forms: range [min, max] of each
+        // component (ordered integer keys, no FP64 compare)
+        int emax[F] = {};
+        [[maybe_unused]] long long kmin[F][NC], kmax[F][NC];
+#pragma unroll
+        for (int f = 0; f < F; ++f)
+#pragma unroll
+            for (int m = 0; m < NC; ++m) {
+                kmin[f][m] = LLONG_MAX;
+                kmax[f][m] = LLONG_MIN;
+            }
+        bool nodes_ok = true;
+        double Jinv[D][D];
+        double det = 0.0;
         if (good) {
             const int cell = tile * kTcRows + t;
             double X[D + 1][D];
@@ -715,25 +754,12 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
 #pragma unroll
                 for (int i = 0; i < D; ++i) X[m][i] = in ? __ldg(a.coords + (size_t)v * D + i) : 0.0;
             }
-            double Jinv[D][D];
-            const double det = cell_geometry<D>(X, Jinv);
+            det = cell_geometry<D>(X, Jinv);
             if constexpr (kHyperJac) {
                 if (a.mu_cell) mu_c = __ldg(a.mu_cell + cell);
                 if (a.lam_cell) lam_c = __ldg(a.lam_cell + cell);
             }
-            // mass: largest exponent of |u|; gradient forms: range [min, max] of each
-            // component (ordered integer keys, no FP64 compare)
-            int emax[F] = {};
-            [[maybe_unused]] long long kmin[F][NC], kmax[F][NC];
-#pragma unroll
-            for (int f = 0; f < F; ++f)
-#pragma unroll
-                for (int m = 0; m < NC; ++m) {
-                    kmin[f][m] = LLONG_MAX;
-                    kmax[f][m] = LLONG_MIN;
-                }
-            bool nodes_ok = true;
-            for (int j0 = 0; j0 < n; j0 += 8) {
+            for (int j0 = 8 * h; j0 < n; j0 += 8 * tpc) {
                 int nd[8];
 #pragma unroll
                 for (int s = 0; s < 8; ++s) nd[s] = j0 + s < n ? snodes[t * P + j0 + s] : -2;
@@ -763,6 +789,48 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
 #pragma unroll
                 for (int s = 0; s < 8; ++s) nodes_ok &= nd[s] != -1;
             }
+        }
+        if (tpc > 1) {
+            // combine the partial ranges of the cell's tpc threads through the
+            // quadrature A-operand region (free until this tile's pointwise phase)
+            constexpr int S = kOffset ? 2 * F * NC + 1 : F + 1;
+            long long *xch = reinterpret_cast<long long *>(hb + L.a2_off);
+            long long *mine = xch + (size_t)(h * kTcRows + t) * S;
+            int q = 0;
+#pragma unroll
+            for (int f = 0; f < F; ++f) {
+                if constexpr (kOffset) {
+#pragma unroll
+                    for (int m = 0; m < NC; ++m) {
+                        mine[q++] = kmin[f][m];
+                        mine[q++] = kmax[f][m];
+                    }
+                } else {
+                    mine[q++] = emax[f];
+                }
+            }
+            mine[q] = nodes_ok ? 1 : 0;
+            pipe_sync(pipe, tpc);
+            for (int hh = 0; hh < tpc; ++hh) {
+                if (hh == h) continue;
+                const long long *other = xch + (size_t)(hh * kTcRows + t) * S;
+                int r = 0;
+#pragma unroll
+                for (int f = 0; f < F; ++f) {
+                    if constexpr (kOffset) {
+#pragma unroll
+                        for (int m = 0; m < NC; ++m) {
+                            kmin[f][m] = min(kmin[f][m], other[r++]);
+                            kmax[f][m] = max(kmax[f][m], other[r++]);
+                        }
+                    } else {
+                        emax[f] = max(emax[f], (int)other[r++]);
+                    }
+                }
+                nodes_ok &= other[r] != 0;
+            }
+        }
+        if (t < nb) {
             if (!good || !nodes_ok) {
                 set_status(a.status, FE_ERR_INDEX);
                 good = false;
@@ -826,7 +894,7 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
         }
         // A operands of the evaluation GEMM (one per field and component): row t =
         // this cell, K = local node j
-        for (int j0 = 0; j0 < L.K1p; j0 += 8) {
+        for (int j0 = 8 * h; j0 < L.K1p; j0 += 8 * tpc) {
             int nd[8];
 #pragma unroll
             for (int s = 0; s < 8; ++s) nd[s] = (good && j0 + s < n) ? snodes[t * P + j0 + s] : -1;
@@ -874,13 +942,13 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
         }
         fence_async_smem();
         tc_fence_before();
-        pipe_sync(pipe);
+        pipe_sync(pipe, tpc);
         tc_fence_after();
 
         const uint32_t id1 = tc_idesc(FMT, kTcRows, L.N1p), id2 = tc_idesc(FMT, kTcRows, L.N2p);
         for (int ch = 0; ch < L.nch; ++ch) {
             // ---- evaluation GEMM of chunk ch (its commit also covers the previous chunk's quadrature GEMM)
-            if (t == 0) {
+            if (pt == 0) {
                 // K steps of KK elements (32 bytes: two core matrices) at 256 B each
                 const uint32_t sbo = (uint32_t)L.K1p * 8u * ESZ;
                 const uint32_t a_region = (uint32_t)(kTcRows * L.K1p * ESZ),
@@ -898,7 +966,7 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
                         }
                 tc_commit(barp);
             }
-            if (!pipe_all(pipe, tc_wait(barp, phase))) {
+            if (!pipe_all(pipe, tpc, tc_wait(barp, phase))) {
                 tc_wait(barp, phase);
                 timed_out = true;
                 break;
@@ -908,10 +976,10 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
 
             // ---- pointwise: this thread's cell at the chunk's points, E' into the quadrature A operand
             if constexpr (kHyperJac) {
-                nh_ok &= tc_pointwise_hyper_jacobian<OP, D, TE, TERMS>(L, tlane, hb, wd, t, ch, a.nq, good, ku[1], Jf, Jh, mu_c,
-                                                          lam_c);
+                nh_ok &= tc_pointwise_hyper_jacobian<OP, D, TE, TERMS>(L, tlane, hb, wd, t, h, tpc, ch, a.nq, good, ku[1],
+                                                                        Jf, Jh, mu_c, lam_c);
             } else
-            for (int blk = 0; blk < L.N1p / 16; ++blk) {
+            for (int blk = h; blk < L.N1p / 16; blk += tpc) {   // the cell's tpc threads split the columns
                 uint32_t r[NC][16];
 #pragma unroll
                 for (int m = 0; m < NC; ++m) tc_ld16(tlane + (uint32_t)(m * L.N1p + blk * 16), r[m]);
@@ -994,11 +1062,11 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
             }
             fence_async_smem();
             tc_fence_before();
-            pipe_sync(pipe);
+            pipe_sync(pipe, tpc);
             tc_fence_after();
 
             // ---- quadrature GEMM of chunk ch, accumulated over the chunks
-            if (t == 0) {
+            if (pt == 0) {
                 const uint32_t sboa = (uint32_t)L.N1p * 8u * ESZ, sbob = (uint32_t)L.K2 * 8u * ESZ;
                 const uint32_t a_region = (uint32_t)(kTcRows * L.N1p * ESZ), b_region = (uint32_t)(L.N2p * L.K2 * ESZ);
                 for (int m = 0; m < NC; ++m)
@@ -1015,8 +1083,8 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
             }
         }
         if (timed_out) break;
-        if (t == 0) tc_commit(barp);
-        if (!pipe_all(pipe, tc_wait(barp, phase))) {
+        if (pt == 0) tc_commit(barp);
+        if (!pipe_all(pipe, tpc, tc_wait(barp, phase))) {
             tc_wait(barp, phase);
             timed_out = true;
             break;
@@ -1024,44 +1092,59 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
         phase ^= 1u;
         tc_fence_after();
 
-        // ---- scatter-add (FP64): row t of Y_m holds this cell's node contributions
-        for (int blk = 0; blk < L.N2p / 16; ++blk) {
-            uint32_t r[NC][16];
+        // ---- scatter-add (FP64): row t of Y_m holds this cell's node contributions;
+        // the cell's tpc threads take every tpc-th group of W nodes (W = 16 for one
+        // thread per cell, 8 otherwise, so that the groups split evenly)
+        auto scatter = [&](auto width) {
+            constexpr int W = decltype(width)::value;
+            for (int blk = h; blk < L.N2p / W; blk += tpc) {
+                uint32_t r[NC][W];
 #pragma unroll
-            for (int m = 0; m < NC; ++m) tc_ld16(tlane + (uint32_t)(L.acc1_cols + m * L.N2p + blk * 16), r[m]);
-            tc_wait_ld();
-            if (a.cell_out && t < nb) {
-                // node-gather scatter: store this cell's outputs (zeros for a skipped cell)
-                double *o = static_cast<double *>(a.cell_out) + (size_t)(tile * kTcRows + t) * n * NC;
-#pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const int j = blk * 16 + i;
-                    if (j < n) {
-#pragma unroll
-                        for (int m = 0; m < NC; ++m)
-                            o[j * NC + m] = good ? widen_pow2(__uint_as_float(r[m][i]) * mdet, K) : 0.0;
-                    }
+                for (int m = 0; m < NC; ++m) {
+                    const uint32_t col = tlane + (uint32_t)(L.acc1_cols + m * L.N2p + blk * W);
+                    if constexpr (W == 16)
+                        tc_ld16(col, r[m]);
+                    else
+                        tc_ld8(col, r[m]);
                 }
-            } else if (good && !a.cell_out) {
+                tc_wait_ld();
+                if (a.cell_out && t < nb) {
+                    // node-gather scatter: store this cell's outputs (zeros for a skipped cell)
+                    double *o = static_cast<double *>(a.cell_out) + (size_t)(tile * kTcRows + t) * n * NC;
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const int j = blk * 16 + i;
-                    if (j < n) {
-                        const int node = snodes[t * P + j];
+                    for (int i = 0; i < W; ++i) {
+                        const int j = blk * W + i;
+                        if (j < n) {
 #pragma unroll
-                        for (int m = 0; m < NC; ++m) {
-                            // y += acc |det J| 2^K: FP32 multiply by the mantissa of |det J|,
-                            // exact widening, exponent add
-                            red_add(a.y + (size_t)node * NC + m, widen_pow2(__uint_as_float(r[m][i]) * mdet, K));
+                            for (int m = 0; m < NC; ++m)
+                                o[j * NC + m] = good ? widen_pow2(__uint_as_float(r[m][i]) * mdet, K) : 0.0;
+                        }
+                    }
+                } else if (good && !a.cell_out) {
+#pragma unroll
+                    for (int i = 0; i < W; ++i) {
+                        const int j = blk * W + i;
+                        if (j < n) {
+                            const int node = snodes[t * P + j];
+#pragma unroll
+                            for (int m = 0; m < NC; ++m) {
+                                // y += acc |det J| 2^K: FP32 multiply by the mantissa of |det J|,
+                                // exact widening, exponent add
+                                red_add(a.y + (size_t)node * NC + m, widen_pow2(__uint_as_float(r[m][i]) * mdet, K));
+                            }
                         }
                     }
                 }
             }
-        }
+        };
+        if (tpc == 1)
+            scatter(std::integral_constant<int, 16>{});
+        else
+            scatter(std::integral_constant<int, 8>{});
         tc_fence_before();
-        pipe_sync(pipe);
+        pipe_sync(pipe, tpc);
     }
-    if (timed_out && t == 0) set_status(a.status, FE_ERR_TIMEOUT);
+    if (timed_out && pt == 0) set_status(a.status, FE_ERR_TIMEOUT);
     if (!nh_ok) set_status(a.status, FE_ERR_NONFINITE);
     tc_fence_before();
     __syncthreads();
