@@ -355,3 +355,52 @@ def test_tc_fp16x2_tables_too_large(fe):
         fe.Plan(M, fe.HELMHOLTZ, 8, precision="fp16x2")
     assert e.value.code == 2
     assert fe.Plan(M, fe.HELMHOLTZ, 8, precision="fp16").info.kernel == 2
+
+
+@pytest.mark.parametrize("prec", ["fp16", "fp16x2"])
+@pytest.mark.parametrize("kind,dim,N,p,q", [("elasticity", 3, 5, 4, 6), ("mass", 2, 13, 3, 6),
+                                            ("nh_jacobian", 2, 13, 4, 8)])
+def test_tc_pipelines_and_threads_per_cell(fe, kind, dim, N, p, q, prec):
+    """Every launch shape gives the same result to rounding: the automatic layout
+    (the most pipelines that fit, then 2 or 4 threads per cell when fewer than
+    four pipelines fit) and each forced pipeline count (one thread per cell)."""
+    from feinputs import lame_fields
+    from feinputs.fields import sinusoid_displacement
+    m, M = make(fe, dim, N, p, 970 + 10 * dim + p)
+    o = oracle.Oracle.from_mesh(m, q)
+    nc = 1 if kind == "mass" else dim
+    u = uniform_field(m.n_nodes * nc, 21 + p)
+    kw, ref = {}, None
+    if kind == "elasticity":
+        kw = dict(lam=1.25, mu=1.0)
+        ref = o.elasticity(u, 1.25, 1.0)
+    elif kind == "mass":
+        ref = o.mass(u)
+    else:
+        mu, lam = lame_fields(m.n_cells, 5)
+        ul = sinusoid_displacement(m, 6)
+        kw = dict(mu_cell=mu, lam_cell=lam, u_lin=cuda(ul))
+        ref = o.nh_jacobian(ul, u, mu, lam)
+    tol = TOL_X2 if prec == "fp16x2" else TOL16[prec]
+    auto = fe.Plan(M, getattr(fe, kind.upper()), q, precision=prec, **kw)
+    y_auto = auto.apply(cuda(u))
+    assert rel(y_auto, ref) <= tol and auto.status() == 0
+    tpb = auto.info.threads_per_block
+    assert tpb in (128, 256, 512) and auto.info.kernel == 2
+    shapes = 0
+    for tc in (128, 256, 512):
+        try:
+            plan = fe.Plan(M, getattr(fe, kind.upper()), q, precision=prec, tile_cells=tc, **kw)
+        except fe.FeError as e:
+            assert e.code == 2   # that many pipelines do not fit this layout
+            continue
+        assert plan.info.threads_per_block == tc
+        y = plan.apply(cuda(u))
+        assert rel(y, ref) <= tol and plan.status() == 0
+        # the same rounded operands; the chunking of the quadrature points (and so the
+        # FP32 accumulation order) and the scatter order may differ
+        assert rel(y, y_auto.cpu().numpy()) <= 1e-5
+        shapes += 1
+    assert shapes >= 1
+    with pytest.raises(fe.FeError):
+        fe.Plan(M, getattr(fe, kind.upper()), q, precision=prec, tile_cells=384, **kw)
