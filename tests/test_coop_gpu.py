@@ -177,3 +177,16 @@ def test_coop_tables_in_global_memory(fe, dim, N, p, prec):
     mp = fe.Plan(M, fe.MASS, q, precision=prec, cooperative=True, tables_global=True, tile_cells=7)
     assert rel(mp.apply(cuda(s)), o.mass(s)) <= tol
     assert res.status() == 0 and mp.status() == 0
+
+
+@pytest.mark.parametrize("prec", ["fp32"])
+def test_hp_mass_p3_reduced_precision_full_size(fe, prec):
+    """hp-sweep size mass P3 (4,008,004 DoFs) with FP32 contractions: every DoF
+    within the FP32 bound of the FP64 oracle."""
+    m, M = make(fe, 2, 667, 3, 20250620 + 667)
+    u = uniform_field(m.n_nodes, 1)
+    plan = fe.Plan(M, fe.MASS, 6, precision=prec)
+    y = plan.apply(cuda(u)).cpu().numpy()
+    ref = oracle.Oracle.from_mesh(m, 6).mass(u, threads=16)
+    assert rel(y, ref) <= TOL32
+    assert plan.status() == 0
