@@ -122,6 +122,14 @@ def cpu_oracle_rate(m, u, budget_cpu_s=12.0, threads=None):
             "single_core_value": dofs * reps1 / el1, "cpu_model": cpu_model()}
 
 
+def hbm_peak_gbs() -> float:
+    """Measured copy bandwidth of this machine's GPUs (GB/s), else the fallback figure."""
+    if os.path.exists(PEAKS_FILE):
+        with open(PEAKS_FILE) as f:
+            return float(json.load(f).get("hbm_gbs", 6800.0))
+    return 6800.0
+
+
 def cpu_model() -> str:
     """Host CPU name from /proc/cpuinfo (x86: model name; Arm: implementer/part ids)."""
     fields = {}
@@ -414,7 +422,9 @@ def time_secondary(fe, torch, flush, M_el, u_el, y64_el):
             t = timed(lambda: plan.apply(u, ys[prec]), reps=5)
             row[prec] = {"ms": t * 1e3, "dofs_per_s": m.n_nodes * nc / t,
                          "gflops": plan.flops() / t / 1e9, "kernel": plan.info.kernel,
-                         "nq": plan.info.nq}
+                         "nq": plan.info.nq,
+                         # footprint bytes / time against the measured copy bandwidth
+                         "hbm_frac": plan.info.bytes_min / t / 1e9 / hbm_peak_gbs()}
             if prec != "fp64":
                 row[prec]["speedup_vs_fp64"] = row["fp64"]["ms"] / row[prec]["ms"]
                 row[prec]["rel_dev_vs_fp64"] = rel(ys[prec], ys["fp64"])
@@ -454,7 +464,8 @@ def time_secondary(fe, torch, flush, M_el, u_el, y64_el):
             ys[prec] = torch.empty_like(u)
             t = timed(lambda: plan.apply(u, ys[prec]), reps=5)
             row[prec] = {"ms": t * 1e3, "dofs_per_s": m.n_nodes * nc / t, "gflops": plan.flops() / t / 1e9,
-                         "kernel": plan.info.kernel, "nq": plan.info.nq}
+                         "kernel": plan.info.kernel, "nq": plan.info.nq,
+                         "hbm_frac": plan.info.bytes_min / t / 1e9 / hbm_peak_gbs()}
             if prec == "fp64":
                 row[prec]["frac_of_fp64_peak"] = row[prec]["gflops"] / FP64_NOMINAL_GFLOPS
             else:
