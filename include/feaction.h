@@ -222,7 +222,10 @@ typedef struct fe_plan fe_plan;
  *   FE_PREC_FP64  rounding level (parity with an FP64 reference to 1e-12,
  *                 except where the action itself is ill-conditioned in FP64);
  *   FE_PREC_FP32  <= 5e-5 (each contraction's forward error is at most
- *                 gamma_256 of its absolute terms; measured 1e-7 - 6e-7);
+ *                 gamma_256 of its absolute terms; measured 1e-7 - 6e-7;
+ *                 DoFs and geometry factors below 2^-126 in magnitude enter
+ *                 the FP32 contractions as zero, so fields and cell volumes
+ *                 must lie in binary32's normal range);
  *   FE_PREC_BF16, FE_PREC_FP16, FE_PREC_TF32  <= 8 u16 with u16 = 2^-8 (BF16)
  *                 or 2^-11 (FP16, TF32), i.e. 3.1e-2 / 3.9e-3 (measured 0.6 - 4.3 u16);
  *   FE_PREC_FP16X2 <= 5e-5 (the FP32 bound).
@@ -439,12 +442,13 @@ int fe_action_noalloc(const fe_form *form, const fe_mesh *mesh, const double *ta
 int fe_measure_fp64_peak(double *scratch, size_t scratch_doubles, double *gflops);
 
 /* Self-test of the mixed-precision kernels' binary64<->binary32 conversions
- * (integer bit-pattern conversions with round-to-nearest-even, used instead of
- * the hardware conversion, which issues on the slow FP64 pipe of this part)
- * against the hardware conversions, over the device array x [n]:
- * count[0] += binary64->binary32 mismatches, count[1] += binary32->binary64
- * mismatches; count is a device array of 2 zero-initialised uint64.
- * Asynchronous on stream. */
+ * (branch-free integer bit-pattern conversions with round-to-nearest-even,
+ * used instead of the hardware conversion, which issues on the slow FP64 pipe
+ * of this part; values below binary32's normal range, |x| < 2^-126, become
+ * signed zero) against the hardware conversions with that flush applied, over
+ * the device array x [n]: count[0] += binary64->binary32 mismatches, count[1]
+ * += binary32->binary64 mismatches; count is a device array of 2
+ * zero-initialised uint64.  Asynchronous on stream. */
 int fe_selftest_conversions(const double *x, long long n, unsigned long long *count, void *stream);
 
 /* Device self-test of the tensor-core kernel's integer conversions binary64 ->

@@ -875,18 +875,21 @@ extern "C" int fe_measure_fp64_peak(double *scratch, size_t scratch_doubles, dou
 
 namespace fe {
 namespace {
-// Self-test of the bit-pattern conversions against the hardware conversions:
-// count[0] += binary64->binary32 mismatches, count[1] += binary32->binary64
-// mismatches (NaN results compare equal to NaN).
+// Self-test of the bit-pattern conversions against the hardware conversions,
+// inputs below binary32's normal range expected as signed zero: count[0] +=
+// binary64->binary32 mismatches, count[1] += binary32->binary64 mismatches (NaN
+// results compare equal to NaN).
 __global__ void k_selftest_conversions(const double *x, long long n, unsigned long long *count)
 {
     unsigned long long bad32 = 0, bad64 = 0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         const double v = x[i];
-        const float a = f64_to_f32_rn(v), b = __double2float_rn(v);
+        const float a = f64_to_f32_rn(v);
+        const float b = fabs(v) < 0x1p-126 ? copysignf(0.f, (float)v) : __double2float_rn(v);
         if (__float_as_uint(a) != __float_as_uint(b) && !(isnan(a) && isnan(b))) ++bad32;
-        const double c = f32_to_f64(b), d = (double)b;
+        const float h = __double2float_rn(v);   // binary32 inputs for the widening, subnormals included
+        const double c = f32_to_f64(h), d = fabsf(h) < 0x1p-126f ? copysign(0.0, (double)h) : (double)h;
         if (__double_as_longlong(c) != __double_as_longlong(d) && !(isnan(c) && isnan(d))) ++bad64;
     }
     if (bad32) atomicAdd(count, bad32);

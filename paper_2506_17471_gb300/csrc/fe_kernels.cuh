@@ -157,33 +157,39 @@ __device__ __forceinline__ double det_cof(const double (&A)[D][D], double (&C)[D
 }
 
 // IEEE 754 binary64 -> binary32 with round-to-nearest-even, computed with
-// integer operations on the bit patterns.  On this part the hardware
-// conversion issues on the FP64 pipe (about 1/64 of the FP32 rate), so the
-// mixed-precision kernels convert DoFs, outputs and geometry this way.  Inputs
-// whose binary32 result would be zero, subnormal or not finite (and NaN) take
-// the hardware conversion.
+// integer operations on the bit patterns and without branches.  On this part
+// the hardware conversion issues on the FP64 pipe (about 1/64 of the FP32
+// rate), and a hardware fallback for rare inputs would be predicated into every
+// call, so the mixed-precision kernels convert DoFs, outputs and geometry this
+// way.  Inputs below binary32's normal range (|x| < 2^-126) give signed zero;
+// overflow gives infinity; NaN stays a quiet NaN.
 __device__ __forceinline__ float f64_to_f32_rn(double x)
 {
     const unsigned hi = (unsigned)__double2hiint(x);
     const unsigned lo = (unsigned)__double2loint(x);
+    const unsigned sign = hi & 0x80000000u;
     const int fexp = (int)((hi >> 20) & 0x7FFu) - 896;   // binary32 biased exponent
-    if ((unsigned)(fexp - 1) >= 254u) return __double2float_rn(x);
-    unsigned bits = (hi & 0x80000000u) | ((unsigned)fexp << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+    unsigned bits = sign | ((unsigned)fexp << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
     const unsigned rest = lo & 0x1FFFFFFFu;               // the 29 discarded mantissa bits
-    const unsigned up = (rest > 0x10000000u) || (rest == 0x10000000u && (bits & 1u));
-    return __uint_as_float(bits + up);                    // a carry may round up to infinity
+    bits += (rest > 0x10000000u) || (rest == 0x10000000u && (bits & 1u));   // a carry may reach infinity
+    const bool nan = fexp == 0x7FF - 896 && ((hi & 0xFFFFFu) | lo);
+    bits = fexp < 1 ? sign : bits;
+    bits = fexp > 254 ? (sign | 0x7F800000u | (nan ? 0x400000u : 0u)) : bits;
+    return __uint_as_float(bits);
 }
 
-// IEEE 754 binary32 -> binary64 (exact), by re-biasing the exponent and
-// widening the mantissa; zero, subnormal, infinite and NaN inputs take the
-// hardware conversion.
+// IEEE 754 binary32 -> binary64 by re-biasing the exponent and widening the
+// mantissa, without branches: exact for normal inputs; zero and subnormal inputs
+// give signed zero; infinity stays infinity, NaN a quiet NaN.
 __device__ __forceinline__ double f32_to_f64(float f)
 {
     const unsigned b = __float_as_uint(f);
-    const unsigned e = (b >> 23) & 0xFFu;
-    if (e == 0u || e == 255u) return (double)f;
-    const unsigned hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7FFFFFu) >> 3);
-    return __hiloint2double((int)hi, (int)(b << 29));
+    const unsigned e = (b >> 23) & 0xFFu, sign = b & 0x80000000u, m = b & 0x7FFFFFu;
+    unsigned hi = sign | ((e + 896u) << 20) | (m >> 3), lo = m << 29;
+    hi = e == 0u ? sign : hi;
+    lo = e == 0u ? 0u : lo;
+    hi = e == 255u ? (sign | 0x7FF00000u | (m >> 3) | (m ? 0x80000u : 0u)) : hi;
+    return __hiloint2double((int)hi, (int)lo);
 }
 
 template <typename U, typename T>

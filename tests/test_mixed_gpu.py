@@ -97,8 +97,9 @@ def test_full_elasticity_p2_3d_fp32(fe):
 
 
 def test_bit_conversions_match_hardware(fe):
-    """The mixed kernels convert binary64 <-> binary32 with integer bit operations
-    (round to nearest even); they must agree bit for bit with CUDA's conversion."""
+    """The mixed kernels convert binary64 <-> binary32 with branch-free integer bit
+    operations (round to nearest even, values below 2^-126 flushed to signed
+    zero); they must agree bit for bit with CUDA's conversion with that flush."""
     import ctypes
     from paper_2506_17471_gb300 import _native as N
     rng = np.random.default_rng(0)
