@@ -210,7 +210,7 @@ def test_nh_residual_is_energy_gradient(oracle_built):
 
 
 def test_nh_jacobian_is_residual_derivative(oracle_built):
-    """BASELINE's FD check: J(u) du = (r(u + h du) - r(u - h du)) / 2h, h = 1e-6."""
+    """Central-difference check of the Jacobian action: J(u) du = (r(u + h du) - r(u - h du)) / 2h, h = 1e-6."""
     m, o, mu, lam = _nh_setup()
     n = m.n_nodes * 2
     u = sinusoid_displacement(m, 41)
