@@ -534,6 +534,53 @@ def time_secondary(fe, torch, flush, M_el, u_el, y64_el):
 _BOUNDARY = []
 
 
+def time_ordering(fe, torch, flush):
+    """Gather locality (Sec. "Behavior at low orders"): the low-order P1 3D elasticity
+    action at ~1e6 tets and the P2 3D workload, each in the structured numbering, in a
+    random numbering (an unstructured mesh whose numbering carries no locality), and
+    in that random numbering renumbered by the Morton + first-touch ordering."""
+    from feinputs import shuffled_mesh, structured_mesh, uniform_field
+
+    def timed(fn, reps=10):
+        for _ in range(3):
+            fn()
+        ts = []
+        for _ in range(reps):
+            flush()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.mean(ts) * 1e-3
+
+    out = {}
+    for name, N, p, q, scheme in (("elasticity_p1_3d_n55", 55, 1, 0, "conical"),
+                                  ("elasticity_p2_3d_n32", 32, 2, 2, "symmetric"),
+                                  # u, y and the maps (~180 MB) larger than the 126 MB L2
+                                  ("elasticity_p2_3d_n64", 64, 2, 2, "symmetric")):
+        m0 = structured_mesh(3, N, p, jitter=0.15, seed=20250640 + N)
+        ms = shuffled_mesh(m0, 7)
+        t0 = time.perf_counter()
+        perm, vnew, nnew = fe.mesh_order(3, ms.coords, ms.cell2vertex, ms.cell2node, ms.n_nodes)
+        x2, c2v, c2n = fe.apply_mesh_order(ms.coords, ms.cell2vertex, ms.cell2node, perm, vnew, nnew)
+        order_s = time.perf_counter() - t0
+        u = torch.from_numpy(uniform_field(m0.n_nodes * 3, 11)).cuda()
+        row = {"cells": m0.n_cells, "dofs": m0.n_nodes * 3, "ordering_host_s": order_s}
+        for numbering, (x, cv, cn) in (("structured", (m0.coords, m0.cell2vertex, m0.cell2node)),
+                                       ("random", (ms.coords, ms.cell2vertex, ms.cell2node)),
+                                       ("reordered", (x2, c2v, c2n))):
+            M = fe.Mesh(3, p, x, cv, cn, m0.n_nodes)
+            for prec in ("fp64", "fp32"):
+                plan = fe.Plan(M, fe.ELASTICITY, q, lam=1.25, mu=1.0, precision=prec, quad_scheme=scheme)
+                y = torch.empty_like(u)
+                t = timed(lambda: plan.apply(u, y))
+                row[f"{numbering}_{prec}_ms"] = t * 1e3
+        out[name] = row
+    return out
+
+
 def time_batched(fe, torch):
     """64 independent meshes (uneven sizes, forms, degrees 1-4, 2D and 3D): per-problem
     launch configuration from the autotuner; per-mesh launches (eager and captured in
@@ -766,6 +813,7 @@ def run_ours(args):
         if not args.no_extra:
             extra.update(time_secondary(fe, torch, flush, M, u, y))
             extra["batched_64_meshes"] = time_batched(fe, torch)
+            extra["mesh_ordering"] = time_ordering(fe, torch, flush)
         hbm_bound = flops / plan.info.bytes_min * peaks.get("hbm_gbs", 6800.0)
         extra["roofline_min_gflops"] = min(FP64_NOMINAL_GFLOPS, hbm_bound)
         extra["arithmetic_intensity_flop_per_byte"] = flops / plan.info.bytes_min

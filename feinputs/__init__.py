@@ -8,15 +8,17 @@ geometry maps, no forms), so both the library under test and the CPU oracle can
 consume its output without sharing any of the method's code.
 
 The workloads follow the paper's experimental setup (Sec. "Experimental Setup"):
-meshes of the unit square and the unit cube, here with the sizes, jitter and
-field recipes stated in the design doc's input recipe.
+meshes of the unit square and the unit cube, with interior vertices jittered by
+a seeded generator.  :func:`shuffled_mesh` renumbers a mesh at random (cells,
+vertices and nodes), standing in for an unstructured mesh whose numbering
+carries no locality.
 """
 
-from .mesh import SimplexMesh, structured_mesh, local_multi_indices, n_local_nodes
+from .mesh import SimplexMesh, structured_mesh, shuffled_mesh, local_multi_indices, n_local_nodes
 from .fields import (uniform_field, sinusoid_displacement, lame_fields,
                      interpolate_at_nodes)
 
 __all__ = [
-    "SimplexMesh", "structured_mesh", "local_multi_indices", "n_local_nodes",
+    "SimplexMesh", "structured_mesh", "shuffled_mesh", "local_multi_indices", "n_local_nodes",
     "uniform_field", "sinusoid_displacement", "lame_fields", "interpolate_at_nodes",
 ]

@@ -181,3 +181,25 @@ def structured_mesh(dim: int, N: int, degree: int, jitter: float = 0.0,
                        cell2node=np.ascontiguousarray(cell2node.astype(np.int32)),
                        n_nodes=int(n_nodes), node_lattice=node_lattice,
                        seed=seed, jitter=jitter, meta={"h": h})
+
+
+def shuffled_mesh(mesh: SimplexMesh, seed: int) -> SimplexMesh:
+    """The same mesh with its cells, vertices and nodes renumbered by seeded
+    random permutations: an unstructured numbering with no locality.  Node k of
+    the result is node ``meta["node_old"][k]`` of ``mesh``; cell k is cell
+    ``meta["cell_old"][k]``."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    cell_old = rng.permutation(mesh.n_cells)
+    vert_old = rng.permutation(mesh.n_vertices)
+    node_old = rng.permutation(mesh.n_nodes)
+    vert_new = np.empty_like(vert_old)
+    vert_new[vert_old] = np.arange(vert_old.size)
+    node_new = np.empty_like(node_old)
+    node_new[node_old] = np.arange(node_old.size)
+    return SimplexMesh(dim=mesh.dim, degree=mesh.degree, N=mesh.N,
+                       coords=np.ascontiguousarray(mesh.coords[vert_old]),
+                       cell2vertex=np.ascontiguousarray(vert_new[mesh.cell2vertex[cell_old]].astype(np.int32)),
+                       cell2node=np.ascontiguousarray(node_new[mesh.cell2node[cell_old]].astype(np.int32)),
+                       n_nodes=mesh.n_nodes, node_lattice=mesh.node_lattice[node_old],
+                       seed=mesh.seed, jitter=mesh.jitter,
+                       meta=dict(mesh.meta, cell_old=cell_old, node_old=node_old, vert_old=vert_old))

@@ -475,6 +475,32 @@ int fe_round16(const double *x, size_t n, int precision, uint16_t *bits);
  * n > 0). */
 int fe_round_tf32(const double *x, size_t n, int from_binary32, uint32_t *bits);
 
+/* ------------------------------------------------------------- mesh orderings
+ * Host functions.  At low order the action is dominated by its indirect
+ * gathers and scatters, whose cache behaviour depends on how close the DoFs of
+ * cells processed together are in memory (Sec. "Behavior at low orders").
+ * These compute locality orderings; applying them is a renumbering, not a
+ * change of the operator. */
+
+/* Cells along a Morton (Z-order) curve of their centroids (bounding box
+ * quantised to 2^21 levels per axis in 3D, 2^32 in 2D; ties keep the input
+ * order).  coords [n_vertices][dim], cell2vertex [n_cells][dim+1] (host);
+ * perm [n_cells] (host, caller-owned) receives the old index of the k-th cell
+ * of the new order.  Errors: FE_ERR_INVALID_ARG, FE_ERR_INDEX (a vertex index
+ * out of range), FE_ERR_BAD_MESH (a non-finite centroid). */
+int fe_order_cells_morton(int dim, int n_vertices, int n_cells, const double *coords,
+                          const int32_t *cell2vertex, int32_t *perm);
+
+/* Entities (nodes or vertices) numbered by first touch: visiting the cells in
+ * the order cell_order [n_cells] (NULL: 0, 1, ...), each not yet numbered
+ * entity of cell2entity [n_cells][per_cell] gets the next index; entities no
+ * cell references follow in their old order.  new_of_old [n_entities] (host,
+ * caller-owned) receives the new index of each old entity.  Errors:
+ * FE_ERR_INVALID_ARG (bad sizes, NULL, cell_order not a permutation),
+ * FE_ERR_INDEX (an index out of range). */
+int fe_order_first_touch(int n_entities, int n_cells, int per_cell, const int32_t *cell2entity,
+                         const int32_t *cell_order, int32_t *new_of_old);
+
 #ifdef __cplusplus
 }
 #endif

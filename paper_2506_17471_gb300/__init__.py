@@ -14,8 +14,10 @@ from .api import (MASS, ELASTICITY, NH_RESIDUAL, NH_JACOBIAN, LAPLACE, HELMHOLTZ
                   PlanInfo,
                   NeoHookeanResidual, Batch, tabulate, measure_fp64_peak, action)
 from .solvers import cg, cg_ir
+from .ordering import mesh_order, apply_mesh_order, permute_dofs, unpermute_dofs
 
 __all__ = ["FeError", "LIB_PATH", "EXPORTS", "MASS", "ELASTICITY", "NH_RESIDUAL", "NH_JACOBIAN",
            "LAPLACE", "HELMHOLTZ", "SVK_RESIDUAL", "SVK_JACOBIAN",
            "FORM_NAMES", "PRECISIONS", "QUAD_SCHEMES", "Mesh", "Plan", "PlanInfo", "NeoHookeanResidual", "Batch", "tabulate",
-           "measure_fp64_peak", "action", "cg", "cg_ir"]
+           "measure_fp64_peak", "action", "cg", "cg_ir", "mesh_order", "apply_mesh_order", "permute_dofs",
+           "unpermute_dofs"]

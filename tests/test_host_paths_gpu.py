@@ -84,3 +84,31 @@ def test_one_call_action_caches_plans(setup):
     # a host input goes through the end-to-end path
     yh = fe.action(M, fe.ELASTICITY, u.cpu(), 2, lam=1.25, mu=1.0)
     assert not yh.is_cuda and float((yh - y.cpu()).abs().max() / y.abs().max()) < 1e-14
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("dim,N,p,q", [(3, 8, 1, 0), (3, 6, 2, 2), (2, 30, 3, 6)])
+def test_reordered_mesh_action(setup, prec, dim, N, p, q):
+    """The action on a randomly numbered mesh, renumbered by the Morton + first-touch
+    ordering, is the same operator: y' = A'(P u) gives y = P^T y'."""
+    import oracle
+    from feinputs import shuffled_mesh
+    fe, _, _ = setup
+    m = shuffled_mesh(structured_mesh(dim, N, p, jitter=0.2 if dim == 2 else 0.15, seed=30 + N), 31)
+    perm, vnew, nnew = fe.mesh_order(dim, m.coords, m.cell2vertex, m.cell2node, m.n_nodes)
+    x2, c2v, c2n = fe.apply_mesh_order(m.coords, m.cell2vertex, m.cell2node, perm, vnew, nnew)
+    kind = fe.ELASTICITY if dim == 3 else fe.MASS
+    nc = dim if kind == fe.ELASTICITY else 1
+    kw = dict(lam=1.25, mu=1.0) if kind == fe.ELASTICITY else {}
+    u = uniform_field(m.n_nodes * nc, 32)
+    M1 = fe.Mesh(dim, p, m.coords, m.cell2vertex, m.cell2node, m.n_nodes)
+    M2 = fe.Mesh(dim, p, x2, c2v, c2n, m.n_nodes)
+    y1 = fe.Plan(M1, kind, q, precision=prec, **kw).apply(torch.from_numpy(u).cuda()).cpu().numpy()
+    y2 = fe.Plan(M2, kind, q, precision=prec, **kw).apply(
+        torch.from_numpy(fe.permute_dofs(u, nnew, nc)).cuda()).cpu().numpy()
+    back = fe.unpermute_dofs(y2, nnew, nc)
+    o = oracle.Oracle(dim, p, q, m.coords, m.cell2vertex, m.cell2node, m.n_nodes)
+    ref = o.elasticity(u, 1.25, 1.0) if kind == fe.ELASTICITY else o.mass(u)
+    tol = 1e-12 if prec == "fp64" else 5e-5
+    assert np.abs(back - ref).max() <= tol * np.abs(ref).max()
+    assert np.abs(y1 - ref).max() <= tol * np.abs(ref).max()
