@@ -648,6 +648,19 @@ extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan 
     return FE_OK;
 }
 
+// Copy streams and events of fe_action_host_pipelined (null handles skipped).
+static void release_pipeline(fe_plan *plan)
+{
+    for (cudaEvent_t &e : plan->pipe_ev) {
+        if (e) cudaEventDestroy(e);
+        e = nullptr;
+    }
+    if (plan->pipe_h2d) cudaStreamDestroy(plan->pipe_h2d);
+    if (plan->pipe_d2h) cudaStreamDestroy(plan->pipe_d2h);
+    plan->pipe_h2d = plan->pipe_d2h = nullptr;
+    plan->pipe_ready = false;
+}
+
 extern "C" int fe_plan_destroy(fe_plan *plan)
 {
     if (!plan) return FE_OK;
@@ -657,11 +670,7 @@ extern "C" int fe_plan_destroy(fe_plan *plan)
     cudaFree(plan->d_cell_out);
     cudaFree(plan->d_node_ptr);
     cudaFree(plan->d_node_inc);
-    if (plan->pipe_ready) {
-        for (cudaEvent_t e : plan->pipe_ev) cudaEventDestroy(e);
-        cudaStreamDestroy(plan->pipe_h2d);
-        cudaStreamDestroy(plan->pipe_d2h);
-    }
+    release_pipeline(plan);
     delete plan;
     return FE_OK;
 }
@@ -777,11 +786,14 @@ extern "C" int fe_action_host_pipelined(fe_plan *plan, int n_steps, const double
     for (int i = 0; i < n_steps; ++i)
         if (!u_host[i] || !y_host[i]) return FE_ERR_INVALID_ARG;
     if (!plan->pipe_ready) {
-        if (cudaStreamCreateWithFlags(&plan->pipe_h2d, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaStreamCreateWithFlags(&plan->pipe_d2h, cudaStreamNonBlocking) != cudaSuccess)
+        bool ok = cudaStreamCreateWithFlags(&plan->pipe_h2d, cudaStreamNonBlocking) == cudaSuccess;
+        ok = ok && cudaStreamCreateWithFlags(&plan->pipe_d2h, cudaStreamNonBlocking) == cudaSuccess;
+        for (cudaEvent_t &e : plan->pipe_ev) ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            release_pipeline(plan);   // whatever was created before the failure
+            cudaGetLastError();
             return FE_ERR_CUDA;
-        for (cudaEvent_t &e : plan->pipe_ev)
-            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return FE_ERR_CUDA;
+        }
         plan->pipe_ready = true;
     }
     cudaStream_t sc = static_cast<cudaStream_t>(stream);
