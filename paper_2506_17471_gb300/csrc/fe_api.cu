@@ -15,7 +15,7 @@
 namespace fe {
 namespace {
 
-constexpr int kMaxVariants = 256;
+constexpr int kMaxVariants = 512;
 Variant g_variants[kMaxVariants];
 int g_nvariants = 0;
 std::once_flag g_once;
@@ -32,7 +32,9 @@ void init_registry()
     n += register_variants_tc3(g_variants + n, kMaxVariants - n);
     n += register_variants_forms(g_variants + n, kMaxVariants - n);
     n += register_variants_coop_forms(g_variants + n, kMaxVariants - n);
-    g_nvariants = n;
+    // a full table means some registration was cut off: serve nothing rather than
+    // a silently incomplete set (every plan then fails with FE_ERR_UNSUPPORTED)
+    g_nvariants = n < kMaxVariants ? n : 0;
 }
 
 // The thread-per-cell variant compiled for exactly this degree, else (or when
