@@ -11,8 +11,9 @@
  * "generalized_bilinear_form", with the quadrature sum of Eq.
  * "poisson_action_w_quadrature" and the tabulations of Eq.
  * "poisson_tabulated_values"); the forms are those of Appendix A (Mass,
- * Elasticity) plus a compressible Neo-Hookean law (residual and its Jacobian
- * action) in place of the appendix's St. Venant-Kirchhoff hyperelasticity.
+ * Laplacian, Helmholtz, Elasticity, St. Venant-Kirchhoff hyperelasticity:
+ * residual and Jacobian action) plus a compressible Neo-Hookean law (residual,
+ * Jacobian action and adjoint with per-cell material derivatives).
  *
  * Conventions shared by every entry point
  * ---------------------------------------
