@@ -90,3 +90,21 @@ def test_gather_scatter_skips_bad_cells(fe):
     keep[77] = False
     o = oracle.Oracle(2, 3, 6, m.coords, m.cell2vertex[keep], m.cell2node[keep], m.n_nodes)
     assert rel(y, o.mass(u)) <= 1e-12
+
+
+@pytest.mark.parametrize("prec,tol", [("fp16", 8 * 2.0 ** -11), ("fp16x2", 5e-5), ("tf32", 8 * 2.0 ** -11)])
+def test_gather_scatter_tensor_cores_threads_per_cell(fe, prec, tol):
+    """Elasticity P4 3D on the tensor cores runs two pipelines (FP16) or one (split
+    FP16, TF32), each with two threads per cell; the per-cell stores of the
+    deterministic scatter are split among the cell's threads."""
+    m = structured_mesh(3, 4, 4, jitter=0.15, seed=93)
+    M = fe.Mesh(3, 4, m.coords, m.cell2vertex, m.cell2node, m.n_nodes)
+    o = oracle.Oracle.from_mesh(m, 6)
+    u = uniform_field(m.n_nodes * 3, 94)
+    plan = fe.Plan(M, fe.ELASTICITY, 6, lam=1.25, mu=1.0, precision=prec, gather_scatter=True)
+    assert plan.info.kernel == 2 and plan.info.threads_per_block == (512 if prec == "fp16" else 256)
+    y1 = plan.apply(cuda(u))
+    y2 = plan.apply(cuda(u))
+    assert torch.equal(y1, y2)
+    assert rel(y1, o.elasticity(u, 1.25, 1.0)) <= tol
+    assert plan.status() == 0
