@@ -404,3 +404,24 @@ def test_tc_pipelines_and_threads_per_cell(fe, kind, dim, N, p, q, prec):
     assert shapes >= 1
     with pytest.raises(fe.FeError):
         fe.Plan(M, getattr(fe, kind.upper()), q, precision=prec, tile_cells=384, **kw)
+
+
+@pytest.mark.parametrize("j", [3, 30])
+def test_tc_bad_index_two_threads_per_cell(fe, j):
+    """Elasticity P4 3D runs two threads per cell, each gathering half of the cell's
+    node batches: a bad index in either half (local node 3: the first thread's
+    batch; 30: the second's) must skip the whole cell on both threads."""
+    from paper_2506_17471_gb300 import _native as N
+    m, _ = make(fe, 3, 5, 4, 46)
+    c2n = m.cell2node.copy()
+    c2n[300, j] = -5
+    M = fe.Mesh(3, 4, m.coords, m.cell2vertex, c2n, m.n_nodes)
+    plan = fe.Plan(M, fe.ELASTICITY, 6, lam=1.25, mu=1.0, precision="fp16")
+    assert plan.info.threads_per_block == 512
+    u = uniform_field(m.n_nodes * 3, 7)
+    y = plan.apply(cuda(u)).cpu().numpy()
+    assert plan.status() == N.FE_ERR_INDEX
+    keep = np.ones(m.n_cells, dtype=bool)
+    keep[300] = False
+    o = oracle.Oracle(3, 4, 6, m.coords, m.cell2vertex[keep], m.cell2node[keep], m.n_nodes)
+    assert rel(y, o.elasticity(u, 1.25, 1.0)) <= TOL16["fp16"]
