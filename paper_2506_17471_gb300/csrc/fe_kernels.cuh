@@ -721,15 +721,19 @@ __device__ __forceinline__ void action_cell(const ActionArgs &a, const R *__rest
 // lane) from a global counter until the cells run out, so SMs that finish early
 // take more work and the tail is at most one chunk.  The last warp to leave
 // resets both counters, so every launch starts from zero without a memset.
+// No fence is needed: every fetch from the first counter is an atomic whose
+// returned value the fetching thread used before its warp (or, for the CTA-level
+// queues, its CTA after a barrier) reached this point, so all fetches are
+// performed before the leave count reaches the last warp; and the next launch
+// sees the reset through the kernel boundary.  (A fence here would make each
+// warp wait for its scatter reductions before it leaves.)
 __device__ __forceinline__ void leave_queue(int32_t *sched)
 {
     if ((threadIdx.x & 31) == 0) {
         const int total_warps = (int)(gridDim.x * (blockDim.x >> 5));
-        __threadfence();
         if (atomicAdd(sched + 1, 1) == total_warps - 1) {
             sched[0] = 0;
             sched[1] = 0;
-            __threadfence();
         }
     }
 }
