@@ -156,6 +156,12 @@ class Plan:
             N.lib.fe_plan_destroy(self._h)
             self._h = ctypes.c_void_p(0)
 
+    def __enter__(self) -> "Plan":
+        return self
+
+    def __exit__(self, *exc) -> None:
+        self.close()
+
     def __del__(self):
         try:
             self.close()
@@ -371,6 +377,12 @@ class Batch:
         if getattr(self, "_h", None) is not None and self._h.value:
             N.lib.fe_batch_destroy(self._h)
             self._h = ctypes.c_void_p(0)
+
+    def __enter__(self) -> "Batch":
+        return self
+
+    def __exit__(self, *exc) -> None:
+        self.close()
 
     def __del__(self):
         try:
