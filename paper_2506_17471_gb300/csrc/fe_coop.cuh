@@ -131,19 +131,28 @@ __device__ __forceinline__ void coop_batch(const ActionArgs &a, const CoopLayout
     int *snodes = S.nodes;
     double *sgeo = S.geo;
     double *sacc = S.acc;
-    // ---- A: gather nodes and DoFs; geometry (one thread per cell)
+    // ---- A: gather nodes and DoFs; geometry (one thread per cell).  Hyperelastic
+    // forms in reduced precision use only gradients and store the DoFs relative to
+    // the cell's first node, differenced in FP64 (see gather_dofs).
+    constexpr bool kRel = !std::is_same<R, double>::value && OpTraits<OP, D>::kNonlinear;
     for (int i = threadIdx.x; i < nb * n; i += blockDim.x) {
         const int c = i / n, j = i - c * n;
         const int node = __ldg(a.c2n + (size_t)(cell0 + c) * n + j);
         const bool ok = (unsigned)node < (unsigned)a.n_nodes;
         if (!ok) set_status(a.status, FE_ERR_INDEX);
         snodes[c * n + j] = ok ? node : -1;
+        [[maybe_unused]] int node0 = node;
+        if constexpr (kRel) node0 = __ldg(a.c2n + (size_t)(cell0 + c) * n);
+        const bool ok0 = (unsigned)node0 < (unsigned)a.n_nodes;
 #pragma unroll
         for (int f = 0; f < FIELDS; ++f) {
             const double *src = (f == 0) ? a.u : a.u_lin;
 #pragma unroll
-            for (int m = 0; m < NC; ++m)
-                sl[c * L.ls + (f * n + j) * NC + m] = ok ? __ldg(src + (size_t)node * NC + m) : 0.0;
+            for (int m = 0; m < NC; ++m) {
+                double v = ok ? __ldg(src + (size_t)node * NC + m) : 0.0;
+                if constexpr (kRel) v = (ok && ok0) ? v - __ldg(src + (size_t)node0 * NC + m) : 0.0;
+                sl[c * L.ls + (f * n + j) * NC + m] = v;
+            }
         }
     }
     for (int c = threadIdx.x; c < nb; c += blockDim.x) {

@@ -403,20 +403,35 @@ __device__ __forceinline__ bool gather_nodes(const int32_t *__restrict__ c2n, in
 }
 
 // Gather DoFs (double in memory) into the contraction type R.
-template <int N, int NC, typename R>
+template <int N, int NC, typename R, bool kRel = false>
 __device__ __forceinline__ void gather_dofs(const double *__restrict__ u, const int (&nodes)[N],
                                             R (&l)[N][NC])
 {
+    // kRel: the DoFs relative to the cell's first node, differenced in FP64 before
+    // the conversion to R.  The basis gradients sum to zero, so the gradients are
+    // unchanged and node 0's term vanishes exactly (its difference is 0); the R
+    // operands carry only the cell-local variation, which a smooth field would
+    // otherwise lose to cancellation when its values are rounded to FP32.
+    double base[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) base[c] = 0.0;
+    if constexpr (kRel) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) base[c] = __ldg(u + (size_t)nodes[0] * NC + c);
+    }
 #pragma unroll
     for (int j = 0; j < N; ++j) {
         const double *p = u + (size_t)nodes[j] * NC;
         if constexpr (NC == 2) {
             const double2 v = __ldg(reinterpret_cast<const double2 *>(p));
-            l[j][0] = cvt<R>(v.x);
-            l[j][1] = cvt<R>(v.y);
+            l[j][0] = cvt<R>(kRel ? v.x - base[0] : v.x);
+            l[j][1] = cvt<R>(kRel ? v.y - base[1] : v.y);
         } else {
 #pragma unroll
-            for (int c = 0; c < NC; ++c) l[j][c] = cvt<R>(__ldg(p + c));
+            for (int c = 0; c < NC; ++c) {
+                const double v = __ldg(p + c);
+                l[j][c] = cvt<R>(kRel ? v - base[c] : v);
+            }
         }
     }
 }
@@ -495,9 +510,12 @@ __device__ __forceinline__ void action_cell(const ActionArgs &a, const R *__rest
 
     // gather DoFs
     R l[N][NC];
-    gather_dofs<N, NC, R>(a.u, nodes, l);
+    // hyperelastic forms in reduced precision use only gradients: gather relative
+    // to node 0 (see gather_dofs)
+    constexpr bool kRel = kMixed && OpTraits<OP, D>::kNonlinear;
+    gather_dofs<N, NC, R, kRel>(a.u, nodes, l);
     [[maybe_unused]] R l0[OpTraits<OP, D>::kTwoFields ? N : 1][NC];
-    if constexpr (OpTraits<OP, D>::kTwoFields) gather_dofs<N, NC, R>(a.u_lin, nodes, l0);
+    if constexpr (OpTraits<OP, D>::kTwoFields) gather_dofs<N, NC, R, kRel>(a.u_lin, nodes, l0);
     double mu = a.mu, lam = a.lam;
     if constexpr (OpTraits<OP, D>::kCellCoeff) {
         if (a.mu_cell) mu = __ldg(a.mu_cell + cell);

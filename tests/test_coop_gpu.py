@@ -169,7 +169,7 @@ def test_coop_tables_in_global_memory(fe, dim, N, p, prec):
     w = uniform_field(m.n_nodes * dim, 5)
     res = fe.Plan(M, fe.NH_RESIDUAL, q, mu_cell=mu, lam_cell=lam, precision=prec, cooperative=True,
                   tables_global=True)
-    assert rel(res.apply(cuda(u)), o.nh_residual(u, mu, lam)) <= (tol if prec == "fp64" else 1e3 * tol)
+    assert rel(res.apply(cuda(u)), o.nh_residual(u, mu, lam)) <= tol
     jtw, dmu, _ = res.adjoint(cuda(u), cuda(w))
     ojtw, odmu, _ = o.nh_adjoint(u, w, mu, lam)
     assert rel(jtw, ojtw) <= tol

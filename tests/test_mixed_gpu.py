@@ -8,9 +8,11 @@ of the sum of the absolute terms.  For the random inputs below the absolute
 terms exceed the result by a small factor, and the parity tolerance is
 TOL32 = 5e-5 (norm-wise, relative to ||y_ref||_inf).  Geometry, the
 Neo-Hookean kinematics/stress/log and the scatter are FP64 and add nothing at
-this level.  The Neo-Hookean residual at a smooth displacement is evaluated
-from gradients ~1e3 times smaller than their terms (see
-tests/test_oracle_conditioning.py), so its mixed tolerance is 1e3 x TOL32.
+this level.  The hyperelastic forms evaluate gradients of a smooth displacement
+that are ~1e3 times smaller than the nodal values (see
+tests/test_oracle_conditioning.py); the kernels gather those DoFs relative to
+each cell's first node in FP64 before rounding to single, so the rounding acts
+on the cell-local variation only and the same TOL32 holds for them.
 """
 
 import numpy as np
@@ -77,13 +79,13 @@ def test_nh_fp32(fe, dim, N, p):
     u = sinusoid_displacement(m, 4)
     w = uniform_field(m.n_nodes * dim, 5)
     res = fe.Plan(M, fe.NH_RESIDUAL, q, mu_cell=mu, lam_cell=lam, precision="fp32")
-    assert rel(res.apply(cuda(u)), o.nh_residual(u, mu, lam)) <= 1e3 * TOL32
+    assert rel(res.apply(cuda(u)), o.nh_residual(u, mu, lam)) <= TOL32
     jac = fe.Plan(M, fe.NH_JACOBIAN, q, mu_cell=mu, lam_cell=lam, u_lin=cuda(u), precision="fp32")
     assert rel(jac.apply(cuda(w)), o.nh_jacobian(u, w, mu, lam)) <= TOL32
     jtw, dmu, dlam = res.adjoint(cuda(u), cuda(w))
     ojtw, odmu, odlam = o.nh_adjoint(u, w, mu, lam)
     assert rel(jtw, ojtw) <= TOL32
-    assert rel(dmu, odmu) <= 1e3 * TOL32 and rel(dlam, odlam) <= 1e3 * TOL32
+    assert rel(dmu, odmu) <= TOL32 and rel(dlam, odlam) <= TOL32
 
 
 def test_full_elasticity_p2_3d_fp32(fe):
@@ -117,3 +119,23 @@ def test_bit_conversions_match_hardware(fe):
                                        ctypes.c_void_p(count.data_ptr()), None)
     assert rc == 0
     assert count.tolist() == [0, 0]
+
+
+def test_full_nh_p4_2d_fp32_smooth_field(fe):
+    """The ill-conditioned case at full size (256^2 x 2 P4 triangles, the smooth
+    sinusoid displacement): FP32 contractions of DoFs gathered relative to each
+    cell's first node keep the residual, the adjoint and the Jacobian action
+    within TOL32 of the FP64 oracle (rounding the absolute DoFs to single lost
+    ~1e-3)."""
+    m, M = make(fe, 2, 256, 4, 20250619)
+    o = oracle.Oracle.from_mesh(m, 8)
+    mu, lam = lame_fields(m.n_cells, 3)
+    u = sinusoid_displacement(m, 4)
+    w = uniform_field(m.n_nodes * 2, 5)
+    res = fe.Plan(M, fe.NH_RESIDUAL, 8, mu_cell=mu, lam_cell=lam, precision="fp32")
+    assert rel(res.apply(cuda(u)), o.nh_residual(u, mu, lam, threads=16)) <= TOL32
+    jtw, dmu, dlam = res.adjoint(cuda(u), cuda(w))
+    assert rel(jtw, o.nh_jacobian(u, w, mu, lam, threads=16)) <= TOL32
+    _, odmu, odlam = o.nh_adjoint(u, w, mu, lam, threads=8, cells=(0, 2000))
+    assert rel(dmu[:2000], odmu[:2000]) <= TOL32 and rel(dlam[:2000], odlam[:2000]) <= TOL32
+    assert res.status() == 0
