@@ -703,6 +703,7 @@ def time_batched(fe, torch):
             "autotune_spearman_mean": (sum(rhos) / len(rhos)) if rhos else None,
             "autotune_topb_recovery_mean": {f"top{b_}": sum(v) / len(v) for b_, v in recov.items()},
             "autotune_topb_recovery_min": {f"top{b_}": min(v) for b_, v in recov.items()},
+            "batch_grid_blocks": batch.info["grid_blocks"], "batch_smem_bytes": batch.info["smem_bytes"],
             "status": batch.status()}
 
 

@@ -78,3 +78,51 @@ def test_batched_rejects_bad_problems(fe):
     bad["quad_degree"] = 99
     with pytest.raises(FeError):
         fe.Batch([bad])
+
+
+def test_full_batch_64_meshes(fe):
+    """The benchmark's batch: 64 meshes (2.38M cells, mass / elasticity /
+    Neo-Hookean, degrees 1-4, 2D and 3D) in one batched launch; one problem of each
+    form and dimension checked in full against the oracle, all for finite output."""
+    specs = batch_specs(64)
+    problems, meshes = [], []
+    for s in specs:
+        dim, p, N, q = s["dim"], s["degree"], s["N"], s["quad_degree"]
+        m = structured_mesh(dim, N, p, jitter=0.2 if dim == 2 else 0.15, seed=s["seed"])
+        M = fe.Mesh(dim, p, m.coords, m.cell2vertex, m.cell2node, m.n_nodes)
+        pb = {"mesh": M, "quad_degree": q}
+        if s["form"] == "mass":
+            u = uniform_field(m.n_nodes, s["seed"])
+            pb.update(kind=fe.MASS)
+        elif s["form"] == "elasticity":
+            u = uniform_field(m.n_nodes * dim, s["seed"])
+            pb.update(kind=fe.ELASTICITY, lam=1.25, mu=1.0)
+        else:
+            u = sinusoid_displacement(m, s["seed"])
+            mu, lam = lame_fields(m.n_cells, s["seed"] + 1)
+            pb.update(kind=fe.NH_RESIDUAL, mu_cell=mu, lam_cell=lam)
+        pb["u"] = torch.from_numpy(u).cuda()
+        problems.append(pb)
+        meshes.append((m, u, pb))
+    batch = fe.Batch(problems)
+    assert sum(s["n_cells"] for s in specs) > 2_000_000
+    ys = batch.run()
+    torch.cuda.synchronize()
+    assert batch.status() == 0
+    assert all(bool(torch.isfinite(y).all()) for y in ys)
+    checked = set()
+    for s, y, (m, u, pb) in zip(specs, ys, meshes):
+        key = (s["form"], s["dim"])
+        if key in checked or s["n_cells"] > 60_000:
+            continue
+        checked.add(key)
+        o = oracle.Oracle.from_mesh(m, s["quad_degree"])
+        if s["form"] == "mass":
+            ref = o.mass(u, threads=16)
+        elif s["form"] == "elasticity":
+            ref = o.elasticity(u, 1.25, 1.0, threads=16)
+        else:
+            ref = o.nh_residual(u, pb["mu_cell"], pb["lam_cell"], threads=16)
+        err = np.abs(y.cpu().numpy() - ref).max() / np.abs(ref).max()
+        assert err <= (TOL if s["form"] != "neo_hookean" else 1e-11), (s, err)
+    assert len(checked) >= 4
