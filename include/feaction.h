@@ -327,7 +327,8 @@ int fe_plan_get_info(const fe_plan *plan, fe_plan_info *info);
  * as fe_action; y is overwritten).  kernel selects the device code used for
  * the problem's tiles: -1 automatic (thread-per-cell where compiled for the
  * degree, else cells-per-CTA), 0 thread-per-cell (tiles of 128 cells), 1
- * cells-per-CTA with tile_cells cells per tile (0: 16).
+ * cells-per-CTA with tile_cells cells per tile (0: the largest tile that keeps
+ * two CTAs per SM, as for a single plan).
  * fe_batch_create validates, tabulates every problem, uploads the tables and
  * the cost-ordered work lists (one per device code), and allocates the
  * batch's device memory, a side stream and two events (synchronous).  Pointers
@@ -349,7 +350,7 @@ typedef struct fe_batch_problem {
     const double *u;             /* device, n_nodes * ncomp                        */
     double *y;                   /* device, n_nodes * ncomp                        */
     int32_t kernel;              /* -1 auto, 0 thread-per-cell, 1 cells-per-CTA    */
-    int32_t tile_cells;          /* cells per tile for kernel 1 (0: 16)            */
+    int32_t tile_cells;          /* cells per tile for kernel 1 (0: automatic)     */
 } fe_batch_problem;
 
 typedef struct fe_batch fe_batch;

@@ -54,19 +54,6 @@ const Variant *find_variant(int form, int dim, int degree, int op, int precision
     return coop;
 }
 
-// Largest cell batch whose shared-memory plan leaves room for two CTAs per SM
-// (at most 64 cells, at least 1).
-int coop_cells_for(int n, int nq, int dim, int ncomp, int fields, size_t esz, size_t budget, bool gt)
-{
-    int best = 1;
-    for (int C = 1; C <= 64; ++C) {
-        const size_t total = esz == sizeof(float)
-                                 ? coop_layout<float>(n, nq, dim, ncomp, C, fields, gt).total
-                                 : coop_layout<double>(n, nq, dim, ncomp, C, fields, gt).total;
-        if (total <= budget) best = C;
-    }
-    return best;
-}
 
 // Tensor-core tile shape: the most 128-cell pipelines per CTA (4, 2, 1, or the
 // count force_pipes asks for) whose staged tables, operands and accumulators

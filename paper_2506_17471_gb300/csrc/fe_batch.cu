@@ -279,8 +279,9 @@ extern "C" int fe_batch_create(const fe_batch_problem *problems, int count, fe_b
         size_t rs, block_bytes, need;
         bool global_tab = false;
         if (kind == 1) {
-            C = pb.tile_cells > 0 ? pb.tile_cells : 16;
             const bool gt = (f.flags & FE_FLAG_TABLES_GLOBAL) || coop_default_global<double>(n, nq, m.dim);
+            // default tile: the largest that keeps two CTAs per SM, as for a single plan
+            C = pb.tile_cells > 0 ? pb.tile_cells : coop_cells_for(n, nq, m.dim, ncomp, 1, sizeof(double), 100 * 1024, gt);
             const CoopLayout L = coop_layout<double>(n, nq, m.dim, ncomp, C, 1, gt);
             rs = L.rs;
             block_bytes = L.table_block_bytes;

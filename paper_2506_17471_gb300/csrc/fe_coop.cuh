@@ -478,4 +478,18 @@ Variant make_coop_variant()
     return v;
 }
 
+// Largest cell batch whose shared-memory plan fits budget (100 KB leaves room for
+// two CTAs per SM); at most 64 cells, at least 1.  Host side.
+inline int coop_cells_for(int n, int nq, int dim, int ncomp, int fields, size_t esz, size_t budget, bool gt)
+{
+    int best = 1;
+    for (int C = 1; C <= 64; ++C) {
+        const size_t total = esz == sizeof(float)
+                                 ? coop_layout<float>(n, nq, dim, ncomp, C, fields, gt).total
+                                 : coop_layout<double>(n, nq, dim, ncomp, C, fields, gt).total;
+        if (total <= budget) best = C;
+    }
+    return best;
+}
+
 }  // namespace fe
