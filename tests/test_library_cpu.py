@@ -216,3 +216,17 @@ def test_round_tf32_matches_ieee_definition(fe, from_binary32):
     assert N.lib.fe_round_tf32(ctypes.c_void_p(nan.ctypes.data), 1, from_binary32,
                                ctypes.c_void_p(bits.ctypes.data)) == 0
     assert (bits[0] & 0x7F800000) == 0x7F800000 and (bits[0] & 0x7FE000)
+
+
+def test_round_tf32_and_round16_reject_null(fe):
+    """Documented errors of the host rounding entry points."""
+    import ctypes
+    from paper_2506_17471_gb300 import _native as N
+    null = ctypes.c_void_p(0)
+    assert N.lib.fe_round_tf32(null, 4, 0, null) == N.FE_ERR_INVALID_ARG
+    assert N.lib.fe_round_tf32(null, 0, 1, null) == N.FE_OK          # nothing to round
+    assert N.lib.fe_round16(null, 3, N.FE_PREC_BF16, null) == N.FE_ERR_INVALID_ARG
+    x = np.zeros(2)
+    b = np.zeros(2, dtype=np.uint16)
+    assert N.lib.fe_round16(ctypes.c_void_p(x.ctypes.data), 2, N.FE_PREC_TF32,
+                            ctypes.c_void_p(b.ctypes.data)) == N.FE_ERR_UNSUPPORTED
