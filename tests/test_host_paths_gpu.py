@@ -86,7 +86,7 @@ def test_one_call_action_caches_plans(setup):
     assert not yh.is_cuda and float((yh - y.cpu()).abs().max() / y.abs().max()) < 1e-14
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16"])
 @pytest.mark.parametrize("dim,N,p,q", [(3, 8, 1, 0), (3, 6, 2, 2), (2, 30, 3, 6)])
 def test_reordered_mesh_action(setup, prec, dim, N, p, q):
     """The action on a randomly numbered mesh, renumbered by the Morton + first-touch
@@ -109,6 +109,6 @@ def test_reordered_mesh_action(setup, prec, dim, N, p, q):
     back = fe.unpermute_dofs(y2, nnew, nc)
     o = oracle.Oracle(dim, p, q, m.coords, m.cell2vertex, m.cell2node, m.n_nodes)
     ref = o.elasticity(u, 1.25, 1.0) if kind == fe.ELASTICITY else o.mass(u)
-    tol = 1e-12 if prec == "fp64" else 5e-5
+    tol = {"fp64": 1e-12, "fp32": 5e-5, "fp16": 8 * 2.0 ** -11}[prec]
     assert np.abs(back - ref).max() <= tol * np.abs(ref).max()
     assert np.abs(y1 - ref).max() <= tol * np.abs(ref).max()

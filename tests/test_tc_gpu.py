@@ -425,3 +425,23 @@ def test_tc_bad_index_two_threads_per_cell(fe, j):
     keep[300] = False
     o = oracle.Oracle(3, 4, 6, m.coords, m.cell2vertex[keep], m.cell2node[keep], m.n_nodes)
     assert rel(y, o.elasticity(u, 1.25, 1.0)) <= TOL16["fp16"]
+
+
+@pytest.mark.parametrize("kind", ["nh_jacobian", "svk_jacobian"])
+@pytest.mark.parametrize("dim,N,p,q", [(2, 13, 3, 6), (3, 5, 2, 4)])
+def test_tc_fp16x2_hyperelastic(fe, kind, dim, N, p, q):
+    """Split binary16 operands for both hyperelastic Jacobian actions, 2D and 3D:
+    the FP32-class bound although the law stays FP64 and the linearisation
+    point is a smooth field."""
+    from feinputs import lame_fields
+    from feinputs.fields import sinusoid_displacement
+    m, M = make(fe, dim, N, p, 990 + 10 * dim + p)
+    o = oracle.Oracle.from_mesh(m, q)
+    mu, lam = lame_fields(m.n_cells, 8)
+    ul = sinusoid_displacement(m, 9)
+    du = uniform_field(m.n_nodes * dim, 10)
+    plan = fe.Plan(M, getattr(fe, kind.upper()), q, mu_cell=mu, lam_cell=lam, u_lin=cuda(ul), precision="fp16x2")
+    assert plan.info.kernel == 2
+    ref = getattr(o, kind)(ul, du, mu, lam)
+    assert rel(plan.apply(cuda(du)), ref) <= TOL_X2
+    assert plan.status() == 0
