@@ -95,8 +95,9 @@ enum fe_precision {
                                 tcgen05 tensor cores with bfloat16 operands (tables, DoFs
                                 scaled per cell by a power of two, pointwise results) and
                                 FP32 accumulation in tensor memory; geometry FP64, linear
-                                stress FP32, scatter-add FP64.  Any degree with at most
-                                256 local nodes.  Error: see fe_plan_create.            */
+                                stress FP32, scatter-add FP64.  Any tabulated degree
+                                (1-10) with at most 256 local nodes (3D P10 has 286).
+                                Error: see fe_plan_create.                             */
     FE_PREC_FP16 = 3,        /* as FE_PREC_BF16 with IEEE binary16 operands (3 more
                                 significand bits, smaller range; the per-cell power-of-two
                                 scaling keeps the operands O(1))                        */

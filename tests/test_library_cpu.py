@@ -230,3 +230,27 @@ def test_round_tf32_and_round16_reject_null(fe):
     b = np.zeros(2, dtype=np.uint16)
     assert N.lib.fe_round16(ctypes.c_void_p(x.ctypes.data), 2, N.FE_PREC_TF32,
                             ctypes.c_void_p(b.ctypes.data)) == N.FE_ERR_UNSUPPORTED
+
+
+def test_plan_create_rejects_out_of_range_sizes(fe):
+    """Host-side argument checks of fe_plan_create run before any device call, so
+    they are testable without a GPU: DoF indices must fit int32 (n_nodes x
+    components < 2^31), the quadrature degree is at most 40, the kind and the
+    precision must be known.  The pointers are never dereferenced here."""
+    import ctypes
+    from paper_2506_17471_gb300 import _native as N
+    fake = ctypes.c_void_p(0x10000)   # 16-byte aligned, never touched on these paths
+
+    def create(dim=3, degree=2, n_nodes=1000, kind=N.FE_FORM_ELASTICITY, q=2, prec=N.FE_PREC_FP64):
+        mesh = N.FeMesh(dim, degree, 100, 10, n_nodes, fake, fake, fake)
+        form = N.FeForm(kind, q, prec, 0, 1.25, 1.0, None, None, None, 0, 0)
+        h = ctypes.c_void_p(0)
+        return N.lib.fe_plan_create(ctypes.byref(form), ctypes.byref(mesh), ctypes.byref(h))
+
+    # 3 components x 715,827,883 nodes = 2^31 + 1: too many DoFs for int32 indices
+    assert create(n_nodes=715_827_883) == N.FE_ERR_INVALID_ARG
+    assert create(q=41) == N.FE_ERR_INVALID_ARG
+    assert create(kind=99) == N.FE_ERR_INVALID_ARG
+    assert create(prec=17) == N.FE_ERR_UNSUPPORTED
+    assert create(dim=4) == N.FE_ERR_INVALID_ARG
+    assert create(kind=N.FE_FORM_NH_RESIDUAL, prec=N.FE_PREC_FP16) == N.FE_ERR_UNSUPPORTED

@@ -445,3 +445,24 @@ def test_tc_fp16x2_hyperelastic(fe, kind, dim, N, p, q):
     ref = getattr(o, kind)(ul, du, mu, lam)
     assert rel(plan.apply(cuda(du)), ref) <= TOL_X2
     assert plan.status() == 0
+
+
+def test_tc_node_limit(fe):
+    """The tensor-core kernel serves every tabulated degree (up to 10) with at most
+    256 local nodes: P9 tetrahedra (220 nodes) plan and run, P10 tetrahedra (286)
+    are refused cleanly.  (At P9 the equispaced basis amplifies the 16-bit operand
+    rounding by its Lebesgue constant, so only the launch and a loose bound against
+    the FP64 kernel are checked here; accuracy is pinned up to P6.)"""
+    m, M = make(fe, 3, 2, 9, 991)
+    u = uniform_field(m.n_nodes, 11)
+    plan = fe.Plan(M, fe.MASS, 2, precision="fp16")
+    assert plan.info.n_loc == 220 and plan.info.kernel == 2
+    y = plan.apply(cuda(u))
+    assert plan.status() == 0 and bool(torch.isfinite(y).all())
+    # against the FP64 cells-per-CTA kernel (the oracle stops below this degree)
+    y64 = fe.Plan(M, fe.MASS, 2).apply(cuda(u)).cpu().numpy()
+    assert rel(y, y64) <= 0.1
+    m2, M2 = make(fe, 3, 1, 10, 992)
+    with pytest.raises(fe.FeError) as e:
+        fe.Plan(M2, fe.MASS, 2, precision="fp16")
+    assert e.value.code == 2
