@@ -462,6 +462,14 @@ int fe_selftest_conversions(const double *x, long long n, unsigned long long *co
  * Errors: FE_ERR_INVALID_ARG, FE_ERR_CUDA. */
 int fe_selftest_conversions16(const double *x, long long n, unsigned long long *count, void *stream);
 
+/* Device self-test of the kernels' bounded waits: one CTA waits on a shared-
+ * memory mbarrier that nothing ever completes, gives up after `polls` polls
+ * (each followed by a ~64 ns sleep) and records FE_ERR_TIMEOUT in *status
+ * (device int32, caller-owned, as a plan's status word: the first error wins).
+ * The context stays usable.  Asynchronous on stream.  Errors: FE_ERR_INVALID_ARG
+ * (NULL status, polls outside [1, 2^24]), FE_ERR_CUDA. */
+int fe_selftest_bounded_wait(int32_t *status, int polls, void *stream);
+
 /* Host function.  Rounds x[n] (host) to the 16-bit type of precision
  * (FE_PREC_BF16 or FE_PREC_FP16) to nearest even, exactly as plans round their
  * tabulation for the tensor-core kernel; bits[n] (host, caller-owned) receives

@@ -47,7 +47,7 @@ EXPORTS = ("fe_status_string", "fe_tabulate", "fe_tabulate_scheme", "fe_plan_cre
            "fe_measure_fp64_peak", "fe_action_noalloc", "fe_cg_start", "fe_cg_direction",
            "fe_cg_update", "fe_cg_new_direction", "fe_vec_axpy", "fe_vec_dot",
            "fe_selftest_conversions", "fe_batch_create", "fe_batch_run", "fe_batch_status",
-           "fe_batch_get_info", "fe_batch_destroy", "fe_selftest_conversions16", "fe_round16", "fe_round_tf32", "fe_order_cells_morton", "fe_order_first_touch",
+           "fe_batch_get_info", "fe_batch_destroy", "fe_selftest_conversions16", "fe_round16", "fe_round_tf32", "fe_order_cells_morton", "fe_order_first_touch", "fe_selftest_bounded_wait",
            "fe_action_host_pipelined")
 FE_CG_PARTIALS = 1024
 FE_CG_WORKSPACE_DOUBLES = FE_CG_PARTIALS + 16
@@ -129,6 +129,7 @@ def _load() -> ctypes.CDLL:
     lib.fe_round_tf32.argtypes = [P, ctypes.c_size_t, I, P]
     lib.fe_order_cells_morton.argtypes = [I, I, I, P, P, P]
     lib.fe_order_first_touch.argtypes = [I, I, I, P, P, P]
+    lib.fe_selftest_bounded_wait.argtypes = [P, I, P]
     lib.fe_batch_create.argtypes = [ctypes.POINTER(FeBatchProblem), I, ctypes.POINTER(P)]
     lib.fe_batch_run.argtypes = [P, P]
     lib.fe_batch_status.argtypes = [P, ctypes.POINTER(I)]

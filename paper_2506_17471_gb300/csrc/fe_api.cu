@@ -897,6 +897,23 @@ __global__ void k_selftest_conversions(const double *x, long long n, unsigned lo
     if (bad64) atomicAdd(count + 1, bad64);
 }
 
+// Self-test of the kernels' bounded mbarrier wait: one CTA waits on an mbarrier
+// that nothing ever completes (no arrival, no copy); the wait must give up after
+// `polls` polls, record FE_ERR_TIMEOUT in the status word and return, leaving
+// the context usable.
+__global__ void k_selftest_bounded_wait(int32_t *status, int polls)
+{
+    __shared__ __align__(8) uint64_t bar;
+    const uint32_t sbar = (uint32_t)__cvta_generic_to_shared(&bar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sbar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const int done = bounded_wait(sbar, 0, polls);
+    if (!__syncthreads_or(done) && threadIdx.x == 0) set_status(status, FE_ERR_TIMEOUT);
+}
+
 // Self-test of the integer binary64 -> bfloat16 / binary16 conversions of the
 // tensor-core kernel against CUDA's conversions: count[0] += bfloat16
 // mismatches, count[1] += binary16 mismatches (NaN compares equal to NaN).
@@ -929,6 +946,13 @@ extern "C" int fe_selftest_conversions16(const double *x, long long n, unsigned 
     long long g = (n + 255) / 256;
     if (g > 4096) g = 4096;
     k_selftest_conversions16<<<(int)g, 256, 0, static_cast<cudaStream_t>(stream)>>>(x, n, count);
+    return cudaGetLastError() == cudaSuccess ? FE_OK : FE_ERR_CUDA;
+}
+
+extern "C" int fe_selftest_bounded_wait(int32_t *status, int polls, void *stream)
+{
+    if (!status || polls < 1 || polls > (1 << 24)) return FE_ERR_INVALID_ARG;
+    k_selftest_bounded_wait<<<1, 64, 0, static_cast<cudaStream_t>(stream)>>>(status, polls);
     return cudaGetLastError() == cudaSuccess ? FE_OK : FE_ERR_CUDA;
 }
 

@@ -47,6 +47,26 @@ __device__ __forceinline__ void set_status(int32_t *status, int32_t code)
     if (status) atomicCAS(status, 0, code);
 }
 
+// Bounded wait on phase `parity` of the shared-memory mbarrier at sbar: at most
+// `limit` polls with a short sleep between them.  Returns 1 if the phase
+// completed, 0 if the wait gave up (the caller records FE_ERR_TIMEOUT).
+__device__ __forceinline__ int bounded_wait(uint32_t sbar, uint32_t parity, int limit)
+{
+    for (int it = 0; it < limit; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(sbar), "r"(parity)
+            : "memory");
+        if (ok) return 1;
+        __nanosleep(64);
+    }
+    return 0;
+}
+
 // Stage the table block into shared memory with one bulk async copy.  Returns
 // false (and records FE_ERR_TIMEOUT) if the copy did not complete within the
 // bounded wait; the caller must then return.
@@ -71,27 +91,12 @@ __device__ __forceinline__ bool stage_table(double *sm_tab, const double *g_tab,
             "l"(gsrc), "r"(bytes), "r"(sbar)
             : "memory");
     }
-    auto poll = [&](int limit) -> int {
-        for (int it = 0; it < limit; ++it) {
-            uint32_t ok;
-            asm volatile(
-                "{\n\t.reg .pred p;\n\t"
-                "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
-                "selp.u32 %0, 1, 0, p;\n\t}"
-                : "=r"(ok)
-                : "r"(sbar)
-                : "memory");
-            if (ok) return 1;
-            __nanosleep(64);
-        }
-        return 0;
-    };
-    const int done = poll(kWaitLimit);
+    const int done = bounded_wait(sbar, 0, kWaitLimit);
     if (__syncthreads_and(done)) return true;
     // The copy did not land in time: record it, give the in-flight copy a second
     // bounded chance to finish before this CTA's shared memory is released.
     if (threadIdx.x == 0) set_status(status, FE_ERR_TIMEOUT);
-    poll(kWaitLimit);
+    bounded_wait(sbar, 0, kWaitLimit);
     __syncthreads();
     return false;
 }

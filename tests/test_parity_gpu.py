@@ -361,3 +361,23 @@ def test_tpc_block_sizes(fe, block):
     assert plan.status() == 0
     with pytest.raises(Exception):
         fe.Plan(M, fe.ELASTICITY, 4, lam=1.25, mu=1.0, tile_cells=48)
+
+
+def test_bounded_wait_times_out_and_context_survives(fe):
+    """Failure detection without a GPU fault: a kernel waits on an mbarrier that
+    nothing ever completes; the kernels' bounded wait gives up, FE_ERR_TIMEOUT
+    reaches the host through the status word, and the context keeps working."""
+    import ctypes
+    from paper_2506_17471_gb300 import _native as N
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    assert N.lib.fe_selftest_bounded_wait(ctypes.c_void_p(st.data_ptr()), 4096, None) == N.FE_OK
+    torch.cuda.synchronize()
+    assert int(st.item()) == N.FE_ERR_TIMEOUT
+    assert N.lib.fe_selftest_bounded_wait(None, 10, None) == N.FE_ERR_INVALID_ARG
+    assert N.lib.fe_selftest_bounded_wait(ctypes.c_void_p(st.data_ptr()), 0, None) == N.FE_ERR_INVALID_ARG
+    m = structured_mesh(2, 8, 2, jitter=0.2, seed=3)
+    M = fe.Mesh(2, 2, m.coords, m.cell2vertex, m.cell2node, m.n_nodes)
+    u = uniform_field(m.n_nodes, 4)
+    plan = fe.Plan(M, fe.MASS, 4)
+    y = plan.apply(torch.from_numpy(u).cuda()).cpu().numpy()
+    assert rel(y, oracle.Oracle.from_mesh(m, 4).mass(u)) <= TOL and plan.status() == 0
