@@ -314,9 +314,15 @@ typedef struct fe_plan_info {
     int32_t threads_per_block;
     int32_t grid_blocks;      /* blocks launched per action                        */
     int64_t n_dofs;           /* n_nodes * ncomp                                   */
-    double flops_per_cell;    /* algorithmic FP64 flops of Algorithm 2 per cell     */
+    double flops_per_cell;    /* algorithmic FP64 flops of Algorithm 2 per cell,
+                                 gradient contractions counted over the structurally
+                                 nonzero reference-gradient entries: d phi_alpha /
+                                 dxhat_k vanishes identically when alpha_0 =
+                                 alpha_k = 0 (barycentric multi-index alpha)       */
     double bytes_min;         /* roofline footprint: each DoF, coordinate and map
                                  entry counted once (Sec. "Roofline Model")         */
+    double flops_per_cell_dense; /* the same counting every table entry (the
+                                 paper's Ops_usable convention, Eq. "ops_usable")   */
 } fe_plan_info;
 
 int fe_plan_get_info(const fe_plan *plan, fe_plan_info *info);

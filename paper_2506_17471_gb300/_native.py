@@ -85,7 +85,8 @@ class FePlanInfo(ctypes.Structure):
     _fields_ = [("nq", ctypes.c_int32), ("n_loc", ctypes.c_int32), ("ncomp", ctypes.c_int32),
                 ("kernel", ctypes.c_int32), ("threads_per_block", ctypes.c_int32),
                 ("grid_blocks", ctypes.c_int32), ("n_dofs", ctypes.c_int64),
-                ("flops_per_cell", ctypes.c_double), ("bytes_min", ctypes.c_double)]
+                ("flops_per_cell", ctypes.c_double), ("bytes_min", ctypes.c_double),
+                ("flops_per_cell_dense", ctypes.c_double)]
 
 
 class FeError(RuntimeError):

@@ -100,6 +100,7 @@ class PlanInfo:
     n_dofs: int
     flops_per_cell: float
     bytes_min: float
+    flops_per_cell_dense: float
 
 
 class Plan:
@@ -145,7 +146,8 @@ class Plan:
         info = N.FePlanInfo()
         N.check(N.lib.fe_plan_get_info(self._h, ctypes.byref(info)), "fe_plan_get_info")
         self.info = PlanInfo(info.nq, info.n_loc, info.ncomp, info.kernel, info.threads_per_block,
-                             info.grid_blocks, info.n_dofs, info.flops_per_cell, info.bytes_min)
+                             info.grid_blocks, info.n_dofs, info.flops_per_cell, info.bytes_min,
+                             info.flops_per_cell_dense)
 
     @property
     def n_dofs(self) -> int:

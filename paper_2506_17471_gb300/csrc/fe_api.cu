@@ -13,6 +13,19 @@
 #include "fe_tc.cuh"
 
 namespace fe {
+
+bool tab_zeros_hold(int dim, int n, int nq, const double *tab)
+{
+    for (int k = 0; k < dim; ++k) {
+        const uint64_t z = grad_zero_mask(dim, n, k);
+        for (int j = 0; j < n && j < 64; ++j)
+            if ((z >> j) & 1u)
+                for (int q = 0; q < nq; ++q)
+                    if (tab[((size_t)(k + 1) * nq + q) * n + j] != 0.0) return false;
+    }
+    return true;
+}
+
 namespace {
 
 constexpr int kMaxVariants = 512;
@@ -77,14 +90,34 @@ bool tc_choose(int n, int nq, int ncomp, int kd, int fields, size_t smem_cap, in
     return false;
 }
 
+// Structurally nonzero entries of the reference gradient tables of the degree-p
+// basis: d * n minus the pairs (node, direction) with alpha_0 = alpha_{k+1} = 0,
+// whose derivative vanishes identically (the zeros grad_zero_mask flags; counted
+// here for every degree, not only for n <= 64).
+int grad_nonzeros(int d, int p)
+{
+    int n = 0, zeros = 0;
+    for (int a = 0; a <= p; ++a)
+        for (int b = 0; b <= p - a; ++b)
+            for (int c = 0; c <= (d == 3 ? p - a - b : 0); ++c) {
+                const int alpha[4] = {p - a - b - c, a, b, c};
+                for (int k = 0; k < d; ++k) zeros += (alpha[0] == 0 && alpha[k + 1] == 0);
+                ++n;
+            }
+    return d * n - zeros;
+}
+
 // Algorithmic FP64 flops of Algorithm 2 for one cell (multiply and add count 1
 // each, an FMA 2; a division or a logarithm 1).  Geometry is counted once per
 // cell as in the untransformed kernel.  Eval/quad terms follow the paper's
-// Ops_usable (Eq. "ops_usable"): 2 N_deriv Q n + 2 N_eval Q n.
-double algorithmic_flops(int op, int d, int n, int nq)
+// Ops_usable (Eq. "ops_usable"): 2 N_deriv Q n + 2 N_eval Q n, with the gradient
+// terms counted over the g structurally nonzero reference-gradient entries
+// (dense = true counts all d * n of them, the paper's convention).
+double algorithmic_flops(int op, int d, int n, int nq, bool dense)
 {
     const double geo = d == 2 ? 11.0 : 50.0;
     const double d2 = double(d) * d;
+    const double g = dense ? double(d) * n : double(grad_nonzeros(d, lagrange_degree(d, n)));
     double eval = 0, pw = 0, quad = 0;
     switch (op) {
     case 0:  // mass
@@ -93,44 +126,44 @@ double algorithmic_flops(int op, int d, int n, int nq)
         quad = 2.0 * n;
         break;
     case 1:  // elasticity
-        eval = 2.0 * d2 * n;
+        eval = 2.0 * d * g;
         pw = d == 2 ? 37.0 : 115.0;
-        quad = 2.0 * d2 * n;
+        quad = 2.0 * d * g;
         break;
     case 2:  // Neo-Hookean residual
-        eval = 2.0 * d2 * n;
+        eval = 2.0 * d * g;
         pw = d == 2 ? 56.0 : 182.0;
-        quad = 2.0 * d2 * n;
+        quad = 2.0 * d * g;
         break;
     case 3:  // Neo-Hookean Jacobian action
-        eval = 4.0 * d2 * n;
+        eval = 4.0 * d * g;
         pw = d == 2 ? 105.0 : 345.0;
-        quad = 2.0 * d2 * n;
+        quad = 2.0 * d * g;
         break;
     case 4:  // Neo-Hookean adjoint (J^T w, dmu, dlambda)
-        eval = 4.0 * d2 * n;
+        eval = 4.0 * d * g;
         pw = d == 2 ? 131.0 : 401.0;
-        quad = 2.0 * d2 * n;
+        quad = 2.0 * d * g;
         break;
     case 5:  // Laplacian: map (2 d^2), scale (d), pull back (2 d^2)
-        eval = 2.0 * d * n;
+        eval = 2.0 * g;
         pw = 4.0 * d2 + d + 1.0;
-        quad = 2.0 * d * n;
+        quad = 2.0 * g;
         break;
     case 6:  // Helmholtz: Laplacian plus the value term
-        eval = 2.0 * (d + 1) * n;
+        eval = 2.0 * (g + n);
         pw = 4.0 * d2 + d + 2.0;
-        quad = 2.0 * (d + 1) * n;
+        quad = 2.0 * (g + n);
         break;
     case 7:  // St. Venant-Kirchhoff residual: map, E, S, P = F S, pull back
-        eval = 2.0 * d2 * n;
+        eval = 2.0 * d * g;
         pw = d == 2 ? 66.0 : 202.0;
-        quad = 2.0 * d2 * n;
+        quad = 2.0 * d * g;
         break;
     case 8:  // St. Venant-Kirchhoff Jacobian action: two maps, E, S, dE, dS, dP, pull back
-        eval = 4.0 * d2 * n;
+        eval = 4.0 * d * g;
         pw = d == 2 ? 129.0 : 395.0;
-        quad = 2.0 * d2 * n;
+        quad = 2.0 * d * g;
         break;
     }
     return geo + nq * (eval + pw + quad);
@@ -459,7 +492,8 @@ static int plan_create_tc(const fe_form &f, const fe_mesh &m, const Variant &v, 
     const long long tiles = ((long long)m.n_cells + kTcRows - 1) / kTcRows;
     const long long want = (tiles + L.pipes - 1) / L.pipes;
     p->grid_blocks = (int)std::max(1LL, std::min(want, (long long)num_sms()));
-    p->flops_per_cell = algorithmic_flops(op_of(f.kind), m.dim, n, nq);
+    p->flops_per_cell = algorithmic_flops(op_of(f.kind), m.dim, n, nq, false);
+    p->flops_per_cell_dense = algorithmic_flops(op_of(f.kind), m.dim, n, nq, true);
     const double dofs = (double)m.n_nodes * ncomp;
     p->bytes_min = 2.0 * dofs * 8.0 + (double)m.n_vertices * m.dim * 8.0 + (double)m.n_cells * (n + m.dim + 1) * 4.0;
     if (f.kind == FE_FORM_NH_JACOBIAN)
@@ -513,6 +547,7 @@ extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan 
     int rc = fe_tabulate_scheme(m.dim, m.degree, f.quad_degree, f.quad_scheme, &nq, pts.data(), wts.data(), tab.data(),
                            tab.size());
     if (rc != FE_OK) return rc;
+    if (!tab_zeros_hold(m.dim, n, nq, tab.data())) return FE_ERR_INVALID_ARG;
     // table block.  Thread-per-cell: tab [nq][1+d][n] in the contraction
     // precision, padded to 8 B, the weights [nq] in double, the weights [nq] in
     // the contraction precision, padded to 16 B.  Cooperative: the same with the
@@ -617,7 +652,8 @@ extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan 
     }
     p->grid_blocks = grid_for(p->var, smem, m.n_cells, coop ? coop_cells : p->var.block);
     p->adj_grid_blocks = adj ? grid_for(p->adj, smem, m.n_cells, coop ? coop_cells : p->adj.block) : 0;
-    p->flops_per_cell = algorithmic_flops(op_of(f.kind), m.dim, n, nq);
+    p->flops_per_cell = algorithmic_flops(op_of(f.kind), m.dim, n, nq, false);
+    p->flops_per_cell_dense = algorithmic_flops(op_of(f.kind), m.dim, n, nq, true);
     const double dofs = (double)m.n_nodes * ncomp;
     double bytes = 2.0 * dofs * 8.0 + (double)m.n_vertices * m.dim * 8.0 +
                    (double)m.n_cells * (n + m.dim + 1) * 4.0;
@@ -847,6 +883,7 @@ extern "C" int fe_plan_get_info(const fe_plan *plan, fe_plan_info *info)
     info->grid_blocks = plan->grid_blocks;
     info->n_dofs = (int64_t)plan->mesh.n_nodes * plan->ncomp;
     info->flops_per_cell = plan->flops_per_cell;
+    info->flops_per_cell_dense = plan->flops_per_cell_dense;
     info->bytes_min = plan->bytes_min;
     return FE_OK;
 }

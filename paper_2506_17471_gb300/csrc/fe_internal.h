@@ -90,6 +90,11 @@ int register_variants_tc3(Variant *out, int cap);
 int register_variants_forms(Variant *out, int cap);
 int register_variants_coop_forms(Variant *out, int cap);
 
+// True when every structural zero of the reference gradient tables (the
+// entries the thread-per-cell contractions skip) holds exactly 0.0 in tab,
+// laid out as fe_tabulate writes it: [(1+dim)][nq][n].
+bool tab_zeros_hold(int dim, int n, int nq, const double *tab);
+
 }  // namespace fe
 
 // The plan object behind the opaque C handle.
@@ -115,6 +120,7 @@ struct fe_plan {
     int tc_wshift;        // tensor-core kernel: staged weights are w_q 2^tc_wshift
     int device;
     double flops_per_cell;
+    double flops_per_cell_dense;   // the same with every gradient-table entry counted
     double bytes_min;
     // fe_action_host_pipelined: two copy streams and, per buffer pair b, the
     // events h2d done, action done, d2h done (created on first use)

@@ -208,6 +208,57 @@ __device__ __forceinline__ U cvt(T x)
         return f32_to_f64(x);
 }
 
+// Structural zeros of the reference gradient tables.  The basis is the product
+// phi_alpha = prod_m L_{alpha_m}(lam_m) over the barycentric coordinates, and
+// d/dxhat_k reaches it only through lam_{k+1} and lam_0 = 1 - sum xhat; the term
+// through lam_m carries L'_{alpha_m}, which vanishes for alpha_m = 0 (L_0 = 1).
+// So d phi_alpha / dxhat_k is identically zero when alpha_0 = alpha_{k+1} = 0,
+// and the tabulation holds exactly 0.0 there at every quadrature point.  Bit j of
+// grad_zero_mask(D, N, k) flags such a local node j (node order of the
+// tabulation: alpha_1 outermost, then alpha_2, alpha_3).  The thread-per-cell
+// contractions skip those terms; the result is unchanged, since a fused
+// multiply-add with a zero factor returns its addend.
+__host__ __device__ constexpr int lagrange_degree(int D, int N)
+{
+    for (int p = 0; p <= 20; ++p) {
+        const int n = D == 2 ? (p + 1) * (p + 2) / 2 : (p + 1) * (p + 2) * (p + 3) / 6;
+        if (n == N) return p;
+    }
+    return -1;
+}
+
+__host__ __device__ constexpr uint64_t grad_zero_mask(int D, int N, int k)
+{
+    const int p = lagrange_degree(D, N);
+    if ((D != 2 && D != 3) || p < 0 || N > 64 || k < 0 || k >= D) return 0;
+    uint64_t mask = 0;
+    int j = 0;
+    for (int a = 0; a <= p; ++a)
+        for (int b = 0; b <= p - a; ++b)
+            for (int c = 0; c <= (D == 3 ? p - a - b : 0); ++c) {
+                const int alpha[4] = {p - a - b - c, a, b, c};
+                if (alpha[0] == 0 && alpha[k + 1] == 0) mask |= uint64_t(1) << j;
+                ++j;
+            }
+    return mask;
+}
+
+static_assert(grad_zero_mask(3, 4, 0) == 0x6 && grad_zero_mask(3, 4, 1) == 0xA &&
+                  grad_zero_mask(3, 4, 2) == 0xC,
+              "P1 tetrahedron: node 1 = (0,0,1), 2 = (0,1,0), 3 = (1,0,0)");
+static_assert(grad_zero_mask(2, 6, 0) == 0x4 && grad_zero_mask(2, 6, 1) == 0x20,
+              "P2 triangle: nodes 2 = (0,2) and 5 = (2,0) in (alpha_1, alpha_2)");
+
+// Whether T_{k+1}[j] is a structural zero (k, j compile-time after unrolling).
+template <int D, int N>
+__device__ __forceinline__ bool grad_zero(int k, int j)
+{
+    constexpr uint64_t z0 = grad_zero_mask(D, N, 0), z1 = grad_zero_mask(D, N, 1),
+                       z2 = grad_zero_mask(D, N, 2);
+    const uint64_t z = k == 0 ? z0 : (k == 1 ? z1 : z2);
+    return (z >> j) & 1u;
+}
+
 // Evaluation phase: reference gradient gh[c][k] = sum_j T_{k+1}[j] l[j][c], in
 // the contraction type R (double, or float for the mixed-precision variant).
 template <int D, int N, int NC, typename R>
@@ -221,6 +272,7 @@ __device__ __forceinline__ void eval_grad(const R *__restrict__ T, const R (&l)[
     for (int j = 0; j < N; ++j) {
 #pragma unroll
         for (int k = 0; k < D; ++k) {
+            if (grad_zero<D, N>(k, j)) continue;
             const R t = T[(k + 1) * N + j];
 #pragma unroll
             for (int c = 0; c < NC; ++c) gh[c][k] = fma(t, l[j][c], gh[c][k]);
@@ -236,6 +288,7 @@ __device__ __forceinline__ void quad_grad(const R *__restrict__ T, const R (&e)[
     for (int j = 0; j < N; ++j) {
 #pragma unroll
         for (int k = 0; k < D; ++k) {
+            if (grad_zero<D, N>(k, j)) continue;
             const R t = T[(k + 1) * N + j];
 #pragma unroll
             for (int c = 0; c < NC; ++c) out[j][c] = fma(t, e[c][k], out[j][c]);
@@ -555,7 +608,8 @@ __device__ __forceinline__ void action_cell(const ActionArgs &a, const R *__rest
 #pragma unroll
             for (int j = 0; j < N; ++j)
 #pragma unroll
-                for (int k = 0; k < D; ++k) gs[k] = fma(T[(k + 1) * N + j], l[j][0], gs[k]);
+                for (int k = 0; k < D; ++k)
+                    if (!grad_zero<D, N>(k, j)) gs[k] = fma(T[(k + 1) * N + j], l[j][0], gs[k]);
             R g[D], e[D];
 #pragma unroll
             for (int i = 0; i < D; ++i) {
@@ -583,7 +637,8 @@ __device__ __forceinline__ void action_cell(const ActionArgs &a, const R *__rest
                 R o = out[j][0];
                 if constexpr (OP == OP_HELMHOLTZ) o = fma(T[j], ev, o);
 #pragma unroll
-                for (int k = 0; k < D; ++k) o = fma(T[(k + 1) * N + j], e[k], o);
+                for (int k = 0; k < D; ++k)
+                    if (!grad_zero<D, N>(k, j)) o = fma(T[(k + 1) * N + j], e[k], o);
                 out[j][0] = o;
             }
         } else if constexpr (OP == OP_SVK_RESIDUAL || OP == OP_SVK_JACOBIAN) {

@@ -111,6 +111,7 @@ extern "C" int fe_action_noalloc(const fe_form *form, const fe_mesh *mesh, const
     long long tab_doubles = (long long)nq * (1 + m.dim) * n + 2ll * nq;  // table, weights twice
     tab_doubles = (tab_doubles + 1) & ~1ll;
     if (tab_doubles > FE_NOALLOC_TABLE_DOUBLES) return FE_ERR_INVALID_ARG;  // beyond the scratch
+    if (!tab_zeros_hold(m.dim, n, nq, tab_host)) return FE_ERR_INVALID_ARG;  // not fe_tabulate's table
     const size_t smem = (size_t)tab_doubles * sizeof(double);
 
     int dev = 0;
