@@ -267,8 +267,12 @@ extern "C" int fe_batch_create(const fe_batch_problem *problems, int count, fe_b
         const int n = nloc(m.dim, m.degree);
         const int ncomp = f.kind == FE_FORM_MASS ? 1 : m.dim;
         std::vector<double> pts((size_t)nq * m.dim), wts(nq), tab((size_t)(1 + m.dim) * nq * n);
-        fe_tabulate_scheme(m.dim, m.degree, f.quad_degree, f.quad_scheme, &nq, pts.data(), wts.data(), tab.data(),
-                           tab.size());
+        if (fe_tabulate_scheme(m.dim, m.degree, f.quad_degree, f.quad_scheme, &nq, pts.data(), wts.data(),
+                               tab.data(), tab.size()) != FE_OK ||
+            !tab_zeros_hold(m.dim, n, nq, tab.data())) {
+            batch_free(b);
+            return FE_ERR_INVALID_ARG;
+        }
         int kind = pb.kernel;
         if (kind < 0) kind = tpc_available(f.kind, m.dim, m.degree) ? 0 : 1;
         if (kind == 0 && !tpc_available(f.kind, m.dim, m.degree)) {
