@@ -314,6 +314,15 @@ def time_secondary(fe, torch, flush, M_el, u_el, y64_el):
     out["nh_p4_2d_n256_fp32"]["adj_speedup_vs_fp64"] = res["fp64"][1] / res["fp32"][1]
     out["nh_p4_2d_n256_fp32"]["rel_dev_fwd_vs_fp64"] = rel(res["fp32"][2], res["fp64"][2])
     out["nh_p4_2d_n256_fp32"]["rel_dev_adj_vs_fp64"] = rel(res["fp32"][3], res["fp64"][3])
+    # the same residual and adjoint with the 16-point fully symmetric degree-8 rule
+    psym = fe.Plan(M, fe.NH_RESIDUAL, 8, mu_cell=mu, lam_cell=lam, quad_scheme="symmetric")
+    ysym = torch.empty_like(u)
+    tfs = timed(lambda: psym.apply(u, ysym))
+    tas = timed(lambda: psym.adjoint(u, w))
+    out["nh_p4_2d_n256_fp64_sym16"] = {
+        "nq": psym.info.nq, "fwd_ms": tfs * 1e3, "adj_ms": tas * 1e3, "fwd_dofs_per_s": n / tfs,
+        "adj_dofs_per_s": n / tas, "adj_over_fwd": tas / tfs, "fwd_gflops": psym.flops() / tfs / 1e9,
+        "rel_dev_vs_conical25": rel(ysym, res["fp64"][2])}
 
     # elasticity P2 3D (the headline workload) with FP32 contractions, and with the
     # 8-point conical-product rule for comparison
