@@ -216,8 +216,9 @@ __device__ __forceinline__ U cvt(T x)
 // and the tabulation holds exactly 0.0 there at every quadrature point.  Bit j of
 // grad_zero_mask(D, N, k) flags such a local node j (node order of the
 // tabulation: alpha_1 outermost, then alpha_2, alpha_3).  The thread-per-cell
-// contractions skip those terms; the result is unchanged, since a fused
-// multiply-add with a zero factor returns its addend.
+// contractions skip those terms; for finite operands the result is unchanged,
+// since a fused multiply-add with a zero factor returns its addend (up to the
+// sign of a zero sum).
 __host__ __device__ constexpr int lagrange_degree(int D, int N)
 {
     for (int p = 0; p <= 20; ++p) {
