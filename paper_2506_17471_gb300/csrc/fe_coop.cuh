@@ -113,6 +113,28 @@ __device__ __forceinline__ CoopSmem<R> coop_smem(unsigned char *base, const Coop
     return S;
 }
 
+// Phase B: the contribution of local node j to the reference gradients gh of
+// the cell's field(s), along the directions in the bit set DIRS only.
+template <int D, int FIELDS, int NC, int DIRS, typename R>
+__device__ __forceinline__ void eval_node(R (&gh)[FIELDS][NC][D], const R *T, const R *TB, bool gtab,
+                                          const double *lc, int n, int nq, int j)
+{
+    R t[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+        if ((DIRS >> k) & 1)
+            t[k] = gtab ? __ldg(TB + ((size_t)(k + 1) * n + j) * nq) : T[(k + 1) * n + j];
+#pragma unroll
+    for (int f = 0; f < FIELDS; ++f)
+#pragma unroll
+        for (int m = 0; m < NC; ++m) {
+            const R lv = cvt<R>(lc[(f * n + j) * NC + m]);
+#pragma unroll
+            for (int k = 0; k < D; ++k)
+                if ((DIRS >> k) & 1) gh[f][m][k] = fma(t[k], lv, gh[f][m][k]);
+        }
+}
+
 // One batch of cells [cell0, cell0 + nb) through phases A-C by the whole CTA.
 // Must be called by every thread of the CTA; ends with a barrier.
 template <int OP, int D, typename R>
@@ -122,6 +144,7 @@ __device__ __forceinline__ void coop_batch(const ActionArgs &a, const CoopLayout
     constexpr int NC = OpTraits<OP, D>::NC;
     constexpr int FIELDS = OpTraits<OP, D>::kTwoFields ? 2 : 1;
     const int n = L.n;
+    [[maybe_unused]] const int deg = lagrange_degree(D, n);   // Lagrange degree of the cell
     const int nq = L.nq;
     const R *tab = S.tab;
     const double *wts = S.wts;
@@ -216,19 +239,47 @@ __device__ __forceinline__ void coop_batch(const ActionArgs &a, const CoopLayout
                 for (int m = 0; m < NC; ++m)
 #pragma unroll
                     for (int k = 0; k < D; ++k) gh[f][m][k] = R(0);
-            for (int j = 0; j < n; ++j) {
-                R t[D];
-#pragma unroll
-                for (int k = 0; k < D; ++k)
-                    t[k] = gtab ? __ldg(TB + ((size_t)(k + 1) * n + j) * nq) : T[(k + 1) * n + j];
-#pragma unroll
-                for (int f = 0; f < FIELDS; ++f)
-#pragma unroll
-                    for (int m = 0; m < NC; ++m) {
-                        const R lv = cvt<R>(lc[(f * n + j) * NC + m]);
-#pragma unroll
-                        for (int k = 0; k < D; ++k) gh[f][m][k] = fma(t[k], lv, gh[f][m][k]);
+            if constexpr (std::is_same<R, double>::value) {
+                // Nodes in tabulation order (alpha_1 outermost); the last node of each
+                // innermost run has alpha_0 = 0, and its derivative along every
+                // direction k with alpha_{k+1} = 0 vanishes identically (the structural
+                // zeros of grad_zero_mask): those terms are skipped.  The branch is
+                // uniform across the warp (every thread walks the same nodes).  Only
+                // the FP64 kernel does this: it is bound by the FP64 pipe, while in the
+                // FP32 kernel the branches cost more than the saved FMAs.
+                int j = 0;
+                for (int a1 = 0; a1 <= deg; ++a1) {
+                    if constexpr (D == 3) {
+                        for (int a2 = 0; a2 <= deg - a1; ++a2) {
+                            const int a3 = deg - a1 - a2;
+                            for (int c3 = 0; c3 < a3; ++c3, ++j)
+                                eval_node<D, FIELDS, NC, 7>(gh, T, TB, gtab, lc, n, nq, j);
+                            switch ((a1 != 0) | ((a2 != 0) << 1) | ((a3 != 0) << 2)) {
+                            case 1: eval_node<D, FIELDS, NC, 1>(gh, T, TB, gtab, lc, n, nq, j); break;
+                            case 2: eval_node<D, FIELDS, NC, 2>(gh, T, TB, gtab, lc, n, nq, j); break;
+                            case 3: eval_node<D, FIELDS, NC, 3>(gh, T, TB, gtab, lc, n, nq, j); break;
+                            case 4: eval_node<D, FIELDS, NC, 4>(gh, T, TB, gtab, lc, n, nq, j); break;
+                            case 5: eval_node<D, FIELDS, NC, 5>(gh, T, TB, gtab, lc, n, nq, j); break;
+                            case 6: eval_node<D, FIELDS, NC, 6>(gh, T, TB, gtab, lc, n, nq, j); break;
+                            default: eval_node<D, FIELDS, NC, 7>(gh, T, TB, gtab, lc, n, nq, j); break;
+                            }
+                            ++j;
+                        }
+                    } else {
+                        const int a2 = deg - a1;
+                        for (int c2 = 0; c2 < a2; ++c2, ++j)
+                            eval_node<D, FIELDS, NC, 3>(gh, T, TB, gtab, lc, n, nq, j);
+                        switch ((a1 != 0) | ((a2 != 0) << 1)) {
+                        case 1: eval_node<D, FIELDS, NC, 1>(gh, T, TB, gtab, lc, n, nq, j); break;
+                        case 2: eval_node<D, FIELDS, NC, 2>(gh, T, TB, gtab, lc, n, nq, j); break;
+                        default: eval_node<D, FIELDS, NC, 3>(gh, T, TB, gtab, lc, n, nq, j); break;
+                        }
+                        ++j;
                     }
+                }
+            } else {
+                for (int j = 0; j < n; ++j)
+                    eval_node<D, FIELDS, NC, (1 << D) - 1>(gh, T, TB, gtab, lc, n, nq, j);
             }
             if constexpr (OP == OP_LAPLACE || OP == OP_HELMHOLTZ) {
                 // e = w |det J| J^{-1} J^{-T} grad_ref u  (+ the value term for Helmholtz)
