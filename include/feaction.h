@@ -435,9 +435,11 @@ int fe_vec_dot(long long n, const double *x, const double *y, const uint8_t *mas
  * capture.  Every call clears the status word and the counters before it
  * launches, and keeps its table in the array afterwards.  Calls whose GPU work
  * overlaps (unordered streams, several host threads) race on the shared array.
- * Errors: FE_ERR_INVALID_ARG (bad arguments, or a table block larger than
- * FE_NOALLOC_TABLE_DOUBLES doubles), FE_ERR_UNSUPPORTED (no thread-per-cell
- * kernel for this form/dim/degree), FE_ERR_CUDA. */
+ * Errors: FE_ERR_INVALID_ARG (bad arguments, a table block larger than
+ * FE_NOALLOC_TABLE_DOUBLES doubles, or a table that is not exactly 0.0 at a
+ * structural zero of the reference gradients, d phi_alpha / dxhat_k with
+ * alpha_0 = alpha_k = 0, which the kernel does not read), FE_ERR_UNSUPPORTED
+ * (no thread-per-cell kernel for this form/dim/degree), FE_ERR_CUDA. */
 #define FE_NOALLOC_TABLE_DOUBLES 12288
 int fe_action_noalloc(const fe_form *form, const fe_mesh *mesh, const double *tab_host,
                       const double *wts_host, int nq, const double *u, double *y,
