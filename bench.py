@@ -1,29 +1,37 @@
 """Benchmark: FE action DoFs/s and roofline fraction on one GB300 (or N replicas).
 
-Workload (one step = one full matrix-free action, every hot-path step):
-linear elasticity, vector P2 Lagrange on tetrahedra, unit cube cut into 32^3
-cubes x 6 Kuhn tets (196,608 cells, 3 x 274,625 DoFs), interior vertices
-jittered by U[-0.15h, 0.15h], lambda = 1.25, mu = 1, quadrature exact to degree
-2 (the 4-point fully symmetric rule), u ~ U[-1, 1], FP64 throughout.
+Headline workload (one step = one full matrix-free action, every hot-path step):
+linear elasticity, vector P4 Lagrange on tetrahedra, unit cube cut into 43^3
+cubes x 6 Kuhn tets (477,042 cells, 3 x 5,177,717 = 15,533,151 DoFs), interior
+vertices jittered by U[-0.15h, 0.15h], lambda = 1.25, mu = 1, quadrature exact
+to degree 6 (the 24-point fully symmetric rule), u ~ U[-1, 1], FP64 throughout:
+the largest single-GPU point of the hp sweep.
 
 Timing: W untimed warm-up steps, then K steps; each step's kernels are bracketed
 by CUDA events on the launch stream and a 256 MB buffer is written between steps
-to flush the 129 MB L2 (outside the events).  The K steps are bracketed by a
-barrier and a device synchronise; the max over ranks is reported.
+to flush the 129 MB L2 (outside the events; the inputs, 330 MB, exceed L2
+anyway).  The K steps are bracketed by a barrier and a device synchronise; the
+max over ranks is reported.
+
+Output: one compact JSON line per secondary measurement first (other
+configurations, precisions, the adjoint, the batch), each with a "secondary"
+key, then the headline JSON line LAST.
 
 ``--impl reference`` times the CPU oracle (the FP64 reference implementation of
-the method) on the host cores instead, on a bounded sample of the same
-workload.  With ``--gpus N > 1`` (under torchrun) every rank runs an
-independent replica of the workload (the action shards by problem with no data
-exchange); ``value`` sums all ranks' DoFs.
+the method; the paper ships no code) on the host cores instead, one full-mesh
+action of the same workload per step.  With ``--gpus N > 1`` (under torchrun)
+every rank runs an independent replica of the workload (the action shards by
+problem with no data exchange); ``value`` sums all ranks' DoFs.
 """
 
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import platform
+import re
 import statistics
 import subprocess
 import sys
@@ -34,22 +42,18 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+from feinputs.workloads import ELASTICITY_P4_3D_N43 as HEADLINE  # noqa: E402
+
 METRIC = "FE action DoFs/s & % roofline, FP64 vs mixed precision, fwd + adjoint"
 UNIT = "DoFs/s"
-N_CELLS_PER_DIR = 32
-SEED = 20250618
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# FP64 FMA peak from the part's unit counts and clocks: 1.25 TFLOP/s nominal for a
-# GB300 (152 SMs at up to 2070 MHz, about 4 FP64 flops per SM per clock).
-FP64_NOMINAL_GFLOPS = 1250.0
-# DRAM traffic of the benchmark kernel per launch (dram__bytes_read.sum + dram__bytes_write.sum)
-# from the ncu capture summarised in profiles/elasticity_p2_3d_n32_fp64_sym4.md; reported only
-# while the kernel's sources (kernel_source_hash) still hash to the captured version.
-MEASURED_TRAFFIC = {"source_hash": "0dd2fade731acc0b", "bytes": 25094144}
-QUAD_SCHEME = "symmetric"   # the 4-point fully symmetric degree-2 rule
-WORKLOAD = ("linear elasticity, vector P2 tets, unit cube 32^3 x 6 Kuhn tets (196,608 cells, "
-            "823,875 DoFs), jitter 0.15h, lambda=1.25 mu=1, quadrature degree 2 (4-point fully "
-            "symmetric rule), FP64")
+# FP64 FMA rate from the part's unit counts and clocks (152 SMs at up to 2070 MHz,
+# about 4 FP64 flops per SM per clock), for context beside the measured rate.
+FP64_NOMINAL_TFLOPS = 1.25
+# DRAM traffic of the headline kernel per launch (dram__bytes_read.sum +
+# dram__bytes_write.sum from one ncu capture of the same workload), reported only
+# while the kernel's sources still hash to the captured version.
+MEASURED_TRAFFIC = {"source_hash": None, "bytes": None}
 
 
 def parse():
@@ -60,6 +64,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-extra", action="store_true", help="skip the secondary workloads")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--extra-json", default=None, help="also write the secondary rows to this file")
     return ap.parse_args()
 
 
@@ -71,11 +76,9 @@ def dist_env():
 
 
 def kernel_source_hash() -> str:
-    """Hash of what the benchmark kernel is compiled from: fe_kernels.cuh and the
-    ActionArgs struct it receives (the host-side plan struct beside it is excluded),
-    with comments and whitespace removed, so that only code changes move it."""
-    import hashlib
-    import re
+    """Hash of what the headline kernel (k_action_coop) is compiled from:
+    fe_coop.cuh, fe_kernels.cuh and the ActionArgs struct it receives, with
+    comments and whitespace removed, so that only code changes move it."""
 
     def code_only(text: str) -> str:
         text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
@@ -84,50 +87,14 @@ def kernel_source_hash() -> str:
 
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2506_17471_gb300", "csrc")
-    with open(os.path.join(csrc, "fe_kernels.cuh")) as fh:
-        h.update(code_only(fh.read()).encode())
+    for name in ("fe_coop.cuh", "fe_kernels.cuh"):
+        with open(os.path.join(csrc, name)) as fh:
+            h.update(code_only(fh.read()).encode())
     with open(os.path.join(csrc, "fe_internal.h")) as fh:
         text = fh.read()
     start = text.index("struct ActionArgs {")
     h.update(code_only(text[start:text.index("};", start)]).encode())
     return h.hexdigest()[:16]
-
-
-def make_inputs():
-    from feinputs import structured_mesh, uniform_field
-    m = structured_mesh(3, N_CELLS_PER_DIR, 2, jitter=0.15, seed=SEED)
-    u = uniform_field(m.n_nodes * 3, SEED + 1)
-    return m, u
-
-
-# ---------------------------------------------------------------- CPU oracle
-def cpu_oracle_rate(m, u, budget_cpu_s=12.0, threads=None):
-    """Oracle DoFs/s on the host cores: repeat the full-mesh oracle action until
-    about ``budget_cpu_s`` CPU-seconds were spent (bounded sample)."""
-    import oracle
-    threads = threads or os.cpu_count() or 1
-    o = oracle.Oracle.from_mesh(m, 2, QUAD_SCHEME)
-    o.elasticity(u, 1.25, 1.0, threads=threads, cells=(0, min(m.n_cells, 2048)))  # warm
-    reps, t0 = 0, time.perf_counter()
-    while True:
-        o.elasticity(u, 1.25, 1.0, threads=threads)
-        reps += 1
-        el = time.perf_counter() - t0
-        if el * threads >= budget_cpu_s or el > budget_cpu_s:
-            break
-    dofs = m.n_nodes * 3
-    # the same action on one core (about 3 s)
-    reps1, t0 = 0, time.perf_counter()
-    while True:
-        o.elasticity(u, 1.25, 1.0, threads=1)
-        reps1 += 1
-        el1 = time.perf_counter() - t0
-        if el1 >= 3.0:
-            break
-    return {"value": dofs * reps / el, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{reps} full-mesh oracle actions ({m.n_cells} cells) in {el:.2f} s wall "
-                      f"on {threads} threads; single core: {reps1} in {el1:.2f} s",
-            "single_core_value": dofs * reps1 / el1, "cpu_model": cpu_model()}
 
 
 def hbm_peak_gbs() -> float:
@@ -155,33 +122,57 @@ def cpu_model() -> str:
     return f"{platform.machine()} {parts.get(part, 'CPU part ' + part)}".strip()
 
 
+def workload_config(m, nq, parallelism):
+    return {"workload": HEADLINE.describe(m, nq), "n_cells": m.n_cells, "n_dofs": m.n_nodes * 3,
+            "quad_points": nq, "parallelism": parallelism,
+            "l2": "inputs (330 MB) larger than L2, and a 256 MB write between steps outside the events"}
+
+
+# ---------------------------------------------------------------- CPU oracle
+def oracle_for(m):
+    import oracle
+    return oracle.Oracle.from_mesh(m, HEADLINE.quad_degree, HEADLINE.quad_scheme)
+
+
+def cpu_oracle_rate(o, m, u, budget_cpu_s=12.0, threads=None):
+    """Oracle DoFs/s on the host cores: full-mesh oracle actions until about
+    ``budget_cpu_s`` CPU-seconds were spent (a bounded sample)."""
+    threads = threads or os.cpu_count() or 1
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        o.elasticity(u, HEADLINE.lam, HEADLINE.mu, threads=threads)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el * threads >= budget_cpu_s or el > budget_cpu_s:
+            break
+    return {"value": m.n_nodes * 3 * reps / el, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{reps} full-mesh oracle actions in {el:.2f} s on {threads} threads ({cpu_model()})"}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    m, u = make_inputs()
+    m = HEADLINE.mesh()
+    u = HEADLINE.field(m)
     threads = os.cpu_count() or 1
-    import oracle
-    o = oracle.Oracle.from_mesh(m, 2, QUAD_SCHEME)
-    # each step: one full-mesh oracle action (tens of ms on the host cores; a
-    # partial-mesh step scaled up would also scale the per-call cost of the
-    # thread-private output vectors, and understate the oracle)
+    o = oracle_for(m)
+    # each step: one full-mesh oracle action on all host cores
     for _ in range(args.warmup):
-        o.elasticity(u, 1.25, 1.0, threads=threads)
+        o.elasticity(u, HEADLINE.lam, HEADLINE.mu, threads=threads)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        o.elasticity(u, 1.25, 1.0, threads=threads)
+        o.elasticity(u, HEADLINE.lam, HEADLINE.mu, threads=threads)
         times.append(time.perf_counter() - t0)
     t = statistics.mean(times)
     value = m.n_nodes * 3 / t
     line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "parallelism": "host threads"},
+            "data": "synthetic", "config": workload_config(m, o.nq, "host threads"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": f"each step: one full-mesh oracle action ({m.n_cells} cells)",
-                             "cpu_model": cpu_model()},
+                             "sample": f"each step: one full-mesh oracle action ({cpu_model()})"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -239,11 +230,42 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-# ---------------------------------------------------------------- GPU arm
-def time_secondary(fe, torch, flush, M_el, u_el, y64_el):
+# ---------------------------------------------------------------- secondary rows
+class Emitter:
+    """Prints each secondary row as its own compact JSON line (before the
+    headline) and keeps them for ``--extra-json``."""
+
+    SPLIT = ("hp_sweep", "other_forms", "tpc_block_sweep", "param_sensitivity", "mesh_ordering")
+
+    def __init__(self):
+        self.rows = {}
+
+    def emit(self, name, row):
+        self.rows[name] = row
+        print(json.dumps({"secondary": name, **row}, separators=(",", ":")), flush=True)
+
+    def emit_all(self, rows):
+        for name, row in rows.items():
+            if name in self.SPLIT and isinstance(row, dict):
+                for sub, r in row.items():
+                    self.emit(f"{name}/{sub}", r if isinstance(r, dict) else {"value": r})
+            else:
+                self.emit(name, row if isinstance(row, dict) else {"value": row})
+
+    def run(self, name, fn):
+        """Run one group of secondary measurements; a failure is reported as a
+        row and does not stop the benchmark."""
+        try:
+            self.emit_all(fn())
+        except Exception as exc:   # noqa: BLE001 - reported, the headline still prints
+            self.emit(name, {"error": f"{type(exc).__name__}: {exc}"[:500]})
+
+
+def time_secondary(fe, torch, flush, peak_gflops):
     """Secondary measurements: mass P2 2D (N=64), Neo-Hookean P4 2D (N=256)
-    forward + adjoint, FP32-contraction (mixed) kernels, and CG with FP64
-    iterative refinement on the clamped elasticity system."""
+    forward + adjoint, elasticity P2 3D (N=32) in FP64, FP32 and TF32, CG with
+    FP64 iterative refinement, the hp sweep, the paper's other forms, the
+    work-group sweep and the parameter sensitivity of the hp forms."""
     import numpy as np
     from feinputs import lame_fields, structured_mesh, uniform_field
     from feinputs.fields import sinusoid_displacement
@@ -332,25 +354,39 @@ def time_secondary(fe, torch, flush, M_el, u_el, y64_el):
         "adj_dofs_per_s": n / tas, "adj_over_fwd": tas / tfs, "fwd_gflops": psym.flops() / tfs / 1e9,
         "rel_dev_vs_conical25": rel(ysym, res["fp64"][2])}
 
-    # elasticity P2 3D (the headline workload) with FP32 contractions, and with the
-    # 8-point conical-product rule for comparison
-    p64 = fe.Plan(M_el, fe.ELASTICITY, 2, lam=1.25, mu=1.0, quad_scheme=QUAD_SCHEME)
-    p32 = fe.Plan(M_el, fe.ELASTICITY, 2, lam=1.25, mu=1.0, precision="fp32", quad_scheme=QUAD_SCHEME)
+    # elasticity P2 3D N=32 (196,608 tets, 823,875 DoFs): FP64 with the 4-point fully
+    # symmetric degree-2 rule (thread-per-cell kernel), the 8-point conical rule, and
+    # FP32 / TF32 contractions
+    m = structured_mesh(3, 32, 2, jitter=0.15, seed=20250618)
+    M_el = fe.Mesh(3, 2, m.coords, m.cell2vertex, m.cell2node, m.n_nodes)
+    boundary = m.boundary_nodes()
+    u_el = torch.from_numpy(uniform_field(m.n_nodes * 3, 20250619)).cuda()
+    y64_el = torch.empty_like(u_el)
+    p64 = fe.Plan(M_el, fe.ELASTICITY, 2, lam=1.25, mu=1.0, quad_scheme="symmetric")
+    p32 = fe.Plan(M_el, fe.ELASTICITY, 2, lam=1.25, mu=1.0, precision="fp32", quad_scheme="symmetric")
+    pacc = fe.Plan(M_el, fe.ELASTICITY, 2, lam=1.25, mu=1.0, quad_scheme="symmetric", accumulate=True)
     pcon = fe.Plan(M_el, fe.ELASTICITY, 2, lam=1.25, mu=1.0)
+    nd = p64.n_dofs
+    t64 = timed(lambda: p64.apply(u_el, y64_el))
+    tk = timed(lambda: pacc.apply(u_el, y64_el))
+    out["elasticity_p2_3d_n32_fp64"] = {
+        "dofs": nd, "ms": t64 * 1e3, "dofs_per_s": nd / t64, "kernel_ms": tk * 1e3,
+        "kernel_gflops": p64.flops() / tk / 1e9, "frac_of_measured_fp64_peak": p64.flops() / tk / 1e9 / peak_gflops,
+        "nq": p64.info.nq, "kernel": "k_action_tpc<ELASTICITY,3,2>"}
+    p64.apply(u_el, y64_el)
     ycon = torch.empty_like(u_el)
     tcon = timed(lambda: pcon.apply(u_el, ycon))
     out["elasticity_p2_3d_n32_conical8"] = {"ms": tcon * 1e3, "dofs_per_s": pcon.n_dofs / tcon,
                                              "gflops": pcon.flops() / tcon / 1e9, "nq": pcon.info.nq}
     y32 = torch.empty_like(u_el)
-    t64 = timed(lambda: p64.apply(u_el, y64_el))
     t32 = timed(lambda: p32.apply(u_el, y32))
-    nd = p32.n_dofs
     out["elasticity_p2_3d_n32_fp32"] = {
         "ms": t32 * 1e3, "dofs_per_s": nd / t32, "speedup_vs_fp64": t64 / t32,
-        "rel_dev_vs_fp64": rel(y32, y64_el)}
+        "rel_dev_vs_fp64": rel(y32, y64_el),
+        "hbm_frac": p32.info.bytes_min / t32 / 1e9 / hbm_peak_gbs()}
     # the same workload with TF32 tensor-core contractions (FP32 accumulate, FP64
     # geometry and scatter)
-    ptf = fe.Plan(M_el, fe.ELASTICITY, 2, lam=1.25, mu=1.0, precision="tf32", quad_scheme=QUAD_SCHEME)
+    ptf = fe.Plan(M_el, fe.ELASTICITY, 2, lam=1.25, mu=1.0, precision="tf32", quad_scheme="symmetric")
     ytf = torch.empty_like(u_el)
     ttf = timed(lambda: ptf.apply(u_el, ytf))
     out["elasticity_p2_3d_n32_tf32"] = {
@@ -358,7 +394,7 @@ def time_secondary(fe, torch, flush, M_el, u_el, y64_el):
         "rel_dev_vs_fp64": rel(ytf, y64_el), "kernel": ptf.info.kernel}
 
     # CG with FP64 iterative refinement, clamped boundary, b = M A_64 x*
-    free = torch.from_numpy(np.repeat(~_BOUNDARY[0], 3).astype(np.uint8)).cuda()
+    free = torch.from_numpy(np.repeat(~boundary, 3).astype(np.uint8)).cuda()
     xs = torch.from_numpy(uniform_field(nd, 5)).cuda() * free
     b = torch.empty_like(xs)
     p64.apply(xs, b)
@@ -379,7 +415,7 @@ def time_secondary(fe, torch, flush, M_el, u_el, y64_el):
         "ir_rel_residual_fp64": stir.rel_residual, "speedup": t_cg / t_ir,
         "note": "relative residuals are true FP64 residuals ||M(b - A_64 x)|| / ||M b||"}
     for prec in ("bf16", "fp16", "fp16x2"):
-        plo = fe.Plan(M_el, fe.ELASTICITY, 2, lam=1.25, mu=1.0, precision=prec, quad_scheme=QUAD_SCHEME)
+        plo = fe.Plan(M_el, fe.ELASTICITY, 2, lam=1.25, mu=1.0, precision=prec, quad_scheme="symmetric")
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         _, st = solvers.cg_ir(lambda a, c: p64.apply(a, c), lambda a, c: plo.apply(a, c), b, free,
@@ -436,7 +472,9 @@ def time_secondary(fe, torch, flush, M_el, u_el, y64_el):
             "ir_rel_residual_fp64": st.rel_residual, "speedup": t_cg / t_lo}
 
     # hp sweep at ~4M and ~16M DoFs: FP64, FP32 contractions, and BF16 / FP16 / split
-    # FP16 (hi + lo) / TF32 tensor-core contractions (kernel 2)
+    # FP16 (hi + lo) / TF32 tensor-core contractions (kernel 2); fully symmetric rules
+    # where one is tabulated (24 points for degree 6 on tets, 12 for degree 6 on
+    # triangles), else the conical-product rule (49 points for degree 12 on triangles)
     hp = {}
     for name, dim, p, N, q in (("nh_jacobian_p6_2d", 2, 6, 236, 12), ("nh_jacobian_p6_2d", 2, 6, 471, 12),
                                ("elasticity_p4_3d", 3, 4, 27, 6), ("elasticity_p4_3d", 3, 4, 43, 6),
@@ -458,7 +496,7 @@ def time_secondary(fe, torch, flush, M_el, u_el, y64_el):
         row = {"dofs": m.n_nodes * nc, "cells": m.n_cells}
         ys = {}
         for prec in ("fp64", "fp32", "bf16", "fp16", "fp16x2", "tf32"):
-            plan = fe.Plan(M, kind, q, precision=prec, **extra_kw)
+            plan = fe.Plan(M, kind, q, precision=prec, quad_scheme="symmetric", **extra_kw)
             ys[prec] = torch.empty_like(u)
             t = timed(lambda: plan.apply(u, ys[prec]), reps=5)
             row[prec] = {"ms": t * 1e3, "dofs_per_s": m.n_nodes * nc / t,
@@ -469,7 +507,7 @@ def time_secondary(fe, torch, flush, M_el, u_el, y64_el):
             if prec != "fp64":
                 row[prec]["speedup_vs_fp64"] = row["fp64"]["ms"] / row[prec]["ms"]
                 row[prec]["rel_dev_vs_fp64"] = rel(ys[prec], ys["fp64"])
-        row["fp64"]["frac_of_fp64_peak"] = row["fp64"]["gflops"] / FP64_NOMINAL_GFLOPS
+        row["fp64"]["frac_of_measured_fp64_peak"] = row["fp64"]["gflops"] / peak_gflops
         hp[f"{name}_n{N}"] = row
     out["hp_sweep"] = hp
 
@@ -508,7 +546,7 @@ def time_secondary(fe, torch, flush, M_el, u_el, y64_el):
                          "kernel": plan.info.kernel, "nq": plan.info.nq,
                          "hbm_frac": plan.info.bytes_min / t / 1e9 / hbm_peak_gbs()}
             if prec == "fp64":
-                row[prec]["frac_of_fp64_peak"] = row[prec]["gflops"] / FP64_NOMINAL_GFLOPS
+                row[prec]["frac_of_measured_fp64_peak"] = row[prec]["gflops"] / peak_gflops
             else:
                 row[prec]["speedup_vs_fp64"] = row["fp64"]["ms"] / row[prec]["ms"]
                 row[prec]["rel_dev_vs_fp64"] = rel(ys[prec], ys["fp64"])
@@ -522,7 +560,7 @@ def time_secondary(fe, torch, flush, M_el, u_el, y64_el):
     for name, kind, dim, p, N, q, scheme, kw in (
             ("mass_p2_2d_n64", fe.MASS, 2, 2, 64, 4, "conical", {}),
             ("nh_residual_p4_2d_n256", fe.NH_RESIDUAL, 2, 4, 256, 8, "conical", "nh"),
-            ("elasticity_p2_3d_n32", fe.ELASTICITY, 3, 2, 32, 2, QUAD_SCHEME, dict(lam=1.25, mu=1.0))):
+            ("elasticity_p2_3d_n32", fe.ELASTICITY, 3, 2, 32, 2, "symmetric", dict(lam=1.25, mu=1.0))):
         m = structured_mesh(dim, N, p, jitter=0.2 if dim == 2 else 0.15, seed=20250640 + N)
         M = fe.Mesh(dim, p, m.coords, m.cell2vertex, m.cell2node, m.n_nodes)
         if kw == "nh":
@@ -570,9 +608,6 @@ def time_secondary(fe, torch, flush, M_el, u_el, y64_el):
                       "spearman": rep.get("spearman")}
     out["param_sensitivity"] = sens
     return out
-
-
-_BOUNDARY = []
 
 
 def time_ordering(fe, torch, flush):
@@ -724,6 +759,7 @@ def time_batched(fe, torch):
             "status": batch.status()}
 
 
+# ---------------------------------------------------------------- headline (GPU arm)
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -742,10 +778,12 @@ def run_ours(args):
         dist.barrier()
     import paper_2506_17471_gb300 as fe
 
-    m, u_np = make_inputs()
-    _BOUNDARY[:] = [m.boundary_nodes()]
-    M = fe.Mesh(3, 2, m.coords, m.cell2vertex, m.cell2node, m.n_nodes, device=dev)
-    plan = fe.Plan(M, fe.ELASTICITY, 2, lam=1.25, mu=1.0, quad_scheme=QUAD_SCHEME)
+    m = HEADLINE.mesh()
+    u_np = HEADLINE.field(m)
+    M = fe.Mesh(3, HEADLINE.degree, m.coords, m.cell2vertex, m.cell2node, m.n_nodes, device=dev)
+    kw = dict(lam=HEADLINE.lam, mu=HEADLINE.mu, quad_scheme=HEADLINE.quad_scheme)
+    plan = fe.Plan(M, fe.ELASTICITY, HEADLINE.quad_degree, **kw)
+    plan_acc = fe.Plan(M, fe.ELASTICITY, HEADLINE.quad_degree, accumulate=True, **kw)
     n_dofs = plan.n_dofs
     u = torch.from_numpy(u_np).to(dev)
     y = torch.empty_like(u)
@@ -757,9 +795,21 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     for _ in range(max(args.warmup, 3)):
         plan.apply(u, y)
+        plan_acc.apply(u, y)
     torch.cuda.synchronize()
-    if plan.status() != 0:
+    if plan.status() != 0 or plan_acc.status() != 0:
         raise RuntimeError("device status after warm-up")
+
+    def event_steps(fn):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush()
+            ev[i][0].record(stream)
+            fn()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in ev]
 
     sampler = ClockSampler(local)
     sampler.start()
@@ -767,144 +817,93 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    wall0 = time.perf_counter()
-    for i in range(args.steps):
-        flush()
-        ev[i][0].record(stream)
-        plan.apply(u, y)          # zero kernel + action kernel
-        ev[i][1].record(stream)
-    torch.cuda.synchronize()
+    step_ms = event_steps(lambda: plan.apply(u, y))            # zero kernel + action kernel
     if world > 1:
         dist.barrier()
-    wall = time.perf_counter() - wall0
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-
-    # the action kernel alone (accumulate plan: no zero kernel) for the roofline
-    plan_acc = fe.Plan(M, fe.ELASTICITY, 2, lam=1.25, mu=1.0, accumulate=True, quad_scheme=QUAD_SCHEME)
-    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
-    for i in range(args.steps):
-        flush()
-        kev[i][0].record(stream)
-        plan_acc.apply(u, y)
-        kev[i][1].record(stream)
-    torch.cuda.synchronize()
+    # the action kernel alone (accumulate plan: no zero kernel), for the roofline
+    kern_ms = event_steps(lambda: plan_acc.apply(u, y))
     clocks = sampler.stop()
-    kern_ms = [a.elapsed_time(b) for a, b in kev]
+    # FP64 FMA throughput measured now, on this GPU (the roofline's denominator)
+    peak_tflops = fe.measure_fp64_peak() / 1e3
 
-    # end to end through the C-ABI with host buffers (pinned): the K steps go
+    # end to end through the C-ABI with host buffers (page-locked): the K steps go
     # through fe_action_host_pipelined, each copying its own input in and its
     # result out, the copies of neighbouring steps overlapping the action
     from feinputs import uniform_field
-    pool = [torch.from_numpy(uniform_field(n_dofs, SEED + 10 + i)).pin_memory() for i in range(4)]
+    pool = [torch.from_numpy(u_np).pin_memory(),
+            torch.from_numpy(uniform_field(n_dofs, HEADLINE.field_seed + 1)).pin_memory()]
     outs = [torch.empty(n_dofs, dtype=torch.float64).pin_memory() for _ in range(2)]
-    ulist = [pool[i % len(pool)] for i in range(args.steps)]
-    ylist = [outs[i % len(outs)] for i in range(args.steps)]
-    plan.apply_host_pipelined(ulist[:3], ylist[:3])
+    ulist = [pool[i % 2] for i in range(args.steps)]
+    ylist = [outs[i % 2] for i in range(args.steps)]
+    plan.apply_host_pipelined(ulist[:2], ylist[:2])
     flush()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     plan.apply_host_pipelined(ulist, ylist)
-    e2e_t = [(time.perf_counter() - t0) / args.steps]
-    last = plan.apply(ulist[-1].cuda())
-    if not torch.equal(ylist[-1].cuda(), last) and float((ylist[-1].cuda() - last).abs().max()) > 1e-12 * float(
-            last.abs().max()):
-        raise RuntimeError("pipelined end-to-end result differs from the device action")
-    # for reference: one synchronous fe_action_host call per step (H2D + action + D2H + sync)
-    u_host = torch.from_numpy(u_np).pin_memory()
-    y_host = torch.empty_like(u_host).pin_memory()
-    u_dev, y_dev = torch.empty_like(u), torch.empty_like(u)
-    plan.apply_host(u_host, y_host, u_dev, y_dev)
-    single_t = []
-    for _ in range(args.steps):
-        flush()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        plan.apply_host(u_host, y_host, u_dev, y_dev)
-        single_t.append(time.perf_counter() - t0)
-    # the action kernel without an L2 flush (the pipelined steps run back to back)
-    for _ in range(3):
-        plan.apply(u, y)
-    wev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for i in range(args.steps):
-        wev[i][0].record(stream)
-        plan.apply(u, y)
-        wev[i][1].record(stream)
-    torch.cuda.synchronize()
-    warm_ms = statistics.mean(a.elapsed_time(b) for a, b in wev)
+    t_e2e = (time.perf_counter() - t0) / args.steps
+    check = plan.apply(ulist[-1].to(dev))
+    if float((ylist[-1].to(dev) - check).abs().max()) > 1e-12 * float(check.abs().max()):
+        raise RuntimeError("end-to-end result differs from the device action")
+    if plan.status() != 0:
+        raise RuntimeError("device status after the timed steps")
 
     t_step = statistics.mean(step_ms) * 1e-3
     t_kern = statistics.mean(kern_ms) * 1e-3
-    t_e2e = statistics.mean(e2e_t)
     if world > 1:
         tt = torch.tensor([t_step, t_kern, t_e2e], dtype=torch.float64, device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_step, t_kern, t_e2e = [float(x) for x in tt.cpu()]
 
-    flops = plan.flops()
-    peaks = {}
-    if os.path.exists(PEAKS_FILE):
-        with open(PEAKS_FILE) as f:
-            peaks = json.load(f)
-    extra = {}
-    if rank == 0:
-        dfma = fe.measure_fp64_peak()
-        extra["fp64_dfma_measured_gflops"] = dfma
-        if not args.no_extra:
-            extra.update(time_secondary(fe, torch, flush, M, u, y))
-            extra["batched_64_meshes"] = time_batched(fe, torch)
-            extra["mesh_ordering"] = time_ordering(fe, torch, flush)
-        hbm_bound = flops / plan.info.bytes_min * peaks.get("hbm_gbs", 6800.0)
-        extra["roofline_min_gflops"] = min(FP64_NOMINAL_GFLOPS, hbm_bound)
-        extra["arithmetic_intensity_flop_per_byte"] = flops / plan.info.bytes_min
-        extra["wall_ms_k_steps_incl_flush"] = wall * 1e3
-        extra["e2e_single_call"] = {
-            "value": n_dofs / statistics.mean(single_t), "unit": UNIT,
-            "note": "one synchronous fe_action_host per step (H2D, action, D2H, stream sync), L2 flushed "
-                    "before each"}
-        extra["action_ms_without_l2_flush"] = warm_ms
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_oracle_rate(oracle_for(m), m, u_np)
+    if rank == 0 and not args.no_extra:
+        del pool, outs, ulist, ylist
+        em = Emitter()
+        peak_g = peak_tflops * 1e3
+        em.emit("fp64_peak", {"measured_tflops": peak_tflops, "nominal_tflops": FP64_NOMINAL_TFLOPS,
+                              "how": "fe_measure_fp64_peak: 8 independent FMA chains per thread, "
+                                     "152 x 8 blocks of 256 threads"})
+        em.emit("headline_detail", {
+            "kernel_ms_mean": t_kern * 1e3, "kernel_ms_min": min(kern_ms), "kernel_ms_max": max(kern_ms),
+            "step_ms_min": min(step_ms), "step_ms_max": max(step_ms),
+            "flops_per_launch_dense": plan.info.flops_per_cell_dense * m.n_cells,
+            "bytes_min": plan.info.bytes_min, "grid_blocks": plan.info.grid_blocks,
+            "threads_per_block": plan.info.threads_per_block})
+        em.run("secondary", lambda: time_secondary(fe, torch, flush, peak_g))
+        em.run("batched_64_meshes", lambda: {"batched_64_meshes": time_batched(fe, torch)})
+        em.run("mesh_ordering", lambda: {"mesh_ordering": time_ordering(fe, torch, flush)})
+        if args.extra_json:
+            with open(args.extra_json, "w") as f:
+                json.dump(em.rows, f, indent=1)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return
 
-    achieved = flops / t_kern / 1e9
+    flops = plan.flops()
+    achieved = flops / t_kern / 1e12
+    traffic = (MEASURED_TRAFFIC["bytes"]
+               if MEASURED_TRAFFIC["source_hash"] and kernel_source_hash() == MEASURED_TRAFFIC["source_hash"]
+               else None)
     line = {
         "metric": METRIC, "value": world * n_dofs / t_step, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_cells": m.n_cells, "n_dofs": n_dofs,
-                   "quad_points": plan.info.nq, "parallelism": f"replicas{world}",
-                   "l2": "flushed between steps (256 MB write, outside the timed events)"},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_GFLOPS,
-                     "unit": "GFLOP/s", "frac": achieved / FP64_NOMINAL_GFLOPS,
-                     "traffic": (MEASURED_TRAFFIC["bytes"]
-                                 if kernel_source_hash() == MEASURED_TRAFFIC["source_hash"] else None),
-                     "traffic_unit": "bytes per launch", "kernel": "k_action_tpc<ELASTICITY,3,2>",
-                     "flops_per_launch": flops,
-                     "flops_note": "gradient contractions counted over the structurally nonzero "
-                                   "reference-gradient entries (the kernel skips the identically "
-                                   "zero ones); counting every entry (Ops_usable) gives "
-                                   "flops_per_launch_dense",
-                     "flops_per_launch_dense": plan.info.flops_per_cell_dense * m.n_cells,
-                     "peak_note": "FP64 FMA peak from unit counts and clocks (1.25 TFLOP/s "
-                                  "nominal); measured DFMA loop in extra"},
+        "config": workload_config(m, plan.info.nq, f"replicas{world}"),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                     "frac": achieved / peak_tflops, "traffic": traffic,
+                     "kernel": "k_action_coop<ELASTICITY,3,double>", "flops_per_launch": flops,
+                     "peak_source": "FP64 FMA loop measured in this run (of measured)"},
         "e2e": {"value": world * n_dofs / t_e2e, "unit": UNIT, "h2d_bytes_per_step": n_dofs * 8,
-                "d2h_bytes_per_step": n_dofs * 8,
-                "api": "fe_action_host_pipelined over the K steps (pinned host inputs cycled over 4 "
-                       "fields; each step copies its input in and its result out; the copies of "
-                       "neighbouring steps overlap the action; no L2 flush between these back-to-back "
-                       "steps, see extra.action_ms_without_l2_flush)"},
+                "d2h_bytes_per_step": n_dofs * 8, "api": "fe_action_host_pipelined, page-locked host buffers"},
         "gpu_launches": 2 * args.steps,
         "clocks": clocks,
-        "extra": extra,
     }
-    if not args.no_cpu and world == 1:
-        line["cpu_baseline"] = cpu_oracle_rate(m, u_np)
-    print(json.dumps(line), flush=True)
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line, separators=(",", ":")), flush=True)
     if world > 1:
         dist.destroy_process_group()
 

@@ -202,7 +202,7 @@ enum fe_quad_scheme {
                               the smallest tabulated degree >= quad_degree, derived at run
                               time by Gauss-Newton on the moment equations from a stated
                               orbit structure; tabulated: triangles degree 2, 4, 6, 8 (3, 6,
-                              12, 16 points), tetrahedra degree 2, 5 (4, 14 points).  Other
+                              12, 16 points), tetrahedra degree 2, 5, 6 (4, 14, 24 points).  Other
                               requests fall back to FE_QUAD_CONICAL.  Points are ordered
                               lexicographically by (xhat_1, xhat_2, xhat_3).            */
 };
@@ -217,7 +217,12 @@ typedef struct fe_plan fe_plan;
 
 /* Validates the form/mesh pair, tabulates on the host, uploads the tables to
  * the current device and selects the kernel.  Synchronous.  The plan stores
- * copies of *form and *mesh (pointers inside them are borrowed).
+ * copies of *form and *mesh (pointers inside them are borrowed).  This is the
+ * set-up that precedes Algorithm 2: the tabulations Phi of Eq.
+ * "poisson_tabulated_values" and the quadrature weights are computed once per
+ * (form, mesh) pair, not per cell (Sec. "Towards Discretization"), and the
+ * kernel's parameters are fixed (the role of the transformation choices of
+ * Sec. "Transformation Space").
  *
  * Accuracy of y = A(u) against the exact-arithmetic action (norm-wise,
  * ||y - y_exact||_inf / ||y_exact||_inf):
@@ -250,7 +255,10 @@ int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan **out);
  * NULL is accepted. */
 int fe_plan_destroy(fe_plan *plan);
 
-/* y = A(u) (or y += A(u) with FE_FLAG_ACCUMULATE), enqueued on stream.
+/* y = A(u) (or y += A(u) with FE_FLAG_ACCUMULATE), enqueued on stream: the
+ * matrix-free action of Algorithm 2, y_i = sum over cells T of the quadrature
+ * sum of Eq. "poisson_action_w_quadrature" for the form of the plan, gathered
+ * through cell2node and scatter-added (Sec. "Towards Discretization").
  * u, y: device arrays of n_nodes * ncomp doubles (ncomp = 1 for MASS, LAPLACE
  * and HELMHOLTZ, dim otherwise); u and y must not alias.  For the Jacobian kinds
  * u is the direction du.
@@ -258,7 +266,10 @@ int fe_plan_destroy(fe_plan *plan);
 int fe_action(fe_plan *plan, const double *u, double *y, void *stream);
 
 /* Adjoint of the Neo-Hookean residual r(u; mu, lambda) (plan built with
- * kind = FE_FORM_NH_RESIDUAL and per-cell or constant Lame parameters):
+ * kind = FE_FORM_NH_RESIDUAL and per-cell or constant Lame parameters).  The
+ * residual is the hyperelastic form of Appendix A with the Neo-Hookean stress
+ * in place of St. Venant-Kirchhoff's; its transpose action has the structure
+ * of Algorithm 2 with the tangent dP/dF applied to grad w at each point:
  *   jtw      = J(u)^T w          (device, n_nodes*dim; overwritten unless
  *                                 FE_FLAG_ACCUMULATE)
  *   dmu[c]     = w . dr/dmu_c     = int_c (F - F^{-T}) : grad w      (device, n_cells)
@@ -424,7 +435,13 @@ int fe_vec_dot(long long n, const double *x, const double *y, const uint8_t *mas
  *   form, mesh: as for fe_plan_create (device pointers inside them).
  *   tab_host, wts_host, nq: the host tabulation exactly as fe_tabulate writes it
  *     for (mesh->dim, mesh->degree, form->quad_degree): tab [(1+dim)][nq][n_loc],
- *     wts [nq].  Read before the call returns.
+ *     wts [nq], in pageable or page-locked host memory.  The call waits for its
+ *     copies of them to finish (a synchronisation of `stream`, which also waits
+ *     for the work queued before the call) before it launches the kernel, so
+ *     the caller may reuse or free both as soon as the call returns.
+ *   form->flags: FE_FLAG_ACCUMULATE or nothing, and form->tile_cells 0; the
+ *     other plan options need plan-owned memory or another kernel and are
+ *     refused with FE_ERR_UNSUPPORTED.
  *   u, y: device DoF vectors as for fe_action (y is overwritten unless
  *     FE_FLAG_ACCUMULATE).
  *   device_status: NULL, or a host int that receives the device status word
@@ -439,7 +456,8 @@ int fe_vec_dot(long long n, const double *x, const double *y, const uint8_t *mas
  * FE_NOALLOC_TABLE_DOUBLES doubles, or a table that is not exactly 0.0 at a
  * structural zero of the reference gradients, d phi_alpha / dxhat_k with
  * alpha_0 = alpha_k = 0, which the kernel does not read), FE_ERR_UNSUPPORTED
- * (no thread-per-cell kernel for this form/dim/degree), FE_ERR_CUDA. */
+ * (no thread-per-cell kernel for this form/dim/degree, a precision other than
+ * FP64, a flag other than FE_FLAG_ACCUMULATE, tile_cells != 0), FE_ERR_CUDA. */
 #define FE_NOALLOC_TABLE_DOUBLES 12288
 int fe_action_noalloc(const fe_form *form, const fe_mesh *mesh, const double *tab_host,
                       const double *wts_host, int nq, const double *u, double *y,

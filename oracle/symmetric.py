@@ -36,6 +36,9 @@ RULES = {
              [0.0722, 0.459, 0.0159, 0.171, 0.0172, 0.0505, 0.00541, 0.00839, 0.263, 0.00227]),
     (3, 2): (["S31"], [0.138, 0.0417]),
     (3, 5): (["S31", "S31", "S22"], [0.311, 0.0188, 0.0927, 0.0122, 0.0455, 0.00709]),
+    # degree 6, 24 points (Keast's orbit structure: three S31 orbits and one S211)
+    (3, 6): (["S31", "S31", "S31", "S211"],
+             [0.215, 0.00665, 0.0407, 0.00168, 0.322, 0.00923, 0.0637, 0.270, 0.00804]),
 }
 NPAR = {"S3": 0, "S4": 0, "S21": 1, "S31": 1, "S22": 1, "S111": 2, "S211": 2}
 

@@ -299,21 +299,27 @@ class NeoHookeanResidual(torch.autograd.Function):
     forward runs the residual kernel; backward(w) runs the adjoint kernel, which
     recomputes the quadrature-point deformation gradients from u (nothing is
     stored between the two calls) and returns J(u)^T w, dR/dmu^T w and
-    dR/dlambda^T w."""
+    dR/dlambda^T w.  The plan's Lame buffers are shared by every call on it, so
+    forward saves the fields it was given and backward writes them back before
+    the adjoint: a later forward on the same plan with other fields does not
+    change this call's gradients."""
 
     @staticmethod
     def forward(ctx, u, mu_cell, lam_cell, plan: Plan):
         if plan.kind != NH_RESIDUAL or plan.mu_cell is None or plan.lam_cell is None:
             raise ValueError("plan must be an NH_RESIDUAL plan with per-cell Lame parameters")
-        plan.set_lame(mu_cell.detach(), lam_cell.detach())
+        mu_d = mu_cell.detach().to(torch.float64).contiguous()
+        lam_d = lam_cell.detach().to(torch.float64).contiguous()
+        plan.set_lame(mu_d, lam_d)
         u = u.detach().contiguous()
-        ctx.save_for_backward(u)
+        ctx.save_for_backward(u, mu_d, lam_d)
         ctx.plan = plan
         return plan.apply(u)
 
     @staticmethod
     def backward(ctx, w):
-        (u,) = ctx.saved_tensors
+        u, mu_d, lam_d = ctx.saved_tensors
+        ctx.plan.set_lame(mu_d, lam_d)
         jtw, dmu, dlam = ctx.plan.adjoint(u, w.contiguous())
         return jtw, dmu, dlam, None
 

@@ -95,6 +95,11 @@ extern "C" int fe_action_noalloc(const fe_form *form, const fe_mesh *mesh, const
     if (m.dim == 2 && reinterpret_cast<uintptr_t>(m.coords) % 16 != 0) return FE_ERR_INVALID_ARG;
     if (f.kind < FE_FORM_MASS || f.kind > FE_FORM_NH_JACOBIAN) return FE_ERR_INVALID_ARG;
     if (f.precision != FE_PREC_FP64) return FE_ERR_UNSUPPORTED;
+    // Only the plain atomic-scatter kernel runs here: the other plan options
+    // (cells-per-CTA kernel, global tables, node-ordered scatter, block size)
+    // would need plan-owned memory or another kernel, so asking for them is an
+    // error rather than a silent fallback.
+    if ((f.flags & ~FE_FLAG_ACCUMULATE) != 0 || f.tile_cells != 0) return FE_ERR_UNSUPPORTED;
     if (f.kind == FE_FORM_NH_JACOBIAN && !f.u_lin) return FE_ERR_INVALID_ARG;
     const int ncomp = f.kind == FE_FORM_MASS ? 1 : m.dim;
     const long long n_dofs = (long long)m.n_nodes * ncomp;
@@ -142,6 +147,11 @@ extern "C" int fe_action_noalloc(const fe_form *form, const fe_mesh *mesh, const
                             (size_t)nq * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess)
             return FE_ERR_CUDA;
     }
+    // From page-locked host memory these copies run asynchronously and would
+    // still read tab_host / wts_host after the call returns; waiting for them
+    // here lets the caller reuse or free the tables as soon as the call returns,
+    // whatever kind of host memory holds them.
+    if (cudaStreamSynchronize(s) != cudaSuccess) return FE_ERR_CUDA;
 
     if (!(f.flags & FE_FLAG_ACCUMULATE) && n_dofs > 0) {
         if (cudaMemsetAsync(y, 0, (size_t)n_dofs * sizeof(double), s) != cudaSuccess) return FE_ERR_CUDA;

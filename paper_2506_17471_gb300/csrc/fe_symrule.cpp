@@ -6,9 +6,11 @@
 // sharing one weight.  Fewer points than the conical-product rule reach the same
 // exactness (the paper's kernels use such rules: its Q column of Table
 // "action_param_space" lists 12 points for degree 6 and 16 for degree 8 on
-// triangles).  Here each rule is derived at run time: given an orbit structure
-// and a rough starting point, Gauss-Newton (central-difference Jacobian,
-// normal equations) drives the residual of the moment equations
+// triangles, and 23 for the degree-6 elasticity P4 tetrahedron, where the
+// fully symmetric rule here has 24).  Here each rule is derived at run time:
+// given an orbit structure and a rough starting point, Gauss-Newton
+// (central-difference Jacobian, normal equations) drives the residual of the
+// moment equations
 //     sum_i w_i xhat_i^alpha = alpha! / (|alpha| + d)!     for all |alpha| <= q
 // to rounding level (each equation relative to its right-hand side); the result
 // is accepted only with positive weights, points strictly inside and relative
@@ -43,6 +45,10 @@ const std::vector<RuleSpec> &specs()
          {0.07216, 0.4593, 0.01585, 0.1706, 0.01720, 0.05055, 0.005410, 0.008395, 0.2631, 0.002269}},
         {3, 2, {S31}, {0.1382, 0.04167}},
         {3, 5, {S31, S31, S22}, {0.3109, 0.01878, 0.09274, 0.01225, 0.04550, 0.007091}},
+        // degree 6, 24 points: three (a,a,a,1-3a) orbits and one (a,a,b,1-2a-b) orbit
+        // (the orbit structure of Keast's positive degree-6 rule)
+        {3, 6, {S31, S31, S31, S211},
+         {0.2146, 0.006654, 0.04067, 0.001680, 0.3223, 0.009226, 0.06366, 0.2697, 0.008036}},
     };
     return s;
 }

@@ -190,3 +190,52 @@ def test_hp_mass_p3_reduced_precision_full_size(fe, prec):
     ref = oracle.Oracle.from_mesh(m, 6).mass(u, threads=16)
     assert rel(y, ref) <= TOL32
     assert plan.status() == 0
+
+
+@pytest.mark.parametrize("N", [3, 4])
+def test_coop_elasticity_p4_3d_symmetric_rule(fe, N):
+    """Elasticity P4 tets with the 24-point fully symmetric degree-6 rule on the
+    cells-per-CTA kernel (the benchmark's configuration): several CTA batches and
+    a ragged last batch (162 and 384 cells)."""
+    m, M = make(fe, 3, N, 4, 500 + N)
+    o = oracle.Oracle.from_mesh(m, 6, "symmetric")
+    assert o.nq == 24
+    u = uniform_field(m.n_nodes * 3, 7)
+    plan = fe.Plan(M, fe.ELASTICITY, 6, lam=1.25, mu=1.0, quad_scheme="symmetric")
+    assert plan.info.kernel == 1 and plan.info.nq == 24
+    assert rel(plan.apply(cuda(u)), o.elasticity(u, 1.25, 1.0)) <= TOL
+    # a degree-6-exact rule integrates the degree-6 integrand exactly on affine
+    # cells, so the 64-point conical-product rule gives the same action
+    conical = fe.Plan(M, fe.ELASTICITY, 6, lam=1.25, mu=1.0)
+    assert conical.info.nq == 64
+    assert rel(conical.apply(cuda(u)), o.elasticity(u, 1.25, 1.0)) <= TOL
+    assert plan.status() == 0 and conical.status() == 0
+
+
+@pytest.mark.parametrize("name", ["elasticity_p4_3d_n27", "elasticity_p4_3d_n43"])
+def test_benchmark_workload_full_size(fe, name):
+    """The benchmark's workloads exactly as it builds them (same generators, same
+    plan options, so the same launch configuration): at ~4M DoFs every DoF against
+    the oracle; at ~16M DoFs sampled output DoFs recomputed by the oracle from the
+    cells that contain them."""
+    from feinputs import workloads
+    wl = {w.name: w for w in (workloads.ELASTICITY_P4_3D_N27, workloads.ELASTICITY_P4_3D_N43)}[name]
+    m = wl.mesh()
+    M = fe.Mesh(3, wl.degree, m.coords, m.cell2vertex, m.cell2node, m.n_nodes)
+    u = wl.field(m)
+    plan = fe.Plan(M, fe.ELASTICITY, wl.quad_degree, lam=wl.lam, mu=wl.mu, quad_scheme=wl.quad_scheme)
+    assert plan.info.kernel == 1
+    y = plan.apply(cuda(u)).cpu().numpy()
+    assert plan.status() == 0
+    if wl.N <= 27:
+        ref = oracle.Oracle.from_mesh(m, wl.quad_degree, wl.quad_scheme).elasticity(u, wl.lam, wl.mu, threads=16)
+        assert rel(y, ref) <= TOL
+    else:
+        rng = np.random.default_rng(wl.N)
+        nodes = rng.choice(m.n_nodes, size=64, replace=False)
+        cells = np.unique(np.nonzero(np.isin(m.cell2node, nodes))[0])
+        o = oracle.Oracle(3, wl.degree, wl.quad_degree, m.coords, m.cell2vertex[cells], m.cell2node[cells],
+                          m.n_nodes, wl.quad_scheme)
+        ref = o.elasticity(u, wl.lam, wl.mu, threads=16)
+        idx = (nodes[:, None] * 3 + np.arange(3)[None, :]).reshape(-1)
+        assert np.abs(y[idx] - ref[idx]).max() <= TOL * np.abs(y).max()

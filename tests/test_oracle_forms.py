@@ -198,6 +198,41 @@ def test_nh_homogeneous_deformation_interior_rows_vanish(oracle_built):
     assert np.abs(r[interior]).max() < 1e-13 * np.abs(r).max()
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_nh_homogeneous_stretch_energy_and_traction_closed_form(oracle_built, dim):
+    """Absolute pins of the Neo-Hookean law.  Under the homogeneous stretch
+    u_k = a_k x_k the deformation gradient is F = diag(1 + a_k) everywhere, so
+    (1) the energy is Pi = Psi(F) |Omega| with |Omega| = 1, Psi = mu/2 (tr F^T F - d)
+    - mu ln J + lambda/2 (ln J)^2, J = det F; and (2) with P constant, the x-rows of
+    the residual summed over the nodes of the face x = 1 equal int_Omega P_1k
+    d_k psi = P_11 (psi = the sum of those nodes' basis functions: 1 on x = 1, 0 on
+    x = 0, and its traces on the faces normal to the other axes cancel in
+    pairs because the boundary vertices are not jittered), with
+    P_11 = mu (F_11 - 1/F_11) + lambda ln J / F_11.  A volumetric term misread
+    consistently in the energy and the residual (J - 1 for ln J, say) passes the
+    energy-gradient check but fails both closed forms."""
+    m = structured_mesh(dim, 3, 2, jitter=0.2 if dim == 2 else 0.15, seed=61)
+    o = Oracle.from_mesh(m, 4)
+    mu_v, lam_v = 0.7, 3.1
+    mu = np.full(m.n_cells, mu_v)
+    lam = np.full(m.n_cells, lam_v)
+    a = np.array([0.13, -0.08, 0.21])[:dim]
+    pos = node_positions(m)
+    u = _vec_field(pos, lambda x: x * a[None, :])
+    f = 1.0 + a
+    J = float(np.prod(f))
+    psi = mu_v / 2 * (np.sum(f ** 2) - dim) - mu_v * np.log(J) + lam_v / 2 * np.log(J) ** 2
+    assert abs(o.nh_energy(u, mu, lam).sum() - psi) < 1e-14 * max(1.0, abs(psi))
+    r = o.nh_residual(u, mu, lam).reshape(-1, dim)
+    face = np.abs(pos[:, 0] - 1.0) < 1e-12
+    p11 = mu_v * (f[0] - 1.0 / f[0]) + lam_v * np.log(J) / f[0]
+    assert abs(r[face, 0].sum() - p11) < 1e-13 * abs(p11)
+    # and the other components: P is diagonal, so the face sums of the y (and z)
+    # rows vanish
+    for k in range(1, dim):
+        assert abs(r[face, k].sum()) < 1e-13 * abs(p11)
+
+
 def test_nh_residual_is_energy_gradient(oracle_built):
     m, o, mu, lam = _nh_setup()
     n = m.n_nodes * 2

@@ -135,7 +135,7 @@ def test_table_sizes_match_paper():
 
 
 # ---------------------------------------------------------------- symmetric rules
-SYM = [(2, 2, 3), (2, 4, 6), (2, 6, 12), (2, 8, 16), (3, 2, 4), (3, 5, 14)]
+SYM = [(2, 2, 3), (2, 4, 6), (2, 6, 12), (2, 8, 16), (3, 2, 4), (3, 5, 14), (3, 6, 24)]
 
 
 @pytest.mark.parametrize("dim,q,npts", SYM)
@@ -171,6 +171,6 @@ def test_symmetric_rule_sizes_match_paper_point_counts():
 
 def test_symmetric_family_falls_back_to_conical():
     from oracle.symmetric import symmetric_rule
-    pts, wts = symmetric_rule(3, 6)
-    p2, w2 = quadrature.simplex_rule(3, 6)
+    pts, wts = symmetric_rule(3, 7)
+    p2, w2 = quadrature.simplex_rule(3, 7)
     assert np.array_equal(pts, p2) and np.array_equal(wts, w2)

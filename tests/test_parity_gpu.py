@@ -285,6 +285,29 @@ def test_autograd_function_matches_oracle_and_fd(fe):
     assert abs(fd - an) <= 1e-7 * abs(an)
 
 
+def test_autograd_second_forward_does_not_change_first_gradients(fe):
+    """Two forwards on one plan with different Lame fields, then backpropagation
+    through the first: its gradients use the first call's fields."""
+    m, M = make(fe, 2, 6, 4, seed=19)
+    o = oracle.Oracle.from_mesh(m, 8)
+    mu1, lam1 = lame_fields(m.n_cells, 21)
+    mu2, lam2 = lame_fields(m.n_cells, 22)
+    u = sinusoid_displacement(m, 23)
+    w = uniform_field(m.n_nodes * 2, 24)
+    plan = fe.Plan(M, fe.NH_RESIDUAL, 8, mu_cell=mu1, lam_cell=lam1)
+    ut = cuda(u).requires_grad_(True)
+    mut = cuda(mu1).requires_grad_(True)
+    lamt = cuda(lam1).requires_grad_(True)
+    r1 = fe.NeoHookeanResidual.apply(ut, mut, lamt, plan)
+    r2 = fe.NeoHookeanResidual.apply(cuda(u), cuda(mu2), cuda(lam2), plan)
+    assert rel(r2, o.nh_residual(u, mu2, lam2)) <= TOL
+    (r1 * cuda(w)).sum().backward()
+    ojtw, odmu, odlam = o.nh_adjoint(u, w, mu1, lam1)
+    assert rel(ut.grad, ojtw) <= TOL
+    assert rel(mut.grad, odmu) <= TOL
+    assert rel(lamt.grad, odlam) <= TOL
+
+
 def test_plans_of_one_kernel_keep_their_shared_memory(fe):
     """A later plan of the same kernel with a smaller table must not break an
     earlier plan that needs more dynamic shared memory."""

@@ -62,7 +62,7 @@ CASES = [
     ("elasticity", 2, 13, 2, 2, "symmetric"), ("elasticity", 2, 13, 4, 6, "symmetric"),
     ("elasticity", 2, 13, 6, 10, "conical"), ("elasticity", 3, 5, 1, 0, "conical"),
     ("elasticity", 3, 5, 2, 2, "symmetric"), ("elasticity", 3, 5, 2, 2, "conical"),
-    ("elasticity", 3, 5, 4, 6, "conical"),
+    ("elasticity", 3, 5, 4, 6, "conical"), ("elasticity", 3, 5, 4, 6, "symmetric"),
 ]
 
 

@@ -5,7 +5,9 @@ that may not call cudaMalloc after start-up, cannot create a plan.  This entry
 point runs the same kernel with its scratch in a static device array of the
 library.  The test calls it through the C-ABI twice in a row, with different
 forms and table sizes (the array keeps the previous call's contents), and checks
-each output against fe_action's within the parity tolerance of the suite.
+each output against fe_action's within the parity tolerance of the suite; a
+second test passes page-locked tables and overwrites them as soon as the call
+returns.
 This file sorts last so that a run stopping at the first failure has already
 run every other test; it also passes on its own in a fresh process.
 """
@@ -76,6 +78,42 @@ def test_noalloc_matches_fe_action_on_two_calls_in_a_row(fe):
     rc, st = call_noalloc(fe, p2, u2, y2)
     assert (rc, st) == (0, 0)
     assert rel(y2, p2.apply(u2)) <= TOL
+
+
+def test_noalloc_reads_page_locked_tables_before_returning(fe):
+    """Tables in page-locked host memory are copied asynchronously; the entry
+    point waits for its copies, so overwriting the tables as soon as it returns
+    (before the stream is synchronised) must not change the result."""
+    m = structured_mesh(3, 5, 2, jitter=0.15, seed=86)
+    M = fe.Mesh(3, 2, m.coords, m.cell2vertex, m.cell2node, m.n_nodes)
+    plan = fe.Plan(M, fe.ELASTICITY, 2, lam=1.25, mu=1.0)
+    _, wts, tab = fe.tabulate(3, 2, 2)
+    tab_p = torch.from_numpy(np.ascontiguousarray(tab)).pin_memory()
+    wts_p = torch.from_numpy(np.ascontiguousarray(wts)).pin_memory()
+    u = torch.from_numpy(uniform_field(m.n_nodes * 3, 87)).cuda()
+    y = torch.empty_like(u)
+    ref = plan.apply(u)
+    torch.cuda.synchronize()
+    for _ in range(2):
+        rc = call_noalloc_async(fe, plan, u, y, tab_p, wts_p)
+        assert rc == 0
+        tab_p.fill_(1e300)      # the caller reuses its buffers right away
+        wts_p.fill_(-1e300)
+        torch.cuda.synchronize()
+        assert rel(y, ref) <= TOL
+        tab_p.copy_(torch.from_numpy(np.ascontiguousarray(tab)))
+        wts_p.copy_(torch.from_numpy(np.ascontiguousarray(wts)))
+
+
+def call_noalloc_async(fe, plan, u, y, tab_p, wts_p):
+    """fe_action_noalloc from page-locked tables, without the status read-back
+    (which would synchronise the stream)."""
+    from paper_2506_17471_gb300 import _native as N
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return N.lib.fe_action_noalloc(ctypes.byref(plan._form), ctypes.byref(plan._mesh_c),
+                                   ctypes.c_void_p(tab_p.data_ptr()), ctypes.c_void_p(wts_p.data_ptr()),
+                                   int(wts_p.numel()), ctypes.c_void_p(u.data_ptr()),
+                                   ctypes.c_void_p(y.data_ptr()), None, stream)
 
 
 def test_noalloc_rejects_tables_beyond_its_scratch(fe):
