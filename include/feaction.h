@@ -496,6 +496,20 @@ int fe_selftest_conversions16(const double *x, long long n, unsigned long long *
  * (NULL status, polls outside [1, 2^24]), FE_ERR_CUDA. */
 int fe_selftest_bounded_wait(int32_t *status, int polls, void *stream);
 
+/* Device self-test of the Neo-Hookean laws' logarithm and reciprocal: the
+ * kernels evaluate log det F by Tang's table-driven method (ACM TOMS 16(4),
+ * 1990: x = 2^e m, m within 2^-8 of a table point c = i/128, log x = e ln2 +
+ * log c + log1p((m - c)/c) with a degree-8 Taylor polynomial) and 1/det F by
+ * the approximate hardware reciprocal refined by two Newton-Raphson steps.
+ * table: device buffer of FE_LOG_TABLE_DOUBLES doubles that receives the
+ * logarithm's table (synchronises stream once); x [n] device; log_out[i] =
+ * the kernels' log(x[i]), rcp_out[i] = their 1/x[i] (device, [n]).
+ * Asynchronous on stream after the table upload.  Errors: FE_ERR_INVALID_ARG,
+ * FE_ERR_CUDA. */
+#define FE_LOG_TABLE_DOUBLES 370
+int fe_selftest_log_rcp(const double *x, long long n, double *table, double *log_out, double *rcp_out,
+                        void *stream);
+
 /* Host function.  Rounds x[n] (host) to the 16-bit type of precision
  * (FE_PREC_BF16 or FE_PREC_FP16) to nearest even, exactly as plans round their
  * tabulation for the tensor-core kernel; bits[n] (host, caller-owned) receives

@@ -48,7 +48,8 @@ EXPORTS = ("fe_status_string", "fe_tabulate", "fe_tabulate_scheme", "fe_plan_cre
            "fe_cg_update", "fe_cg_new_direction", "fe_vec_axpy", "fe_vec_dot",
            "fe_selftest_conversions", "fe_batch_create", "fe_batch_run", "fe_batch_status",
            "fe_batch_get_info", "fe_batch_destroy", "fe_selftest_conversions16", "fe_round16", "fe_round_tf32", "fe_order_cells_morton", "fe_order_first_touch", "fe_selftest_bounded_wait",
-           "fe_action_host_pipelined")
+           "fe_action_host_pipelined", "fe_selftest_log_rcp")
+FE_LOG_TABLE_DOUBLES = 370
 FE_CG_PARTIALS = 1024
 FE_CG_WORKSPACE_DOUBLES = FE_CG_PARTIALS + 16
 

@@ -413,6 +413,47 @@ static void tc_fill_block(const TcLayout &L, int kind, const std::vector<double>
     }
 }
 
+static_assert(kLogTabDoubles == FE_LOG_TABLE_DOUBLES, "log table size of the header");
+
+namespace fe {
+void fill_log_table(double *t)
+{
+    // per table point c = i/128: c, 1/c rounded, and log c split into a head on
+    // the 2^-42 grid and a tail; then ln 2 split the same way (section on fe_log)
+    const long double grid = 4398046511104.0L;   // 2^42
+    for (int i = kLogTabFirst; i <= kLogTabLast; ++i) {
+        double *e = t + 4 * (i - kLogTabFirst);
+        const long double L = logl((long double)i / 128.0L);
+        const long double head = nearbyintl(L * grid) / grid;
+        e[0] = (double)i / 128.0;
+        e[1] = 128.0 / (double)i;
+        e[2] = (double)head;
+        e[3] = (double)(L - head);
+    }
+    const long double L2 = logl(2.0L);
+    const long double head2 = nearbyintl(L2 * grid) / grid;
+    t[kLogTabDoubles - 2] = (double)head2;
+    t[kLogTabDoubles - 1] = (double)(L2 - head2);
+}
+}  // namespace fe
+
+// Neo-Hookean plans evaluate log det F with fe_log: upload its table.
+static int attach_log_table(fe_plan *p)
+{
+    const int k = p->form.kind;
+    if (k != FE_FORM_NH_RESIDUAL && k != FE_FORM_NH_JACOBIAN) return FE_OK;
+    std::vector<double> t(kLogTabDoubles);
+    fill_log_table(t.data());
+    if (cudaMalloc(&p->d_log_tab, t.size() * sizeof(double)) != cudaSuccess) {
+        p->d_log_tab = nullptr;
+        cudaGetLastError();
+        return FE_ERR_NO_MEMORY;
+    }
+    if (cudaMemcpy(p->d_log_tab, t.data(), t.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+        return FE_ERR_CUDA;
+    return FE_OK;
+}
+
 static int plan_create_tc(const fe_form &f, const fe_mesh &m, const Variant &v, int nq, int n, int ncomp,
                           const std::vector<double> &wts, const std::vector<double> &tab, fe_plan **out)
 {
@@ -488,6 +529,10 @@ static int plan_create_tc(const fe_form &f, const fe_mesh &m, const Variant &v, 
         fe_plan_destroy(p);
         return FE_ERR_CUDA;
     }
+    if (const int lrc = attach_log_table(p); lrc != FE_OK) {
+        fe_plan_destroy(p);
+        return lrc;
+    }
     // one CTA per SM (a kernel that uses tensor memory is resident alone on its SM)
     const long long tiles = ((long long)m.n_cells + kTcRows - 1) / kTcRows;
     const long long want = (tiles + L.pipes - 1) / L.pipes;
@@ -559,14 +604,27 @@ extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan 
     const int fields_max =
         (f.kind == FE_FORM_NH_JACOBIAN || f.kind == FE_FORM_SVK_JACOBIAN || (adj != nullptr)) ? 2 : 1;
     int coop_cells = 0;
+    int coop_block = kCoopBlock;
     bool global_tab = false;
     size_t rs = (size_t)(1 + m.dim) * n, woff, smem, block_bytes;
     if (coop) {
         const bool gt = (f.flags & FE_FLAG_TABLES_GLOBAL) ||
                         (esz == sizeof(float) ? coop_default_global<float>(n, nq, m.dim)
                                               : coop_default_global<double>(n, nq, m.dim));
-        coop_cells = f.tile_cells > 0 ? f.tile_cells
-                                      : coop_cells_for(n, nq, m.dim, ncomp, fields_max, esz, 100 * 1024, gt);
+        if (f.tile_cells > 0) {
+            coop_cells = f.tile_cells;
+        } else if (esz == sizeof(double)) {
+            // FP64: the wide layout (one 512-thread CTA per SM, a batch of 64 or 32
+            // cells) where its shared memory fits
+            for (int C : {64, 32}) {
+                if (coop_layout<double>(n, nq, m.dim, ncomp, C, fields_max, gt).total <= kCoopWideSmemBytes) {
+                    coop_cells = C;
+                    coop_block = kCoopWideBlock;
+                    break;
+                }
+            }
+        }
+        if (coop_cells == 0) coop_cells = coop_cells_for(n, nq, m.dim, ncomp, fields_max, esz, 100 * 1024, gt);
         CoopLayout L = esz == sizeof(float) ? coop_layout<float>(n, nq, m.dim, ncomp, coop_cells, fields_max, gt)
                                             : coop_layout<double>(n, nq, m.dim, ncomp, coop_cells, fields_max, gt);
         rs = L.rs;
@@ -580,7 +638,7 @@ extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan 
         smem = block_bytes;
     }
     const int tab_doubles = (int)(block_bytes / sizeof(double));
-    if (smem > 200 * 1024) return FE_ERR_UNSUPPORTED;
+    if (smem > (coop_block == kCoopWideBlock ? kCoopWideSmemBytes : (size_t)200 * 1024)) return FE_ERR_UNSUPPORTED;
     // global-memory tables of the cooperative kernel follow the staged block:
     // phase B [1+d][n][nq], then phase C [nq][1+d][n], each 16-byte aligned
     const size_t gsz = global_tab ? (((size_t)(1 + m.dim) * n * nq * esz + 15) & ~(size_t)15) : 0;
@@ -628,6 +686,10 @@ extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan 
         p->var.block = f.tile_cells;
         if (adj) p->adj.block = f.tile_cells;
     }
+    if (coop) {
+        p->var.block = coop_block;
+        if (adj) p->adj.block = coop_block;
+    }
     p->smem_bytes = smem;
     cudaGetDevice(&p->device);
     p->coop_cells = coop_cells;
@@ -649,6 +711,10 @@ extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan 
     if (allow_max_dynamic_smem(v->func) != cudaSuccess || (adj && allow_max_dynamic_smem(adj->func) != cudaSuccess)) {
         fe_plan_destroy(p);
         return FE_ERR_CUDA;
+    }
+    if (const int lrc = attach_log_table(p); lrc != FE_OK) {
+        fe_plan_destroy(p);
+        return lrc;
     }
     p->grid_blocks = grid_for(p->var, smem, m.n_cells, coop ? coop_cells : p->var.block);
     p->adj_grid_blocks = adj ? grid_for(p->adj, smem, m.n_cells, coop ? coop_cells : p->adj.block) : 0;
@@ -695,6 +761,7 @@ extern "C" int fe_plan_destroy(fe_plan *plan)
     cudaFree(plan->d_cell_out);
     cudaFree(plan->d_node_ptr);
     cudaFree(plan->d_node_inc);
+    cudaFree(plan->d_log_tab);
     release_pipeline(plan);
     delete plan;
     return FE_OK;
@@ -729,6 +796,7 @@ static ActionArgs make_args(const fe_plan *p, const double *u, double *y)
     a.tc_pipes = p->tc_pipes;
     a.tc_wshift = p->tc_wshift;
     a.cell_out = p->d_cell_out;
+    a.log_tab = p->d_log_tab;
     return a;
 }
 
@@ -990,6 +1058,36 @@ extern "C" int fe_selftest_bounded_wait(int32_t *status, int polls, void *stream
 {
     if (!status || polls < 1 || polls > (1 << 24)) return FE_ERR_INVALID_ARG;
     k_selftest_bounded_wait<<<1, 64, 0, static_cast<cudaStream_t>(stream)>>>(status, polls);
+    return cudaGetLastError() == cudaSuccess ? FE_OK : FE_ERR_CUDA;
+}
+
+namespace fe {
+namespace {
+__global__ void k_selftest_log_rcp(const double *x, long long n, const double *tab, double *log_out, double *rcp_out)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double v = x[i];
+        log_out[i] = fe_log(v, tab);
+        rcp_out[i] = fe_rcp(v);
+    }
+}
+}  // namespace
+}  // namespace fe
+
+extern "C" int fe_selftest_log_rcp(const double *x, long long n, double *table, double *log_out, double *rcp_out,
+                                   void *stream)
+{
+    if (n < 0 || !table || (n > 0 && (!x || !log_out || !rcp_out))) return FE_ERR_INVALID_ARG;
+    std::vector<double> t(kLogTabDoubles);
+    fill_log_table(t.data());
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(table, t.data(), t.size() * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return FE_ERR_CUDA;
+    if (n == 0) return FE_OK;
+    long long g = (n + 255) / 256;
+    if (g > 4096) g = 4096;
+    k_selftest_log_rcp<<<(int)g, 256, 0, s>>>(x, n, table, log_out, rcp_out);
     return cudaGetLastError() == cudaSuccess ? FE_OK : FE_ERR_CUDA;
 }
 

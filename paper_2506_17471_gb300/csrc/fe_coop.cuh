@@ -29,7 +29,17 @@
 namespace fe {
 
 constexpr int kCoopBlock = 256;
+// Wide layout of the FP64 kernel: one CTA of 512 threads per SM with a batch of
+// C = 64 (or 32) cells, a multiple of the warp size, so that in phase C every
+// warp works on one local node for 32 cells and can leave out that node's
+// structurally zero derivative directions without diverging.
+constexpr int kCoopWideBlock = 512;
+constexpr size_t kCoopWideSmemBytes = 224 * 1024;
 constexpr size_t kCoopSmemTableBytes = 96 * 1024;   // larger tables stay in global memory
+// Per-cell geometry record in shared memory: J^{-1} (D*D), |det J|, mu, lambda,
+// a validity flag; the stride is odd so that threads reading the records of
+// consecutive cells hit distinct banks.
+constexpr int kCoopGeoStride = 17;
 
 // Shared-memory plan of one CTA, computed identically on host and device.
 struct CoopLayout {
@@ -38,6 +48,8 @@ struct CoopLayout {
     int rs;        // table row stride per quadrature point (elements), odd
     int ls;        // per-cell DoF stride (doubles), odd
     int es;        // per-(cell, q) stride of e (elements), odd
+    int ecs;       // per-cell stride of e (elements), odd: threads of a warp that read
+                   // the same (q, k) entry of 32 consecutive cells hit distinct banks
     size_t tab_bytes, wts_off, wtsr_off, table_block_bytes;   // the staged table block
     size_t off_l, off_e, off_nodes, off_geo, off_acc, total;
 };
@@ -64,6 +76,7 @@ __host__ __device__ inline CoopLayout coop_layout(int n, int nq, int D, int NC, 
     L.rs = ((1 + D) * n) | 1;
     L.ls = (fields * n * NC) | 1;
     L.es = ((D * NC > 1 + D) ? D * NC : 1 + D) | 1;   // gradient terms, or value + gradient
+    L.ecs = (nq * L.es) | 1;
     L.global_tab = global_tab ? 1 : 0;
     L.tab_bytes = L.global_tab ? 0 : (size_t)nq * L.rs * sizeof(R);
     L.wts_off = (L.tab_bytes + 7) & ~(size_t)7;
@@ -71,10 +84,9 @@ __host__ __device__ inline CoopLayout coop_layout(int n, int nq, int D, int NC, 
     L.table_block_bytes = (L.wtsr_off + (size_t)nq * sizeof(R) + 15) & ~(size_t)15;
     L.off_l = L.table_block_bytes;
     L.off_e = (L.off_l + (size_t)C * L.ls * sizeof(double) + 15) & ~(size_t)15;
-    L.off_nodes = (L.off_e + (size_t)C * nq * L.es * sizeof(R) + 15) & ~(size_t)15;
+    L.off_nodes = (L.off_e + (size_t)C * L.ecs * sizeof(R) + 15) & ~(size_t)15;
     L.off_geo = (L.off_nodes + (size_t)C * n * sizeof(int) + 15) & ~(size_t)15;
-    // per cell: Jinv (D*D), |det J|, mu, lam, a validity flag -> 16 doubles
-    L.off_acc = L.off_geo + (size_t)C * 16 * sizeof(double);
+    L.off_acc = L.off_geo + (size_t)C * kCoopGeoStride * sizeof(double);
     // adjoint accumulators dmu, dlam per cell
     L.total = (L.off_acc + (size_t)C * 2 * sizeof(double) + 15) & ~(size_t)15;
     return L;
@@ -135,6 +147,56 @@ __device__ __forceinline__ void eval_node(R (&gh)[FIELDS][NC][D], const R *T, co
         }
 }
 
+// Number of multi-indices with `dims` nonnegative entries summing to at most s.
+__device__ __forceinline__ int simplex_count(int dims, int s)
+{
+    return dims == 0 ? 1 : (dims == 1 ? s + 1 : (s + 1) * (s + 2) / 2);
+}
+
+// Directions k (bit k) along which the reference derivative of the basis
+// function of local node j can be nonzero.  The node's multi-index alpha is
+// recovered from j in the documented nested-loop order (alpha_1 outermost).  A
+// node with alpha_0 = deg - |alpha| > 0 may vary along every direction; on the
+// face alpha_0 = 0 the derivative along k vanishes identically where alpha_k = 0
+// (the structural zeros of grad_zero_mask).
+template <int D>
+__device__ __forceinline__ int node_dirs(int deg, int j)
+{
+    int rem = deg, dirs = 0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        int t = 0;
+        for (;;) {
+            const int cnt = simplex_count(D - 1 - k, rem - t);
+            if (j < cnt || t >= rem) break;
+            j -= cnt;
+            ++t;
+        }
+        if (t > 0) dirs |= 1 << k;
+        rem -= t;
+    }
+    return rem > 0 ? (1 << D) - 1 : dirs;
+}
+
+// Phase C for one (cell, node): out[m] += sum_q sum_k Phi_k[q][j] e[q][m][k],
+// over the directions in the bit set DIRS only.
+template <int D, int NC, int DIRS, typename R>
+__device__ __forceinline__ void quad_node(R (&out)[NC], const R *tab, const R *tab_c, bool gtab,
+                                          const R *ec, int rs, int es, int n, int nq, int j)
+{
+    for (int q = 0; q < nq; ++q) {
+        const R *T = gtab ? tab_c + (size_t)q * (D + 1) * n : tab + (size_t)q * rs;
+        const R *e = ec + (size_t)q * es;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            if (!((DIRS >> k) & 1)) continue;
+            const R t = gtab ? __ldg(T + (k + 1) * n + j) : T[(k + 1) * n + j];
+#pragma unroll
+            for (int m = 0; m < NC; ++m) out[m] = fma(t, e[m * D + k], out[m]);
+        }
+    }
+}
+
 // One batch of cells [cell0, cell0 + nb) through phases A-C by the whole CTA.
 // Must be called by every thread of the CTA; ends with a barrier.
 template <int OP, int D, typename R>
@@ -191,7 +253,7 @@ __device__ __forceinline__ void coop_batch(const ActionArgs &a, const CoopLayout
         }
         double Jinv[D][D];
         const double det = cell_geometry<D>(X, Jinv);
-        double *g = sgeo + c * 16;
+        double *g = sgeo + c * kCoopGeoStride;
         const bool good = ok && (det != 0.0) && isfinite(det);
         if (!ok) set_status(a.status, FE_ERR_INDEX);
         else if (!good) set_status(a.status, FE_ERR_BAD_MESH);
@@ -212,12 +274,12 @@ __device__ __forceinline__ void coop_batch(const ActionArgs &a, const CoopLayout
     bool nh_ok = true;
     for (int i = threadIdx.x; i < nb * nq; i += blockDim.x) {
         const int c = i / nq, q = i - c * nq;
-        const double *g = sgeo + c * 16;
+        const double *g = sgeo + c * kCoopGeoStride;
         const R *T = tab + (size_t)q * L.rs;
         const bool gtab = L.global_tab;
         const R *TB = S.tab_b + q;   // [k][j][q]: element (k, j) at TB[(k * n + j) * nq]
         const double *lc = sl + c * L.ls;
-        R *e = se + ((size_t)c * nq + q) * L.es;
+        R *e = se + (size_t)c * L.ecs + (size_t)q * L.es;
         const double absdet = g[D * D];
         double Jinv[D][D];
 #pragma unroll
@@ -358,10 +420,11 @@ __device__ __forceinline__ void coop_batch(const ActionArgs &a, const CoopLayout
                 for (int ii = 0; ii < D; ++ii) F[ii][ii] += 1.0;
                 const double Jd = det_cof<D>(F, C2);
                 nh_ok &= (Jd > 0.0);
-                const double lnJ = log(Jd);
+                const double lnJ = law_log(Jd, a.log_tab);
+                const double rJ = a.log_tab ? fe_rcp(Jd) : 1.0 / Jd;
                 if constexpr (OP == OP_NH_RESIDUAL) {
                     const double smu = wdet * mu;
-                    const double scf = wdet * fma(lam, lnJ, -mu) / Jd;
+                    const double scf = wdet * fma(lam, lnJ, -mu) * rJ;
 #pragma unroll
                     for (int ii = 0; ii < D; ++ii)
 #pragma unroll
@@ -370,7 +433,6 @@ __device__ __forceinline__ void coop_batch(const ActionArgs &a, const CoopLayout
                     double H[D][D], Fit[D][D], A[D][D];
                     convert<D, D>(gh[0], ghd);
                     map_grad<D, double>(ghd, Jinv, H);
-                    const double rJ = 1.0 / Jd;
                     double tr = 0.0;
 #pragma unroll
                     for (int ii = 0; ii < D; ++ii)
@@ -424,12 +486,26 @@ __device__ __forceinline__ void coop_batch(const ActionArgs &a, const CoopLayout
     if (!nh_ok) set_status(a.status, FE_ERR_NONFINITE);
     __syncthreads();
 
-    // ---- C: quadrature contraction + scatter per (cell, node)
+    // ---- C: quadrature contraction + scatter per (cell, node).  With a batch of a
+    // multiple of 32 cells the items are node-major (item i: node i / C, cell
+    // i % C), so every warp holds one node for 32 cells and the FP64 kernel can
+    // skip that node's structurally zero directions with a warp-uniform branch;
+    // otherwise cell-major (consecutive threads: consecutive nodes of a cell).
     const bool store = OP != OP_NH_ADJOINT && a.cell_out;   // node-gather scatter
-    for (int i = threadIdx.x; i < nb * n; i += blockDim.x) {
-        const int c = i / n, j = i - c * n;
+    const bool node_major = (L.C % 32) == 0;
+    const int items = node_major ? n * L.C : nb * n;
+    for (int i = threadIdx.x; i < items; i += blockDim.x) {
+        int c, j;
+        if (node_major) {
+            j = i / L.C;
+            c = i - j * L.C;
+            if (c >= nb) continue;   // ragged last batch
+        } else {
+            c = i / n;
+            j = i - c * n;
+        }
         const int node = snodes[c * n + j];
-        if (node < 0 || sgeo[c * 16 + D * D + 3] == 0.0) {
+        if (node < 0 || sgeo[c * kCoopGeoStride + D * D + 3] == 0.0) {
             if (store) {
                 R *o = static_cast<R *>(a.cell_out) + ((size_t)(cell0 + c) * n + j) * NC;
 #pragma unroll
@@ -440,25 +516,43 @@ __device__ __forceinline__ void coop_batch(const ActionArgs &a, const CoopLayout
         R out[NC];
 #pragma unroll
         for (int m = 0; m < NC; ++m) out[m] = R(0);
-        const R *ec = se + (size_t)c * nq * L.es;
+        const R *ec = se + (size_t)c * L.ecs;
         const bool gtab = L.global_tab;
-        for (int q = 0; q < nq; ++q) {
-            const R *T = gtab ? S.tab_c + (size_t)q * (D + 1) * n : tab + (size_t)q * L.rs;
-            const R *e = ec + (size_t)q * L.es;
-            if constexpr (OP == OP_MASS) {
-                out[0] = fma(gtab ? __ldg(T + j) : T[j], e[0], out[0]);
-            } else if constexpr (OP == OP_HELMHOLTZ) {
-                R o = fma(gtab ? __ldg(T + j) : T[j], e[0], out[0]);
+        if constexpr (OP == OP_MASS || OP == OP_HELMHOLTZ) {
+            for (int q = 0; q < nq; ++q) {
+                const R *T = gtab ? S.tab_c + (size_t)q * (D + 1) * n : tab + (size_t)q * L.rs;
+                const R *e = ec + (size_t)q * L.es;
+                if constexpr (OP == OP_MASS) {
+                    out[0] = fma(gtab ? __ldg(T + j) : T[j], e[0], out[0]);
+                } else {
+                    R o = fma(gtab ? __ldg(T + j) : T[j], e[0], out[0]);
 #pragma unroll
-                for (int k = 0; k < D; ++k)
-                    o = fma(gtab ? __ldg(T + (k + 1) * n + j) : T[(k + 1) * n + j], e[1 + k], o);
-                out[0] = o;
+                    for (int k = 0; k < D; ++k)
+                        o = fma(gtab ? __ldg(T + (k + 1) * n + j) : T[(k + 1) * n + j], e[1 + k], o);
+                    out[0] = o;
+                }
+            }
+        } else {
+            constexpr int kAll = (1 << D) - 1;
+            // the structural-zero skip only where the branch is warp-uniform, and
+            // only in FP64 (the FP32 kernel is not bound by its FMA pipe)
+            const int dirs = (std::is_same<R, double>::value && node_major) ? node_dirs<D>(deg, j) : kAll;
+            const R *tc_ = S.tab_c;
+            if constexpr (D == 3) {
+                switch (dirs) {
+                case 1: quad_node<D, NC, 1>(out, tab, tc_, gtab, ec, L.rs, L.es, n, nq, j); break;
+                case 2: quad_node<D, NC, 2>(out, tab, tc_, gtab, ec, L.rs, L.es, n, nq, j); break;
+                case 3: quad_node<D, NC, 3>(out, tab, tc_, gtab, ec, L.rs, L.es, n, nq, j); break;
+                case 4: quad_node<D, NC, 4>(out, tab, tc_, gtab, ec, L.rs, L.es, n, nq, j); break;
+                case 5: quad_node<D, NC, 5>(out, tab, tc_, gtab, ec, L.rs, L.es, n, nq, j); break;
+                case 6: quad_node<D, NC, 6>(out, tab, tc_, gtab, ec, L.rs, L.es, n, nq, j); break;
+                default: quad_node<D, NC, kAll>(out, tab, tc_, gtab, ec, L.rs, L.es, n, nq, j); break;
+                }
             } else {
-#pragma unroll
-                for (int k = 0; k < D; ++k) {
-                    const R t = gtab ? __ldg(T + (k + 1) * n + j) : T[(k + 1) * n + j];
-#pragma unroll
-                    for (int m = 0; m < NC; ++m) out[m] = fma(t, e[m * D + k], out[m]);
+                switch (dirs) {
+                case 1: quad_node<D, NC, 1>(out, tab, tc_, gtab, ec, L.rs, L.es, n, nq, j); break;
+                case 2: quad_node<D, NC, 2>(out, tab, tc_, gtab, ec, L.rs, L.es, n, nq, j); break;
+                default: quad_node<D, NC, kAll>(out, tab, tc_, gtab, ec, L.rs, L.es, n, nq, j); break;
                 }
             }
         }
@@ -481,7 +575,7 @@ __device__ __forceinline__ void coop_batch(const ActionArgs &a, const CoopLayout
 }
 
 template <int OP, int D, typename R>
-__global__ void __launch_bounds__(kCoopBlock) k_action_coop(const ActionArgs a, const int n, const int C)
+__global__ void __launch_bounds__(kCoopWideBlock, 1) k_action_coop(const ActionArgs a, const int n, const int C)
 {
     constexpr int NC = OpTraits<OP, D>::NC;
     constexpr int FIELDS = OpTraits<OP, D>::kTwoFields ? 2 : 1;

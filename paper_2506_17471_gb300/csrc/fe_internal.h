@@ -45,6 +45,9 @@ struct ActionArgs {
     // each cell's outputs to cell_out[cell][j][comp] (float for FP32 contractions,
     // double otherwise) instead of adding them into y; skipped cells store zeros.
     void *cell_out;
+    // Hyperelastic laws: table of the logarithm (fe_log in fe_kernels.cuh) in
+    // global memory, or nullptr for CUDA's log and the IEEE division.
+    const double *log_tab;
 };
 
 // Launch function of one compiled kernel variant.
@@ -95,6 +98,10 @@ int register_variants_coop_forms(Variant *out, int cap);
 // laid out as fe_tabulate writes it: [(1+dim)][nq][n].
 bool tab_zeros_hold(int dim, int n, int nq, const double *tab);
 
+// The table of fe_log (fe_kernels.cuh), kLogTabDoubles doubles, from the C
+// library's long double logarithm.
+void fill_log_table(double *t);
+
 }  // namespace fe
 
 // The plan object behind the opaque C handle.
@@ -125,6 +132,7 @@ struct fe_plan {
     // fe_action_host_pipelined: two copy streams and, per buffer pair b, the
     // events h2d done, action done, d2h done (created on first use)
     // FE_FLAG_GATHER_SCATTER: per-cell outputs and the node -> (cell*n + j) incidences
+    double *d_log_tab = nullptr;   // Neo-Hookean plans: the logarithm's table (fe_log)
     void *d_cell_out = nullptr;
     int32_t *d_node_ptr = nullptr;   // [n_nodes + 1]
     int32_t *d_node_inc = nullptr;   // [incidences]

@@ -47,6 +47,78 @@ __device__ __forceinline__ void set_status(int32_t *status, int32_t code)
     if (status) atomicCAS(status, 0, code);
 }
 
+// Natural logarithm for the hyperelastic laws, by Tang's table-driven method
+// (P. T. P. Tang, "Table-driven implementation of the logarithm function in IEEE
+// floating-point arithmetic", ACM TOMS 16(4), 1990).  x = 2^e m with m in
+// [1/sqrt2, sqrt2); c = i/128 is the table point nearest to m (i in 91..181), so
+// log x = e ln2 + log c + log1p(u), u = (m - c)/c, |u| <= 2^-7.4.  m - c is exact
+// (Sterbenz), u is carried as u + ur with ur = (m - c - u c)/c from one fused
+// multiply-add, and log1p(u) is its Taylor polynomial to degree 8 (truncation
+// below 2^-58 relative).  The table (built on the host, see fill_log_table)
+// holds per i: c, 1/c rounded, and log c split into a head that is a multiple
+// of 2^-42 and a tail; its last two entries split ln 2 the same way, so
+// e ln2_head + logc_head is exact and only the final addition rounds.  Zero,
+// negative, subnormal, infinite and NaN arguments take CUDA's log.
+constexpr int kLogTabFirst = 90, kLogTabLast = 181;
+constexpr int kLogTabDoubles = 4 * (kLogTabLast - kLogTabFirst + 1) + 2;
+
+__device__ __forceinline__ double fe_log(double x, const double *__restrict__ t)
+{
+    const long long b = __double_as_longlong(x);
+    if (!(x >= 0x1p-1022) || b >= 0x7ff0000000000000LL) return log(x);
+    const long long mant = b & 0x000fffffffffffffLL;
+    int e = (int)(b >> 52) - 1023;
+    long long mb;
+    int i;
+    if (mant >= 0x6a09e667f3bcdLL) {   // m >= sqrt 2: take m / 2 and e + 1
+        ++e;
+        mb = mant | 0x3fe0000000000000LL;
+        i = (int)(((1LL << 52) + mant + (1LL << 45)) >> 46);
+    } else {
+        mb = mant | 0x3ff0000000000000LL;
+        i = (int)(((1LL << 52) + mant + (1LL << 44)) >> 45);
+    }
+    const double m = __longlong_as_double(mb);
+    const double *ti = t + 4 * (i - kLogTabFirst);
+    const double c = __ldg(ti), inv = __ldg(ti + 1);
+    const double f = m - c;
+    const double u = f * inv;
+    const double ur = fma(-u, c, f) * inv;
+    double q = -0.125;
+    q = fma(q, u, 1.0 / 7.0);
+    q = fma(q, u, -1.0 / 6.0);
+    q = fma(q, u, 0.2);
+    q = fma(q, u, -0.25);
+    q = fma(q, u, 1.0 / 3.0);
+    q = fma(q, u, -0.5);
+    const double ed = (double)e;
+    const double head = fma(ed, __ldg(t + kLogTabDoubles - 2), __ldg(ti + 2));   // exact
+    const double tail = fma(ed, __ldg(t + kLogTabDoubles - 1), __ldg(ti + 3)) + ur;
+    return head + (fma(u * u, q, u) + tail);
+}
+
+// 1/x for the hyperelastic laws: the hardware's approximate reciprocal
+// (rcp.approx.ftz.f64) refined by two Newton-Raphson steps r <- r + r (1 - x r),
+// each of which squares the relative error.  Zero, subnormal, infinite and NaN
+// arguments take the IEEE division.
+__device__ __forceinline__ double fe_rcp(double x)
+{
+    const double ax = fabs(x);
+    if (!(ax >= 0x1p-1022) || !(ax < 0x1p1020)) return 1.0 / x;
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    double e = fma(-x, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-x, r, 1.0);
+    return fma(r, e, r);
+}
+
+// log(x) through the table when the plan provides one, else CUDA's log.
+__device__ __forceinline__ double law_log(double x, const double *t)
+{
+    return t ? fe_log(x, t) : log(x);
+}
+
 // Bounded wait on phase `parity` of the shared-memory mbarrier at sbar: at most
 // `limit` polls with a short sleep between them.  Returns 1 if the phase
 // completed, 0 if the wait gave up (the caller records FE_ERR_TIMEOUT).
@@ -702,10 +774,10 @@ __device__ __forceinline__ void action_cell(const ActionArgs &a, const R *__rest
             for (int i = 0; i < D; ++i) F[i][i] += 1.0;
             const double Jd = det_cof<D>(F, C);  // F^{-T} = C / Jd
             nh_ok &= (Jd > 0.0);
-            const double lnJ = log(Jd);
+            const double lnJ = law_log(Jd, a.log_tab);
             // P = mu F + (lam lnJ - mu) F^{-T}, scaled by w_q |det J|
             const double smu = wdet * mu;
-            const double scf = wdet * fma(lam, lnJ, -mu) / Jd;
+            const double scf = wdet * fma(lam, lnJ, -mu) * (a.log_tab ? fe_rcp(Jd) : 1.0 / Jd);
 #pragma unroll
             for (int i = 0; i < D; ++i)
 #pragma unroll
@@ -727,8 +799,8 @@ __device__ __forceinline__ void action_cell(const ActionArgs &a, const R *__rest
             map_grad<D, double>(gh, Jinv, H);
             const double Jd = det_cof<D>(F, C);
             nh_ok &= (Jd > 0.0);
-            const double rJ = 1.0 / Jd;
-            const double lnJ = log(Jd);
+            const double rJ = a.log_tab ? fe_rcp(Jd) : 1.0 / Jd;
+            const double lnJ = law_log(Jd, a.log_tab);
             double tr = 0.0;  // tr(F^{-1} H) = F^{-T} : H
 #pragma unroll
             for (int i = 0; i < D; ++i)

@@ -506,7 +506,8 @@ template <int OP, int D, typename TE, int TERMS>
 __device__ __forceinline__ bool tc_pointwise_hyper_jacobian(const TcLayout &L, uint32_t tlane, unsigned char *hb,
                                                             const double *wd, int t, int h, int tpc, int ch, int nq, bool good,
                                                             int ku_lin, const float (&Jf)[D][D],
-                                                            const float (&Jh)[D][D], double mu, double lam)
+                                                            const float (&Jh)[D][D], double mu, double lam,
+                                                            const double *log_tab)
 {
     constexpr int NC = D, KDP = (D == 2) ? 2 : 4, PPB = 8 / KDP;
     // 2^ku_lin as a binary32 value (the u_lin gradient is O(h) in reference
@@ -561,8 +562,8 @@ __device__ __forceinline__ bool tc_pointwise_hyper_jacobian(const TcLayout &L, u
                 const double Jd = det_cof<D>(F, C);
                 ok &= !live || (Jd > 0.0);
                 const double Jd_safe = live && Jd > 0.0 ? Jd : 1.0;
-                const double rJ = 1.0 / Jd_safe;
-                const double lnJ = log(Jd_safe);
+                const double rJ = log_tab ? fe_rcp(Jd_safe) : 1.0 / Jd_safe;
+                const double lnJ = law_log(Jd_safe, log_tab);
                 double tr = 0.0;   // F^{-T} : H
 #pragma unroll
                 for (int i = 0; i < D; ++i)
@@ -977,7 +978,7 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
             // ---- pointwise: this thread's cell at the chunk's points, E' into the quadrature A operand
             if constexpr (kHyperJac) {
                 nh_ok &= tc_pointwise_hyper_jacobian<OP, D, TE, TERMS>(L, tlane, hb, wd, t, h, tpc, ch, a.nq, good, ku[1],
-                                                                        Jf, Jh, mu_c, lam_c);
+                                                                        Jf, Jh, mu_c, lam_c, a.log_tab);
             } else
             for (int blk = h; blk < L.N1p / 16; blk += tpc) {   // the cell's tpc threads split the columns
                 uint32_t r[NC][16];
