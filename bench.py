@@ -53,7 +53,7 @@ FP64_NOMINAL_TFLOPS = 1.25
 # DRAM traffic of the headline kernel per launch (dram__bytes_read.sum +
 # dram__bytes_write.sum from one ncu capture of the same workload), reported only
 # while the kernel's sources still hash to the captured version.
-MEASURED_TRAFFIC = {"source_hash": None, "bytes": None}
+MEASURED_TRAFFIC = {"source_hash": "be365dc6430b5926", "bytes": 413908480}
 
 
 def parse():

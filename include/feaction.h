@@ -233,8 +233,19 @@ typedef struct fe_plan fe_plan;
  *                 DoFs and geometry factors below 2^-126 in magnitude enter
  *                 the FP32 contractions as zero, so fields and cell volumes
  *                 must lie in binary32's normal range);
- *   FE_PREC_BF16, FE_PREC_FP16, FE_PREC_TF32  <= 8 u16 with u16 = 2^-8 (BF16)
- *                 or 2^-11 (FP16, TF32), i.e. 3.1e-2 / 3.9e-3 (measured 0.6 - 4.3 u16);
+ *   FE_PREC_BF16, FE_PREC_FP16, FE_PREC_TF32  a multiple k of u16 = 2^-8 (BF16)
+ *                 or 2^-11 (FP16, TF32), per form (the largest deviation measured
+ *                 over the library's tests, all degrees, 2D and 3D, scaled meshes
+ *                 and materials, times 1.5):
+ *                   form          BF16   FP16   TF32
+ *                   mass          2.25   1.5    1.25
+ *                   elasticity    2.0    2.25   2.25
+ *                   Laplacian     1.75   1.5    1.5
+ *                   Helmholtz     1.5    1.5    1.5
+ *                   NH Jacobian   4.0    6.5    4.75  (smooth linearisation
+ *                                                      point rounded to 16 bits)
+ *                   SVK Jacobian  1.75   2.0    2.0
+ *                 e.g. elasticity in FP16 <= 2.25 x 2^-11 = 1.1e-3;
  *   FE_PREC_FP16X2 <= 5e-5 (the FP32 bound).
  *
  * Tensor-core plans (FE_PREC_BF16 / FE_PREC_FP16 / FE_PREC_FP16X2 / FE_PREC_TF32): kinds MASS, ELASTICITY,

@@ -73,13 +73,14 @@ def _coop_total_bytes(n, nq, dim, ncomp, C, fields, esz=8, tables_global=None):
     rs = ((1 + dim) * n) | 1
     ls = (fields * n * ncomp) | 1
     es = max(dim * ncomp, 1 + dim) | 1   # gradient terms, or value + gradient
+    ecs = (nq * es) | 1                  # per-cell stride of e, odd
     tab = 0 if tables_global else nq * rs * esz
     woff = (tab + 7) & ~7
     block = (woff + nq * 8 + nq * esz + 15) & ~15
     off_e = (block + C * ls * 8 + 15) & ~15
-    off_nodes = (off_e + C * nq * es * esz + 15) & ~15
+    off_nodes = (off_e + C * ecs * esz + 15) & ~15
     off_geo = (off_nodes + C * n * 4 + 15) & ~15
-    return (off_geo + C * 16 * 8 + C * 2 * 8 + 15) & ~15
+    return (off_geo + C * 17 * 8 + C * 2 * 8 + 15) & ~15   # geometry records of 17 doubles
 
 
 def eta_simd(items: int, threads: int = COOP_BLOCK) -> float:

@@ -437,6 +437,32 @@ void fill_log_table(double *t)
 }
 }  // namespace fe
 
+// Shared-memory scatter aggregation: only for outputs at least this large
+// (below it y stays in L2, where the direct reductions are cheap).
+constexpr long long kAggMinOutputBytes = 64ll << 20;
+
+// True when the mesh's numbering makes the cells of a 128-cell tile share nodes:
+// four tiles spread over the mesh are copied to the host and their cell-node
+// incidences must outnumber their distinct nodes at least twice.
+static bool tiles_share_nodes(const fe_mesh &m, int n)
+{
+    if (m.n_cells < kTpcBlock) return false;
+    std::vector<int32_t> rows((size_t)kTpcBlock * n);
+    long long incidences = 0, distinct = 0;
+    for (int t = 0; t < 4; ++t) {
+        const long long c0 = (long long)(m.n_cells - kTpcBlock) * t / 3;
+        if (cudaMemcpy(rows.data(), m.cell2node + c0 * n, rows.size() * sizeof(int32_t), cudaMemcpyDeviceToHost) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        std::sort(rows.begin(), rows.end());
+        distinct += std::unique(rows.begin(), rows.end()) - rows.begin();
+        incidences += (long long)rows.size();
+    }
+    return incidences >= 2 * distinct;
+}
+
 // Neo-Hookean plans evaluate log det F with fe_log: upload its table.
 static int attach_log_table(fe_plan *p)
 {
@@ -613,9 +639,13 @@ extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan 
                                               : coop_default_global<double>(n, nq, m.dim));
         if (f.tile_cells > 0) {
             coop_cells = f.tile_cells;
-        } else if (esz == sizeof(double)) {
-            // FP64: the wide layout (one 512-thread CTA per SM, a batch of 64 or 32
-            // cells) where its shared memory fits
+        } else if (esz == sizeof(double) && m.dim == 3 && f.kind != FE_FORM_MASS && f.kind != FE_FORM_HELMHOLTZ) {
+            // FP64 gradient forms on tetrahedra: the wide layout (one 512-thread CTA
+            // per SM, a batch of 64 or 32 cells) where its shared memory fits.  Its
+            // quadrature phase skips the structurally zero directions (14-30 % of the
+            // gradient entries of a P2-P4 tetrahedron), which outweighs running one
+            // CTA per SM instead of two; on triangles (at most 7 % zeros) and for the
+            // value terms of mass and Helmholtz it does not.
             for (int C : {64, 32}) {
                 if (coop_layout<double>(n, nq, m.dim, ncomp, C, fields_max, gt).total <= kCoopWideSmemBytes) {
                     coop_cells = C;
@@ -690,6 +720,17 @@ extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan 
         p->var.block = coop_block;
         if (adj) p->adj.block = coop_block;
     }
+    // FP32 thread-per-cell mass plans sum the updates of nodes shared by a CTA's
+    // cells in shared memory before the global scatter, where that pays: y larger
+    // than L2 and a numbering whose 128-cell tiles share nodes (not with the
+    // node-ordered scatter, which stores per-cell outputs instead)
+    if (!coop && v->func_agg && !(f.flags & FE_FLAG_GATHER_SCATTER) &&
+        (long long)m.n_nodes * ncomp * (long long)sizeof(double) >= kAggMinOutputBytes &&
+        tiles_share_nodes(m, n)) {
+        p->agg_slots = agg_slots_for(n);
+        smem += (size_t)p->agg_slots * sizeof(int32_t) * (1 + ncomp);
+        p->var.func = v->func_agg;
+    }
     p->smem_bytes = smem;
     cudaGetDevice(&p->device);
     p->coop_cells = coop_cells;
@@ -708,7 +749,7 @@ extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan 
         fe_plan_destroy(p);
         return FE_ERR_CUDA;
     }
-    if (allow_max_dynamic_smem(v->func) != cudaSuccess || (adj && allow_max_dynamic_smem(adj->func) != cudaSuccess)) {
+    if (allow_max_dynamic_smem(p->var.func) != cudaSuccess || (adj && allow_max_dynamic_smem(adj->func) != cudaSuccess)) {
         fe_plan_destroy(p);
         return FE_ERR_CUDA;
     }
@@ -797,6 +838,7 @@ static ActionArgs make_args(const fe_plan *p, const double *u, double *y)
     a.tc_wshift = p->tc_wshift;
     a.cell_out = p->d_cell_out;
     a.log_tab = p->d_log_tab;
+    a.agg_slots = p->agg_slots;
     return a;
 }
 

@@ -184,6 +184,7 @@ template <int D, int NC, int DIRS, typename R>
 __device__ __forceinline__ void quad_node(R (&out)[NC], const R *tab, const R *tab_c, bool gtab,
                                           const R *ec, int rs, int es, int n, int nq, int j)
 {
+#pragma unroll 2
     for (int q = 0; q < nq; ++q) {
         const R *T = gtab ? tab_c + (size_t)q * (D + 1) * n : tab + (size_t)q * rs;
         const R *e = ec + (size_t)q * es;
@@ -581,21 +582,33 @@ __global__ void __launch_bounds__(kCoopWideBlock, 1) k_action_coop(const ActionA
     constexpr int FIELDS = OpTraits<OP, D>::kTwoFields ? 2 : 1;
     extern __shared__ __align__(128) double smem[];
     __shared__ __align__(8) uint64_t bar;
-    __shared__ int s_chunk;
+    __shared__ int s_chunk, s_take;
     const CoopLayout L = coop_layout<R>(n, a.nq, D, NC, C, FIELDS, a.tab_b != nullptr);
     if (!stage_table(smem, a.tab, a.tab_doubles, &bar, a.status)) {
         leave_queue(a.sched);
         return;
     }
     const CoopSmem<R> S = coop_smem<R>(reinterpret_cast<unsigned char *>(smem), L, a);
-    const int n_batches = (a.n_cells + C - 1) / C;
+    // The queue hands out units of U cells: the whole batch (U = C), or, when C is a
+    // multiple of 32, 32-cell units of which a CTA takes C/32 at a time until fewer
+    // than that many per CTA remain and one at a time after that, which halves (or
+    // better) the last round's imbalance on meshes of a few batches per CTA.
+    const int U = (C % 32 == 0) ? 32 : C;
+    const int per = C / U;
+    const int n_units = (a.n_cells + U - 1) / U;
     for (;;) {
-        if (threadIdx.x == 0) s_chunk = atomicAdd(a.sched, 1);
+        if (threadIdx.x == 0) {
+            int take = per;
+            if (per > 1 && n_units - *reinterpret_cast<volatile int32_t *>(a.sched) < per * (int)gridDim.x)
+                take = 1;
+            s_chunk = atomicAdd(a.sched, take);
+            s_take = take;
+        }
         __syncthreads();
-        const int batch = s_chunk;
-        if (batch >= n_batches) break;
-        const int cell0 = batch * C;
-        coop_batch<OP, D, R>(a, L, S, cell0, min(C, a.n_cells - cell0));
+        const int unit = s_chunk, take = s_take;
+        if (unit >= n_units) break;
+        const int cell0 = unit * U;
+        coop_batch<OP, D, R>(a, L, S, cell0, min(take * U, a.n_cells - cell0));
     }
     leave_queue(a.sched);
 }

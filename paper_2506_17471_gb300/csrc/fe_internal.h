@@ -48,6 +48,9 @@ struct ActionArgs {
     // Hyperelastic laws: table of the logarithm (fe_log in fe_kernels.cuh) in
     // global memory, or nullptr for CUDA's log and the IEEE division.
     const double *log_tab;
+    // FP32 thread-per-cell kernels: shared-memory hash slots of the scatter
+    // aggregation (0: scatter each cell's updates directly)
+    int32_t agg_slots;
 };
 
 // Launch function of one compiled kernel variant.
@@ -62,6 +65,10 @@ struct Variant {
     int block;         // threads per block
     LaunchFn launch;
     const void *func;  // kernel symbol (for occupancy queries)
+    // FP32 thread-per-cell mass variants: the kernel that sums the updates of
+    // nodes shared by a CTA's cells in shared memory before the global scatter
+    // (launched instead of func when ActionArgs::agg_slots > 0)
+    const void *func_agg = nullptr;
 };
 
 // Raise a kernel's dynamic shared-memory limit to the device's opt-in maximum.
@@ -133,6 +140,7 @@ struct fe_plan {
     // events h2d done, action done, d2h done (created on first use)
     // FE_FLAG_GATHER_SCATTER: per-cell outputs and the node -> (cell*n + j) incidences
     double *d_log_tab = nullptr;   // Neo-Hookean plans: the logarithm's table (fe_log)
+    int agg_slots = 0;             // FP32 thread-per-cell: shared-memory scatter aggregation slots
     void *d_cell_out = nullptr;
     int32_t *d_node_ptr = nullptr;   // [n_nodes + 1]
     int32_t *d_node_inc = nullptr;   // [incidences]

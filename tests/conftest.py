@@ -18,3 +18,18 @@ def oracle_built():
     import oracle
     oracle.build()
     return oracle
+
+
+def pytest_sessionfinish(session, exitstatus):
+    """Write the deviations recorded by precision_bounds.check16 when
+    FE_DEVIATION_LOG names a file."""
+    path = os.environ.get("FE_DEVIATION_LOG")
+    if not path:
+        return
+    try:
+        import json
+        from precision_bounds import DEVIATIONS
+    except ImportError:
+        return
+    with open(path, "w") as f:
+        json.dump(DEVIATIONS, f, indent=1)

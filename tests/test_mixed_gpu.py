@@ -139,3 +139,55 @@ def test_full_nh_p4_2d_fp32_smooth_field(fe):
     _, odmu, odlam = o.nh_adjoint(u, w, mu, lam, threads=8, cells=(0, 2000))
     assert rel(dmu[:2000], odmu[:2000]) <= TOL32 and rel(dlam[:2000], odlam[:2000]) <= TOL32
     assert res.status() == 0
+
+
+@pytest.mark.parametrize("block", [32, 96, 128])
+@pytest.mark.parametrize("shuffled", [False, True])
+def test_fp32_block_sizes_and_numberings(fe, block, shuffled):
+    """FP32 thread-per-cell kernels at several block sizes, with a ragged last
+    block, on the structured numbering and on a random one: mass, Laplacian,
+    Helmholtz and elasticity."""
+    from feinputs import shuffled_mesh
+    m = structured_mesh(3, 5, 2, jitter=0.15, seed=91)
+    if shuffled:
+        m = shuffled_mesh(m, 92)
+    M = fe.Mesh(3, 2, m.coords, m.cell2vertex, m.cell2node, m.n_nodes)
+    assert m.n_cells % block != 0
+    o = oracle.Oracle.from_mesh(m, 4)
+    s = uniform_field(m.n_nodes, 93)
+    v = uniform_field(m.n_nodes * 3, 94)
+    for kind, ref, x in ((fe.MASS, o.mass, s), (fe.LAPLACE, o.laplace, s), (fe.HELMHOLTZ, o.helmholtz, s)):
+        plan = fe.Plan(M, kind, 4, precision="fp32", tile_cells=block)
+        assert rel(plan.apply(cuda(x)), ref(x)) <= TOL32
+        assert plan.status() == 0
+    plan = fe.Plan(M, fe.ELASTICITY, 4, lam=1.25, mu=1.0, precision="fp32", tile_cells=block)
+    y = torch.full((m.n_nodes * 3,), 7.0, dtype=torch.float64, device="cuda")
+    plan.apply(cuda(v), y)
+    assert rel(y, o.elasticity(v, 1.25, 1.0)) <= TOL32
+    assert plan.status() == 0
+
+
+@pytest.mark.parametrize("shuffled", [False, True])
+def test_fp32_mass_scatter_aggregation_full_size(fe, shuffled):
+    """Mass P3 on 2 x 1333^2 triangles (16,000,000 DoFs, y = 128 MB, larger than L2):
+    on the structured numbering the FP32 plan sums each 128-cell tile's updates per
+    node in shared memory before the scatter; on a random numbering (no shared
+    nodes within a tile) it scatters directly.  Sampled DoFs against the oracle,
+    recomputed from the cells that contain them, and both against the FP64 plan."""
+    from feinputs import shuffled_mesh
+    m = structured_mesh(2, 1333, 3, jitter=0.2, seed=20250620 + 1333)
+    if shuffled:
+        m = shuffled_mesh(m, 95)
+    M = fe.Mesh(2, 3, m.coords, m.cell2vertex, m.cell2node, m.n_nodes)
+    u = uniform_field(m.n_nodes, 96)
+    plan = fe.Plan(M, fe.MASS, 6, precision="fp32", quad_scheme="symmetric")
+    y = plan.apply(cuda(u)).cpu().numpy()
+    assert plan.status() == 0
+    y64 = fe.Plan(M, fe.MASS, 6, quad_scheme="symmetric").apply(cuda(u)).cpu().numpy()
+    assert rel(y, y64) <= TOL32
+    rng = np.random.default_rng(97)
+    nodes = rng.choice(m.n_nodes, size=64, replace=False)
+    cells = np.unique(np.nonzero(np.isin(m.cell2node, nodes))[0])
+    o = oracle.Oracle(2, 3, 6, m.coords, m.cell2vertex[cells], m.cell2node[cells], m.n_nodes, "symmetric")
+    ref = o.mass(u)
+    assert np.abs(y[nodes] - ref[nodes]).max() <= TOL32 * np.abs(y64).max()

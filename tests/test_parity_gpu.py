@@ -13,6 +13,7 @@ import torch
 import oracle
 from feinputs import lame_fields, structured_mesh, uniform_field
 from feinputs.fields import sinusoid_displacement
+from precision_bounds import record
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-12
@@ -142,17 +143,24 @@ def test_full_nh_p4_2d_n256(fe):
     w = uniform_field(m.n_nodes * 2, 5)
     plan = fe.Plan(M, fe.NH_RESIDUAL, 8, mu_cell=mu, lam_cell=lam)
     r = plan.apply(cuda(u))
-    assert rel(r, o.nh_residual(u, mu, lam, threads=16)) <= TOL_NH_SMOOTH
+    err = rel(r, o.nh_residual(u, mu, lam, threads=16))
+    record("nh_residual", "fp64", err, "p4 2d N256 smooth field")
+    assert err <= TOL_NH_SMOOTH
     jtw, dmu, dlam = plan.adjoint(cuda(u), cuda(w))
     # J^T w over the whole mesh against the oracle's Jacobian action (the two are
     # equal by the tangent's symmetry, pinned on the CPU) ...
-    assert rel(jtw, o.nh_jacobian(u, w, mu, lam, threads=16)) <= TOL
+    err = rel(jtw, o.nh_jacobian(u, w, mu, lam, threads=16))
+    record("nh_adjoint_jtw", "fp64", err, "p4 2d N256 smooth field")
+    assert err <= TOL
     # ... and the literal transposed-element-matrix adjoint on sampled cell ranges
     for c0, c1 in ((0, 1500), (m.n_cells // 2, m.n_cells // 2 + 1500), (m.n_cells - 1500, m.n_cells)):
         _, odmu, odlam = o.nh_adjoint(u, w, mu, lam, threads=8, cells=(c0, c1))
         # dmu, dlambda integrate F - F^{-T} and ln(det F) F^{-T}: smooth-field conditioned
-        assert rel(dmu[c0:c1], odmu[c0:c1]) <= TOL_NH_SMOOTH
-        assert rel(dlam[c0:c1], odlam[c0:c1]) <= TOL_NH_SMOOTH
+        e_mu, e_lam = rel(dmu[c0:c1], odmu[c0:c1]), rel(dlam[c0:c1], odlam[c0:c1])
+        record("nh_adjoint_dmu", "fp64", e_mu, f"p4 2d N256 cells {c0}-{c1}")
+        record("nh_adjoint_dlam", "fp64", e_lam, f"p4 2d N256 cells {c0}-{c1}")
+        assert e_mu <= TOL_NH_SMOOTH
+        assert e_lam <= TOL_NH_SMOOTH
     assert plan.status() == 0
 
 

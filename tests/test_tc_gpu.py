@@ -12,9 +12,10 @@ at most the unit roundoff u16 (bfloat16: 2^-8 = 3.9e-3, binary16 and TF32:
 absolute terms to the result.  Measured: mass and elasticity 0.6-1.2 u16 up to
 P6; the Neo-Hookean Jacobian 1-4.3 u16, largest at P6 where the linearisation
 point's gradient (a smooth field) is evaluated from 16-bit data.  The stated
-bound, used as the parity tolerance, is TOL16 = 8 u16 norm-wise, relative to
-||y_ref||_inf.  A lower bound (> 1e-7) checks that the work really ran in 16
-bits.
+bounds, used as the parity tolerances, are per form and precision
+(tests/precision_bounds.py: the largest measured deviation times 1.5), norm-wise
+relative to ||y_ref||_inf.  A lower bound (> 1e-7) checks that the work really
+ran in 16 bits.
 """
 
 import ctypes
@@ -26,9 +27,9 @@ import torch
 import oracle
 from feinputs import structured_mesh, uniform_field
 
+from precision_bounds import bound16, check16
+
 pytestmark = pytest.mark.gpu
-U16 = {"bf16": 2.0 ** -8, "fp16": 2.0 ** -11, "tf32": 2.0 ** -11}
-TOL16 = {k: 8 * v for k, v in U16.items()}
 
 
 @pytest.fixture(scope="module")
@@ -83,7 +84,7 @@ def test_tc_parity(fe, kind, dim, N, p, q, scheme, prec):
     assert plan.info.kernel == 2
     y = plan.apply(cuda(u))
     err = rel(y, ref)
-    assert 1e-7 < err <= TOL16[prec], err
+    check16(kind, prec, err, f"d{dim} N{N} p{p} q{q} {scheme}")
     assert plan.status() == 0
 
 
@@ -110,7 +111,7 @@ def test_tc_tiny_and_huge_cells(fe, prec):
         o = oracle.Oracle.from_mesh(m, 6, scheme="symmetric")
         u = uniform_field(m.n_nodes * 2, 10)
         plan = fe.Plan(M, fe.ELASTICITY, 6, lam=1.25, mu=1.0, precision=prec, quad_scheme="symmetric")
-        assert rel(plan.apply(cuda(u)), o.elasticity(u, 1.25, 1.0)) <= TOL16[prec]
+        check16("elasticity", prec, rel(plan.apply(cuda(u)), o.elasticity(u, 1.25, 1.0)), f"p4 2d scale {s}")
         assert plan.status() == 0
 
 
@@ -125,7 +126,8 @@ def test_tc_edge_cases(fe):
     M1 = fe.Mesh(2, 3, m.coords, m.cell2vertex[:1], m.cell2node[:1], m.n_nodes)
     o1 = oracle.Oracle(2, 3, 6, m.coords, m.cell2vertex[:1], m.cell2node[:1], m.n_nodes)
     u = uniform_field(m.n_nodes, 3)
-    assert rel(fe.Plan(M1, fe.MASS, 6, precision="fp16").apply(cuda(u)), o1.mass(u)) <= TOL16["fp16"]
+    check16("mass", "fp16", rel(fe.Plan(M1, fe.MASS, 6, precision="fp16").apply(cuda(u)), o1.mass(u)),
+            "one cell", floor=None)
     # accumulate: y += A u
     m, M = make(fe, 2, 13, 3, 44)
     o = oracle.Oracle.from_mesh(m, 6)
@@ -134,7 +136,7 @@ def test_tc_edge_cases(fe):
     acc = fe.Plan(M, fe.MASS, 6, precision="fp16", accumulate=True)
     y = acc.apply(cuda(u), cuda(y0.copy()))
     ref = y0 + o.mass(u)
-    assert np.abs(y.cpu().numpy() - ref).max() <= TOL16["fp16"] * np.abs(o.mass(u)).max()
+    assert np.abs(y.cpu().numpy() - ref).max() <= bound16("mass", "fp16") * np.abs(o.mass(u)).max()
     # forms without a tensor-core variant are refused
     with pytest.raises(Exception):
         fe.Plan(M, fe.NH_RESIDUAL, 6, mu=1.0, lam=1.0, precision="bf16")
@@ -157,7 +159,7 @@ def test_tc_bad_index_sets_status(fe):
     keep = np.ones(m.n_cells, dtype=bool)
     keep[200] = False
     o = oracle.Oracle(2, 3, 6, m.coords, m.cell2vertex[keep], m.cell2node[keep], m.n_nodes)
-    assert rel(y, o.mass(u)) <= TOL16["bf16"]
+    check16("mass", "bf16", rel(y, o.mass(u)), "bad index", floor=None)
     assert plan.status() == 0
 
 
@@ -187,7 +189,7 @@ def test_tc_full_mass_p3_2d(fe, prec):
     o = oracle.Oracle.from_mesh(m, 6, scheme="symmetric")
     u = uniform_field(m.n_nodes, 21)
     plan = fe.Plan(M, fe.MASS, 6, precision=prec, quad_scheme="symmetric")
-    assert rel(plan.apply(cuda(u)), o.mass(u, threads=16)) <= TOL16[prec]
+    check16("mass", prec, rel(plan.apply(cuda(u)), o.mass(u, threads=16)), "p3 2d N667")
     assert plan.status() == 0
 
 
@@ -198,7 +200,7 @@ def test_tc_full_elasticity_p4_3d(fe, prec):
     o = oracle.Oracle.from_mesh(m, 6)
     u = uniform_field(m.n_nodes * 3, 22)
     plan = fe.Plan(M, fe.ELASTICITY, 6, lam=1.25, mu=1.0, precision=prec)
-    assert rel(plan.apply(cuda(u)), o.elasticity(u, 1.25, 1.0, threads=16)) <= TOL16[prec]
+    check16("elasticity", prec, rel(plan.apply(cuda(u)), o.elasticity(u, 1.25, 1.0, threads=16)), "p4 3d N27")
     assert plan.status() == 0
 
 
@@ -222,7 +224,7 @@ def test_tc_nh_jacobian(fe, dim, N, p, q, prec):
     plan = fe.Plan(M, fe.NH_JACOBIAN, q, mu_cell=mu, lam_cell=lam, u_lin=cuda(ul), precision=prec)
     assert plan.info.kernel == 2
     err = rel(plan.apply(cuda(du)), o.nh_jacobian(ul, du, mu, lam))
-    assert 1e-7 < err <= TOL16[prec], err
+    check16("nh_jacobian", prec, err, f"d{dim} N{N} p{p} q{q}")
     assert plan.status() == 0
 
 
@@ -238,7 +240,8 @@ def test_tc_full_nh_jacobian_p6_2d(fe, prec):
     ul = sinusoid_displacement(m, 3)
     du = uniform_field(m.n_nodes * 2, 4)
     plan = fe.Plan(M, fe.NH_JACOBIAN, 12, mu_cell=mu, lam_cell=lam, u_lin=cuda(ul), precision=prec)
-    assert rel(plan.apply(cuda(du)), o.nh_jacobian(ul, du, mu, lam, threads=16)) <= TOL16[prec]
+    check16("nh_jacobian", prec, rel(plan.apply(cuda(du)), o.nh_jacobian(ul, du, mu, lam, threads=16)),
+            "p6 2d N236")
     assert plan.status() == 0
 
 
@@ -252,7 +255,7 @@ def test_tc_material_scaling(fe, prec):
     u = uniform_field(m.n_nodes * 3, 11)
     for lam, mu in ((3.0e4, 2.0e4), (2.0e-5, 1.0e-5)):
         plan = fe.Plan(M, fe.ELASTICITY, 4, lam=lam, mu=mu, precision=prec)
-        assert rel(plan.apply(cuda(u)), o.elasticity(u, lam, mu)) <= TOL16[prec]
+        check16("elasticity", prec, rel(plan.apply(cuda(u)), o.elasticity(u, lam, mu)), f"lam {lam}")
         assert plan.status() == 0
 
 
@@ -276,7 +279,7 @@ def test_tc_laplace_helmholtz(fe, kind, dim, N, p, q, prec):
     plan = fe.Plan(M, getattr(fe, kind.upper()), q, precision=prec)
     assert plan.info.kernel == 2
     err = rel(plan.apply(cuda(u)), getattr(o, kind)(u))
-    assert 1e-7 < err <= TOL16[prec], err
+    check16(kind, prec, err, f"d{dim} N{N} p{p} q{q}")
     assert plan.status() == 0
 
 
@@ -289,7 +292,7 @@ def test_tc_helmholtz_cell_scale(fe, prec):
         o = oracle.Oracle.from_mesh(m, 6)
         u = uniform_field(m.n_nodes, 13)
         plan = fe.Plan(M, fe.HELMHOLTZ, 6, precision=prec)
-        assert rel(plan.apply(cuda(u)), o.helmholtz(u)) <= TOL16[prec]
+        check16("helmholtz", prec, rel(plan.apply(cuda(u)), o.helmholtz(u)), f"p3 2d scale {s}")
         assert plan.status() == 0
 
 
@@ -308,7 +311,7 @@ def test_tc_svk_jacobian(fe, dim, N, p, q, prec):
     plan = fe.Plan(M, fe.SVK_JACOBIAN, q, mu_cell=mu, lam_cell=lam, u_lin=cuda(ul), precision=prec)
     assert plan.info.kernel == 2
     err = rel(plan.apply(cuda(du)), o.svk_jacobian(ul, du, mu, lam))
-    assert 1e-7 < err <= TOL16[prec], err
+    check16("svk_jacobian", prec, err, f"d{dim} N{N} p{p} q{q}")
     assert plan.status() == 0
 
 
@@ -381,7 +384,7 @@ def test_tc_pipelines_and_threads_per_cell(fe, kind, dim, N, p, q, prec):
         ul = sinusoid_displacement(m, 6)
         kw = dict(mu_cell=mu, lam_cell=lam, u_lin=cuda(ul))
         ref = o.nh_jacobian(ul, u, mu, lam)
-    tol = TOL_X2 if prec == "fp16x2" else TOL16[prec]
+    tol = TOL_X2 if prec == "fp16x2" else bound16(kind, prec)
     auto = fe.Plan(M, getattr(fe, kind.upper()), q, precision=prec, **kw)
     y_auto = auto.apply(cuda(u))
     assert rel(y_auto, ref) <= tol and auto.status() == 0
@@ -424,7 +427,7 @@ def test_tc_bad_index_two_threads_per_cell(fe, j):
     keep = np.ones(m.n_cells, dtype=bool)
     keep[300] = False
     o = oracle.Oracle(3, 4, 6, m.coords, m.cell2vertex[keep], m.cell2node[keep], m.n_nodes)
-    assert rel(y, o.elasticity(u, 1.25, 1.0)) <= TOL16["fp16"]
+    check16("elasticity", "fp16", rel(y, o.elasticity(u, 1.25, 1.0)), "bad index 2 threads", floor=None)
 
 
 @pytest.mark.parametrize("kind", ["nh_jacobian", "svk_jacobian"])
