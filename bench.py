@@ -729,6 +729,21 @@ def time_batched(fe, torch):
             ts.append(e0.elapsed_time(e1) * 1e-3)
         return statistics.mean(ts)
 
+    # each problem's action timed alone (events around one launch pair, median of
+    # 5): their sum is the device work the per-mesh launches carry, so the
+    # per-mesh graph's time minus it is what one persistent launch can remove
+    per_problem = []
+    for plan, u, y in runs:
+        plan.apply(u, y)
+        ts = []
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            plan.apply(u, y)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1) * 1e-3)
+        per_problem.append(statistics.median(ts))
     t_eager = ev_time(per_mesh)
     torch.cuda.synchronize()
     g_mesh = torch.cuda.CUDAGraph()
@@ -746,6 +761,7 @@ def time_batched(fe, torch):
     return {"problems": len(specs), "cells": sum(s_["n_cells"] for s_ in specs), "dofs": dofs,
             "per_mesh_eager_ms": t_eager * 1e3, "per_mesh_graph_ms": t_graph_mesh * 1e3,
             "batched_graph_ms": t_batch * 1e3, "batched_dofs_per_s": dofs / t_batch,
+            "sum_of_single_actions_ms": sum(per_problem) * 1e3,
             "batched_gflops": flops / t_batch / 1e9,
             "speedup_vs_per_mesh_eager": t_eager / t_batch,
             "speedup_vs_per_mesh_graph": t_graph_mesh / t_batch,

@@ -595,12 +595,14 @@ __device__ __forceinline__ void store_zero_cell(const ActionArgs &a, int cell)
 // locality (a 128-cell run of the structured P3 triangle mesh touches ~400
 // distinct nodes through 1,280 cell-node incidences), so their updates are
 // first summed per node in an open-addressing hash table in shared memory and
-// then added to y with one global reduction per distinct node.  Where y is
-// larger than L2 the scatter's reductions reach DRAM and dominate this
-// gather/scatter-bound kernel; cutting them by the sharing factor pays (mass P3
-// on 3.6M triangles: 0.48 -> 0.29 ms).  Measured elsewhere (vector forms, y in
-// L2, random numberings) the table's atomics cost more than they save, so plans
-// enable it only for mass with a large y and a numbering that shares nodes.
+// then added to y with one global reduction per distinct node.  For large y
+// the scatter's reductions dominate this gather/scatter-bound kernel, and
+// cutting them by the sharing factor pays (mass P3 on 3.6M triangles: 0.48 ->
+// 0.29 ms, y larger than L2; 0.103 -> 0.092 ms on 0.9M triangles).  Measured on
+// the vector forms (elasticity P1/P2 tetrahedra, structured or random
+// numbering), on Helmholtz and the Laplacian with y in L2, the table's atomics
+// cost more than they save, so plans enable it only for mass, with y of at
+// least 16 MB and a numbering whose tiles share nodes.
 // agg_slots_for(N) >= 2 x 128 N slots: a tile has at most 128 N distinct nodes,
 // so the table is at most half full and probe chains stay short.
 __host__ __device__ constexpr int agg_slots_for(int n_loc)

@@ -469,3 +469,20 @@ def test_tc_node_limit(fe):
     with pytest.raises(fe.FeError) as e:
         fe.Plan(M2, fe.MASS, 2, precision="fp16")
     assert e.value.code == 2
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_tc_benchmark_workload_elasticity_p4_3d_n27(fe, prec):
+    """The hp-sweep workload as the benchmark builds it (24-point fully symmetric
+    degree-6 rule) on the tensor cores: every output against the oracle."""
+    from feinputs.workloads import ELASTICITY_P4_3D_N27 as wl
+    m = wl.mesh()
+    M = fe.Mesh(3, wl.degree, m.coords, m.cell2vertex, m.cell2node, m.n_nodes)
+    u = wl.field(m)
+    o = oracle.Oracle.from_mesh(m, wl.quad_degree, scheme=wl.quad_scheme)
+    plan = fe.Plan(M, fe.ELASTICITY, wl.quad_degree, lam=wl.lam, mu=wl.mu, precision=prec,
+                   quad_scheme=wl.quad_scheme)
+    assert plan.info.kernel == 2 and plan.info.nq == 24
+    check16("elasticity", prec, rel(plan.apply(cuda(u)), o.elasticity(u, wl.lam, wl.mu, threads=16)),
+            "p4 3d N27 24-point rule")
+    assert plan.status() == 0
