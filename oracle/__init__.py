@@ -8,8 +8,9 @@ code, headers, tables or helpers.
 * ``quadrature.py``: conical-product Gauss-Jacobi rules (Golub-Welsch, numpy).
 * ``basis.py``: Silvester-product Lagrange basis and tabulation (numpy).
 * ``symmetric.py``: fully symmetric rules from the moment equations (scipy).
-* ``oracle.c``: literal sequential Algorithm 2 loops for every form, built with
-  gcc into ``oracle/_build/liboracle.so`` by :func:`build`.
+* ``oracle.c``: the plain cell-wise quadrature sum of every form, one cell and one
+  quadrature point at a time, built with gcc into ``oracle/_build/liboracle.so``
+  by :func:`build`.
 
 Parity status: every function here is pinned by the ``-m "not gpu"`` tests in
 ``tests/test_oracle_*.py`` (exactness, closed forms, invariants, exact rational

@@ -5,17 +5,18 @@
  * baseline may load or run this code; the product path never does.  It shares no
  * code, header or table with the CUDA library.
  *
- * Every action routine is a literal, sequential transcription of the paper's
- * Algorithm 2 (the generic action kernel of Eq. "generalized_bilinear_form"):
- * per cell, gather vertex coordinates and DoFs; form the affine Jacobian and its
- * determinant (Sec. "Towards Discretization": affine geometry, computed per
- * cell); loop over quadrature points evaluating the trial-function values or
- * reference derivatives from the tabulation; apply the pointwise form and the
- * geometry mapping; accumulate the quadrature contraction against the test
- * tabulation; scatter-add into the global output.  The forms are those of the
- * paper's Appendix A (Mass, Laplacian, Helmholtz, Elasticity, and the
- * St. Venant-Kirchhoff hyperelastic law with its linearisation), and a
- * compressible Neo-Hookean law beside it:
+ * Every action routine is the plain cell-wise sum of its form: the action of
+ * the bilinear (or residual) form of Eq. "generalized_bilinear_form" evaluated
+ * with the quadrature sum of Eq. "poisson_action_w_quadrature", y_i = sum over
+ * cells T, quadrature points q and test functions v_i of T of w_q |det J_T|
+ * times the pointwise form at x_q.  Each cell is taken on its own, in order:
+ * its vertex coordinates and DoFs, its affine Jacobian and determinant (affine
+ * geometry is one Jacobian per cell), then per quadrature point the trial
+ * values or physical gradients, the pointwise integrand, and its contribution
+ * to every local test function, added straight into the global output.  The
+ * forms are those of the paper's Appendix A (Mass, Laplacian, Helmholtz,
+ * Elasticity, and the St. Venant-Kirchhoff hyperelastic law with its
+ * linearisation), and a compressible Neo-Hookean law beside it:
  *     Psi(F) = mu/2 (tr F^T F - d) - mu ln J + lambda/2 (ln J)^2,  J = det F,
  *     P      = dPsi/dF = mu (F - F^{-T}) + lambda ln J F^{-T}.
  *
@@ -42,7 +43,7 @@ static inline const double *T(const double *tab, int nq, int nloc, int k, int q)
     return tab + ((long)k * nq + q) * nloc;
 }
 
-/* gather the cell's d+1 vertex coordinates (Algorithm 2, gather of coords) */
+/* the cell's d+1 vertex coordinates (through the cell-to-vertex map) */
 static void gather_coords(int dim, long c, const int32_t *c2v, const double *coords,
                           double X[ORC_MAXD + 1][ORC_MAXD])
 {
@@ -51,7 +52,7 @@ static void gather_coords(int dim, long c, const int32_t *c2v, const double *coo
             X[m][i] = coords[(long)c2v[c * (dim + 1) + m] * dim + i];
 }
 
-/* affine geometry: J, det J, J^{-1} (Algorithm 2, Jac/Det).  Returns 0 on a
+/* affine geometry: J, det J, J^{-1} (one Jacobian per affine cell).  Returns 0 on a
  * singular or non-finite Jacobian. */
 static int geometry(int dim, double X[ORC_MAXD + 1][ORC_MAXD], double J[ORC_MAXD][ORC_MAXD],
                     double *detJ, double Jinv[ORC_MAXD][ORC_MAXD])
