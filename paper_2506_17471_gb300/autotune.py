@@ -80,7 +80,8 @@ def _coop_total_bytes(n, nq, dim, ncomp, C, fields, esz=8, tables_global=None):
     off_e = (block + C * ls * 8 + 15) & ~15
     off_nodes = (off_e + C * ecs * esz + 15) & ~15
     off_geo = (off_nodes + C * n * 4 + 15) & ~15
-    return (off_geo + C * 17 * 8 + C * 2 * 8 + 15) & ~15   # geometry records of 17 doubles
+    # geometry records of 17 doubles, adjoint accumulators, then the node order (n ints)
+    return (off_geo + C * 17 * 8 + C * 2 * 8 + n * 4 + 15) & ~15
 
 
 def eta_simd(items: int, threads: int = COOP_BLOCK) -> float:

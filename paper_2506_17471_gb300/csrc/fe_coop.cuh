@@ -51,7 +51,7 @@ struct CoopLayout {
     int ecs;       // per-cell stride of e (elements), odd: threads of a warp that read
                    // the same (q, k) entry of 32 consecutive cells hit distinct banks
     size_t tab_bytes, wts_off, wtsr_off, table_block_bytes;   // the staged table block
-    size_t off_l, off_e, off_nodes, off_geo, off_acc, total;
+    size_t off_l, off_e, off_nodes, off_geo, off_acc, off_order, total;
 };
 
 // Default table residency of the cells-per-CTA kernel: shared memory unless the
@@ -87,8 +87,9 @@ __host__ __device__ inline CoopLayout coop_layout(int n, int nq, int D, int NC, 
     L.off_nodes = (L.off_e + (size_t)C * L.ecs * sizeof(R) + 15) & ~(size_t)15;
     L.off_geo = (L.off_nodes + (size_t)C * n * sizeof(int) + 15) & ~(size_t)15;
     L.off_acc = L.off_geo + (size_t)C * kCoopGeoStride * sizeof(double);
-    // adjoint accumulators dmu, dlam per cell
-    L.total = (L.off_acc + (size_t)C * 2 * sizeof(double) + 15) & ~(size_t)15;
+    // adjoint accumulators dmu, dlam per cell, then the quadrature phase's node order
+    L.off_order = L.off_acc + (size_t)C * 2 * sizeof(double);
+    L.total = (L.off_order + (size_t)n * sizeof(int) + 15) & ~(size_t)15;
     return L;
 }
 
@@ -103,6 +104,7 @@ struct CoopSmem {
     double *l;
     R *e;
     int *nodes;
+    int *order;     // node-major quadrature phase: local nodes by decreasing work
     double *geo;
     double *acc;
 };
@@ -122,6 +124,7 @@ __device__ __forceinline__ CoopSmem<R> coop_smem(unsigned char *base, const Coop
     S.nodes = reinterpret_cast<int *>(base + L.off_nodes);
     S.geo = reinterpret_cast<double *>(base + L.off_geo);
     S.acc = reinterpret_cast<double *>(base + L.off_acc);
+    S.order = reinterpret_cast<int *>(base + L.off_order);
     return S;
 }
 
@@ -198,6 +201,26 @@ __device__ __forceinline__ void quad_node(R (&out)[NC], const R *tab, const R *t
             for (int m = 0; m < NC; ++m) out[m] = fma(t, e[m * D + k], out[m]);
         }
     }
+}
+
+// The node order of the node-major quadrature phase: local nodes by decreasing
+// number of derivative directions contracted (FP64 skips the structurally zero
+// ones), so that with the items dealt round-robin to the warps the lightest come
+// last and the warps reach the batch's final barrier closer together.  Filled
+// once per CTA (a counting sort by the direction count); ends with a barrier.
+template <int D, typename R>
+__device__ __forceinline__ void coop_node_order(const CoopSmem<R> &S, int n)
+{
+    if (threadIdx.x == 0) {
+        const int deg = lagrange_degree(D, n);
+        int k = 0;
+        for (int w = D; w >= 1; --w)
+            for (int j = 0; j < n; ++j) {
+                const int dirs = std::is_same<R, double>::value ? node_dirs<D>(deg, j) : (1 << D) - 1;
+                if (__popc(dirs) == w) S.order[k++] = j;
+            }
+    }
+    __syncthreads();
 }
 
 // One batch of cells [cell0, cell0 + nb) through phases A-C by the whole CTA.
@@ -500,8 +523,9 @@ __device__ __forceinline__ void coop_batch(const ActionArgs &a, const CoopLayout
     for (int i = threadIdx.x; i < items; i += blockDim.x) {
         int c, j;
         if (node_major) {
-            j = i / L.C;
-            c = i - j * L.C;
+            const int r = i / L.C;
+            c = i - r * L.C;
+            j = S.order[r];          // heaviest nodes first: the last items are the light ones
             if (c >= nb) continue;   // ragged last batch
         } else {
             c = i / n;
@@ -591,6 +615,7 @@ __global__ void __launch_bounds__(kCoopWideBlock, 1) k_action_coop(const ActionA
         return;
     }
     const CoopSmem<R> S = coop_smem<R>(reinterpret_cast<unsigned char *>(smem), L, a);
+    if (C % 32 == 0) coop_node_order<D, R>(S, n);
     // The queue hands out units of U cells: the whole batch (U = C), or, when C is a
     // multiple of 32, 32-cell units of which a CTA takes C/32 at a time until fewer
     // than that many per CTA remain and one at a time after that, which halves (or
