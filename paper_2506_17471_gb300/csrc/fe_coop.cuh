@@ -277,11 +277,15 @@ __device__ __forceinline__ void coop_batch(const ActionArgs &a, const CoopLayout
 #pragma unroll
             for (int i = 0; i < D; ++i) X[m][i] = ok ? __ldg(a.coords + (size_t)v * D + i) : 0.0;
         }
+        // a cell with an out-of-range node index contributes nothing at all (as in
+        // the other kernels); its row of cell2node was just read by the gather above
+        bool nodes_ok = true;
+        for (int j = 0; j < n; ++j) nodes_ok &= (unsigned)__ldg(a.c2n + (size_t)cell * n + j) < (unsigned)a.n_nodes;
         double Jinv[D][D];
         const double det = cell_geometry<D>(X, Jinv);
         double *g = sgeo + c * kCoopGeoStride;
-        const bool good = ok && (det != 0.0) && isfinite(det);
-        if (!ok) set_status(a.status, FE_ERR_INDEX);
+        const bool good = ok && nodes_ok && (det != 0.0) && isfinite(det);
+        if (!ok || !nodes_ok) set_status(a.status, FE_ERR_INDEX);
         else if (!good) set_status(a.status, FE_ERR_BAD_MESH);
 #pragma unroll
         for (int i = 0; i < D; ++i)
