@@ -246,23 +246,55 @@ __device__ __forceinline__ void coop_batch(const ActionArgs &a, const CoopLayout
     // forms in reduced precision use only gradients and store the DoFs relative to
     // the cell's first node, differenced in FP64 (see gather_dofs).
     constexpr bool kRel = !std::is_same<R, double>::value && OpTraits<OP, D>::kNonlinear;
-    for (int i = threadIdx.x; i < nb * n; i += blockDim.x) {
-        const int c = i / n, j = i - c * n;
-        const int node = __ldg(a.c2n + (size_t)(cell0 + c) * n + j);
-        const bool ok = (unsigned)node < (unsigned)a.n_nodes;
-        if (!ok) set_status(a.status, FE_ERR_INDEX);
-        snodes[c * n + j] = ok ? node : -1;
-        [[maybe_unused]] int node0 = node;
-        if constexpr (kRel) node0 = __ldg(a.c2n + (size_t)(cell0 + c) * n);
-        const bool ok0 = (unsigned)node0 < (unsigned)a.n_nodes;
+    // The (cell, node) items are taken kG per thread at a time: all of the group's
+    // node indices are loaded first, then all of its DoFs, so a thread waits for
+    // two memory round trips per group instead of two per item.
+    constexpr int kG = 4;
+    const int a_items = nb * n;
+    const int stride = (int)blockDim.x;
+    for (int i0 = threadIdx.x; i0 < a_items; i0 += kG * stride) {
+        int node[kG];
+        [[maybe_unused]] int node0[kG];
 #pragma unroll
-        for (int f = 0; f < FIELDS; ++f) {
-            const double *src = (f == 0) ? a.u : a.u_lin;
+        for (int g = 0; g < kG; ++g) {
+            const int i = i0 + g * stride;
+            node[g] = -1;
+            node0[g] = -1;
+            if (i < a_items) {
+                const int c = i / n;
+                node[g] = __ldg(a.c2n + (size_t)cell0 * n + i);
+                if constexpr (kRel) node0[g] = __ldg(a.c2n + (size_t)(cell0 + c) * n);
+            }
+        }
+        double v[kG][FIELDS][NC];
 #pragma unroll
-            for (int m = 0; m < NC; ++m) {
-                double v = ok ? __ldg(src + (size_t)node * NC + m) : 0.0;
-                if constexpr (kRel) v = (ok && ok0) ? v - __ldg(src + (size_t)node0 * NC + m) : 0.0;
-                sl[c * L.ls + (f * n + j) * NC + m] = v;
+        for (int g = 0; g < kG; ++g) {
+            const bool ok = (unsigned)node[g] < (unsigned)a.n_nodes;
+#pragma unroll
+            for (int f = 0; f < FIELDS; ++f) {
+                const double *src = (f == 0) ? a.u : a.u_lin;
+#pragma unroll
+                for (int m = 0; m < NC; ++m) v[g][f][m] = ok ? __ldg(src + (size_t)node[g] * NC + m) : 0.0;
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < kG; ++g) {
+            const int i = i0 + g * stride;
+            if (i >= a_items) break;
+            const int c = i / n, j = i - c * n;
+            const bool ok = (unsigned)node[g] < (unsigned)a.n_nodes;
+            if (!ok) set_status(a.status, FE_ERR_INDEX);
+            snodes[c * n + j] = ok ? node[g] : -1;
+            [[maybe_unused]] const bool ok0 = (unsigned)node0[g] < (unsigned)a.n_nodes;
+#pragma unroll
+            for (int f = 0; f < FIELDS; ++f) {
+                [[maybe_unused]] const double *src = (f == 0) ? a.u : a.u_lin;
+#pragma unroll
+                for (int m = 0; m < NC; ++m) {
+                    double x = v[g][f][m];
+                    if constexpr (kRel) x = (ok && ok0) ? x - __ldg(src + (size_t)node0[g] * NC + m) : 0.0;
+                    sl[c * L.ls + (f * n + j) * NC + m] = x;
+                }
             }
         }
     }
