@@ -634,6 +634,7 @@ extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan 
         (f.kind == FE_FORM_NH_JACOBIAN || f.kind == FE_FORM_SVK_JACOBIAN || (adj != nullptr)) ? 2 : 1;
     int coop_cells = 0;
     int coop_block = kCoopBlock;
+    int coop_groups = 1;
     bool global_tab = false;
     size_t rs = (size_t)(1 + m.dim) * n, woff, smem, block_bytes;
     if (coop) {
@@ -644,16 +645,25 @@ extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan 
             coop_cells = f.tile_cells;
         } else if (esz == sizeof(double) && m.dim == 3 && f.kind != FE_FORM_MASS && f.kind != FE_FORM_HELMHOLTZ) {
             // FP64 gradient forms on tetrahedra: the wide layout (one 512-thread CTA
-            // per SM, a batch of 64 or 32 cells) where its shared memory fits.  Its
-            // quadrature phase skips the structurally zero directions (14-30 % of the
-            // gradient entries of a P2-P4 tetrahedron), which outweighs running one
-            // CTA per SM instead of two; on triangles (at most 7 % zeros) and for the
-            // value terms of mass and Helmholtz it does not.
-            for (int C : {64, 32}) {
-                if (coop_layout<double>(n, nq, m.dim, ncomp, C, fields_max, gt).total <= kCoopWideSmemBytes) {
-                    coop_cells = C;
-                    coop_block = kCoopWideBlock;
-                    break;
+            // per SM) where its shared memory fits, preferably as two independent
+            // 256-thread groups with 32-cell batches each (one group's gather phase
+            // overlaps the other's FP64 work), else one group with 64 or 32 cells.
+            // Its quadrature phase skips the structurally zero directions (14-30 % of
+            // the gradient entries of a P2-P4 tetrahedron), which outweighs running
+            // one CTA per SM instead of two; on triangles (at most 7 % zeros) and for
+            // the value terms of mass and Helmholtz it does not.
+            const CoopLayout L32 = coop_layout<double>(n, nq, m.dim, ncomp, 32, fields_max, gt);
+            if (L32.table_block_bytes + 2 * (L32.total - L32.table_block_bytes) <= kCoopWideSmemBytes) {
+                coop_cells = 32;
+                coop_groups = 2;
+                coop_block = kCoopWideBlock;
+            } else {
+                for (int C : {64, 32}) {
+                    if (coop_layout<double>(n, nq, m.dim, ncomp, C, fields_max, gt).total <= kCoopWideSmemBytes) {
+                        coop_cells = C;
+                        coop_block = kCoopWideBlock;
+                        break;
+                    }
                 }
             }
         }
@@ -663,7 +673,7 @@ extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan 
         rs = L.rs;
         woff = L.wts_off;
         block_bytes = L.table_block_bytes;
-        smem = L.total;
+        smem = L.total + (size_t)(coop_groups - 1) * (L.total - L.table_block_bytes);
         global_tab = L.global_tab != 0;
     } else {
         woff = ((size_t)nq * rs * esz + 7) & ~(size_t)7;
@@ -737,6 +747,7 @@ extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan 
     p->smem_bytes = smem;
     cudaGetDevice(&p->device);
     p->coop_cells = coop_cells;
+    p->coop_groups = coop_groups;
     if (cudaMalloc(&p->d_tab, alloc_bytes) != cudaSuccess ||
         cudaMalloc(&p->d_status, 8 * sizeof(int32_t)) != cudaSuccess) {
         cudaFree(p->d_tab);
@@ -760,8 +771,9 @@ extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan 
         fe_plan_destroy(p);
         return lrc;
     }
-    p->grid_blocks = grid_for(p->var, smem, m.n_cells, coop ? coop_cells : p->var.block);
-    p->adj_grid_blocks = adj ? grid_for(p->adj, smem, m.n_cells, coop ? coop_cells : p->adj.block) : 0;
+    p->grid_blocks = grid_for(p->var, smem, m.n_cells, coop ? coop_cells * coop_groups : p->var.block);
+    p->adj_grid_blocks =
+        adj ? grid_for(p->adj, smem, m.n_cells, coop ? coop_cells * coop_groups : p->adj.block) : 0;
     p->flops_per_cell = algorithmic_flops(op_of(f.kind), m.dim, n, nq, false);
     p->flops_per_cell_dense = algorithmic_flops(op_of(f.kind), m.dim, n, nq, true);
     const double dofs = (double)m.n_nodes * ncomp;
@@ -834,6 +846,7 @@ static ActionArgs make_args(const fe_plan *p, const double *u, double *y)
     a.sched = p->d_sched;
     a.coop_n = p->n_loc;
     a.coop_cells = p->coop_cells;
+    a.coop_groups = p->coop_groups;
     a.tab_b = p->d_tab_b;
     a.tab_c = p->d_tab_c;
     a.tc_qc = p->tc_qc;

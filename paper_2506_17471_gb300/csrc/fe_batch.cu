@@ -85,7 +85,7 @@ __device__ __forceinline__ void run_coop(const BatchProblemDev &P, unsigned char
     constexpr int NC = OpTraits<OP, D>::NC;
     const CoopLayout L = coop_layout<double>(P.a.coop_n, P.a.nq, D, NC, P.coop_cells, 1, P.a.tab_b != nullptr);
     const CoopSmem<double> S = coop_smem<double>(base, L, P.a);
-    if (L.C % 32 == 0) coop_node_order<D, double>(S, L.n);   // the node-major quadrature phase's order
+    if (L.C % 32 == 0) coop_node_order<D, double>(S, L.n, whole_cta());   // the node-major phase's order
     coop_batch<OP, D, double>(P.a, L, S, cell0, min(P.coop_cells, P.a.n_cells - cell0));
 }
 

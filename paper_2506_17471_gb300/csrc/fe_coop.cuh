@@ -34,6 +34,7 @@ constexpr int kCoopBlock = 256;
 // warp works on one local node for 32 cells and can leave out that node's
 // structurally zero derivative directions without diverging.
 constexpr int kCoopWideBlock = 512;
+constexpr int kCoopMaxGroups = 2;   // thread groups of the wide layout (see CtaGroup)
 constexpr size_t kCoopWideSmemBytes = 224 * 1024;
 constexpr size_t kCoopSmemTableBytes = 96 * 1024;   // larger tables stay in global memory
 // Per-cell geometry record in shared memory: J^{-1} (D*D), |det J|, mu, lambda,
@@ -111,7 +112,7 @@ struct CoopSmem {
 
 template <typename R>
 __device__ __forceinline__ CoopSmem<R> coop_smem(unsigned char *base, const CoopLayout &L,
-                                                 const ActionArgs &a)
+                                                 const ActionArgs &a, size_t scratch_shift = 0)
 {
     CoopSmem<R> S;
     S.tab = reinterpret_cast<const R *>(base);
@@ -119,6 +120,7 @@ __device__ __forceinline__ CoopSmem<R> coop_smem(unsigned char *base, const Coop
     S.tab_c = reinterpret_cast<const R *>(a.tab_c);
     S.wts = reinterpret_cast<const double *>(base + L.wts_off);
     S.wts_r = reinterpret_cast<const R *>(base + L.wtsr_off);
+    base += scratch_shift;   // this group's batch scratch
     S.l = reinterpret_cast<double *>(base + L.off_l);
     S.e = reinterpret_cast<R *>(base + L.off_e);
     S.nodes = reinterpret_cast<int *>(base + L.off_nodes);
@@ -203,15 +205,38 @@ __device__ __forceinline__ void quad_node(R (&out)[NC], const R *tab, const R *t
     }
 }
 
+// The threads that process one batch together: the whole CTA (barrier id 0, i.e.
+// __syncthreads), or one of several equal groups of it, each with its own named
+// barrier (ids 1, 2, ...) and its own batches, so that one group's gather phase
+// overlaps another group's FP64 work and a group waiting at its barrier does not
+// stop the other.
+struct CtaGroup {
+    int tid;    // thread index within the group
+    int size;   // threads in the group (a multiple of 32)
+    int bar;    // 0: the whole CTA; else the named barrier id of the group
+    __device__ __forceinline__ void sync() const
+    {
+        if (bar == 0)
+            __syncthreads();
+        else
+            asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(size) : "memory");
+    }
+};
+
+__device__ __forceinline__ CtaGroup whole_cta()
+{
+    return CtaGroup{(int)threadIdx.x, (int)blockDim.x, 0};
+}
+
 // The node order of the node-major quadrature phase: local nodes by decreasing
 // number of derivative directions contracted (FP64 skips the structurally zero
 // ones), so that with the items dealt round-robin to the warps the lightest come
 // last and the warps reach the batch's final barrier closer together.  Filled
 // once per CTA (a counting sort by the direction count); ends with a barrier.
 template <int D, typename R>
-__device__ __forceinline__ void coop_node_order(const CoopSmem<R> &S, int n)
+__device__ __forceinline__ void coop_node_order(const CoopSmem<R> &S, int n, const CtaGroup &grp)
 {
-    if (threadIdx.x == 0) {
+    if (grp.tid == 0) {
         const int deg = lagrange_degree(D, n);
         int k = 0;
         for (int w = D; w >= 1; --w)
@@ -220,14 +245,15 @@ __device__ __forceinline__ void coop_node_order(const CoopSmem<R> &S, int n)
                 if (__popc(dirs) == w) S.order[k++] = j;
             }
     }
-    __syncthreads();
+    grp.sync();
 }
 
-// One batch of cells [cell0, cell0 + nb) through phases A-C by the whole CTA.
-// Must be called by every thread of the CTA; ends with a barrier.
+// One batch of cells [cell0, cell0 + nb) through phases A-C by one group of
+// threads (the whole CTA by default).  Must be called by every thread of the
+// group; ends with the group's barrier.
 template <int OP, int D, typename R>
 __device__ __forceinline__ void coop_batch(const ActionArgs &a, const CoopLayout &L, const CoopSmem<R> &S,
-                                           const int cell0, const int nb)
+                                           const int cell0, const int nb, const CtaGroup grp = whole_cta())
 {
     constexpr int NC = OpTraits<OP, D>::NC;
     constexpr int FIELDS = OpTraits<OP, D>::kTwoFields ? 2 : 1;
@@ -251,8 +277,8 @@ __device__ __forceinline__ void coop_batch(const ActionArgs &a, const CoopLayout
     // two memory round trips per group instead of two per item.
     constexpr int kG = 4;
     const int a_items = nb * n;
-    const int stride = (int)blockDim.x;
-    for (int i0 = threadIdx.x; i0 < a_items; i0 += kG * stride) {
+    const int stride = grp.size;
+    for (int i0 = grp.tid; i0 < a_items; i0 += kG * stride) {
         int node[kG];
         [[maybe_unused]] int node0[kG];
 #pragma unroll
@@ -298,7 +324,7 @@ __device__ __forceinline__ void coop_batch(const ActionArgs &a, const CoopLayout
             }
         }
     }
-    for (int c = threadIdx.x; c < nb; c += blockDim.x) {
+    for (int c = grp.tid; c < nb; c += grp.size) {
         const int cell = cell0 + c;
         double X[D + 1][D];
         bool ok = true;
@@ -330,11 +356,11 @@ __device__ __forceinline__ void coop_batch(const ActionArgs &a, const CoopLayout
         sacc[2 * c] = 0.0;
         sacc[2 * c + 1] = 0.0;
     }
-    __syncthreads();
+    grp.sync();
 
     // ---- B: evaluation + pointwise per (cell, quadrature point)
     bool nh_ok = true;
-    for (int i = threadIdx.x; i < nb * nq; i += blockDim.x) {
+    for (int i = grp.tid; i < nb * nq; i += grp.size) {
         const int c = i / nq, q = i - c * nq;
         const double *g = sgeo + c * kCoopGeoStride;
         const R *T = tab + (size_t)q * L.rs;
@@ -546,7 +572,7 @@ __device__ __forceinline__ void coop_batch(const ActionArgs &a, const CoopLayout
         }
     }
     if (!nh_ok) set_status(a.status, FE_ERR_NONFINITE);
-    __syncthreads();
+    grp.sync();
 
     // ---- C: quadrature contraction + scatter per (cell, node).  With a batch of a
     // multiple of 32 cells the items are node-major (item i: node i / C, cell
@@ -556,7 +582,7 @@ __device__ __forceinline__ void coop_batch(const ActionArgs &a, const CoopLayout
     const bool store = OP != OP_NH_ADJOINT && a.cell_out;   // node-gather scatter
     const bool node_major = (L.C % 32) == 0;
     const int items = node_major ? n * L.C : nb * n;
-    for (int i = threadIdx.x; i < items; i += blockDim.x) {
+    for (int i = grp.tid; i < items; i += grp.size) {
         int c, j;
         if (node_major) {
             const int r = i / L.C;
@@ -629,12 +655,12 @@ __device__ __forceinline__ void coop_batch(const ActionArgs &a, const CoopLayout
         }
     }
     if constexpr (OP == OP_NH_ADJOINT) {
-        for (int c = threadIdx.x; c < nb; c += blockDim.x) {
+        for (int c = grp.tid; c < nb; c += grp.size) {
             a.dmu[cell0 + c] = sacc[2 * c];
             a.dlam[cell0 + c] = sacc[2 * c + 1];
         }
     }
-    __syncthreads();   // the batch's shared state is reused by the next batch
+    grp.sync();   // the batch's shared state is reused by the next batch
 }
 
 template <int OP, int D, typename R>
@@ -644,14 +670,22 @@ __global__ void __launch_bounds__(kCoopWideBlock, 1) k_action_coop(const ActionA
     constexpr int FIELDS = OpTraits<OP, D>::kTwoFields ? 2 : 1;
     extern __shared__ __align__(128) double smem[];
     __shared__ __align__(8) uint64_t bar;
-    __shared__ int s_chunk, s_take;
+    __shared__ int s_chunks[kCoopMaxGroups], s_takes[kCoopMaxGroups];
     const CoopLayout L = coop_layout<R>(n, a.nq, D, NC, C, FIELDS, a.tab_b != nullptr);
     if (!stage_table(smem, a.tab, a.tab_doubles, &bar, a.status)) {
         leave_queue(a.sched);
         return;
     }
-    const CoopSmem<R> S = coop_smem<R>(reinterpret_cast<unsigned char *>(smem), L, a);
-    if (C % 32 == 0) coop_node_order<D, R>(S, n);
+    // a.coop_groups groups of threads, each with its own batches and its own copy
+    // of the batch scratch behind the shared table block
+    const int groups = a.coop_groups > 1 ? a.coop_groups : 1;
+    const int gsize = (int)blockDim.x / groups, g = (int)threadIdx.x / gsize;
+    const CtaGroup grp{(int)threadIdx.x - g * gsize, gsize, groups > 1 ? 1 + g : 0};
+    const CoopSmem<R> S = coop_smem<R>(reinterpret_cast<unsigned char *>(smem), L, a,
+                                       (size_t)g * (L.total - L.table_block_bytes));
+    if (C % 32 == 0) coop_node_order<D, R>(S, n, grp);
+    int &s_chunk = s_chunks[g];
+    int &s_take = s_takes[g];
     // The queue hands out units of U cells: the whole batch (U = C), or, when C is a
     // multiple of 32, 32-cell units of which a CTA takes C/32 at a time until fewer
     // than that many per CTA remain and one at a time after that, which halves (or
@@ -660,18 +694,18 @@ __global__ void __launch_bounds__(kCoopWideBlock, 1) k_action_coop(const ActionA
     const int per = C / U;
     const int n_units = (a.n_cells + U - 1) / U;
     for (;;) {
-        if (threadIdx.x == 0) {
+        if (grp.tid == 0) {
             int take = per;
-            if (per > 1 && n_units - *reinterpret_cast<volatile int32_t *>(a.sched) < per * (int)gridDim.x)
+            if (per > 1 && n_units - *reinterpret_cast<volatile int32_t *>(a.sched) < per * (int)gridDim.x * groups)
                 take = 1;
             s_chunk = atomicAdd(a.sched, take);
             s_take = take;
         }
-        __syncthreads();
+        grp.sync();
         const int unit = s_chunk, take = s_take;
         if (unit >= n_units) break;
         const int cell0 = unit * U;
-        coop_batch<OP, D, R>(a, L, S, cell0, min(take * U, a.n_cells - cell0));
+        coop_batch<OP, D, R>(a, L, S, cell0, min(take * U, a.n_cells - cell0), grp);
     }
     leave_queue(a.sched);
 }

@@ -35,7 +35,8 @@ struct ActionArgs {
     int32_t *status;          // device status word (first error wins)
     int32_t *sched;           // [2] work-queue counters: next chunk, warps finished (self-resetting)
     int32_t coop_n;           // cooperative kernel: local nodes per cell
-    int32_t coop_cells;       // cooperative kernel: cells per CTA batch
+    int32_t coop_cells;       // cooperative kernel: cells per batch (of one thread group)
+    int32_t coop_groups;      // cooperative kernel: independent thread groups per CTA (0/1: one)
     const void *tab_b;        // cooperative kernel, large tables: [1+D][N][nq] in global memory
     const void *tab_c;        // cooperative kernel, large tables: [nq][1+D][N] in global memory
     int32_t tc_qc;            // tensor-core kernel: quadrature points per chunk
@@ -128,7 +129,8 @@ struct fe_plan {
     int grid_blocks;
     int adj_grid_blocks;
     size_t smem_bytes;
-    int coop_cells;       // cells per CTA batch (cooperative kernel), else 0
+    int coop_cells;       // cells per batch (cooperative kernel), else 0
+    int coop_groups = 1;  // cooperative kernel: thread groups per CTA, each with its own batches
     int tc_qc;            // tensor-core kernel: quadrature points per chunk, else 0
     int tc_pipes;         // tensor-core kernel: 128-cell pipelines per CTA, else 0
     int tc_wshift;        // tensor-core kernel: staged weights are w_q 2^tc_wshift

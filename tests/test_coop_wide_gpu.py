@@ -1,7 +1,7 @@
 """Edge cases of the cells-per-CTA kernel's wide layout (FP64 gradient forms on
-tetrahedra: one 512-thread CTA per SM, 64-cell batches, node-major quadrature
-phase that skips the structurally zero directions, 32-cell work units handed
-out two at a time, then one at a time near the end).
+tetrahedra: one 512-thread CTA per SM as two independent 256-thread groups, each
+with its own 32-cell batches, named barrier and batch scratch behind a shared
+table; node-major quadrature phase that skips the structurally zero directions).
 
 Cases: batch boundaries (1, 63, 64, 65, 129 cells), meshes with fewer units than
 CTAs and with many units per CTA, the accumulate flag, out-of-range indices and a
@@ -62,8 +62,8 @@ def test_wide_layout_batch_boundaries(fe, n_cells):
 
 @pytest.mark.parametrize("N", [6, 11])
 def test_wide_layout_units_per_cta(fe, N):
-    """N=6: 1,296 cells, 41 units for 152 CTAs (one unit each from the start);
-    N=11: 7,986 cells, 250 units (two at a time, then one)."""
+    """N=6: 1,296 cells, 41 units for 152 CTAs (some groups get none); N=11:
+    7,986 cells, 250 units for 304 groups."""
     m = structured_mesh(3, N, 4, jitter=0.15, seed=610 + N)
     M = fe.Mesh(3, 4, m.coords, m.cell2vertex, m.cell2node, m.n_nodes)
     o = oracle.Oracle.from_mesh(m, 6, "symmetric")
