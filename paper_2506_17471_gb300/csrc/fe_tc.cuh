@@ -408,6 +408,17 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&r)[16])
         : "r"(taddr));
 }
 
+// 16 consecutive columns of this warp's 32 lanes from registers (no wait).
+__device__ __forceinline__ void tc_st16(uint32_t taddr, const uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
+        ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+          "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+}
+__device__ __forceinline__ void tc_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 // 8 consecutive accumulator columns of this warp's 32 lanes (no wait).
 __device__ __forceinline__ void tc_ld8(uint32_t taddr, uint32_t (&r)[8])
 {
@@ -680,6 +691,14 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
     const uint32_t a2s = (uint32_t)__cvta_generic_to_shared(hb + L.a2_off);
     const uint32_t tpipe = tbase + (uint32_t)(pipe * (L.tmem_cols / L.pipes));
     const uint32_t tlane = tpipe + ((uint32_t)((warp & 3) * 32) << 16);   // this warp's TMEM lanes
+    // the DoFs staged in TMEM between the two gather passes: 2 columns per binary64
+    // value, nodes padded to a multiple of 8 (one 16-column store per 8 nodes).
+    // Only with one pipeline per CTA: there the second gather's latency is exposed
+    // and staging saves 4-5 % (elasticity P4 tets, split FP16 and TF32); with two or
+    // four pipelines the others hide it and the TMEM round trip costs up to 5 %
+    // (mass P3 triangles, four pipelines).
+    const int n8 = (n + 7) & ~7;
+    const bool stage_tm = L.pipes == 1 && 2 * F * NC * n8 <= L.tmem_cols;
     const int n_tiles = (a.n_cells + kTcRows - 1) / kTcRows;
     // elasticity: lambda, mu scaled by a power of two 2^km > max(|lambda|, |mu|)
     // (E' stays O(1) for any material); the factor returns in the output exponent
@@ -719,6 +738,7 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
             }
         }
         pipe_sync(pipe, tpc);
+        tc_fence_after();   // the previous tile's TMEM reads come before this tile's stores
 
         // geometry in FP64 (this thread's cell), then the DoFs' largest exponent
         int K = 0;              // output factor 2^K (with mdet below)
@@ -760,37 +780,55 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
                 if (a.mu_cell) mu_c = __ldg(a.mu_cell + cell);
                 if (a.lam_cell) lam_c = __ldg(a.lam_cell + cell);
             }
-            for (int j0 = 8 * h; j0 < n; j0 += 8 * tpc) {
-                int nd[8];
-#pragma unroll
-                for (int s = 0; s < 8; ++s) nd[s] = j0 + s < n ? snodes[t * P + j0 + s] : -2;
-#pragma unroll
-                for (int f = 0; f < F; ++f) {
-                    const double *uf = f == 0 ? a.u : a.u_lin;
-                    double v[8][NC];
-#pragma unroll
-                    for (int s = 0; s < 8; ++s)
-#pragma unroll
-                        for (int m = 0; m < NC; ++m) v[s][m] = nd[s] >= 0 ? __ldg(uf + (size_t)nd[s] * NC + m) : 0.0;
-#pragma unroll
-                    for (int s = 0; s < 8; ++s)
-#pragma unroll
-                        for (int m = 0; m < NC; ++m) {
-                            if constexpr (kOffset) {
-                                if (nd[s] >= 0) {
-                                    const long long key = ordered_key(v[s][m]);
-                                    kmin[f][m] = min(kmin[f][m], key);
-                                    kmax[f][m] = max(kmax[f][m], key);
-                                }
-                            } else {
-                                emax[f] = max(emax[f], exp_field(v[s][m]));
-                            }
-                        }
-                }
-#pragma unroll
-                for (int s = 0; s < 8; ++s) nodes_ok &= nd[s] != -1;
-            }
         }
+        // the DoF range pass (every thread of the warp together: the TMEM stores
+        // below are warp-collective).  Where the pipeline's TMEM columns can hold
+        // the cell's DoFs (free until the evaluation GEMM), the binary64 values are
+        // kept there, two 32-bit columns each, and the rounding pass below reads
+        // them back instead of gathering them from global memory a second time.
+        for (int j0 = 8 * h; j0 < n; j0 += 8 * tpc) {
+            int nd[8];
+#pragma unroll
+            for (int s = 0; s < 8; ++s) nd[s] = (good && j0 + s < n) ? snodes[t * P + j0 + s] : -2;
+#pragma unroll
+            for (int f = 0; f < F; ++f) {
+                const double *uf = f == 0 ? a.u : a.u_lin;
+                double v[8][NC];
+#pragma unroll
+                for (int s = 0; s < 8; ++s)
+#pragma unroll
+                    for (int m = 0; m < NC; ++m) v[s][m] = nd[s] >= 0 ? __ldg(uf + (size_t)nd[s] * NC + m) : 0.0;
+#pragma unroll
+                for (int s = 0; s < 8; ++s)
+#pragma unroll
+                    for (int m = 0; m < NC; ++m) {
+                        if constexpr (kOffset) {
+                            if (nd[s] >= 0) {
+                                const long long key = ordered_key(v[s][m]);
+                                kmin[f][m] = min(kmin[f][m], key);
+                                kmax[f][m] = max(kmax[f][m], key);
+                            }
+                        } else {
+                            emax[f] = max(emax[f], exp_field(v[s][m]));
+                        }
+                    }
+                if (stage_tm) {
+#pragma unroll
+                    for (int m = 0; m < NC; ++m) {
+                        uint32_t w[16];
+#pragma unroll
+                        for (int s = 0; s < 8; ++s) {
+                            w[2 * s] = (uint32_t)__double2loint(v[s][m]);
+                            w[2 * s + 1] = (uint32_t)__double2hiint(v[s][m]);
+                        }
+                        tc_st16(tlane + (uint32_t)(2 * ((f * NC + m) * n8 + j0)), w);
+                    }
+                }
+            }
+#pragma unroll
+            for (int s = 0; s < 8; ++s) nodes_ok &= nd[s] != -1;
+        }
+        if (stage_tm) tc_wait_st();
         if (tpc > 1) {
             // combine the partial ranges of the cell's tpc threads through the
             // quadrature A-operand region (free until this tile's pointwise phase)
@@ -903,10 +941,29 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
             for (int f = 0; f < F; ++f) {
                 const double *uf = f == 0 ? a.u : a.u_lin;
                 double v[8][NC];
+                if (stage_tm) {
+                    if (j0 < n) {
+                        uint32_t w[NC][16];
 #pragma unroll
-                for (int s = 0; s < 8; ++s)
+                        for (int m = 0; m < NC; ++m) tc_ld16(tlane + (uint32_t)(2 * ((f * NC + m) * n8 + j0)), w[m]);
+                        tc_wait_ld();
 #pragma unroll
-                    for (int m = 0; m < NC; ++m) v[s][m] = nd[s] >= 0 ? __ldg(uf + (size_t)nd[s] * NC + m) : 0.0;
+                        for (int s = 0; s < 8; ++s)
+#pragma unroll
+                            for (int m = 0; m < NC; ++m)
+                                v[s][m] = nd[s] >= 0 ? __hiloint2double((int)w[m][2 * s + 1], (int)w[m][2 * s]) : 0.0;
+                    } else {
+#pragma unroll
+                        for (int s = 0; s < 8; ++s)
+#pragma unroll
+                            for (int m = 0; m < NC; ++m) v[s][m] = 0.0;
+                    }
+                } else {
+#pragma unroll
+                    for (int s = 0; s < 8; ++s)
+#pragma unroll
+                        for (int m = 0; m < NC; ++m) v[s][m] = nd[s] >= 0 ? __ldg(uf + (size_t)nd[s] * NC + m) : 0.0;
+                }
 #pragma unroll
                 for (int m = 0; m < NC; ++m) {
                     const size_t region = (size_t)kTcRows * L.K1p;
