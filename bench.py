@@ -145,8 +145,17 @@ def cpu_oracle_rate(o, m, u, budget_cpu_s=12.0, threads=None):
         el = time.perf_counter() - t0
         if el * threads >= budget_cpu_s or el > budget_cpu_s:
             break
-    return {"value": m.n_nodes * 3 * reps / el, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{reps} full-mesh oracle actions in {el:.2f} s on {threads} threads ({cpu_model()})"}
+    out = {"value": m.n_nodes * 3 * reps / el, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": f"{reps} full-mesh oracle actions in {el:.2f} s on {threads} threads ({cpu_model()})"}
+    # one core: the first 1/16 of the cells on one thread, the rate scaled to the
+    # whole mesh (DoFs of the full action / (16 x the subset's time))
+    sub = max(1, m.n_cells // 16)
+    t0 = time.perf_counter()
+    o.elasticity(u, HEADLINE.lam, HEADLINE.mu, threads=1, cells=(0, sub))
+    el1 = (time.perf_counter() - t0) * m.n_cells / sub
+    out["single_core"] = {"value": m.n_nodes * 3 / el1, "unit": UNIT,
+                          "sample": f"{sub} of {m.n_cells} cells on one thread, scaled to the whole mesh"}
+    return out
 
 
 def run_reference(args):
