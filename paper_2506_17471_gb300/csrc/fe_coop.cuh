@@ -189,10 +189,10 @@ __device__ __forceinline__ int node_dirs(int deg, int j)
 // 0.6 % slower on elasticity P4 3D: the FP64 pipe, not the chain latency, binds.)
 template <int D, int NC, int DIRS, typename R>
 __device__ __forceinline__ void quad_node(R (&out)[NC], const R *tab, const R *tab_c, bool gtab,
-                                          const R *ec, int rs, int es, int n, int nq, int j)
+                                          const R *ec, int rs, int es, int n, int q0, int q1, int j)
 {
 #pragma unroll 2
-    for (int q = 0; q < nq; ++q) {
+    for (int q = q0; q < q1; ++q) {
         const R *T = gtab ? tab_c + (size_t)q * (D + 1) * n : tab + (size_t)q * rs;
         const R *e = ec + (size_t)q * es;
 #pragma unroll
@@ -249,17 +249,27 @@ __device__ __forceinline__ void coop_node_order(const CoopSmem<R> &S, int n, con
 }
 
 // One batch of cells [cell0, cell0 + nb) through phases A-C by one group of
-// threads (the whole CTA by default).  Must be called by every thread of the
-// group; ends with the group's barrier.
-template <int OP, int D, typename R>
+// threads (the whole CTA by default), over the quadrature points [q0, q1) (all of
+// them by default; a sub-range adds that part of the quadrature sum into y, the
+// rest being added by other calls: the action is linear in the sum over points).
+// Must be called by every thread of the group; ends with the group's barrier.
+// RANGE = false compiles the full sum (q0, q1 ignored), so that the ordinary
+// batches carry no range arithmetic.
+template <int OP, int D, typename R, bool RANGE = false>
 __device__ __forceinline__ void coop_batch(const ActionArgs &a, const CoopLayout &L, const CoopSmem<R> &S,
-                                           const int cell0, const int nb, const CtaGroup grp = whole_cta())
+                                           const int cell0, const int nb, const CtaGroup grp = whole_cta(),
+                                           int q0 = 0, int q1 = 0)
 {
     constexpr int NC = OpTraits<OP, D>::NC;
     constexpr int FIELDS = OpTraits<OP, D>::kTwoFields ? 2 : 1;
     const int n = L.n;
     [[maybe_unused]] const int deg = lagrange_degree(D, n);   // Lagrange degree of the cell
     const int nq = L.nq;
+    if constexpr (!RANGE) {
+        q0 = 0;
+        q1 = nq;
+    }
+    const int nqs = RANGE ? q1 - q0 : nq;   // quadrature points of this call
     const R *tab = S.tab;
     const double *wts = S.wts;
     const R *wts_r = S.wts_r;
@@ -360,8 +370,8 @@ __device__ __forceinline__ void coop_batch(const ActionArgs &a, const CoopLayout
 
     // ---- B: evaluation + pointwise per (cell, quadrature point)
     bool nh_ok = true;
-    for (int i = grp.tid; i < nb * nq; i += grp.size) {
-        const int c = i / nq, q = i - c * nq;
+    for (int i = grp.tid; i < nb * nqs; i += grp.size) {
+        const int c = i / nqs, q = q0 + (i - c * nqs);
         const double *g = sgeo + c * kCoopGeoStride;
         const R *T = tab + (size_t)q * L.rs;
         const bool gtab = L.global_tab;
@@ -608,7 +618,7 @@ __device__ __forceinline__ void coop_batch(const ActionArgs &a, const CoopLayout
         const R *ec = se + (size_t)c * L.ecs;
         const bool gtab = L.global_tab;
         if constexpr (OP == OP_MASS || OP == OP_HELMHOLTZ) {
-            for (int q = 0; q < nq; ++q) {
+            for (int q = q0; q < q1; ++q) {
                 const R *T = gtab ? S.tab_c + (size_t)q * (D + 1) * n : tab + (size_t)q * L.rs;
                 const R *e = ec + (size_t)q * L.es;
                 if constexpr (OP == OP_MASS) {
@@ -629,19 +639,19 @@ __device__ __forceinline__ void coop_batch(const ActionArgs &a, const CoopLayout
             const R *tc_ = S.tab_c;
             if constexpr (D == 3) {
                 switch (dirs) {
-                case 1: quad_node<D, NC, 1>(out, tab, tc_, gtab, ec, L.rs, L.es, n, nq, j); break;
-                case 2: quad_node<D, NC, 2>(out, tab, tc_, gtab, ec, L.rs, L.es, n, nq, j); break;
-                case 3: quad_node<D, NC, 3>(out, tab, tc_, gtab, ec, L.rs, L.es, n, nq, j); break;
-                case 4: quad_node<D, NC, 4>(out, tab, tc_, gtab, ec, L.rs, L.es, n, nq, j); break;
-                case 5: quad_node<D, NC, 5>(out, tab, tc_, gtab, ec, L.rs, L.es, n, nq, j); break;
-                case 6: quad_node<D, NC, 6>(out, tab, tc_, gtab, ec, L.rs, L.es, n, nq, j); break;
-                default: quad_node<D, NC, kAll>(out, tab, tc_, gtab, ec, L.rs, L.es, n, nq, j); break;
+                case 1: quad_node<D, NC, 1>(out, tab, tc_, gtab, ec, L.rs, L.es, n, q0, q1, j); break;
+                case 2: quad_node<D, NC, 2>(out, tab, tc_, gtab, ec, L.rs, L.es, n, q0, q1, j); break;
+                case 3: quad_node<D, NC, 3>(out, tab, tc_, gtab, ec, L.rs, L.es, n, q0, q1, j); break;
+                case 4: quad_node<D, NC, 4>(out, tab, tc_, gtab, ec, L.rs, L.es, n, q0, q1, j); break;
+                case 5: quad_node<D, NC, 5>(out, tab, tc_, gtab, ec, L.rs, L.es, n, q0, q1, j); break;
+                case 6: quad_node<D, NC, 6>(out, tab, tc_, gtab, ec, L.rs, L.es, n, q0, q1, j); break;
+                default: quad_node<D, NC, kAll>(out, tab, tc_, gtab, ec, L.rs, L.es, n, q0, q1, j); break;
                 }
             } else {
                 switch (dirs) {
-                case 1: quad_node<D, NC, 1>(out, tab, tc_, gtab, ec, L.rs, L.es, n, nq, j); break;
-                case 2: quad_node<D, NC, 2>(out, tab, tc_, gtab, ec, L.rs, L.es, n, nq, j); break;
-                default: quad_node<D, NC, kAll>(out, tab, tc_, gtab, ec, L.rs, L.es, n, nq, j); break;
+                case 1: quad_node<D, NC, 1>(out, tab, tc_, gtab, ec, L.rs, L.es, n, q0, q1, j); break;
+                case 2: quad_node<D, NC, 2>(out, tab, tc_, gtab, ec, L.rs, L.es, n, q0, q1, j); break;
+                default: quad_node<D, NC, kAll>(out, tab, tc_, gtab, ec, L.rs, L.es, n, q0, q1, j); break;
                 }
             }
         }
@@ -693,19 +703,46 @@ __global__ void __launch_bounds__(kCoopWideBlock, 1) k_action_coop(const ActionA
     const int U = (C % 32 == 0) ? 32 : C;
     const int per = C / U;
     const int n_units = (a.n_cells + U - 1) / U;
+    // Tail split: with one unit per take, the T units of the last, partial round
+    // (T = n_units mod the number of groups) would run on T groups while the rest
+    // idle for a whole unit.  When T is at most half a round, each of them is
+    // handed out instead as `split` items over consecutive ranges of quadrature
+    // points, so the last round costs about 1/split of a unit plus one gather.
+    // Not for the adjoint (its per-cell outputs are stored, not summed) nor the
+    // node-gather scatter (which stores each cell's outputs); FP64 only, whose long
+    // FP64-pipe-bound units make the tail expensive (the FP32 kernels' are short).
+    constexpr bool kTailSplit = OP != OP_NH_ADJOINT && std::is_same<R, double>::value;
+    const int n_groups = (int)gridDim.x * groups;
+    int tail = 0, split = 1;
+    if (kTailSplit && per == 1 && !a.cell_out) {
+        const int T = n_units % n_groups;
+        if (T > 0 && 2 * T <= n_groups) {
+            split = min(L.nq, n_groups / T);
+            if (split > 1) tail = T;
+        }
+    }
+    const int n_full = n_units - tail;
+    const int n_items = n_full + tail * split;
     for (;;) {
         if (grp.tid == 0) {
             int take = per;
-            if (per > 1 && n_units - *reinterpret_cast<volatile int32_t *>(a.sched) < per * (int)gridDim.x * groups)
+            if (per > 1 && n_units - *reinterpret_cast<volatile int32_t *>(a.sched) < per * n_groups)
                 take = 1;
             s_chunk = atomicAdd(a.sched, take);
             s_take = take;
         }
         grp.sync();
-        const int unit = s_chunk, take = s_take;
-        if (unit >= n_units) break;
-        const int cell0 = unit * U;
-        coop_batch<OP, D, R>(a, L, S, cell0, min(take * U, a.n_cells - cell0), grp);
+        const int item = s_chunk, take = s_take;
+        if (item >= n_items) break;
+        if (item < n_full) {
+            const int cell0 = item * U;
+            coop_batch<OP, D, R>(a, L, S, cell0, min(take * U, a.n_cells - cell0), grp);
+        } else if constexpr (kTailSplit) {
+            // a tail item: one unit (take is 1 here), one range of quadrature points
+            const int sub = item - n_full, part = sub % split, cell0 = (n_full + sub / split) * U;
+            coop_batch<OP, D, R, true>(a, L, S, cell0, min(U, a.n_cells - cell0), grp, part * L.nq / split,
+                                       (part + 1) * L.nq / split);
+        }
     }
     leave_queue(a.sched);
 }

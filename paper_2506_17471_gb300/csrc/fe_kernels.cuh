@@ -954,15 +954,16 @@ __device__ __forceinline__ void leave_queue(int32_t *sched)
 // 287 -> 262 us with five (at most 102 registers, no more spills than it can
 // hide); elasticity P2 tets gets slower with any cap (52.9 -> 57.0 us at five,
 // 66.2 us at eight: the spills cost more than the extra warps return), so every
-// other variant keeps the compiler's choice.
-template <int OP, typename R>
+// other variant (the tetrahedral Neo-Hookean ones included) keeps the compiler's
+// choice.
+template <int OP, int D, typename R>
 __host__ __device__ constexpr int tpc_min_blocks()
 {
-    return (OP == OP_NH_RESIDUAL && sizeof(R) == 4) ? 5 : 1;
+    return (OP == OP_NH_RESIDUAL && D == 2 && sizeof(R) == 4) ? 5 : 1;
 }
 
 template <int OP, int D, int P, typename R>
-__global__ void __launch_bounds__(kTpcBlock, tpc_min_blocks<OP, R>()) k_action_tpc(const ActionArgs a)
+__global__ void __launch_bounds__(kTpcBlock, tpc_min_blocks<OP, D, R>()) k_action_tpc(const ActionArgs a)
 {
     extern __shared__ __align__(128) double smem[];
     __shared__ __align__(8) uint64_t bar;

@@ -4,7 +4,8 @@ with its own 32-cell batches, named barrier and batch scratch behind a shared
 table; node-major quadrature phase that skips the structurally zero directions).
 
 Cases: batch boundaries (1, 63, 64, 65, 129 cells), meshes with fewer units than
-CTAs and with many units per CTA, the accumulate flag, out-of-range indices and a
+CTAs and with many units per CTA, the last partial round of units split by
+quadrature points, the accumulate flag, out-of-range indices and a
 degenerate cell in the middle of a batch (the rest of the batch is still applied),
 and the Neo-Hookean adjoint (per-cell material derivatives) on a ragged batch.
 """
@@ -75,6 +76,34 @@ def test_wide_layout_units_per_cta(fe, N):
     y2 = plan.apply(cuda(u))
     assert rel(y2, y.cpu().numpy()) <= 1e-15
     assert plan.status() == 0
+
+
+def test_wide_layout_tail_split(fe):
+    """17^3 x 6 = 29,478 cells, 922 32-cell units (the last one ragged) for 304
+    groups: three full rounds, then a tail of 10 units that the kernel hands out as
+    10 x 24 items of one quadrature point each, every item adding its part of the
+    quadrature sum through the same scatter.  Elasticity and the Neo-Hookean
+    residual and Jacobian action against the oracle, and the accumulate flag."""
+    m = structured_mesh(3, 17, 4, jitter=0.15, seed=615)
+    M = fe.Mesh(3, 4, m.coords, m.cell2vertex, m.cell2node, m.n_nodes)
+    o = oracle.Oracle.from_mesh(m, 6, "symmetric")
+    u = uniform_field(m.n_nodes * 3, 616)
+    plan = wide_plan(fe, M)
+    assert plan.info.grid_blocks == 152
+    y = plan.apply(cuda(u))
+    assert rel(y, o.elasticity(u, 1.25, 1.0, threads=16)) <= TOL
+    y0 = uniform_field(m.n_nodes * 3, 617)
+    acc = wide_plan(fe, M, accumulate=True)
+    assert rel(acc.apply(cuda(u), cuda(y0.copy())), y0 + o.elasticity(u, 1.25, 1.0, threads=16)) <= TOL
+    mu, lam = lame_fields(m.n_cells, 618)
+    ud = sinusoid_displacement(m, 619)
+    res = fe.Plan(M, fe.NH_RESIDUAL, 6, mu_cell=mu, lam_cell=lam, quad_scheme="symmetric")
+    assert res.info.kernel == 1 and res.info.threads_per_block == 512
+    assert rel(res.apply(cuda(ud)), o.nh_residual(ud, mu, lam, threads=16)) <= TOL
+    jac = fe.Plan(M, fe.NH_JACOBIAN, 6, mu_cell=mu, lam_cell=lam, u_lin=ud, quad_scheme="symmetric")
+    assert rel(jac.apply(cuda(u)), o.nh_jacobian(ud, u, mu, lam, threads=16)) <= TOL
+    for p in (plan, acc, res, jac):
+        assert p.status() == 0
 
 
 def test_wide_layout_accumulate(fe):
