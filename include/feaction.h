@@ -491,11 +491,15 @@ int fe_measure_fp64_peak(double *scratch, size_t scratch_doubles, double *gflops
  * zero-initialised uint64.  Asynchronous on stream. */
 int fe_selftest_conversions(const double *x, long long n, unsigned long long *count, void *stream);
 
-/* Device self-test of the tensor-core kernel's integer conversions binary64 ->
- * bfloat16 and binary64 -> binary16 (round to nearest even, done without the
- * FP64 pipe) against CUDA's __double2bfloat16 / __double2half: x device
- * [n]; count device [2] unsigned 64-bit, count[0] += bfloat16 mismatches,
- * count[1] += binary16 mismatches (NaN results compare equal).  Asynchronous.
+/* Device self-test of the tensor-core kernel's conversions.  The integer
+ * conversions binary64 -> bfloat16 and binary64 -> binary16 (round to nearest
+ * even, done without the FP64 pipe) against CUDA's __double2bfloat16 /
+ * __double2half: count[0] += bfloat16 mismatches, count[1] += binary16
+ * mismatches (NaN results compare equal).  The kernel's rounding pass (binary64
+ * times 2^-k narrowed to binary32 by rounding to odd, then rounded by the
+ * hardware's binary32 conversion) against the integer conversions bit for bit,
+ * for bfloat16, binary16 and TF32 at k = 0, -5, 9, 20: count[2] += mismatches.
+ * x device [n]; count device [3] unsigned 64-bit.  Asynchronous.
  * Errors: FE_ERR_INVALID_ARG, FE_ERR_CUDA. */
 int fe_selftest_conversions16(const double *x, long long n, unsigned long long *count, void *stream);
 

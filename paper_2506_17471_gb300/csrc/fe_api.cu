@@ -1077,12 +1077,15 @@ __global__ void k_selftest_bounded_wait(int32_t *status, int polls)
     if (!__syncthreads_or(done) && threadIdx.x == 0) set_status(status, FE_ERR_TIMEOUT);
 }
 
-// Self-test of the integer binary64 -> bfloat16 / binary16 conversions of the
-// tensor-core kernel against CUDA's conversions: count[0] += bfloat16
-// mismatches, count[1] += binary16 mismatches (NaN compares equal to NaN).
+// Self-test of the binary64 -> bfloat16 / binary16 / TF32 conversions of the
+// tensor-core kernel.  The exact integer conversions against CUDA's: count[0] +=
+// bfloat16 mismatches, count[1] += binary16 mismatches (NaN compares equal to
+// NaN).  The rounding-to-odd conversions of the rounding pass against the exact
+// integer ones, bit for bit, at scales 2^0, 2^5, 2^-9 and 2^-20: count[2] +=
+// mismatches (bfloat16, binary16 and TF32).
 __global__ void k_selftest_conversions16(const double *x, long long n, unsigned long long *count)
 {
-    unsigned long long bad_b = 0, bad_h = 0;
+    unsigned long long bad_b = 0, bad_h = 0, bad_odd = 0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         const double v = x[i];
@@ -1094,9 +1097,19 @@ __global__ void k_selftest_conversions16(const double *x, long long n, unsigned 
         const bool nan_h = (rh & 0x7C00) == 0x7C00 && (rh & 0x3FF), nan_mh = (mh & 0x7C00) == 0x7C00 && (mh & 0x3FF);
         if (rb != mb && !(nan_b && nan_mb)) ++bad_b;
         if (rh != mh && !(nan_h && nan_mh)) ++bad_h;
+        const int ks[4] = {0, -5, 9, 20};
+        for (int t = 0; t < 4; ++t) {
+            const int k = ks[t];
+            const uint32_t eb = to16_bits<__nv_bfloat16>(v, k), eh = to16_bits<__half>(v, k);
+            const uint32_t pb = pack2_from_f64<__nv_bfloat16>(v, -v, k), ph = pack2_from_f64<__half>(v, -v, k);
+            const uint32_t nb = to16_bits<__nv_bfloat16>(-v, k), nh = to16_bits<__half>(-v, k);
+            if (pb != (eb | (nb << 16)) || ph != (eh | (nh << 16))) ++bad_odd;
+            if (tf32_from_f64(v, k) != to_tf32_bits(v, k)) ++bad_odd;
+        }
     }
     if (bad_b) atomicAdd(count, bad_b);
     if (bad_h) atomicAdd(count + 1, bad_h);
+    if (bad_odd) atomicAdd(count + 2, bad_odd);
 }
 
 }  // namespace

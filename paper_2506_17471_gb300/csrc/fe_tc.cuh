@@ -313,6 +313,55 @@ __device__ __forceinline__ uint32_t pack2<__half>(float lo, float hi)
     return *reinterpret_cast<const uint32_t *>(&v);
 }
 
+// binary64 x times 2^-k narrowed to binary32 with rounding to odd: the 29 dropped
+// fraction bits are truncated and the last kept bit is set if any of them was
+// nonzero (integer operations only).  Returns false, leaving f = 0, where the
+// result is not a binary32 normal number or zero (x subnormal, inf or NaN, or
+// x 2^-k outside [2^-126, 2^128)).
+__device__ __forceinline__ bool f64_to_f32_odd(double x, int k, float &f)
+{
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const unsigned sign = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7FFu);
+    f = 0.f;
+    if (((hi & 0x7FFFFFFFu) | lo) == 0u) {
+        f = __uint_as_float(sign);
+        return true;
+    }
+    const int fe = e - 1023 + 127 - k;   // binary32 biased exponent
+    if (e == 0 || e == 0x7FF || fe < 1 || fe > 254) return false;
+    const unsigned bits = sign | ((unsigned)fe << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29) |
+                          ((lo & 0x1FFFFFFFu) != 0u ? 1u : 0u);
+    f = __uint_as_float(bits);
+    return true;
+}
+
+// Two binary64 values times 2^-k rounded to nearest even 16-bit values (TE),
+// packed, the first at the lower address; equal to to16_bits on each.  Each is
+// narrowed to binary32 by rounding to odd, then rounded by the hardware's
+// binary32 -> 16-bit conversion: rounding to odd at 24 bits followed by rounding
+// to nearest at p <= 22 bits equals rounding to nearest directly (Boldo and
+// Melquiond, "Emulation of FMA and correctly rounded sums: proved algorithms
+// using rounding to odd", IEEE Trans. Computers 57(4), 2008).  Values outside
+// binary32's normal range take the exact integer path.
+template <typename TE>
+__device__ __forceinline__ uint32_t pack2_from_f64(double x0, double x1, int k)
+{
+    float f0, f1;
+    const bool ok0 = f64_to_f32_odd(x0, k, f0), ok1 = f64_to_f32_odd(x1, k, f1);
+    if (ok0 && ok1) return pack2<TE>(f0, f1);
+    return (uint32_t)to16_bits<TE>(x0, k) | ((uint32_t)to16_bits<TE>(x1, k) << 16);
+}
+
+// x times 2^-k rounded to nearest even TF32 (container bits); equal to
+// to_tf32_bits, by the same rounding-to-odd argument (TF32 keeps 11 bits).
+__device__ __forceinline__ uint32_t tf32_from_f64(double x, int k)
+{
+    float f;
+    if (f64_to_f32_odd(x, k, f)) return f32_bits_to_tf32(__float_as_uint(f));
+    return to_tf32_bits(x, k);
+}
+
 // The two 16-bit values of a packed pair back in binary32.
 template <typename TE>
 __device__ __forceinline__ float2 unpack2(uint32_t w);
@@ -973,7 +1022,7 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
                         uint32_t w[8];
 #pragma unroll
                         for (int s = 0; s < 8; ++s)
-                            w[s] = to_tf32_bits(nd[s] >= 0 ? v[s][m] - off[f][m] : 0.0, ku[f]);
+                            w[s] = tf32_from_f64(nd[s] >= 0 ? v[s][m] - off[f][m] : 0.0, ku[f]);
                         TE *q = A1 + tc_off(t, j0, L.K1p, ESZ);
                         *reinterpret_cast<uint4 *>(q) = make_uint4(w[0], w[1], w[2], w[3]);
                         *reinterpret_cast<uint4 *>(q + 32) = make_uint4(w[4], w[5], w[6], w[7]);
@@ -982,10 +1031,8 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
                         uint32_t w[4];
 #pragma unroll
                         for (int h = 0; h < 4; ++h)
-                            w[h] = (uint32_t)to16_bits<TE>(nd[2 * h] >= 0 ? v[2 * h][m] - off[f][m] : 0.0, ku[f]) |
-                                   ((uint32_t)to16_bits<TE>(nd[2 * h + 1] >= 0 ? v[2 * h + 1][m] - off[f][m] : 0.0,
-                                                             ku[f])
-                                    << 16);
+                            w[h] = pack2_from_f64<TE>(nd[2 * h] >= 0 ? v[2 * h][m] - off[f][m] : 0.0,
+                                                      nd[2 * h + 1] >= 0 ? v[2 * h + 1][m] - off[f][m] : 0.0, ku[f]);
                         *reinterpret_cast<uint4 *>(A1 + tc_off(t, j0, L.K1p, ESZ)) = make_uint4(w[0], w[1], w[2], w[3]);
                     } else {
                         // hi + lo pair from the scaled value in binary32
