@@ -748,6 +748,15 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
     // (mass P3 triangles, four pipelines).
     const int n8 = (n + 7) & ~7;
     const bool stage_tm = L.pipes == 1 && 2 * F * NC * n8 <= L.tmem_cols;
+    // With tpc > 1 the cell's threads combine their DoF ranges through kXS 64-bit
+    // words each; where the region also holds kGeoWords 32-bit words per cell, the
+    // geometry (16 loads and ~60 FP64-pipe instructions) is computed once per cell
+    // and shared instead of by each of its threads.
+    constexpr int kXS = kOffset ? 2 * F * NC + 1 : F + 1;
+    constexpr int kGeoWords = 3 + (OP == OP_HELMHOLTZ ? 2 : 0) + (OP != OP_MASS ? D * D : 0) + (kHyperJac ? D * D : 0);
+    const bool share_geo = tpc > 1 && (size_t)kTcRows * tpc * kXS * 8 + (size_t)kTcRows * kGeoWords * 4 <=
+                                          L.nodes_off - L.a2_off;
+    const bool do_geo = !share_geo || h == 0;
     const int n_tiles = (a.n_cells + kTcRows - 1) / kTcRows;
     // elasticity: lambda, mu scaled by a power of two 2^km > max(|lambda|, |mu|)
     // (E' stays O(1) for any material); the factor returns in the output exponent
@@ -811,21 +820,31 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
                 kmax[f][m] = LLONG_MIN;
             }
         bool nodes_ok = true;
-        double Jinv[D][D];
-        double det = 0.0;
-        if (good) {
+        // The cell's geometry and what derives from it alone: geo bit 0 = vertex
+        // indices in range, bit 1 = det J nonzero and finite; Kg = the exponent of
+        // the output factor without the DoF scale.  With shared geometry only the
+        // cell's first thread computes them, the others read them after the
+        // exchange below.
+        int geo = 0, Kg = 0;
+        double Jinv[D][D], det = 0.0;
+        bool in_all = true;
+        if (good && do_geo) {
             const int cell = tile * kTcRows + t;
             double X[D + 1][D];
 #pragma unroll
             for (int m = 0; m <= D; ++m) {
                 const int v = __ldg(a.c2v + (size_t)cell * (D + 1) + m);
                 const bool in = (unsigned)v < (unsigned)a.n_vertices;
-                good &= in;
+                in_all &= in;
 #pragma unroll
                 for (int i = 0; i < D; ++i) X[m][i] = in ? __ldg(a.coords + (size_t)v * D + i) : 0.0;
             }
             det = cell_geometry<D>(X, Jinv);
-            if constexpr (kHyperJac) {
+            good &= in_all;
+        }
+        if constexpr (kHyperJac) {
+            if (good) {
+                const int cell = tile * kTcRows + t;
                 if (a.mu_cell) mu_c = __ldg(a.mu_cell + cell);
                 if (a.lam_cell) lam_c = __ldg(a.lam_cell + cell);
             }
@@ -878,12 +897,51 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
             for (int s = 0; s < 8; ++s) nodes_ok &= nd[s] != -1;
         }
         if (stage_tm) tc_wait_st();
+        // the geometry-derived values (of a cell with geo == 3): with shared geometry
+        // the cell's first thread derives them here, before the exchange; otherwise
+        // every thread does below, after its status checks
+        auto derive = [&]() {
+            const int ed = exp_field(det) - 1023;
+            const double m64 = __hiloint2double((__double2hiint(det) & 0x000FFFFF) | (1023 << 20),
+                                                __double2loint(det));
+            mdet = narrow_pow2_ftz(m64, 0);
+            Kg = ed - a.tc_wshift;
+            if constexpr (OP == OP_ELASTICITY) Kg += km_el;
+            if constexpr (OP != OP_MASS) {
+                int ej = 0;
+#pragma unroll
+                for (int i = 0; i < D; ++i)
+#pragma unroll
+                    for (int k = 0; k < D; ++k) ej = max(ej, exp_field(Jinv[i][k]));
+                const int kj = ej - 1022;   // s_J = 2^kj > max |J^{-1}_ik|
+                if constexpr (OP == OP_HELMHOLTZ) {
+                    // value term ~ |det J| u, gradient term ~ |det J| 2^2kj (O(1) each
+                    // before these factors): the common scale follows the larger one
+                    const int sig = max(2 * kj, 0);
+                    Kg += sig;
+                    s_val = exp2_float(-sig);
+                    s_grad = exp2_float(2 * kj - sig);
+                } else {
+                    Kg += 2 * kj;
+                }
+#pragma unroll
+                for (int i = 0; i < D; ++i)
+#pragma unroll
+                    for (int k = 0; k < D; ++k) {
+                        Jh[i][k] = narrow_pow2_ftz(Jinv[i][k], kj);
+                        if constexpr (kHyperJac) Jf[i][k] = narrow_pow2_ftz(Jinv[i][k], 0);
+                    }
+            }
+        };
+        if (good && do_geo) geo = (in_all ? 1 : 0) | ((det != 0.0) && isfinite(det) ? 2 : 0);
+        if (share_geo && h == 0 && geo == 3) derive();
         if (tpc > 1) {
             // combine the partial ranges of the cell's tpc threads through the
-            // quadrature A-operand region (free until this tile's pointwise phase)
-            constexpr int S = kOffset ? 2 * F * NC + 1 : F + 1;
+            // quadrature A-operand region (free until this tile's pointwise phase);
+            // with shared geometry the cell's first thread also leaves its
+            // geometry words there, behind the range slots
             long long *xch = reinterpret_cast<long long *>(hb + L.a2_off);
-            long long *mine = xch + (size_t)(h * kTcRows + t) * S;
+            long long *mine = xch + (size_t)(h * kTcRows + t) * kXS;
             int q = 0;
 #pragma unroll
             for (int f = 0; f < F; ++f) {
@@ -898,10 +956,33 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
                 }
             }
             mine[q] = nodes_ok ? 1 : 0;
+            uint32_t *gx = reinterpret_cast<uint32_t *>(xch + (size_t)tpc * kTcRows * kXS) + (size_t)t * kGeoWords;
+            if (share_geo && h == 0) {
+                int w = 0;
+                gx[w++] = (uint32_t)geo;
+                gx[w++] = (uint32_t)Kg;
+                gx[w++] = __float_as_uint(mdet);
+                if constexpr (OP == OP_HELMHOLTZ) {
+                    gx[w++] = __float_as_uint(s_val);
+                    gx[w++] = __float_as_uint(s_grad);
+                }
+                if constexpr (OP != OP_MASS) {
+#pragma unroll
+                    for (int i = 0; i < D; ++i)
+#pragma unroll
+                        for (int k = 0; k < D; ++k) gx[w++] = __float_as_uint(Jh[i][k]);
+                }
+                if constexpr (kHyperJac) {
+#pragma unroll
+                    for (int i = 0; i < D; ++i)
+#pragma unroll
+                        for (int k = 0; k < D; ++k) gx[w++] = __float_as_uint(Jf[i][k]);
+                }
+            }
             pipe_sync(pipe, tpc);
             for (int hh = 0; hh < tpc; ++hh) {
                 if (hh == h) continue;
-                const long long *other = xch + (size_t)(hh * kTcRows + t) * S;
+                const long long *other = xch + (size_t)(hh * kTcRows + t) * kXS;
                 int r = 0;
 #pragma unroll
                 for (int f = 0; f < F; ++f) {
@@ -917,12 +998,34 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
                 }
                 nodes_ok &= other[r] != 0;
             }
+            if (share_geo && h != 0) {
+                int w = 0;
+                geo = (int)gx[w++];
+                Kg = (int)gx[w++];
+                mdet = __uint_as_float(gx[w++]);
+                if constexpr (OP == OP_HELMHOLTZ) {
+                    s_val = __uint_as_float(gx[w++]);
+                    s_grad = __uint_as_float(gx[w++]);
+                }
+                if constexpr (OP != OP_MASS) {
+#pragma unroll
+                    for (int i = 0; i < D; ++i)
+#pragma unroll
+                        for (int k = 0; k < D; ++k) Jh[i][k] = __uint_as_float(gx[w++]);
+                }
+                if constexpr (kHyperJac) {
+#pragma unroll
+                    for (int i = 0; i < D; ++i)
+#pragma unroll
+                        for (int k = 0; k < D; ++k) Jf[i][k] = __uint_as_float(gx[w++]);
+                }
+            }
         }
         if (t < nb) {
-            if (!good || !nodes_ok) {
+            if (!good || !nodes_ok || !(geo & 1)) {
                 set_status(a.status, FE_ERR_INDEX);
                 good = false;
-            } else if (!(det != 0.0) || !isfinite(det)) {
+            } else if (!(geo & 2)) {
                 set_status(a.status, FE_ERR_BAD_MESH);
                 good = false;
             }
@@ -941,42 +1044,13 @@ __global__ void __launch_bounds__(kTcMaxPipes * kTcRows, 1) k_action_tc(const Ac
                 // s_u = 2^ku > max |u - c| >= 2^(ku-1) (no scaling for zero or non-finite ranges)
 #pragma unroll
                 for (int f = 0; f < F; ++f) ku[f] = (emax[f] == 0 || emax[f] == 0x7FF) ? 0 : emax[f] - 1022;
-                const int ed = exp_field(det) - 1023;
-                const double m64 = __hiloint2double((__double2hiint(det) & 0x000FFFFF) | (1023 << 20),
-                                                    __double2loint(det));
-                mdet = narrow_pow2_ftz(m64, 0);
-                K = ed + ku[0] - a.tc_wshift;
-                if constexpr (OP == OP_ELASTICITY) K += km_el;
+                if (!share_geo) derive();
+                K = Kg + ku[0];
                 if constexpr (kHyperJac) {
                     const int km = mat_shift(lam_c, mu_c);
                     K += km;
                     mu_c = ldexp(mu_c, -km);
                     lam_c = ldexp(lam_c, -km);
-                }
-                if constexpr (OP != OP_MASS) {
-                    int ej = 0;
-#pragma unroll
-                    for (int i = 0; i < D; ++i)
-#pragma unroll
-                        for (int k = 0; k < D; ++k) ej = max(ej, exp_field(Jinv[i][k]));
-                    const int kj = ej - 1022;   // s_J = 2^kj > max |J^{-1}_ik|
-                    if constexpr (OP == OP_HELMHOLTZ) {
-                        // value term ~ |det J| u, gradient term ~ |det J| 2^2kj (O(1) each
-                        // before these factors): the common scale follows the larger one
-                        const int sig = max(2 * kj, 0);
-                        K += sig;
-                        s_val = exp2_float(-sig);
-                        s_grad = exp2_float(2 * kj - sig);
-                    } else {
-                        K += 2 * kj;
-                    }
-#pragma unroll
-                    for (int i = 0; i < D; ++i)
-#pragma unroll
-                        for (int k = 0; k < D; ++k) {
-                            Jh[i][k] = narrow_pow2_ftz(Jinv[i][k], kj);
-                            if constexpr (kHyperJac) Jf[i][k] = narrow_pow2_ftz(Jinv[i][k], 0);
-                        }
                 }
             }
         }
