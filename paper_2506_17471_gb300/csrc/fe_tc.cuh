@@ -7,10 +7,12 @@
 // U_m holds the tile's gathered DoFs, E'_m the weighted pointwise stress pulled
 // back to the reference cell (Sec. "Towards Discretization": evaluation,
 // pointwise and quadrature phases).  Row c of every GEMM is cell c, which is
-// TMEM lane c and thread c of the tile: a thread gathers its cell, computes its
-// geometry, reads its own accumulator row with tcgen05.ld, evaluates the
+// TMEM lane c and thread c of the tile (or its tpc threads, each taking every
+// tpc-th node batch, column block and output group, the cell's geometry computed
+// by the first and shared where shared memory allows): the cell's thread gathers
+// its cell, reads its own accumulator row with tcgen05.ld, evaluates the
 // pointwise form for its cell at every point and scatter-adds its own result,
-// exactly like the thread-per-cell kernel, while the contractions run on the
+// like the thread-per-cell kernel, while the contractions run on the
 // tensor cores (tcgen05.mma kind::f16, BF16 or FP16 operands, FP32 accumulators
 // in TMEM, issued by one thread, completion through tcgen05.commit and an
 // mbarrier with a bounded wait).
@@ -40,7 +42,10 @@
 // rounding) and an exponent add on the widened FP64 value.  All power-of-two
 // scalings are exponent arithmetic on the bit patterns: on this part FP64
 // instructions issue at about 1/64 of the FP32 rate, and the only ones left are
-// the FP64 geometry (det J, J^{-1}) and the FP64 scatter-add.
+// the FP64 geometry (det J, J^{-1}), the offset subtraction u - c and the FP64
+// scatter-add.  The rounding of u - c to 16 bits narrows it to binary32 by
+// rounding to odd with integer operations and leaves the last rounding to the
+// hardware's binary32 conversion (pack2_from_f64).
 //
 // Operand layout (K-major, no swizzle): 8x8 core matrices of 16-bit elements
 // (128 bytes), ordered [row group][K group][row][col]; LBO = 128 B between
