@@ -135,6 +135,7 @@ def candidates(kind, dim, degree, nq, n_loc, ncomp, fields=1, eta_min=0.3, max_t
 
 
 SMEM_PER_SM = 228 * 1024
+TAIL_GATHER = 0.05            # a tail item's gather phase, as a fraction of a whole unit
 WARPS_TO_FILL_SM = 8          # warps per SM that keep the FP64 pipe busy (measured: 95 % at 8)
 
 
@@ -146,8 +147,10 @@ def model_time(c: Candidate, n_cells, flops, bytes_min, nq, n_loc, ncomp=1, fiel
     tail: eta = warps / (W ceil(warps / W)), W = SMs x WARPS_TO_FILL_SM.
     Cells-per-CTA: ceil(n_cells / C) CTAs of 256 threads over SMs x resident
     slots (resident CTAs per SM from the shared-memory plan, at most 4), the
-    same fill/tail factor over slots, times the lane efficiency of its two
-    phases, whose idle lanes co-resident CTAs partly fill."""
+    same fill/tail factor over slots (a last round at most half full counts as
+    1/split of a round plus its gather: the FP64 kernel's tail split), times the
+    lane efficiency of its two phases, whose idle lanes co-resident CTAs partly
+    fill."""
     t_mem = bytes_min / (HBM_GBS * 1e9)
     if c.kernel == 0:
         warps = max(1, math.ceil(n_cells / 32))
@@ -160,6 +163,16 @@ def model_time(c: Candidate, n_cells, flops, bytes_min, nq, n_loc, ncomp=1, fiel
         ctas = max(1, math.ceil(n_cells / c.tile_cells))
         slots = N_SMS * resident
         eta_par = ctas / (slots * math.ceil(ctas / slots))
+        # the FP64 kernel's tail split: with one unit per take (C not a multiple of
+        # 32, or 32), the T units of a last round that is at most half full are run
+        # as `split` items of 1/split of the points each, plus the unit's gather
+        # (about 5 % of a unit), instead of a whole round
+        if c.tile_cells % 32 != 0 or c.tile_cells == 32:
+            T = ctas % slots
+            if T > 0 and 2 * T <= slots:
+                split = min(nq, slots // T)
+                if split > 1:
+                    eta_par = (ctas / slots) / (ctas // slots + 1.0 / split + TAIL_GATHER)
         lanes = 0.5 * eta_simd(c.tile_cells * nq) + 0.5 * eta_simd(c.tile_cells * n_loc)
         eta = eta_par * (1.0 - (1.0 - lanes) / resident)
         rounds = math.ceil(ctas / slots)

@@ -55,6 +55,26 @@ def test_cost_model_monotone(at):
     assert small_coop < small_tpc
 
 
+def test_cost_model_tail_split(at):
+    """The FP64 cells-per-CTA kernel splits a last round that is at most half full
+    by quadrature points, so a few extra units cost a fraction of a round; a last
+    round more than half full still costs a whole round."""
+    C, n, nq = 10, 20, 27
+    resident = max(1, min(4, at.SMEM_PER_SM // at._coop_total_bytes(n, nq, 3, 1, C, 1)))
+    slots = at.N_SMS * resident
+    c = at.Candidate(1, C)
+
+    def t(units):   # FP64 work in proportion to the units; launch and batch overheads left out
+        rounds = -(-units // slots)
+        return at.model_time(c, units * C, 1e6 * units, 0.0, nq, n, 1, dim=3) - at.T_LAUNCH_S \
+            - rounds * at.T_BATCH_S
+
+    one = t(slots)
+    assert t(slots + 3) < 1.2 * one                            # 3 units split min(27, slots/3) ways
+    assert t(slots + (3 * slots) // 4) == pytest.approx(2 * one, rel=1e-9)   # no split: a whole round
+    assert t(2 * slots) == pytest.approx(2 * one, rel=1e-9)
+
+
 def test_spearman(at):
     assert at.spearman([1, 2, 3, 4], [10, 20, 30, 40]) == 1.0
     assert at.spearman([1, 2, 3, 4], [4, 3, 2, 1]) == -1.0
