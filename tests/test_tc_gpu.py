@@ -432,6 +432,31 @@ def test_tc_bad_index_two_threads_per_cell(fe, j):
     check16("elasticity", "fp16", rel(y, o.elasticity(u, 1.25, 1.0)), "bad index 2 threads", floor=None)
 
 
+@pytest.mark.parametrize("bad", ["vertex", "degenerate"])
+def test_tc_shared_geometry_invalid_cell(fe, bad):
+    """With two threads per cell the cell's first thread computes the geometry and
+    hands it to the second: an out-of-range vertex index (FE_ERR_INDEX) or a
+    degenerate cell (FE_ERR_BAD_MESH) must skip the whole cell on both threads,
+    and every other cell (their geometry shared the same way) is applied."""
+    from paper_2506_17471_gb300 import _native as N
+    m, _ = make(fe, 3, 5, 4, 47)
+    c2v = m.cell2vertex.copy()
+    if bad == "vertex":
+        c2v[310, 2] = m.coords.shape[0] + 11
+    else:
+        c2v[310, 3] = c2v[310, 1]                  # the cell collapses onto a face
+    M = fe.Mesh(3, 4, m.coords, c2v, m.cell2node, m.n_nodes)
+    plan = fe.Plan(M, fe.ELASTICITY, 6, lam=1.25, mu=1.0, precision="fp16")
+    assert plan.info.threads_per_block == 512
+    u = uniform_field(m.n_nodes * 3, 8)
+    y = plan.apply(cuda(u)).cpu().numpy()
+    assert plan.status() == (N.FE_ERR_INDEX if bad == "vertex" else N.FE_ERR_BAD_MESH)
+    keep = np.ones(m.n_cells, dtype=bool)
+    keep[310] = False
+    o = oracle.Oracle(3, 4, 6, m.coords, m.cell2vertex[keep], m.cell2node[keep], m.n_nodes)
+    check16("elasticity", "fp16", rel(y, o.elasticity(u, 1.25, 1.0)), "shared geometry " + bad, floor=None)
+
+
 @pytest.mark.parametrize("kind", ["nh_jacobian", "svk_jacobian"])
 @pytest.mark.parametrize("dim,N,p,q", [(2, 13, 3, 6), (3, 5, 2, 4)])
 def test_tc_fp16x2_hyperelastic(fe, kind, dim, N, p, q):
