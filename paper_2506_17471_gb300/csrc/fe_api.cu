@@ -414,6 +414,11 @@ static void tc_fill_block(const TcLayout &L, int kind, const std::vector<double>
 }
 
 static_assert(kLogTabDoubles == FE_LOG_TABLE_DOUBLES, "log table size of the header");
+// the plan folds the quadrature weights into the tables exactly where the
+// cells-per-CTA kernel expects them folded (FP64 linear elasticity only)
+static_assert(coop_weights_folded<OP_ELASTICITY, double>() && !coop_weights_folded<OP_ELASTICITY, float>() &&
+                  !coop_weights_folded<OP_LAPLACE, double>() && !coop_weights_folded<OP_MASS, double>(),
+              "table folding of the cells-per-CTA kernel");
 
 namespace fe {
 void fill_log_table(double *t)
@@ -694,10 +699,14 @@ extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan 
         else
             reinterpret_cast<double *>(blk + byte_off)[idx] = t;
     };
+    // FP64 linear elasticity in the cells-per-CTA kernel: the rows of point q
+    // scaled by sqrt(w_q) (coop_weights_folded; the kernel then leaves out w_q)
+    const bool fold_w = coop && esz == sizeof(double) && f.kind == FE_FORM_ELASTICITY;
     for (int q = 0; q < nq; ++q)
         for (int k = 0; k <= m.dim; ++k)
             for (int j = 0; j < n; ++j) {
-                const double t = tab[((size_t)k * nq + q) * n + j];
+                double t = tab[((size_t)k * nq + q) * n + j];
+                if (fold_w) t *= std::sqrt(wts[q]);
                 if (global_tab) {
                     put(block_bytes, ((size_t)k * n + j) * nq + q, t);
                     put(block_bytes + gsz, ((size_t)q * (1 + m.dim) + k) * n + j, t);

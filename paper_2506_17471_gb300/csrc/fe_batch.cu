@@ -15,6 +15,7 @@
 // (the second on a batch-owned stream forked from and joined back to the
 // caller's stream with events), and the whole can be captured in a CUDA graph.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -310,10 +311,14 @@ extern "C" int fe_batch_create(const fe_batch_problem *problems, int count, fe_b
         const size_t gdoubles = global_tab ? (((size_t)(1 + m.dim) * n * nq + 1) & ~(size_t)1) : 0;
         std::vector<double> &blk = blocks[i];
         blk.assign(block_bytes / 8 + 2 * gdoubles, 0.0);
+        // cells-per-CTA linear elasticity: rows of point q scaled by sqrt(w_q), as
+        // the kernel expects (coop_weights_folded)
+        const bool fold_w = kind == 1 && f.kind == FE_FORM_ELASTICITY;
         for (int q = 0; q < nq; ++q)
             for (int k = 0; k <= m.dim; ++k)
                 for (int j = 0; j < n; ++j) {
-                    const double t = tab[((size_t)k * nq + q) * n + j];
+                    double t = tab[((size_t)k * nq + q) * n + j];
+                    if (fold_w) t *= std::sqrt(wts[q]);
                     if (global_tab) {
                         blk[block_bytes / 8 + ((size_t)k * n + j) * nq + q] = t;
                         blk[block_bytes / 8 + gdoubles + ((size_t)q * (1 + m.dim) + k) * n + j] = t;

@@ -38,9 +38,22 @@ constexpr int kCoopMaxGroups = 2;   // thread groups of the wide layout (see Cta
 constexpr size_t kCoopWideSmemBytes = 224 * 1024;
 constexpr size_t kCoopSmemTableBytes = 96 * 1024;   // larger tables stay in global memory
 // Per-cell geometry record in shared memory: J^{-1} (D*D), |det J|, mu, lambda,
-// a validity flag; the stride is odd so that threads reading the records of
+// a validity flag, and for FP64 linear elasticity 2 mu |det J|, lambda |det J|,
+// mu |det J|; the stride is odd so that threads reading the records of
 // consecutive cells hit distinct banks.
 constexpr int kCoopGeoStride = 17;
+
+// FP64 linear elasticity in the cells-per-CTA kernel takes its tables with the
+// quadrature weights folded in, every row of point q scaled by sqrt(w_q) (the
+// plan and the batch build them so): the evaluation then yields sqrt(w_q) times
+// the reference gradient, the stress is linear in it, and the quadrature
+// contraction with the same table supplies the other sqrt(w_q), so the action is
+// unchanged while the per-point weight products drop out of the FP64 work.
+template <int OP, typename R>
+__host__ __device__ constexpr bool coop_weights_folded()
+{
+    return OP == OP_ELASTICITY && sizeof(R) == sizeof(double);
+}
 
 // Shared-memory plan of one CTA, computed identically on host and device.
 struct CoopLayout {
@@ -363,6 +376,11 @@ __device__ __forceinline__ void coop_batch(const ActionArgs &a, const CoopLayout
         g[D * D + 1] = (OpTraits<OP, D>::kCellCoeff && a.mu_cell) ? __ldg(a.mu_cell + cell) : a.mu;
         g[D * D + 2] = (OpTraits<OP, D>::kCellCoeff && a.lam_cell) ? __ldg(a.lam_cell + cell) : a.lam;
         g[D * D + 3] = good ? 1.0 : 0.0;
+        if constexpr (coop_weights_folded<OP, R>()) {
+            g[D * D + 4] = 2.0 * g[D * D + 1] * g[D * D];
+            g[D * D + 5] = g[D * D + 2] * g[D * D];
+            g[D * D + 6] = g[D * D + 1] * g[D * D];
+        }
         sacc[2 * c] = 0.0;
         sacc[2 * c + 1] = 0.0;
     }
@@ -490,12 +508,22 @@ __device__ __forceinline__ void coop_batch(const ActionArgs &a, const CoopLayout
                 R tr = G[0][0];
 #pragma unroll
                 for (int ii = 1; ii < D; ++ii) tr += G[ii][ii];
-                const R wdet_r = wts_r[q] * cvt<R>(absdet);
-                const R smu = wdet_r * cvt<R>(mu);
-                const R slt = wdet_r * cvt<R>(lam) * tr;
+                // mu and lambda times w_q |det J| (the weight folded into the tables
+                // in FP64: the per-cell products from the geometry record)
+                R smu, smu2, slt;
+                if constexpr (coop_weights_folded<OP, R>()) {
+                    smu2 = g[D * D + 4];
+                    slt = g[D * D + 5] * tr;
+                    smu = g[D * D + 6];
+                } else {
+                    const R wdet_r = wts_r[q] * cvt<R>(absdet);
+                    smu = wdet_r * cvt<R>(mu);
+                    smu2 = R(2) * smu;
+                    slt = wdet_r * cvt<R>(lam) * tr;
+                }
 #pragma unroll
                 for (int ii = 0; ii < D; ++ii) {
-                    S[ii][ii] = fma(R(2) * smu, G[ii][ii], slt);
+                    S[ii][ii] = fma(smu2, G[ii][ii], slt);
 #pragma unroll
                     for (int k = ii + 1; k < D; ++k) {
                         const R s = smu * (G[ii][k] + G[k][ii]);
