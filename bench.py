@@ -53,7 +53,7 @@ FP64_NOMINAL_TFLOPS = 1.25
 # DRAM traffic of the headline kernel per launch (dram__bytes_read.sum +
 # dram__bytes_write.sum from one ncu capture of the same workload), reported only
 # while the kernel's sources still hash to the captured version.
-MEASURED_TRAFFIC = {"source_hash": "c9f835de7f112623", "bytes": 414912768}
+MEASURED_TRAFFIC = {"source_hash": "1fb2f8a73cb795fe", "bytes": 414899712}
 
 
 def parse():

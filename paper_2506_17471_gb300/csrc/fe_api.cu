@@ -416,8 +416,10 @@ static void tc_fill_block(const TcLayout &L, int kind, const std::vector<double>
 static_assert(kLogTabDoubles == FE_LOG_TABLE_DOUBLES, "log table size of the header");
 // the plan folds the quadrature weights into the tables exactly where the
 // cells-per-CTA kernel expects them folded (FP64 linear elasticity only)
-static_assert(coop_weights_folded<OP_ELASTICITY, double>() && !coop_weights_folded<OP_ELASTICITY, float>() &&
-                  !coop_weights_folded<OP_LAPLACE, double>() && !coop_weights_folded<OP_MASS, double>(),
+static_assert(coop_weights_folded<OP_ELASTICITY, double>() && coop_weights_folded<OP_LAPLACE, double>() &&
+                  coop_weights_folded<OP_HELMHOLTZ, double>() && coop_weights_folded<OP_MASS, double>() &&
+                  !coop_weights_folded<OP_ELASTICITY, float>() && !coop_weights_folded<OP_NH_RESIDUAL, double>() &&
+                  !coop_weights_folded<OP_SVK_RESIDUAL, double>(),
               "table folding of the cells-per-CTA kernel");
 
 namespace fe {
@@ -699,9 +701,11 @@ extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan 
         else
             reinterpret_cast<double *>(blk + byte_off)[idx] = t;
     };
-    // FP64 linear elasticity in the cells-per-CTA kernel: the rows of point q
-    // scaled by sqrt(w_q) (coop_weights_folded; the kernel then leaves out w_q)
-    const bool fold_w = coop && esz == sizeof(double) && f.kind == FE_FORM_ELASTICITY;
+    // FP64 linear forms in the cells-per-CTA kernel: the rows of point q scaled by
+    // sqrt(w_q) (coop_weights_folded; the kernel then leaves out w_q)
+    const bool fold_w = coop && esz == sizeof(double) &&
+                        (f.kind == FE_FORM_ELASTICITY || f.kind == FE_FORM_LAPLACE || f.kind == FE_FORM_HELMHOLTZ ||
+                         f.kind == FE_FORM_MASS);
     for (int q = 0; q < nq; ++q)
         for (int k = 0; k <= m.dim; ++k)
             for (int j = 0; j < n; ++j) {

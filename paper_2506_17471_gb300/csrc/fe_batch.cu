@@ -311,9 +311,10 @@ extern "C" int fe_batch_create(const fe_batch_problem *problems, int count, fe_b
         const size_t gdoubles = global_tab ? (((size_t)(1 + m.dim) * n * nq + 1) & ~(size_t)1) : 0;
         std::vector<double> &blk = blocks[i];
         blk.assign(block_bytes / 8 + 2 * gdoubles, 0.0);
-        // cells-per-CTA linear elasticity: rows of point q scaled by sqrt(w_q), as
-        // the kernel expects (coop_weights_folded)
-        const bool fold_w = kind == 1 && f.kind == FE_FORM_ELASTICITY;
+        // cells-per-CTA linear forms: rows of point q scaled by sqrt(w_q), as the
+        // kernel expects (coop_weights_folded)
+        const bool fold_w = kind == 1 && (f.kind == FE_FORM_ELASTICITY || f.kind == FE_FORM_LAPLACE ||
+                                          f.kind == FE_FORM_HELMHOLTZ || f.kind == FE_FORM_MASS);
         for (int q = 0; q < nq; ++q)
             for (int k = 0; k <= m.dim; ++k)
                 for (int j = 0; j < n; ++j) {

@@ -43,16 +43,21 @@ constexpr size_t kCoopSmemTableBytes = 96 * 1024;   // larger tables stay in glo
 // consecutive cells hit distinct banks.
 constexpr int kCoopGeoStride = 17;
 
-// FP64 linear elasticity in the cells-per-CTA kernel takes its tables with the
-// quadrature weights folded in, every row of point q scaled by sqrt(w_q) (the
-// plan and the batch build them so): the evaluation then yields sqrt(w_q) times
-// the reference gradient, the stress is linear in it, and the quadrature
+// The FP64 linear forms (elasticity, Laplacian, Helmholtz, mass) in the
+// cells-per-CTA kernel take their tables with the quadrature weights folded in,
+// every row of point q scaled by sqrt(w_q) (the plan and the batch build them
+// so): the evaluation then yields sqrt(w_q) times the values and reference
+// gradients, the pointwise form is linear in them, and the quadrature
 // contraction with the same table supplies the other sqrt(w_q), so the action is
-// unchanged while the per-point weight products drop out of the FP64 work.
+// unchanged while the per-point weight products drop out of the FP64 work.  The
+// Laplacian and Helmholtz forms keep M = |det J| J^{-1} J^{-T} in the geometry
+// record in place of J^{-1}: their gradient term is then M times the reference
+// gradient.
 template <int OP, typename R>
 __host__ __device__ constexpr bool coop_weights_folded()
 {
-    return OP == OP_ELASTICITY && sizeof(R) == sizeof(double);
+    return (OP == OP_ELASTICITY || OP == OP_LAPLACE || OP == OP_HELMHOLTZ || OP == OP_MASS) &&
+           sizeof(R) == sizeof(double);
 }
 
 // Shared-memory plan of one CTA, computed identically on host and device.
@@ -372,6 +377,19 @@ __device__ __forceinline__ void coop_batch(const ActionArgs &a, const CoopLayout
         for (int i = 0; i < D; ++i)
 #pragma unroll
             for (int k = 0; k < D; ++k) g[i * D + k] = good ? Jinv[i][k] : 0.0;
+        if constexpr ((OP == OP_LAPLACE || OP == OP_HELMHOLTZ) && coop_weights_folded<OP, R>()) {
+            // M = |det J| J^{-1} J^{-T} (symmetric) in place of J^{-1}
+            const double ad = good ? fabs(det) : 0.0;
+#pragma unroll
+            for (int i = 0; i < D; ++i)
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    double mk = Jinv[i][0] * Jinv[k][0];
+#pragma unroll
+                    for (int r = 1; r < D; ++r) mk = fma(Jinv[i][r], Jinv[k][r], mk);
+                    g[i * D + k] = good ? ad * mk : 0.0;
+                }
+        }
         g[D * D] = good ? fabs(det) : 0.0;
         g[D * D + 1] = (OpTraits<OP, D>::kCellCoeff && a.mu_cell) ? __ldg(a.mu_cell + cell) : a.mu;
         g[D * D + 2] = (OpTraits<OP, D>::kCellCoeff && a.lam_cell) ? __ldg(a.lam_cell + cell) : a.lam;
@@ -407,7 +425,10 @@ __device__ __forceinline__ void coop_batch(const ActionArgs &a, const CoopLayout
             R uq = R(0);
             for (int j = 0; j < n; ++j)
                 uq = fma(gtab ? __ldg(TB + (size_t)j * nq) : T[j], cvt<R>(lc[j]), uq);
-            e[0] = uq * (wts_r[q] * cvt<R>(absdet));
+            if constexpr (coop_weights_folded<OP, R>())
+                e[0] = uq * absdet;
+            else
+                e[0] = uq * (wts_r[q] * cvt<R>(absdet));
         } else {
             // reference gradients of the field(s) at q
             R gh[FIELDS][NC][D];
@@ -459,7 +480,24 @@ __device__ __forceinline__ void coop_batch(const ActionArgs &a, const CoopLayout
                 for (int j = 0; j < n; ++j)
                     eval_node<D, FIELDS, NC, (1 << D) - 1>(gh, T, TB, gtab, lc, n, nq, j);
             }
-            if constexpr (OP == OP_LAPLACE || OP == OP_HELMHOLTZ) {
+            if constexpr ((OP == OP_LAPLACE || OP == OP_HELMHOLTZ) && coop_weights_folded<OP, R>()) {
+                // e = M grad_ref u with M = |det J| J^{-1} J^{-T} from the geometry record
+                // (in place of J^{-1}) and the weight in the tables (+ |det J| u for Helmholtz)
+                constexpr int kV = (OP == OP_HELMHOLTZ) ? 1 : 0;
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    R sk = Jinv[k][0] * gh[0][0][0];
+#pragma unroll
+                    for (int ii = 1; ii < D; ++ii) sk = fma(Jinv[k][ii], gh[0][0][ii], sk);
+                    e[kV + k] = sk;
+                }
+                if constexpr (OP == OP_HELMHOLTZ) {
+                    R uq = R(0);
+                    for (int j = 0; j < n; ++j)
+                        uq = fma(gtab ? __ldg(TB + (size_t)j * nq) : T[j], cvt<R>(lc[j]), uq);
+                    e[0] = uq * absdet;
+                }
+            } else if constexpr (OP == OP_LAPLACE || OP == OP_HELMHOLTZ) {
                 // e = w |det J| J^{-1} J^{-T} grad_ref u  (+ the value term for Helmholtz)
                 R Jr[D][D], g[D];
                 convert<D, D>(Jinv, Jr);
