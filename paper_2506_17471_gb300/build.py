@@ -21,7 +21,8 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["fe_api.cu", "fe_inst_2d_linear.cu", "fe_inst_2d_nh.cu", "fe_inst_3d.cu", "fe_tabulate.cpp",
            "fe_noalloc.cu", "fe_solver.cu", "fe_inst_coop.cu", "fe_batch.cu", "fe_symrule.cpp", "fe_reorder.cpp",
-           "fe_inst_tc.cu", "fe_inst_tc2.cu", "fe_inst_tc3.cu", "fe_inst_forms.cu", "fe_inst_coop_forms.cu"]
+           "fe_inst_tc.cu", "fe_inst_tc2.cu", "fe_inst_tc3.cu", "fe_inst_forms.cu", "fe_inst_coop_forms.cu",
+           "fe_inst_fold.cu"]
 GENCODE = "arch=compute_103a,code=sm_103a"
 
 

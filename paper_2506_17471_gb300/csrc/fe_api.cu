@@ -36,6 +36,8 @@ std::once_flag g_once;
 void init_registry()
 {
     int n = 0;
+    // weight-folded thread-per-cell variants first: find_variant returns the first match
+    n += register_variants_fold(g_variants + n, kMaxVariants - n);
     n += register_variants_2d_linear(g_variants + n, kMaxVariants - n);
     n += register_variants_2d_nh(g_variants + n, kMaxVariants - n);
     n += register_variants_3d(g_variants + n, kMaxVariants - n);
@@ -701,11 +703,13 @@ extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan 
         else
             reinterpret_cast<double *>(blk + byte_off)[idx] = t;
     };
-    // FP64 linear forms in the cells-per-CTA kernel: the rows of point q scaled by
-    // sqrt(w_q) (coop_weights_folded; the kernel then leaves out w_q)
-    const bool fold_w = coop && esz == sizeof(double) &&
-                        (f.kind == FE_FORM_ELASTICITY || f.kind == FE_FORM_LAPLACE || f.kind == FE_FORM_HELMHOLTZ ||
-                         f.kind == FE_FORM_MASS);
+    // FP64 linear forms in the cells-per-CTA kernel, and the thread-per-cell
+    // variants that ask for it: the rows of point q scaled by sqrt(w_q)
+    // (coop_weights_folded, Variant::wfold; the kernel then leaves out w_q)
+    const bool fold_w = (coop && esz == sizeof(double) &&
+                         (f.kind == FE_FORM_ELASTICITY || f.kind == FE_FORM_LAPLACE ||
+                          f.kind == FE_FORM_HELMHOLTZ || f.kind == FE_FORM_MASS)) ||
+                        (!coop && v->wfold);
     for (int q = 0; q < nq; ++q)
         for (int k = 0; k <= m.dim; ++k)
             for (int j = 0; j < n; ++j) {

@@ -70,6 +70,9 @@ struct Variant {
     // nodes shared by a CTA's cells in shared memory before the global scatter
     // (launched instead of func when ActionArgs::agg_slots > 0)
     const void *func_agg = nullptr;
+    // thread-per-cell FP64 mass / elasticity: the kernel takes tables whose rows of
+    // point q are scaled by sqrt(w_q) (the plan builds them so)
+    bool wfold = false;
 };
 
 // Raise a kernel's dynamic shared-memory limit to the device's opt-in maximum.
@@ -94,6 +97,7 @@ inline cudaError_t allow_max_dynamic_smem(const void *func)
 int register_variants_2d_linear(Variant *out, int cap);
 int register_variants_2d_nh(Variant *out, int cap);
 int register_variants_3d(Variant *out, int cap);
+int register_variants_fold(Variant *out, int cap);
 int register_variants_coop(Variant *out, int cap);
 int register_variants_tc(Variant *out, int cap);
 int register_variants_tc2(Variant *out, int cap);

@@ -637,7 +637,12 @@ __device__ __forceinline__ int agg_slot(const AggTable<NC> &t, int node)
     return -1;
 }
 
-template <int OP, int D, int P, typename R, int AGG_NC = 0>
+// WF: the table's rows of point q are scaled by sqrt(w_q) (FP64 mass and
+// elasticity plans; see the plan's table construction).  The evaluation then
+// yields sqrt(w_q) times the values / reference gradients, the pointwise form is
+// linear in them and the quadrature contraction supplies the other sqrt(w_q), so
+// w_q |det J| becomes the per-cell |det J| and its per-point products drop out.
+template <int OP, int D, int P, typename R, int AGG_NC = 0, bool WF = false>
 __device__ __forceinline__ void action_cell(const ActionArgs &a, const R *__restrict__ tab,
                                             const double *__restrict__ wts, const R *__restrict__ wts_r,
                                             int cell, const AggTable<(AGG_NC > 0 ? AGG_NC : 1)> *agg = nullptr)
@@ -709,10 +714,13 @@ __device__ __forceinline__ void action_cell(const ActionArgs &a, const R *__rest
     bool nh_ok = true;
 
     [[maybe_unused]] const R mu_r = cvt<R>(mu), lam_r = cvt<R>(lam);
+    // weight-folded elasticity: mu |det J|, 2 mu |det J| and lambda |det J| per cell
+    [[maybe_unused]] const R c_smu = WF ? mu_r * absdet_r : R(0), c_smu2 = R(2) * c_smu,
+                             c_slam = WF ? lam_r * absdet_r : R(0);
     for (int q = 0; q < a.nq; ++q) {
         const R *__restrict__ T = tab + (size_t)q * (D + 1) * N;
         // w_q |det J| in R for the forms evaluated in R, in FP64 for Neo-Hookean
-        const R wdet_r = wts_r[q] * absdet_r;
+        [[maybe_unused]] const R wdet_r = WF ? absdet_r : wts_r[q] * absdet_r;
         if constexpr (OP == OP_MASS) {
             R uq = R(0);
 #pragma unroll
@@ -793,11 +801,12 @@ __device__ __forceinline__ void action_cell(const ActionArgs &a, const R *__rest
             R tr = G[0][0];
 #pragma unroll
             for (int i = 1; i < D; ++i) tr += G[i][i];
-            const R smu = wdet_r * mu_r;
-            const R slt = wdet_r * lam_r * tr;
+            const R smu = WF ? c_smu : wdet_r * mu_r;
+            const R smu2 = WF ? c_smu2 : R(2) * smu;
+            const R slt = WF ? c_slam * tr : wdet_r * lam_r * tr;
 #pragma unroll
             for (int i = 0; i < D; ++i) {
-                S[i][i] = fma(R(2) * smu, G[i][i], slt);
+                S[i][i] = fma(smu2, G[i][i], slt);
 #pragma unroll
                 for (int k = i + 1; k < D; ++k) {
                     const R s = smu * (G[i][k] + G[k][i]);
@@ -962,7 +971,7 @@ __host__ __device__ constexpr int tpc_min_blocks()
     return (OP == OP_NH_RESIDUAL && D == 2 && sizeof(R) == 4) ? 5 : 1;
 }
 
-template <int OP, int D, int P, typename R>
+template <int OP, int D, int P, typename R, bool WF = false>
 __global__ void __launch_bounds__(kTpcBlock, tpc_min_blocks<OP, D, R>()) k_action_tpc(const ActionArgs a)
 {
     extern __shared__ __align__(128) double smem[];
@@ -984,7 +993,7 @@ __global__ void __launch_bounds__(kTpcBlock, tpc_min_blocks<OP, D, R>()) k_actio
         chunk = __shfl_sync(0xffffffffu, chunk, 0);
         if (chunk >= n_chunks) break;
         const int cell = (chunk << 5) + lane;
-        if (cell < a.n_cells) action_cell<OP, D, P, R>(a, tab, wts, wts_r, cell);
+        if (cell < a.n_cells) action_cell<OP, D, P, R, 0, WF>(a, tab, wts, wts_r, cell);
     }
     leave_queue(a.sched);
 }
@@ -1044,7 +1053,7 @@ __global__ void __launch_bounds__(kTpcBlock) k_action_tpc_agg(const ActionArgs a
     leave_queue(a.sched);
 }
 
-template <int OP, int D, int P, typename R>
+template <int OP, int D, int P, typename R, bool WF = false>
 cudaError_t launch_tpc(const ActionArgs &a, int grid, int block, size_t smem, cudaStream_t s)
 {
     if constexpr (std::is_same<R, float>::value && OP == OP_MASS) {
@@ -1053,11 +1062,12 @@ cudaError_t launch_tpc(const ActionArgs &a, int grid, int block, size_t smem, cu
             return cudaGetLastError();
         }
     }
-    k_action_tpc<OP, D, P, R><<<grid, block, smem, s>>>(a);
+    k_action_tpc<OP, D, P, R, WF><<<grid, block, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-template <int OP, int D, int P, typename R = double>
+// WF: the variant takes weight-folded tables (action_cell)
+template <int OP, int D, int P, typename R = double, bool WF = false>
 Variant make_tpc_variant()
 {
     Variant v;
@@ -1068,8 +1078,11 @@ Variant make_tpc_variant()
     v.precision = std::is_same<R, double>::value ? FE_PREC_FP64 : FE_PREC_FP32;
     v.kernel_id = 0;
     v.block = kTpcBlock;
-    v.launch = &launch_tpc<OP, D, P, R>;
-    v.func = reinterpret_cast<const void *>(&k_action_tpc<OP, D, P, R>);
+    static_assert(!WF || (std::is_same<R, double>::value && (OP == OP_MASS || OP == OP_ELASTICITY)),
+                  "weight-folded tables: FP64 mass and elasticity");
+    v.wfold = WF;
+    v.launch = &launch_tpc<OP, D, P, R, WF>;
+    v.func = reinterpret_cast<const void *>(&k_action_tpc<OP, D, P, R, WF>);
     if constexpr (std::is_same<R, float>::value && OP == OP_MASS)
         v.func_agg = reinterpret_cast<const void *>(&k_action_tpc_agg<OP, D, P, R>);
     return v;
