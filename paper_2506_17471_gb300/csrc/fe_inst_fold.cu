@@ -1,5 +1,5 @@
 // Thread-per-cell variants that take weight-folded tables (rows of point q scaled
-// by sqrt(w_q)): FP64 mass and elasticity.  Registered ahead of the plain
+// by sqrt(w_q)): the FP64 linear forms (mass, elasticity, Laplacian, Helmholtz).  Registered ahead of the plain
 // variants, so plans take them; the no-allocation entry point, which stages the
 // caller's unfolded tables, keeps the plain ones.
 #include "fe_kernels.cuh"
@@ -25,6 +25,18 @@ int register_variants_fold(Variant *out, int cap)
         make_tpc_variant<OP_ELASTICITY, 2, 4, double, true>(),
         make_tpc_variant<OP_ELASTICITY, 3, 1, double, true>(),
         make_tpc_variant<OP_ELASTICITY, 3, 2, double, true>(),
+        make_tpc_variant<OP_LAPLACE, 2, 1, double, true>(),
+        make_tpc_variant<OP_LAPLACE, 2, 2, double, true>(),
+        make_tpc_variant<OP_LAPLACE, 2, 3, double, true>(),
+        make_tpc_variant<OP_LAPLACE, 2, 4, double, true>(),
+        make_tpc_variant<OP_LAPLACE, 3, 1, double, true>(),
+        make_tpc_variant<OP_LAPLACE, 3, 2, double, true>(),
+        make_tpc_variant<OP_HELMHOLTZ, 2, 1, double, true>(),
+        make_tpc_variant<OP_HELMHOLTZ, 2, 2, double, true>(),
+        make_tpc_variant<OP_HELMHOLTZ, 2, 3, double, true>(),
+        make_tpc_variant<OP_HELMHOLTZ, 2, 4, double, true>(),
+        make_tpc_variant<OP_HELMHOLTZ, 3, 1, double, true>(),
+        make_tpc_variant<OP_HELMHOLTZ, 3, 2, double, true>(),
     };
     int n = 0;
     for (const Variant &x : v)

@@ -70,7 +70,7 @@ struct Variant {
     // nodes shared by a CTA's cells in shared memory before the global scatter
     // (launched instead of func when ActionArgs::agg_slots > 0)
     const void *func_agg = nullptr;
-    // thread-per-cell FP64 mass / elasticity: the kernel takes tables whose rows of
+    // thread-per-cell FP64 linear forms: the kernel takes tables whose rows of
     // point q are scaled by sqrt(w_q) (the plan builds them so)
     bool wfold = false;
 };

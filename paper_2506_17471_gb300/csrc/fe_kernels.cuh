@@ -637,8 +637,8 @@ __device__ __forceinline__ int agg_slot(const AggTable<NC> &t, int node)
     return -1;
 }
 
-// WF: the table's rows of point q are scaled by sqrt(w_q) (FP64 mass and
-// elasticity plans; see the plan's table construction).  The evaluation then
+// WF: the table's rows of point q are scaled by sqrt(w_q) (FP64 plans of the
+// linear forms; see the plan's table construction).  The evaluation then
 // yields sqrt(w_q) times the values / reference gradients, the pointwise form is
 // linear in them and the quadrature contraction supplies the other sqrt(w_q), so
 // w_q |det J| becomes the per-cell |det J| and its per-point products drop out.
@@ -717,6 +717,21 @@ __device__ __forceinline__ void action_cell(const ActionArgs &a, const R *__rest
     // weight-folded elasticity: mu |det J|, 2 mu |det J| and lambda |det J| per cell
     [[maybe_unused]] const R c_smu = WF ? mu_r * absdet_r : R(0), c_smu2 = R(2) * c_smu,
                              c_slam = WF ? lam_r * absdet_r : R(0);
+    // weight-folded Laplacian / Helmholtz: M = |det J| J^{-1} J^{-T} per cell, so that
+    // the gradient term at a point is M times the reference gradient
+    constexpr bool kFoldM = WF && (OP == OP_LAPLACE || OP == OP_HELMHOLTZ);
+    [[maybe_unused]] R Mw[kFoldM ? D : 1][D];
+    if constexpr (kFoldM) {
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                double mk = Jinv[i][0] * Jinv[k][0];
+#pragma unroll
+                for (int r = 1; r < D; ++r) mk = fma(Jinv[i][r], Jinv[k][r], mk);
+                Mw[i][k] = absdet * mk;
+            }
+    }
     for (int q = 0; q < a.nq; ++q) {
         const R *__restrict__ T = tab + (size_t)q * (D + 1) * N;
         // w_q |det J| in R for the forms evaluated in R, in FP64 for Neo-Hookean
@@ -738,20 +753,31 @@ __device__ __forceinline__ void action_cell(const ActionArgs &a, const R *__rest
 #pragma unroll
                 for (int k = 0; k < D; ++k)
                     if (!grad_zero<D, N>(k, j)) gs[k] = fma(T[(k + 1) * N + j], l[j][0], gs[k]);
-            R g[D], e[D];
+            R e[D];
+            if constexpr (kFoldM) {
 #pragma unroll
-            for (int i = 0; i < D; ++i) {
-                R s = R(0);
+                for (int k = 0; k < D; ++k) {
+                    R s = Mw[k][0] * gs[0];
 #pragma unroll
-                for (int k = 0; k < D; ++k) s = fma(gs[k], kMixed ? Jinv_r[k][i] : R(Jinv[k][i]), s);
-                g[i] = s * wdet_r;
-            }
+                    for (int i = 1; i < D; ++i) s = fma(Mw[k][i], gs[i], s);
+                    e[k] = s;
+                }
+            } else {
+                R g[D];
 #pragma unroll
-            for (int k = 0; k < D; ++k) {
-                R s = R(0);
+                for (int i = 0; i < D; ++i) {
+                    R s = R(0);
 #pragma unroll
-                for (int i = 0; i < D; ++i) s = fma(g[i], kMixed ? Jinv_r[k][i] : R(Jinv[k][i]), s);
-                e[k] = s;
+                    for (int k = 0; k < D; ++k) s = fma(gs[k], kMixed ? Jinv_r[k][i] : R(Jinv[k][i]), s);
+                    g[i] = s * wdet_r;
+                }
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    R s = R(0);
+#pragma unroll
+                    for (int i = 0; i < D; ++i) s = fma(g[i], kMixed ? Jinv_r[k][i] : R(Jinv[k][i]), s);
+                    e[k] = s;
+                }
             }
             [[maybe_unused]] R ev = R(0);
             if constexpr (OP == OP_HELMHOLTZ) {
@@ -1078,8 +1104,9 @@ Variant make_tpc_variant()
     v.precision = std::is_same<R, double>::value ? FE_PREC_FP64 : FE_PREC_FP32;
     v.kernel_id = 0;
     v.block = kTpcBlock;
-    static_assert(!WF || (std::is_same<R, double>::value && (OP == OP_MASS || OP == OP_ELASTICITY)),
-                  "weight-folded tables: FP64 mass and elasticity");
+    static_assert(!WF || (std::is_same<R, double>::value && (OP == OP_MASS || OP == OP_ELASTICITY ||
+                                                             OP == OP_LAPLACE || OP == OP_HELMHOLTZ)),
+                  "weight-folded tables: the FP64 linear forms");
     v.wfold = WF;
     v.launch = &launch_tpc<OP, D, P, R, WF>;
     v.func = reinterpret_cast<const void *>(&k_action_tpc<OP, D, P, R, WF>);
