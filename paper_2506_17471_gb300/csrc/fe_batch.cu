@@ -67,14 +67,16 @@ __device__ __forceinline__ void run_tpc(const ActionArgs &a, int degree, const d
     const int nq = a.nq;
     const double *wts_r = wts + nq;
     (void)tab;
+    // mass and elasticity take weight-folded tables (built so by fe_batch_create)
+    constexpr bool WF = OP == OP_MASS || OP == OP_ELASTICITY;
     switch (degree) {
-    case 1: action_cell<OP, D, 1, double>(a, tab, wts, wts_r, cell); break;
-    case 2: action_cell<OP, D, 2, double>(a, tab, wts, wts_r, cell); break;
+    case 1: action_cell<OP, D, 1, double, 0, WF>(a, tab, wts, wts_r, cell); break;
+    case 2: action_cell<OP, D, 2, double, 0, WF>(a, tab, wts, wts_r, cell); break;
     case 3:
-        if constexpr (D == 2 || OP == OP_MASS) action_cell<OP, D, 3, double>(a, tab, wts, wts_r, cell);
+        if constexpr (D == 2 || OP == OP_MASS) action_cell<OP, D, 3, double, 0, WF>(a, tab, wts, wts_r, cell);
         break;
     case 4:
-        if constexpr (D == 2 || OP == OP_MASS) action_cell<OP, D, 4, double>(a, tab, wts, wts_r, cell);
+        if constexpr (D == 2 || OP == OP_MASS) action_cell<OP, D, 4, double, 0, WF>(a, tab, wts, wts_r, cell);
         break;
     default: break;
     }
@@ -311,10 +313,12 @@ extern "C" int fe_batch_create(const fe_batch_problem *problems, int count, fe_b
         const size_t gdoubles = global_tab ? (((size_t)(1 + m.dim) * n * nq + 1) & ~(size_t)1) : 0;
         std::vector<double> &blk = blocks[i];
         blk.assign(block_bytes / 8 + 2 * gdoubles, 0.0);
-        // cells-per-CTA linear forms: rows of point q scaled by sqrt(w_q), as the
-        // kernel expects (coop_weights_folded)
-        const bool fold_w = kind == 1 && (f.kind == FE_FORM_ELASTICITY || f.kind == FE_FORM_LAPLACE ||
-                                          f.kind == FE_FORM_HELMHOLTZ || f.kind == FE_FORM_MASS);
+        // rows of point q scaled by sqrt(w_q) where the kernel expects it: the
+        // cells-per-CTA linear forms (coop_weights_folded) and the thread-per-cell
+        // mass and elasticity (run_tpc)
+        const bool fold_w = (kind == 1 && (f.kind == FE_FORM_ELASTICITY || f.kind == FE_FORM_LAPLACE ||
+                                           f.kind == FE_FORM_HELMHOLTZ || f.kind == FE_FORM_MASS)) ||
+                            (kind == 0 && (f.kind == FE_FORM_ELASTICITY || f.kind == FE_FORM_MASS));
         for (int q = 0; q < nq; ++q)
             for (int k = 0; k <= m.dim; ++k)
                 for (int j = 0; j < n; ++j) {
