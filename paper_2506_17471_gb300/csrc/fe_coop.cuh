@@ -22,6 +22,11 @@
 // resident) in two layouts, [1+D][N][nq] for phase B (consecutive threads read
 // consecutive quadrature points) and [nq][1+D][N] for phase C (consecutive
 // nodes), so shared memory holds only the batch scratch and the weights.
+// The FP64 kernel of the tetrahedral gradient forms runs the wide layout (below)
+// as two independent 256-thread groups per CTA; it hands out the last, partial
+// round of batches split by ranges of quadrature points (k_action_coop), and the
+// FP64 linear forms take tables with the quadrature weights folded in
+// (coop_weights_folded).
 #pragma once
 
 #include "fe_kernels.cuh"
