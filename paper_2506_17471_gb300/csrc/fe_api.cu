@@ -652,15 +652,15 @@ extern "C" int fe_plan_create(const fe_form *form, const fe_mesh *mesh, fe_plan 
                                               : coop_default_global<double>(n, nq, m.dim));
         if (f.tile_cells > 0) {
             coop_cells = f.tile_cells;
-        } else if (esz == sizeof(double) && m.dim == 3 && f.kind != FE_FORM_MASS && f.kind != FE_FORM_HELMHOLTZ) {
-            // FP64 gradient forms on tetrahedra: the wide layout (one 512-thread CTA
-            // per SM) where its shared memory fits, preferably as two independent
-            // 256-thread groups with 32-cell batches each (one group's gather phase
-            // overlaps the other's FP64 work), else one group with 64 or 32 cells.
-            // Its quadrature phase skips the structurally zero directions (14-30 % of
-            // the gradient entries of a P2-P4 tetrahedron), which outweighs running
-            // one CTA per SM instead of two; on triangles (at most 7 % zeros) and for
-            // the value terms of mass and Helmholtz it does not.
+        } else if (esz == sizeof(double) && m.dim == 3 && f.kind != FE_FORM_MASS) {
+            // FP64 gradient forms on tetrahedra (Helmholtz included): the wide layout
+            // (one 512-thread CTA per SM) where its shared memory fits, preferably as
+            // two independent 256-thread groups with 32-cell batches each (one group's
+            // gather phase overlaps the other's FP64 work), else one group with 64 or
+            // 32 cells.  Its quadrature phase skips the structurally zero directions
+            // (14-30 % of the gradient entries of a P2-P4 tetrahedron), which outweighs
+            // running one CTA per SM instead of two; on triangles (at most 7 % zeros)
+            // it does not (measured: SVK P4 and NH Jacobian P6 2-3 % slower).
             const CoopLayout L32 = coop_layout<double>(n, nq, m.dim, ncomp, 32, fields_max, gt);
             if (L32.table_block_bytes + 2 * (L32.total - L32.table_block_bytes) <= kCoopWideSmemBytes) {
                 coop_cells = 32;
