@@ -278,7 +278,7 @@ __device__ __forceinline__ void coop_node_order(const CoopSmem<R> &S, int n, con
 // Must be called by every thread of the group; ends with the group's barrier.
 // RANGE = false compiles the full sum (q0, q1 ignored), so that the ordinary
 // batches carry no range arithmetic.
-template <int OP, int D, typename R, bool RANGE = false>
+template <int OP, int D, typename R, bool RANGE = false, int KG = 4>
 __device__ __forceinline__ void coop_batch(const ActionArgs &a, const CoopLayout &L, const CoopSmem<R> &S,
                                            const int cell0, const int nb, const CtaGroup grp = whole_cta(),
                                            int q0 = 0, int q1 = 0)
@@ -305,10 +305,10 @@ __device__ __forceinline__ void coop_batch(const ActionArgs &a, const CoopLayout
     // forms in reduced precision use only gradients and store the DoFs relative to
     // the cell's first node, differenced in FP64 (see gather_dofs).
     constexpr bool kRel = !std::is_same<R, double>::value && OpTraits<OP, D>::kNonlinear;
-    // The (cell, node) items are taken kG per thread at a time: all of the group's
+    // The (cell, node) items are taken KG per thread at a time: all of the group's
     // node indices are loaded first, then all of its DoFs, so a thread waits for
     // two memory round trips per group instead of two per item.
-    constexpr int kG = 4;
+    constexpr int kG = KG;
     const int a_items = nb * n;
     const int stride = grp.size;
     for (int i0 = grp.tid; i0 < a_items; i0 += kG * stride) {
@@ -783,6 +783,10 @@ __global__ void __launch_bounds__(kCoopWideBlock, 1) k_action_coop(const ActionA
     // node-gather scatter (which stores each cell's outputs); FP64 only, whose long
     // FP64-pipe-bound units make the tail expensive (the FP32 kernels' are short).
     constexpr bool kTailSplit = OP != OP_NH_ADJOINT && std::is_same<R, double>::value;
+    // gather items per thread per round trip: 6 for FP64 (headline 11.65 -> 11.62 ms
+    // against 4, same 116 registers), 4 for FP32, whose kernels would spill or lose a
+    // resident CTA with 6
+    constexpr int kGather = std::is_same<R, double>::value ? 6 : 4;
     const int n_groups = (int)gridDim.x * groups;
     int tail = 0, split = 1;
     if (kTailSplit && per == 1 && !a.cell_out) {
@@ -807,12 +811,12 @@ __global__ void __launch_bounds__(kCoopWideBlock, 1) k_action_coop(const ActionA
         if (item >= n_items) break;
         if (item < n_full) {
             const int cell0 = item * U;
-            coop_batch<OP, D, R>(a, L, S, cell0, min(take * U, a.n_cells - cell0), grp);
+            coop_batch<OP, D, R, false, kGather>(a, L, S, cell0, min(take * U, a.n_cells - cell0), grp);
         } else if constexpr (kTailSplit) {
             // a tail item: one unit (take is 1 here), one range of quadrature points
             const int sub = item - n_full, part = sub % split, cell0 = (n_full + sub / split) * U;
-            coop_batch<OP, D, R, true>(a, L, S, cell0, min(U, a.n_cells - cell0), grp, part * L.nq / split,
-                                       (part + 1) * L.nq / split);
+            coop_batch<OP, D, R, true, kGather>(a, L, S, cell0, min(U, a.n_cells - cell0), grp,
+                                                part * L.nq / split, (part + 1) * L.nq / split);
         }
     }
     leave_queue(a.sched);
