@@ -53,7 +53,7 @@ FP64_NOMINAL_TFLOPS = 1.25
 # DRAM traffic of the headline kernel per launch (dram__bytes_read.sum +
 # dram__bytes_write.sum from one ncu capture of the same workload), reported only
 # while the kernel's sources still hash to the captured version.
-MEASURED_TRAFFIC = {"source_hash": "e741844add0c85f6", "bytes": 414471424}
+MEASURED_TRAFFIC = {"source_hash": "e741844add0c85f6", "bytes": 414281984}
 
 
 def parse():
